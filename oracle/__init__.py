@@ -1,0 +1,170 @@
+"""ctypes binding of the CPU FP64 oracle (``gmg_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the slow, plain reference that the CUDA solver is
+checked against.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  It shares no code with
+the CUDA library and never imports it.
+
+Arrays are numpy float64 with all (n+1)^d grid nodes, x fastest (shape
+``(n+1, n+1)`` in 2D and ``(n+1, n+1, n+1)`` in 3D, indexed ``[k, j, i]``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gmg_oracle.c")
+_LIB = os.path.join(_HERE, "libgmg_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+WJACOBI = 0
+RBGS = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+             _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int), ("levels", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("omega", ctypes.c_double),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarse_sweeps", ctypes.c_int)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            D = ctypes.c_double
+            for name, args, res in [
+                ("orc_apply_stencil", [I, I, P, P], None),
+                ("orc_residual", [I, I, P, P, P], None),
+                ("orc_norm2", [I, I, P], D),
+                ("orc_rbgs", [I, I, P, P, I], None),
+                ("orc_wjacobi", [I, I, P, P, D, I], None),
+                ("orc_restrict_fw", [I, I, P, P], None),
+                ("orc_prolong_add", [I, I, P, P], None),
+                ("orc_coarse_solve", [I, I, P, P, I], None),
+                ("orc_vcycle", [ctypes.POINTER(Cfg), P, P], I),
+                ("orc_scale_rhs", [I, I, P, P], None),
+                ("orc_solve", [ctypes.POINTER(Cfg), P, P, D, I, P], I),
+            ]:
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dn(a: np.ndarray):
+    d = a.ndim
+    n = a.shape[0] - 1
+    assert d in (2, 3) and all(s == n + 1 for s in a.shape)
+    return d, n
+
+
+def max_levels(n: int) -> int:
+    """Number of grids from n intervals down to 2 intervals (one unknown)."""
+    return int(np.log2(n))
+
+
+def make_cfg(d, n, levels=0, smoother=RBGS, omega=0.8, nu1=2, nu2=2, coarse_sweeps=1) -> Cfg:
+    return Cfg(d, n, levels if levels > 0 else max_levels(n), smoother, omega, nu1, nu2,
+               coarse_sweeps)
+
+
+def apply_stencil(u):
+    d, n = _dn(u)
+    out = np.empty_like(u)
+    lib().orc_apply_stencil(d, n, _p(u), _p(out))
+    return out
+
+
+def residual(b, u):
+    d, n = _dn(u)
+    r = np.empty_like(u)
+    lib().orc_residual(d, n, _p(b), _p(u), _p(r))
+    return r
+
+
+def norm2(r):
+    d, n = _dn(r)
+    return lib().orc_norm2(d, n, _p(r))
+
+
+def rbgs(b, u, sweeps):
+    d, n = _dn(u)
+    lib().orc_rbgs(d, n, _p(b), _p(u), sweeps)
+    return u
+
+
+def wjacobi(b, u, omega, sweeps):
+    d, n = _dn(u)
+    lib().orc_wjacobi(d, n, _p(b), _p(u), omega, sweeps)
+    return u
+
+
+def restrict_fw(r):
+    d, n = _dn(r)
+    nc = n // 2
+    bc = np.empty((nc + 1,) * d)
+    lib().orc_restrict_fw(d, n, _p(r), _p(bc))
+    return bc
+
+
+def prolong_add(uc, u):
+    d, nc = _dn(uc)
+    lib().orc_prolong_add(d, nc, _p(uc), _p(u))
+    return u
+
+
+def coarse_solve(b, sweeps=1):
+    d, n = _dn(b)
+    u = np.empty_like(b)
+    lib().orc_coarse_solve(d, n, _p(b), _p(u), sweeps)
+    return u
+
+
+def scale_rhs(f):
+    d, n = _dn(f)
+    b = np.empty_like(f)
+    lib().orc_scale_rhs(d, n, _p(f), _p(b))
+    return b
+
+
+def vcycle(cfg: Cfg, b, u):
+    rc = lib().orc_vcycle(ctypes.byref(cfg), _p(b), _p(u))
+    if rc != 0:
+        raise ValueError("oracle V-cycle: bad configuration")
+    return u
+
+
+def solve(cfg: Cfg, f, u, rtol=1e-10, maxit=100):
+    """Returns (cycles, relres history); u is updated in place."""
+    hist = np.zeros(maxit)
+    it = lib().orc_solve(ctypes.byref(cfg), _p(f), _p(u), rtol, maxit, _p(hist))
+    if it < 0:
+        raise ValueError("oracle solve: bad configuration")
+    return it, hist[:it].copy()

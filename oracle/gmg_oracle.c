@@ -1,0 +1,359 @@
+/*
+ * gmg_oracle.c -- plain CPU FP64 oracle for the geometric multigrid (GMG)
+ * V-cycle of Feng, Shu, Xu & Zhang, "Numerical Study of Geometric Multigrid
+ * Methods on CPU-GPU Heterogeneous Computers" (arXiv:1208.4247).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the slow, obviously-correct reference the
+ * CUDA library is checked against.  Only the test suite, the smoke check and
+ * the benchmark's CPU-baseline leg load it; the solver library never does, and
+ * the two share no source, header, table or helper.
+ *
+ * Conventions (the paper's section 2.2 and section 4):
+ *   - d = 2 or 3, n = 2^k intervals per dimension, h = 1/n, nodes 0..n.
+ *   - Arrays hold all (n+1)^d nodes, x fastest: index ((k*(n+1))+j)*(n+1)+i
+ *     (k = 0 in 2D).  Only interior nodes 1..n-1 are unknowns; boundary nodes
+ *     are read as zero whatever the array holds (Dirichlet data u = 0).
+ *   - Every level works in the unscaled form of the 5-/7-point scheme:
+ *         A' u = b,  A' u_p = 2d u_p - sum of the 2d neighbours,  b = h^2 f.
+ *     On coarse levels b_{l+1} = 4 * FW(r_l), the factor (h_{l+1}/h_l)^2 = 4
+ *     taking the residual of the fine unscaled equation to the right-hand side
+ *     of the coarse unscaled equation.  All scalings are powers of two.
+ *   - Compiled with -ffp-contract=off: every expression is evaluated as
+ *     written, one rounding per operation, no fused multiply-add.
+ *
+ * Pins (tests/test_oracle_pins.py): sine eigenpairs of A' (section 2.2),
+ * dense direct solves, the closed-form discretisation error that the paper's
+ * FFT error tables print, brute-force dense two-grid spectral radii, the
+ * triangular-solve form of red-black Gauss-Seidel, the adjoint relation
+ * FW = P^T / 2^d and exact interpolation of linear functions.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ grid */
+
+static inline int64_t nodes(int d, int n)
+{
+    int64_t m = n + 1;
+    return d == 2 ? m * m : m * m * m;
+}
+
+static inline int64_t IDX(int n, int i, int j, int k)
+{
+    return ((int64_t)k * (n + 1) + j) * (n + 1) + i;
+}
+
+static inline int interior(int d, int n, int i, int j, int k)
+{
+    if (i <= 0 || i >= n || j <= 0 || j >= n) return 0;
+    if (d == 3 && (k <= 0 || k >= n)) return 0;
+    return 1;
+}
+
+/* Value of a grid function at a node; boundary (and outside) nodes are 0. */
+static inline double val(const double* u, int d, int n, int i, int j, int k)
+{
+    return interior(d, n, i, j, k) ? u[IDX(n, i, j, k)] : 0.0;
+}
+
+/* Sum of the 2d axis neighbours in the fixed order x-, x+, y-, y+, z-, z+. */
+static inline double nbr_sum(const double* u, int d, int n, int i, int j, int k)
+{
+    double s = val(u, d, n, i - 1, j, k);
+    s = s + val(u, d, n, i + 1, j, k);
+    s = s + val(u, d, n, i, j - 1, k);
+    s = s + val(u, d, n, i, j + 1, k);
+    if (d == 3) {
+        s = s + val(u, d, n, i, j, k - 1);
+        s = s + val(u, d, n, i, j, k + 1);
+    }
+    return s;
+}
+
+static inline int kmin(int d) { return d == 3 ? 1 : 0; }
+static inline int kmax(int d, int n) { return d == 3 ? n - 1 : 0; }
+
+/* ------------------------------------------------------- single operators */
+
+/* out = A' u on interior nodes (section 2.2, 5-point / 7-point scheme without
+ * the 1/h^2), boundary entries of out set to 0. */
+void orc_apply_stencil(int d, int n, const double* u, double* out)
+{
+    memset(out, 0, sizeof(double) * nodes(d, n));
+#pragma omp parallel for schedule(static)
+    for (int k = kmin(d); k <= kmax(d, n); ++k)
+        for (int j = 1; j < n; ++j)
+            for (int i = 1; i < n; ++i)
+                out[IDX(n, i, j, k)] = (2.0 * d) * u[IDX(n, i, j, k)] - nbr_sum(u, d, n, i, j, k);
+}
+
+/* r = b - A' u (section 4.1, eq. residual_2D; 3D item (1)). */
+void orc_residual(int d, int n, const double* b, const double* u, double* r)
+{
+    memset(r, 0, sizeof(double) * nodes(d, n));
+#pragma omp parallel for schedule(static)
+    for (int k = kmin(d); k <= kmax(d, n); ++k)
+        for (int j = 1; j < n; ++j)
+            for (int i = 1; i < n; ++i) {
+                int64_t p = IDX(n, i, j, k);
+                r[p] = b[p] - ((2.0 * d) * u[p] - nbr_sum(u, d, n, i, j, k));
+            }
+}
+
+/* Euclidean norm over interior nodes, summed sequentially in index order
+ * (section 4.1 eq. Inner_product2D prints the sum of squares; the square root
+ * is taken here, see the readings in the design notes). */
+double orc_norm2(int d, int n, const double* r)
+{
+    double s = 0.0;
+    for (int k = kmin(d); k <= kmax(d, n); ++k)
+        for (int j = 1; j < n; ++j)
+            for (int i = 1; i < n; ++i) {
+                double v = r[IDX(n, i, j, k)];
+                s = s + v * v;
+            }
+    return sqrt(s);
+}
+
+/* Red-black Gauss-Seidel: per sweep, first every interior node with i+j+k
+ * even ("red"), then every node with i+j+k odd ("black"); each update solves
+ * its own equation, u_p = (b_p + sum of neighbours) / (2d) (section 4.1,
+ * eq. relax_2D; two colours as in the smoother comparison table). */
+void orc_rbgs(int d, int n, const double* b, double* u, int sweeps)
+{
+    for (int s = 0; s < sweeps; ++s)
+        for (int color = 0; color < 2; ++color) {
+#pragma omp parallel for schedule(static)
+            for (int k = kmin(d); k <= kmax(d, n); ++k)
+                for (int j = 1; j < n; ++j)
+                    for (int i = 1; i < n; ++i) {
+                        if (((i + j + k) & 1) != color) continue;
+                        int64_t p = IDX(n, i, j, k);
+                        u[p] = (b[p] + nbr_sum(u, d, n, i, j, k)) / (2.0 * d);
+                    }
+        }
+}
+
+/* Weighted Jacobi: u <- u + omega * (b - A' u) / (2d), all nodes from the
+ * previous iterate (Remark 1 of section 3.2; smoother comparison table). */
+void orc_wjacobi(int d, int n, const double* b, double* u, double omega, int sweeps)
+{
+    int64_t m = nodes(d, n);
+    double* old = (double*)malloc(sizeof(double) * m);
+    for (int s = 0; s < sweeps; ++s) {
+        memcpy(old, u, sizeof(double) * m);
+#pragma omp parallel for schedule(static)
+        for (int k = kmin(d); k <= kmax(d, n); ++k)
+            for (int j = 1; j < n; ++j)
+                for (int i = 1; i < n; ++i) {
+                    int64_t p = IDX(n, i, j, k);
+                    double res = b[p] - ((2.0 * d) * old[p] - nbr_sum(old, d, n, i, j, k));
+                    u[p] = old[p] + omega * res / (2.0 * d);
+                }
+    }
+    free(old);
+}
+
+/* 1D full-weighting weight for an offset -1, 0, +1: 1/4, 1/2, 1/4. */
+static inline double fw1(int delta) { return delta == 0 ? 0.5 : 0.25; }
+
+/* bc = 4 * FW(r): full-weighting restriction from the fine grid (n
+ * intervals) to the coarse grid (n/2 intervals), tensor product of
+ * [1/4 1/2 1/4], times the (h_c/h)^2 = 4 of the unscaled form (Algorithm 1,
+ * f_{l+1} = R r_l; the paper's own 7-point R of eq. Restriction2d is replaced
+ * by full weighting). */
+void orc_restrict_fw(int d, int n, const double* r, double* bc)
+{
+    int nc = n / 2;
+    memset(bc, 0, sizeof(double) * nodes(d, nc));
+    int dz = d == 3 ? 1 : 0;
+#pragma omp parallel for schedule(static)
+    for (int K = kmin(d); K <= kmax(d, nc); ++K)
+        for (int J = 1; J < nc; ++J)
+            for (int I = 1; I < nc; ++I) {
+                double s = 0.0;
+                for (int c = -dz; c <= dz; ++c)
+                    for (int b = -1; b <= 1; ++b)
+                        for (int a = -1; a <= 1; ++a) {
+                            double w = fw1(a) * fw1(b) * (d == 3 ? fw1(c) : 1.0);
+                            s = s + w * val(r, d, n, 2 * I + a, 2 * J + b, 2 * K + c);
+                        }
+                bc[IDX(nc, I, J, K)] = 4.0 * s;
+            }
+}
+
+/* 1D linear-interpolation weights from coarse index c to fine index i:
+ * fine even node i = 2c gets 1, fine odd node gets 1/2 from each side. */
+static inline double lin1(int i, int c)
+{
+    int dd = i - 2 * c;
+    if (dd == 0) return 1.0;
+    if (dd == 1 || dd == -1) return 0.5;
+    return 0.0;
+}
+
+/* u += P uc: (bi/tri)linear prolongation of the coarse correction (nc
+ * intervals) onto the fine grid (2 nc intervals) and correction of u
+ * (Algorithm 1, u_l = u_l + P u_{l+1}; the paper's own interpolation of
+ * eq. Prolongation2d is replaced by the tensor-product linear one).  Coarse
+ * boundary nodes carry the Dirichlet value 0. */
+void orc_prolong_add(int d, int nc, const double* uc, double* u)
+{
+    int n = 2 * nc;
+#pragma omp parallel for schedule(static)
+    for (int k = kmin(d); k <= kmax(d, n); ++k)
+        for (int j = 1; j < n; ++j)
+            for (int i = 1; i < n; ++i) {
+                double s = 0.0;
+                int c0 = (i - 1) / 2, c1 = (i + 1) / 2;
+                int e0 = (j - 1) / 2, e1 = (j + 1) / 2;
+                int g0 = d == 3 ? (k - 1) / 2 : 0, g1 = d == 3 ? (k + 1) / 2 : 0;
+                for (int C = g0; C <= g1; ++C)
+                    for (int B = e0; B <= e1; ++B)
+                        for (int A = c0; A <= c1; ++A) {
+                            double w = lin1(i, A) * lin1(j, B) * (d == 3 ? lin1(k, C) : 1.0);
+                            if (w != 0.0) s = s + w * val(uc, d, nc, A, B, C);
+                        }
+                u[IDX(n, i, j, k)] = u[IDX(n, i, j, k)] + s;
+            }
+}
+
+/* Coarsest-level solve.  With one unknown (n = 2) the single equation is
+ * solved exactly, u = b / (2d) (Remark on the coarsest-level solver).  A
+ * coarsest grid with more unknowns (a truncated hierarchy) is solved
+ * approximately by `sweeps` red-black sweeps from zero. */
+void orc_coarse_solve(int d, int n, const double* b, double* u, int sweeps)
+{
+    memset(u, 0, sizeof(double) * nodes(d, n));
+    if (n == 2) {
+        int64_t p = IDX(n, 1, 1, d == 3 ? 1 : 0);
+        u[p] = b[p] / (2.0 * d);
+        return;
+    }
+    orc_rbgs(d, n, b, u, sweeps);
+}
+
+/* ---------------------------------------------------------------- V-cycle */
+
+enum { ORC_WJACOBI = 0, ORC_RBGS = 1 };
+
+typedef struct {
+    int d;             /* 2 or 3 */
+    int n;             /* finest intervals per dimension, a power of two */
+    int levels;        /* number of grids, finest = 0 .. coarsest = levels-1 */
+    int smoother;      /* ORC_WJACOBI or ORC_RBGS */
+    double omega;      /* weighted-Jacobi weight */
+    int nu1, nu2;      /* pre- and post-smoothing sweeps */
+    int coarse_sweeps; /* red-black sweeps when the coarsest grid has > 1 unknown */
+} orc_cfg;
+
+static void relax(const orc_cfg* c, int n, const double* b, double* u, int sweeps)
+{
+    if (c->smoother == ORC_RBGS)
+        orc_rbgs(c->d, n, b, u, sweeps);
+    else
+        orc_wjacobi(c->d, n, b, u, c->omega, sweeps);
+}
+
+/* One V-cycle (Algorithm 1) on the right-hand side b0 = h^2 f of the finest
+ * level, updating u0 in place.  Coarse iterates start from zero on every
+ * descent.  Returns 0, or -1 on a bad configuration / allocation failure. */
+int orc_vcycle(const orc_cfg* c, const double* b0, double* u0)
+{
+    int d = c->d, L = c->levels;
+    if (L < 1 || (c->n >> (L - 1)) < 2) return -1;
+    double** b = (double**)calloc(L, sizeof(double*));
+    double** u = (double**)calloc(L, sizeof(double*));
+    double* r = (double*)malloc(sizeof(double) * nodes(d, c->n));
+    if (!b || !u || !r) return -1;
+    b[0] = (double*)b0;
+    u[0] = u0;
+    for (int l = 1; l < L; ++l) {
+        b[l] = (double*)calloc(nodes(d, c->n >> l), sizeof(double));
+        u[l] = (double*)calloc(nodes(d, c->n >> l), sizeof(double));
+    }
+    /* down: relax, residual, restrict (Algorithm 1, first loop) */
+    for (int l = 0; l + 1 < L; ++l) {
+        int nl = c->n >> l;
+        relax(c, nl, b[l], u[l], c->nu1);
+        orc_residual(d, nl, b[l], u[l], r);
+        orc_restrict_fw(d, nl, r, b[l + 1]);
+        memset(u[l + 1], 0, sizeof(double) * nodes(d, nl / 2));
+    }
+    /* coarsest level */
+    if (L == 1)
+        relax(c, c->n, b[0], u[0], c->nu1);
+    else
+        orc_coarse_solve(d, c->n >> (L - 1), b[L - 1], u[L - 1], c->coarse_sweeps);
+    /* up: prolongate-correct, relax (Algorithm 1, second loop, l = L-2..0) */
+    for (int l = L - 2; l >= 0; --l) {
+        int nl = c->n >> l;
+        orc_prolong_add(d, nl / 2, u[l + 1], u[l]);
+        relax(c, nl, b[l], u[l], c->nu2);
+    }
+    for (int l = 1; l < L; ++l) {
+        free(b[l]);
+        free(u[l]);
+    }
+    free(b);
+    free(u);
+    free(r);
+    return 0;
+}
+
+/* b = h^2 f on interior nodes, 0 on the boundary (section 2.2). */
+void orc_scale_rhs(int d, int n, const double* f, double* b)
+{
+    double h = 1.0 / n;
+    memset(b, 0, sizeof(double) * nodes(d, n));
+    for (int k = kmin(d); k <= kmax(d, n); ++k)
+        for (int j = 1; j < n; ++j)
+            for (int i = 1; i < n; ++i) {
+                int64_t p = IDX(n, i, j, k);
+                b[p] = (h * h) * f[p];
+            }
+}
+
+/* GMGSolve (Algorithm 3 with every level on one device): from the initial
+ * guess u, repeat V-cycles while ||b - A'u|| > rtol * ||b - A'u_initial||
+ * and fewer than maxit cycles ran.  relres_hist (may be NULL) receives the
+ * relative residual after each cycle.  Returns the cycle count, or -1. */
+int orc_solve(const orc_cfg* c, const double* f, double* u, double rtol, int maxit,
+              double* relres_hist)
+{
+    int d = c->d, n = c->n;
+    int64_t m = nodes(d, n);
+    double* b = (double*)malloc(sizeof(double) * m);
+    double* r = (double*)malloc(sizeof(double) * m);
+    if (!b || !r) return -1;
+    orc_scale_rhs(d, n, f, b);
+    for (int k = kmin(d); k <= kmax(d, n); ++k)
+        for (int j = 0; j <= n; ++j)
+            for (int i = 0; i <= n; ++i)
+                if (!interior(d, n, i, j, k)) u[IDX(n, i, j, k)] = 0.0;
+    if (d == 3) { /* the k = 0 and k = n planes */
+        for (int j = 0; j <= n; ++j)
+            for (int i = 0; i <= n; ++i) {
+                u[IDX(n, i, j, 0)] = 0.0;
+                u[IDX(n, i, j, n)] = 0.0;
+            }
+    }
+    orc_residual(d, n, b, u, r);
+    double resinit = orc_norm2(d, n, r), res = resinit;
+    int iter = 0;
+    while (res > rtol * resinit && iter < maxit) {
+        if (orc_vcycle(c, b, u) != 0) {
+            iter = -1;
+            break;
+        }
+        orc_residual(d, n, b, u, r);
+        res = orc_norm2(d, n, r);
+        if (relres_hist) relres_hist[iter] = resinit > 0.0 ? res / resinit : 0.0;
+        iter++;
+    }
+    free(b);
+    free(r);
+    return iter;
+}

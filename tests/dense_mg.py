@@ -1,0 +1,135 @@
+"""Dense-matrix multigrid operators for brute-force checks on tiny grids.
+
+Independent of both the oracle and the CUDA library: every operator is built
+as an explicit matrix from Kronecker products of 1D stencils, and red-black
+Gauss-Seidel is the textbook splitting (a lower-triangular solve in red-first
+ordering).  Vectors hold interior unknowns only, x fastest.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+
+def _kron_all(mats):
+    out = mats[0]
+    for m in mats[1:]:
+        out = np.kron(out, m)
+    return out
+
+
+def lap(d: int, n: int) -> np.ndarray:
+    """A' = sum over axes of the 1D [-1 2 -1] matrix (unscaled 5/7-point)."""
+    m = n - 1
+    T = 2.0 * np.eye(m) - np.eye(m, k=1) - np.eye(m, k=-1)
+    I = np.eye(m)
+    A = np.zeros((m ** d, m ** d))
+    for ax in range(d):
+        A += _kron_all([T if a == ax else I for a in range(d)])
+    return A
+
+
+def prolong(d: int, nc: int) -> np.ndarray:
+    """Tensor-product linear interpolation, coarse interior -> fine interior."""
+    n = 2 * nc
+    P1 = np.zeros((n - 1, nc - 1))
+    for i in range(1, n):
+        for c in range(1, nc):
+            if i == 2 * c:
+                P1[i - 1, c - 1] = 1.0
+            elif abs(i - 2 * c) == 1:
+                P1[i - 1, c - 1] = 0.5
+    return _kron_all([P1] * d)
+
+
+def restrict(d: int, n: int) -> np.ndarray:
+    """4 x full weighting (1D weights 1/4 1/2 1/4), fine -> coarse interior."""
+    nc = n // 2
+    R1 = np.zeros((nc - 1, n - 1))
+    for c in range(1, nc):
+        for i in range(1, n):
+            if i == 2 * c:
+                R1[c - 1, i - 1] = 0.5
+            elif abs(i - 2 * c) == 1:
+                R1[c - 1, i - 1] = 0.25
+    return 4.0 * _kron_all([R1] * d)
+
+
+def colours(d: int, n: int) -> np.ndarray:
+    """0 for red (i+j(+k) even), 1 for black, interior nodes in x-fastest order."""
+    r = np.arange(1, n)
+    grids = np.meshgrid(*([r] * d), indexing="ij")  # slowest axis first
+    return (sum(grids) % 2).reshape(-1)
+
+
+def rbgs_iteration_matrix(d: int, n: int) -> np.ndarray:
+    """Error propagation of one red-then-black sweep: I - M^-1 A' with M the
+    lower triangle (with diagonal) of A' in red-first ordering."""
+    A = lap(d, n)
+    c = colours(d, n)
+    perm = np.concatenate([np.where(c == 0)[0], np.where(c == 1)[0]])
+    Ap = A[np.ix_(perm, perm)]
+    M = np.tril(Ap)
+    Sp = np.eye(len(perm)) - sla.solve_triangular(M, Ap, lower=True)
+    S = np.empty_like(Sp)
+    S[np.ix_(perm, perm)] = Sp
+    return S
+
+
+def rbgs_sweep(d: int, n: int, b: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """One red-then-black sweep as a triangular solve: M u_new = b - (A'-M) u."""
+    A = lap(d, n)
+    c = colours(d, n)
+    perm = np.concatenate([np.where(c == 0)[0], np.where(c == 1)[0]])
+    Ap = A[np.ix_(perm, perm)]
+    M = np.tril(Ap)
+    rhs = b[perm] - (Ap - M) @ u[perm]
+    up = sla.solve_triangular(M, rhs, lower=True)
+    out = np.empty_like(u)
+    out[perm] = up
+    return out
+
+
+def wj_iteration_matrix(d: int, n: int, omega: float) -> np.ndarray:
+    return np.eye((n - 1) ** d) - (omega / (2 * d)) * lap(d, n)
+
+
+def smoother_matrix(d, n, smoother, omega, sweeps):
+    S = rbgs_iteration_matrix(d, n) if smoother == 1 else wj_iteration_matrix(d, n, omega)
+    return np.linalg.matrix_power(S, sweeps)
+
+
+def vcycle_error_matrix(d, n, levels, smoother=1, omega=0.8, nu1=2, nu2=2,
+                        coarse_sweeps=1):
+    """Error propagation E of one V-cycle with `levels` grids; coarse
+    iterates start from zero, the coarsest grid is solved exactly when it has
+    one unknown and by `coarse_sweeps` red-black sweeps from zero otherwise."""
+    A = lap(d, n)
+    I = np.eye(A.shape[0])
+    if levels == 1:
+        return smoother_matrix(d, n, smoother, omega, nu1)
+    nc = n // 2
+    if levels == 2:
+        Ac = lap(d, nc)
+        if nc == 2:
+            Bc = np.linalg.inv(Ac)
+        else:
+            Sc = np.linalg.matrix_power(rbgs_iteration_matrix(d, nc), coarse_sweeps)
+            Bc = (np.eye(Ac.shape[0]) - Sc) @ np.linalg.inv(Ac)
+    else:
+        Ec = vcycle_error_matrix(d, nc, levels - 1, smoother, omega, nu1, nu2, coarse_sweeps)
+        Ac = lap(d, nc)
+        Bc = (np.eye(Ac.shape[0]) - Ec) @ np.linalg.inv(Ac)
+    CG = I - prolong(d, nc) @ Bc @ restrict(d, n) @ A
+    return (smoother_matrix(d, n, smoother, omega, nu2) @ CG
+            @ smoother_matrix(d, n, smoother, omega, nu1))
+
+
+def to_vec(a: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(a[(slice(1, -1),) * a.ndim]).reshape(-1)
+
+
+def from_vec(v: np.ndarray, d: int, n: int) -> np.ndarray:
+    a = np.zeros((n + 1,) * d)
+    a[(slice(1, -1),) * d] = v.reshape((n - 1,) * d)
+    return a

@@ -1,0 +1,260 @@
+"""Pins of the CPU FP64 oracle against facts fixed by the paper and by the
+mathematics (no GPU).  Each test fails for a plausible slip in the oracle:
+a wrong sign, a dropped neighbour, a missing factor 4 in the restriction, a
+swapped colour order, a mis-weighted interpolation or a wrong norm.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import dense_mg as dm
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _sine_mode(d, n, ks):
+    x = np.arange(n + 1) / n
+    parts = []
+    for k in ks:
+        s = np.sin(k * np.pi * x)
+        s[0] = s[-1] = 0.0
+        parts.append(s)
+    if d == 2:
+        ky, kx = parts[1], parts[0]
+        return np.ascontiguousarray(ky[:, None] * kx[None, :])
+    kz, ky, kx = parts[2], parts[1], parts[0]
+    return np.ascontiguousarray(kz[:, None, None] * ky[None, :, None] * kx[None, None, :])
+
+
+def _eig(n, ks):
+    """h^2 lambda_k of the unscaled operator: 4 sum_m sin^2(k_m pi h / 2)."""
+    h = 1.0 / n
+    return 4.0 * sum(np.sin(k * np.pi * h / 2) ** 2 for k in ks)
+
+
+@pytest.mark.parametrize("d,n", [(2, 8), (2, 32), (3, 8), (3, 16)])
+def test_stencil_sine_eigenpairs(d, n):
+    """Section 2.2 scheme: A' phi_k = h^2 lambda_k phi_k on sine modes."""
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        ks = rng.integers(1, n, size=d)
+        phi = _sine_mode(d, n, ks)
+        out = oracle.apply_stencil(phi)
+        assert np.max(np.abs(out - _eig(n, ks) * phi)) <= 1e-13 * np.max(np.abs(phi)) * 4 * d
+
+
+@pytest.mark.parametrize("d,n,omega", [(2, 16, 0.8), (3, 8, 6.0 / 7.0)])
+def test_wjacobi_error_symbol(d, n, omega):
+    """Weighted Jacobi damps phi_k by 1 - omega h^2 lambda_k / (2d) (b = 0)."""
+    ks = [3, 5, 2][:d]
+    phi = _sine_mode(d, n, ks)
+    u = phi.copy()
+    oracle.wjacobi(np.zeros_like(u), u, omega, 1)
+    g = 1.0 - omega * _eig(n, ks) / (2 * d)
+    assert np.max(np.abs(u - g * phi)) <= 1e-14
+
+
+@pytest.mark.parametrize("d,n", [(2, 8), (2, 16), (3, 8)])
+def test_rbgs_is_red_first_triangular_solve(d, n):
+    """One red-black sweep equals the Gauss-Seidel triangular solve in
+    red-first ordering (textbook splitting, scipy solve_triangular)."""
+    rng = np.random.default_rng(1)
+    b = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)
+    u = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)
+    ref = dm.rbgs_sweep(d, n, dm.to_vec(b), dm.to_vec(u))
+    oracle.rbgs(b, u, 1)
+    assert np.max(np.abs(dm.to_vec(u) - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def _op_matrix(op, d, n_in, n_out):
+    cols = []
+    for e in np.eye((n_in - 1) ** d):
+        cols.append(dm.to_vec(op(dm.from_vec(e, d, n_in))))
+    return np.array(cols).T
+
+
+@pytest.mark.parametrize("d,n", [(2, 8), (2, 16), (3, 8)])
+def test_transfer_operators_match_definitions(d, n):
+    """Full weighting [1/4 1/2 1/4]^d times 4, (bi/tri)linear interpolation,
+    and the adjoint relation 4 FW = 4 P^T / 2^d."""
+    nc = n // 2
+    R = _op_matrix(oracle.restrict_fw, d, n, nc)
+    P = _op_matrix(lambda uc: oracle.prolong_add(uc, np.zeros((n + 1,) * d)), d, nc, n)
+    np.testing.assert_allclose(R, dm.restrict(d, n), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(P, dm.prolong(d, nc), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(R, 4.0 * P.T / 2 ** d, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_prolong_exact_on_multilinear(d):
+    """Linear interpolation reproduces a multilinear function wherever every
+    parent coarse node is an interior node."""
+    nc = 8
+    n = 2 * nc
+    xc = np.arange(nc + 1) / nc
+    xf = np.arange(n + 1) / n
+    fx = lambda x: 1.0 + 2.0 * x
+    fy = lambda y: 3.0 - y
+    fz = lambda z: 0.5 + z
+    if d == 2:
+        gc = fy(xc)[:, None] * fx(xc)[None, :]
+        gf = fy(xf)[:, None] * fx(xf)[None, :]
+    else:
+        gc = fz(xc)[:, None, None] * fy(xc)[None, :, None] * fx(xc)[None, None, :]
+        gf = fz(xf)[:, None, None] * fy(xf)[None, :, None] * fx(xf)[None, None, :]
+    gc = np.ascontiguousarray(gc)
+    out = oracle.prolong_add(gc, np.zeros((n + 1,) * d))
+    sl = (slice(2, n - 1),) * d
+    np.testing.assert_allclose(out[sl], gf[sl], rtol=1e-15, atol=1e-15)
+
+
+def test_norm2_is_euclidean():
+    rng = np.random.default_rng(2)
+    r = dm.from_vec(rng.standard_normal(15 ** 3), 3, 16)
+    assert oracle.norm2(r) == pytest.approx(np.linalg.norm(dm.to_vec(r)), rel=1e-14)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_coarsest_one_unknown_is_exact(d):
+    """Remark (coarsest level): with one unknown the solve is exact."""
+    b = np.zeros((3,) * d)
+    b[(1,) * d] = 0.7
+    u = oracle.coarse_solve(b)
+    assert np.max(np.abs(oracle.apply_stencil(u) - b)) == 0.0
+
+
+VCYCLE_CASES = [
+    # d, n, levels, smoother, omega, nu1, nu2, coarse_sweeps
+    (2, 8, 3, oracle.RBGS, 0.8, 1, 1, 1),
+    (2, 16, 4, oracle.RBGS, 0.8, 2, 2, 1),
+    (2, 16, 4, oracle.WJACOBI, 0.8, 2, 2, 1),
+    (2, 16, 2, oracle.RBGS, 0.8, 1, 1, 3),
+    (2, 16, 3, oracle.WJACOBI, 0.8, 1, 2, 2),
+    (3, 8, 3, oracle.RBGS, 0.8, 2, 2, 1),
+    (3, 8, 3, oracle.WJACOBI, 6.0 / 7.0, 1, 1, 1),
+    (3, 8, 2, oracle.RBGS, 0.8, 1, 1, 4),
+]
+
+
+@pytest.mark.parametrize("case", VCYCLE_CASES)
+def test_vcycle_equals_dense_cycle(case):
+    """Algorithm 1 as a linear map: u1 = E u0 + (I - E) A'^-1 b, with E the
+    dense error propagation built from the Kronecker-product operators."""
+    d, n, L, sm, om, nu1, nu2, cs = case
+    rng = np.random.default_rng(3)
+    E = dm.vcycle_error_matrix(d, n, L, sm, om, nu1, nu2, cs)
+    A = dm.lap(d, n)
+    u0 = rng.standard_normal((n - 1) ** d)
+    b = rng.standard_normal((n - 1) ** d)
+    ref = E @ u0 + (np.eye(len(u0)) - E) @ np.linalg.solve(A, b)
+    cfg = oracle.make_cfg(d, n, L, sm, om, nu1, nu2, cs)
+    u = dm.from_vec(u0, d, n)
+    oracle.vcycle(cfg, dm.from_vec(b, d, n), u)
+    assert np.max(np.abs(dm.to_vec(u) - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("d,n,sm,om,nu,rho_ref", [
+    (2, 32, oracle.WJACOBI, 0.8, 1, 0.358),
+    (2, 32, oracle.RBGS, 0.8, 1, 0.074),
+    (2, 32, oracle.RBGS, 0.8, 2, 0.041),
+    (3, 8, oracle.RBGS, 0.8, 2, None),
+])
+def test_two_grid_contraction(d, n, sm, om, nu, rho_ref):
+    """Brute-force two-grid spectral radius vs the oracle's asymptotic
+    per-cycle contraction (levels = 2, coarse grid solved to round-off)."""
+    cs = 1000 if d == 2 else 200
+    E = dm.vcycle_error_matrix(d, n, 2, sm, om, nu, nu, cs)
+    rho = max(abs(np.linalg.eigvals(E)))
+    if rho_ref is not None:
+        assert rho == pytest.approx(rho_ref, abs=1.5e-3)
+    cfg = oracle.make_cfg(d, n, 2, sm, om, nu, nu, cs)
+    rng = np.random.default_rng(4)
+    u = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)
+    b = np.zeros_like(u)
+    norms = []
+    for _ in range(30):
+        oracle.vcycle(cfg, b, u)
+        norms.append(np.linalg.norm(u))
+        if norms[-1] < 1e-200:
+            break
+    rate = (norms[-1] / norms[-11]) ** 0.1
+    assert rate == pytest.approx(rho, rel=0.02)
+
+
+@pytest.mark.parametrize("d,n,sm,om", [
+    (2, 16, oracle.RBGS, 0.8), (2, 16, oracle.WJACOBI, 0.8),
+    (3, 8, oracle.RBGS, 0.8), (3, 8, oracle.WJACOBI, 6.0 / 7.0),
+])
+def test_converged_solve_matches_dense_direct(d, n, sm, om):
+    """Iterating to round-off reproduces numpy.linalg.solve of A' u = h^2 f."""
+    rng = np.random.default_rng(5)
+    f = dm.from_vec(rng.uniform(-1, 1, (n - 1) ** d), d, n)
+    u = np.zeros_like(f)
+    cfg = oracle.make_cfg(d, n, 0, sm, om, 2, 2, 1)
+    it, hist = oracle.solve(cfg, f, u, rtol=0.0, maxit=60)
+    ref = np.linalg.solve(dm.lap(d, n), dm.to_vec(f) / n ** 2)
+    assert np.max(np.abs(dm.to_vec(u) - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def _closed_form_error(d, n):
+    """u = prod sin(pi x), f = d pi^2 u: the discrete solution is
+    (d pi^2 / lambda_1) u with lambda_1 = (4d/h^2) sin^2(pi h/2), so
+    ||u - u_h||_h = |d pi^2/lambda_1 - 1| * 2^(-d/2) with ||v||_h^2 = h^d sum v^2."""
+    h = 1.0 / n
+    lam = 4 * d / h ** 2 * np.sin(np.pi * h / 2) ** 2
+    return abs(d * np.pi ** 2 / lam - 1.0) * 2.0 ** (-d / 2)
+
+
+def _golden():
+    rows = []
+    with open(os.path.join(GOLDEN, "paper_fft_error.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                d, L, e = line.split()
+                rows.append((int(d), int(L), float(e)))
+    return rows
+
+
+def test_closed_form_matches_paper_fft_table():
+    """The paper's FFT errors are the discrete solution's error (within the
+    printed digits and a <0.4% spread in 2D)."""
+    for d, L, e in _golden():
+        cf = _closed_form_error(d, 2 ** L)
+        assert e == pytest.approx(cf, rel=4e-3 if d == 2 else 6e-4), (d, L)
+
+
+@pytest.mark.parametrize("d,Ls", [(2, [6, 7, 8, 9]), (3, [4, 5, 6])])
+def test_discretisation_error_closed_form_and_order(d, Ls):
+    """GMG solved to 1e-12 reproduces the closed-form error; O(h^2)."""
+    errs = []
+    for L in Ls:
+        n = 2 ** L
+        ue = oracle_u = None
+        from paper_1208_4247_gb300 import inputs
+        ue = inputs.manufactured_u(d, n)
+        f = np.ascontiguousarray(d * np.pi ** 2 * ue)
+        u = np.zeros_like(f)
+        cfg = oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1)
+        oracle.solve(cfg, f, u, rtol=1e-12, maxit=50)
+        err = np.sqrt((1.0 / n) ** d * np.sum((u - ue) ** 2))
+        assert err == pytest.approx(_closed_form_error(d, n), rel=1e-6)
+        errs.append(err)
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    for r in ratios:
+        assert r == pytest.approx(4.0, rel=0.02)
+
+
+def test_solver_reaches_rtol_and_history_monotone():
+    from paper_1208_4247_gb300 import inputs
+    n = 64
+    f = inputs.rhs_uniform(3, n, 2)
+    u = np.zeros_like(f)
+    cfg = oracle.make_cfg(3, n, 0, oracle.RBGS, 0.8, 2, 2, 1)
+    it, hist = oracle.solve(cfg, f, u, rtol=1e-10, maxit=50)
+    assert hist[-1] <= 1e-10 and it < 20
+    assert np.all(np.diff(hist) < 0)
+    b = oracle.scale_rhs(f)
+    r = oracle.residual(b, u)
+    assert oracle.norm2(r) / oracle.norm2(b) == pytest.approx(hist[-1], rel=1e-9)
