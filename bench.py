@@ -1,0 +1,295 @@
+"""Benchmark: DOF/s to a 1e-10 relative residual on the 3D Poisson 257^3
+workload (255^3 unknowns, 7-point FD, f = U[-1,1] seed 2, plain FP64 V(2,2)
+red-black Gauss-Seidel, full weighting, trilinear prolongation, coarsest 3^3
+solved exactly).  One step = one whole solve from u = 0.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64
+oracle on this host's cores on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF/s to 1e-10 rel. residual (FP64-accurate) and HBM GB/s vs peak, per form"
+D, N, SEED, RTOL = 3, 256, 2, 1e-10
+WORKLOAD = ("3D Poisson -Lap u = f, 257^3 grid (255^3 = 16.58M unknowns), 7-point FD, zero "
+            "Dirichlet, f = U[-1,1] i.i.d. (seed 2), plain FP64 V(2,2) red-black GS, 27-point "
+            "full weighting, trilinear prolongation, coarsest 3^3 exact, to relative residual 1e-10")
+UNKNOWNS = (N - 1) ** D
+# FP64 pipe: 2 DFMA/DADD issue slots per clock per SM (GB300 nominal 1.25 TFLOP/s FP64 =
+# 2 flop x 2 inst/clk x 152 SMs x 2.07 GHz), 152 SMs, 2070 MHz max SM clock.
+FP64_INST_PER_CLK_SM = 2
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_solve_timed(f, cores_note):
+    import oracle
+    cfg = oracle.make_cfg(D, N, 0, oracle.RBGS, 0.8, 2, 2, 1)
+    u = np.zeros_like(f)
+    t0 = time.perf_counter()
+    it, hist = oracle.solve(cfg, f, u, RTOL, 100)
+    dt = time.perf_counter() - t0
+    return it, dt
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, ws):
+    """The CPU FP64 oracle on this host's cores, same workload and metric."""
+    if rank != 0:
+        return
+    from paper_1208_4247_gb300 import inputs
+    import oracle
+    oracle.build()
+    f = inputs.rhs_uniform(D, N, SEED)
+    for _ in range(args.warmup):
+        oracle_solve_timed(f, None)
+    times, its = [], []
+    for _ in range(args.steps):
+        it, dt = oracle_solve_timed(f, None)
+        times.append(dt)
+        its.append(it)
+    t = sum(times) / len(times)
+    value = UNKNOWNS / t
+    c = cores()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "cycles": its[-1]},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": c, "kind": "oracle",
+                             "sample": "full 257^3 solve to 1e-10 per step (OpenMP, all cores)"},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, ws, local):
+    import torch
+    from paper_1208_4247_gb300 import build as _b
+    from paper_1208_4247_gb300 import inputs
+    from paper_1208_4247_gb300.gmg import Solver
+
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or ws == 1:
+        _b.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f_np = inputs.rhs_uniform(D, N, SEED)
+    f = torch.from_numpy(f_np).to(dev)
+    u = torch.zeros_like(f)
+    S = Solver(D, N)
+    S.set_timing(True)
+    cycles = None
+    for _ in range(args.warmup):
+        u.zero_()
+        cycles, rel, conv = S.solve(f, u, RTOL)
+        assert conv, "warm-up solve did not converge"
+    S.timing_reset()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            u.zero_()
+            cycles, rel, conv = S.solve(f, u, RTOL)
+        ev1.record(stream)
+        barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    stats, launches = S.timing_report()
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = UNKNOWNS * ws / (ms_step * 1e-3)
+
+    # dominant kernel: largest summed device time; achieved = its per-launch
+    # FP64 instruction count / its average launch time (level 0 record)
+    by_kernel = {}
+    for s in stats:
+        by_kernel.setdefault(s["kernel"], []).append(s)
+    tot_ms = {k: sum(r["ms"] for r in v) for k, v in by_kernel.items()}
+    dom = max(tot_ms, key=tot_ms.get)
+    rec = [r for r in by_kernel[dom] if r["level"] == 0][0]
+    avg_s = rec["ms"] / rec["launches"] * 1e-3
+    clocks = clk.summary()
+    peak_inst = FP64_INST_PER_CLK_SM * NUM_SMS * SM_MAX_MHZ * 1e6 / 1e12  # T inst/s
+    achieved = rec["dp_ops"] / avg_s / 1e12
+    pk, pk_kind = peaks()
+    alg_bytes = sum(r["bytes"] * r["launches"] for r in stats) / args.steps
+    roof = {"bound": "alu", "kernel": f"{dom} (level 0)", "achieved": achieved,
+            "peak": peak_inst, "unit": "T FP64-pipe inst/s", "frac": achieved / peak_inst,
+            "traffic": None,
+            "peak_note": "2 FP64 inst/clk/SM x 152 SMs x 2070 MHz (derived, nominal)",
+            "kernel_share": tot_ms[dom] / sum(tot_ms.values()),
+            "kernel_hbm_gbs": rec["bytes"] / avg_s / 1e9}
+    hbm = {"solve_alg_bytes": alg_bytes, "achieved_gbs": alg_bytes / (ms_step * 1e-3) / 1e9,
+           "peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind,
+           "frac": alg_bytes / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"]}
+
+    # end to end through the public API: pinned host f, u; H2D + solve + D2H
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.empty(f_np.shape, dtype=torch.float64, pin_memory=True).numpy()
+        fh[...] = f_np
+        uh = torch.empty(f_np.shape, dtype=torch.float64, pin_memory=True).numpy()
+        S.set_timing(False)
+        uh[...] = 0.0
+        S.solve_host(fh, uh, RTOL)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            uh[...] = 0.0
+            S.solve_host(fh, uh, RTOL)
+        e1.record(stream)
+        barrier()
+        e_ms = e0.elapsed_time(e1) / args.steps
+        e2e = {"value": UNKNOWNS * ws / (e_ms * 1e-3), "unit": "DOF/s", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": 2 * fh.nbytes, "d2h_bytes_per_step": uh.nbytes}
+    S.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        it_o, dt = oracle_solve_timed(f_np, None)
+        cpu = {"value": UNKNOWNS / dt, "unit": "DOF/s", "cores": cores(), "kind": "oracle",
+               "sample": f"one full 257^3 solve to 1e-10 ({it_o} cycles, {dt:.1f} s, OpenMP)"}
+    line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cycles": cycles,
+                       "l2": "inputs larger than L2 (u, q, r: 3 x 136 MB at level 0)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks}
+    if args.kernels:
+        line["kernels"] = stats
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels", action="store_true", help="add per-kernel records")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws, local)
+
+
+if __name__ == "__main__":
+    main()

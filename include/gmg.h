@@ -1,0 +1,150 @@
+/*
+ * gmg.h -- C ABI of the GB300 geometric multigrid (GMG) library for the
+ * finite-difference Poisson equation
+ *
+ *     -Laplace(u) = f in (0,1)^d,  u = 0 on the boundary,  d = 2 or 3,
+ *
+ * discretised by the 5-point (2D) / 7-point (3D) central-difference scheme on
+ * a uniform grid with n intervals per dimension (h = 1/n), section 2.2 of
+ * Feng, Shu, Xu & Zhang, "Numerical Study of Geometric Multigrid Methods on
+ * CPU-GPU Heterogeneous Computers" (arXiv:1208.4247).  The solver runs the
+ * V-cycle of Algorithm 1 inside the stopping loop of Algorithm 3 (GMGSolve),
+ * with every level on the GPU.
+ *
+ * Array convention for every f / u argument: double precision, all (n+1)^d
+ * grid nodes including the boundary, C order with x fastest (element
+ * ((k*(n+1)) + j)*(n+1) + i; k = 0 in 2D), densely packed.  f on boundary
+ * nodes is ignored; the solver writes 0 to u's boundary nodes.
+ *
+ * Ownership: the caller owns f and u.  A handle owns the level hierarchy
+ * (about 3.3-4 N values, section 4 remark on space complexity) and a CUDA
+ * graph of one cycle; it is bound to the CUDA device current at
+ * gmg_create and to the stream given there.
+ *
+ * Errors: every call returns a gmg_status; on failure gmg_last_error()
+ * returns a message for the calling thread (valid until its next call).
+ * No call aborts the process.  Calls on one handle must not run
+ * concurrently from several threads.
+ */
+#ifndef GMG_H
+#define GMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GMG_OK = 0,
+    GMG_ERR_ARG = 1,            /* bad argument or configuration */
+    GMG_ERR_LAYOUT = 2,         /* pointer not usable (null, host vs device, misaligned) */
+    GMG_ERR_ALLOC = 3,          /* device or pinned host allocation failed */
+    GMG_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+    GMG_ERR_NONFINITE = 5,      /* residual norm became NaN / Inf */
+    GMG_ERR_NOT_CONVERGED = 6,  /* maxit reached; u holds the last iterate */
+    GMG_ERR_DEVICE_TIMEOUT = 7, /* a bounded device-side wait gave up */
+    GMG_ERR_UNSUPPORTED = 8     /* configuration not built in this library */
+} gmg_status;
+
+typedef enum { GMG_WJACOBI = 0, GMG_RBGS = 1, GMG_LEARNED = 2 } gmg_smoother;
+typedef enum { GMG_FP64 = 0, GMG_FP32_IR = 1, GMG_BF16_IR = 2 } gmg_precision;
+typedef enum { GMG_VCYCLE = 0 } gmg_cycle;
+
+typedef struct {
+    int d;             /* 2 or 3 */
+    int n;             /* intervals per dimension: a power of two, 2..4096 (2D) / 2..1024 (3D) */
+    int levels;        /* grids in the hierarchy (Algorithm 1's L); 0 = down to n = 2,
+                          whose single unknown is solved exactly (Remark, coarsest level) */
+    int smoother;      /* gmg_smoother: weighted Jacobi or red-black Gauss-Seidel
+                          (red = i+j+k even, red before black in pre- and post-smoothing) */
+    double omega;      /* weighted-Jacobi weight (ignored by red-black GS) */
+    int nu1, nu2;      /* pre- / post-smoothing sweeps (Algorithm 1's mu_f, mu_b), 0..16 */
+    int cycle;         /* gmg_cycle: GMG_VCYCLE */
+    int precision;     /* gmg_precision: plain FP64, or FP32 / BF16 V-cycles inside
+                          FP64 iterative refinement */
+    int maxit;         /* cap on V-cycles (FP64) or on outer refinement steps */
+    int inner_cycles;  /* FP32 / BF16 forms: V-cycles per outer refinement step */
+    int coarse_sweeps; /* red-black sweeps from zero on a coarsest grid with more than
+                          one unknown (truncated hierarchy); unused otherwise */
+} gmg_config;
+
+typedef struct gmg_handle_s* gmg_handle;
+
+/* Fill *cfg with defaults for d, n: all levels, red-black GS, omega = 4/5,
+ * V(2,2), plain FP64, maxit 100, 4 inner cycles, 64 coarse sweeps. */
+gmg_status gmg_config_init(gmg_config* cfg, int d, int n);
+
+/* Create a solver for *cfg on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream) on which every later call on
+ * the handle is ordered.  Allocates the level hierarchy on the device. */
+gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out);
+
+/* GMGSolve (Algorithm 3, all levels on the device): starting from the initial
+ * guess in u, run cycles while ||h^2 f - A'u||_2 > rtol * ||h^2 f - A'u_0||_2
+ * (A' the unscaled 5/7-point operator, norm over interior nodes) and fewer
+ * than maxit cycles have run.  f, u: device pointers (layout above).
+ * iters_out (may be NULL): cycles run.  relres_out (may be NULL): final
+ * relative residual.  Returns GMG_ERR_NOT_CONVERGED with a valid u when
+ * maxit stops the loop.  Synchronises the handle's stream once per cycle to
+ * read the residual norm. */
+gmg_status gmg_solve(gmg_handle h, const double* f, double* u, double rtol,
+                     int* iters_out, double* relres_out);
+
+/* As gmg_solve, but f and u are HOST pointers: f and the initial u are copied
+ * to device buffers owned by the handle, the solve runs, u is copied back. */
+gmg_status gmg_solve_host(gmg_handle h, const double* f_host, double* u_host, double rtol,
+                          int* iters_out, double* relres_out);
+
+/* Exactly ncycles cycles of Algorithm 1 from the given u (no stopping test),
+ * e.g. for per-cycle comparisons.  relres_out (may be NULL, else ncycles
+ * entries) receives ||h^2 f - A'u|| / ||h^2 f - A'u_0|| after each cycle.
+ * f, u: device pointers. */
+gmg_status gmg_cycles(gmg_handle h, const double* f, double* u, int ncycles,
+                      double* relres_out);
+
+/* Relative-residual history of the last solve / cycles call: writes up to
+ * cap entries to relres (host), the count to *count. */
+gmg_status gmg_history(gmg_handle h, double* relres, int cap, int* count);
+
+/* Per-kernel device timing (diagnostics, the paper's per-function and
+ * per-level profiles of section 5.3).  While enabled, every kernel of the
+ * cycle graph is bracketed by CUDA events recorded on the handle's stream,
+ * and after each cycle its device time is added to a record keyed by
+ * (kernel, level).  Enabling or disabling re-captures the cycle graph. */
+gmg_status gmg_set_timing(gmg_handle h, int enable);
+
+typedef struct {
+    char kernel[24];   /* kernel name, e.g. "rb_half", "restrict", "resnorm" */
+    int level;         /* grid level (0 = finest) */
+    int64_t launches;  /* launches timed since the last reset */
+    double ms;         /* summed device time of those launches */
+    double dp_ops;     /* FP64 pipe instructions per launch (arithmetic model) */
+    double bytes;      /* algorithmic DRAM bytes per launch (each value read/written once) */
+} gmg_kernel_stat;
+
+/* Copy up to cap records to out (host); *count receives the number of
+ * records.  *launches_out (may be NULL) receives every kernel launch the
+ * handle made since the last reset, timed or not. */
+gmg_status gmg_timing_report(gmg_handle h, gmg_kernel_stat* out, int cap, int* count,
+                             int64_t* launches_out);
+
+/* Zero the timing records and the launch counter. */
+gmg_status gmg_timing_reset(gmg_handle h);
+
+/* Release every device and host resource of the handle.  NULL is a no-op. */
+gmg_status gmg_destroy(gmg_handle h);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* gmg_last_error(void);
+
+/* Version of this ABI (GMG_ABI_VERSION). */
+int gmg_abi_version(void);
+#define GMG_ABI_VERSION 1
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMG_H */

@@ -1,0 +1,628 @@
+// C ABI of the solver (include/gmg.h): handle lifetime, the V-cycle schedule
+// of Algorithm 1 captured once into a CUDA graph, and the stopping loop of
+// Algorithm 3 with every level on the device.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "gmg_internal.cuh"
+
+namespace gmg {
+
+namespace {
+thread_local std::string g_err;
+}
+void set_error(const std::string& msg) { g_err = msg; }
+const std::string& last_error() { return g_err; }
+
+}  // namespace gmg
+
+using namespace gmg;
+
+struct gmg_handle_s {
+    gmg_config cfg{};
+    int device = 0;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;  // owned, non-blocking; ordered after user_stream per call
+    cudaEvent_t ev = nullptr;
+    std::vector<Level> lv;
+    double* u0_tmp = nullptr;  // level-0 ping-pong buffer (weighted Jacobi)
+    double* partial = nullptr;
+    double* d_res2 = nullptr;
+    double* h_res2 = nullptr;  // pinned
+    cudaGraphExec_t graph = nullptr;
+    const double* graph_u = nullptr;  // level-0 iterate baked into the graph
+    std::vector<double> hist;
+    double* f_stage = nullptr;  // device copies for gmg_solve_host
+    double* u_stage = nullptr;
+    std::vector<void*> allocs;
+    // launch accounting and optional per-kernel event timing
+    int64_t launches = 0;     // every kernel launch since the last reset
+    int graph_kernels = 0;    // kernels per launch of the cycle graph
+    bool timing = false;
+    struct TimedLaunch {
+        int kind, level;
+        double ops, bytes;
+    };
+    std::vector<TimedLaunch> timed;  // timed launches of one graph run, in order
+    std::vector<cudaEvent_t> tev;    // two events per timed launch
+    struct Stat {
+        int64_t launches = 0;
+        double ms = 0.0, ops = 0.0, bytes = 0.0;
+    };
+    std::map<std::pair<int, int>, Stat> stats;
+};
+
+namespace {
+
+bool is_pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+int64_t nodes_of(int d, int n) {
+    int64_t m = n + 1;
+    return d == 3 ? m * m * m : m * m;
+}
+
+gmg_status check_cfg(const gmg_config* c) {
+    if (!c) {
+        set_error("config is NULL");
+        return GMG_ERR_ARG;
+    }
+    if (c->d != 2 && c->d != 3) {
+        set_error("d must be 2 or 3");
+        return GMG_ERR_ARG;
+    }
+    const int nmax = c->d == 2 ? 16384 : 1024;
+    if (!is_pow2(c->n) || c->n > nmax) {
+        set_error("n must be a power of two in [2, " + std::to_string(nmax) + "]");
+        return GMG_ERR_ARG;
+    }
+    const int lmax = ilog2(c->n);
+    if (c->levels < 0 || c->levels > lmax) {
+        set_error("levels must be 0 (all) or 1.." + std::to_string(lmax));
+        return GMG_ERR_ARG;
+    }
+    if (c->smoother != GMG_WJACOBI && c->smoother != GMG_RBGS) {
+        set_error(c->smoother == GMG_LEARNED ? "learned smoother: use the gmg_learned_* calls"
+                                             : "unknown smoother");
+        return c->smoother == GMG_LEARNED ? GMG_ERR_UNSUPPORTED : GMG_ERR_ARG;
+    }
+    if (!(c->omega > 0.0 && c->omega < 2.0)) {
+        set_error("omega must lie in (0, 2)");
+        return GMG_ERR_ARG;
+    }
+    if (c->nu1 < 0 || c->nu2 < 0 || c->nu1 > 16 || c->nu2 > 16) {
+        set_error("nu1, nu2 must lie in 0..16");
+        return GMG_ERR_ARG;
+    }
+    if (c->cycle != GMG_VCYCLE) {
+        set_error("cycle must be GMG_VCYCLE");
+        return GMG_ERR_ARG;
+    }
+    if (c->precision != GMG_FP64) {
+        set_error("precision: only GMG_FP64 is built into gmg_create");
+        return GMG_ERR_UNSUPPORTED;
+    }
+    if (c->maxit < 0 || c->maxit > 100000) {
+        set_error("maxit must lie in 0..100000");
+        return GMG_ERR_ARG;
+    }
+    if (c->coarse_sweeps < 0 || c->coarse_sweeps > 100000) {
+        set_error("coarse_sweeps must lie in 0..100000");
+        return GMG_ERR_ARG;
+    }
+    return GMG_OK;
+}
+
+gmg_status dev_alloc(gmg_handle h, double** p, int64_t count) {
+    cudaError_t e = cudaMalloc((void**)p, sizeof(double) * count);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return GMG_ERR_ALLOC;
+    }
+    h->allocs.push_back(*p);
+    e = cudaMemsetAsync(*p, 0, sizeof(double) * count, h->stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+        return GMG_ERR_CUDA;
+    }
+    return GMG_OK;
+}
+
+gmg_status check_device_ptr(const void* p, const char* name) {
+    if (!p) {
+        set_error(std::string(name) + " is NULL");
+        return GMG_ERR_LAYOUT;
+    }
+    if (((uintptr_t)p) % alignof(double) != 0) {
+        set_error(std::string(name) + " is not 8-byte aligned");
+        return GMG_ERR_LAYOUT;
+    }
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess || (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        set_error(std::string(name) + " is not a device pointer");
+        return GMG_ERR_LAYOUT;
+    }
+    return GMG_OK;
+}
+
+int num_levels(const gmg_config& c) { return c.levels > 0 ? c.levels : ilog2(c.n); }
+
+enum Kind { K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_PREPARE, K_COUNT };
+const char* kKindName[K_COUNT] = {"rb_half", "wj_sweep", "residual", "restrict",
+                                  "prolong_add", "resnorm", "copy", "prepare"};
+
+// Arithmetic model per launch: FP64 pipe instructions the kernel issues and
+// the algorithmic DRAM bytes (every value the operation needs read once,
+// every value it produces written once), both from the level size.
+std::pair<double, double> model(int kind, int d, int n, bool red_only) {
+    const double N = std::pow((double)(n - 1), d);
+    const int nc = n / 2;
+    const double Nc = std::pow((double)std::max(nc - 1, 0), d);
+    const double cells = std::pow((double)nc, d);
+    const bool t = d == 3;
+    switch (kind) {
+        case K_RB_HALF: return {N / 2 * (t ? 6 : 4), N / 2 * 24};
+        case K_WJ: return {N * (t ? 8 : 6), N * 24};
+        case K_RESIDUAL:
+            return red_only ? std::make_pair(N / 2 * (t ? 7 : 5), N * 16)
+                            : std::make_pair(N * (t ? 7 : 5), N * 24);
+        case K_RESTRICT:
+            return red_only ? std::make_pair(Nc * (t ? 13 : 4), N / 2 * 8 + Nc * 16)
+                            : std::make_pair(Nc * (t ? 27 : 8), N * 8 + Nc * 16);
+        case K_PROLONG: return {cells * (t ? 20 : 8), Nc * 8 + N * 16};
+        case K_RESNORM: return {N * (t ? 8 : 6), N * 16};
+        case K_COPY: return {0.0, N * 16};
+        case K_PREPARE: return {N, N * 24};
+    }
+    return {0.0, 0.0};
+}
+
+// Enqueue one kernel (launch() issues it on h->stream), bracketed by event
+// record nodes when timing is on.
+template <class F>
+void timed(gmg_handle h, int kind, int level, int n, bool red_only, F&& launch) {
+    if (h->timing) {
+        const size_t i = h->timed.size();
+        while (h->tev.size() < 2 * (i + 1)) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            h->tev.push_back(e);
+        }
+        cudaEventRecordWithFlags(h->tev[2 * i], h->stream, cudaEventRecordExternal);
+        launch();
+        cudaEventRecordWithFlags(h->tev[2 * i + 1], h->stream, cudaEventRecordExternal);
+        auto m = model(kind, h->cfg.d, n, red_only);
+        h->timed.push_back({kind, level, m.first, m.second});
+    } else {
+        launch();
+    }
+    h->graph_kernels++;
+}
+
+// After a graph run: add each timed launch's device time to its record.
+void collect_timing(gmg_handle h) {
+    for (size_t i = 0; i < h->timed.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->tev[2 * i], h->tev[2 * i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        auto& t = h->timed[i];
+        auto& s = h->stats[{t.kind, t.level}];
+        s.launches++;
+        s.ms += ms;
+        s.ops = t.ops;
+        s.bytes = t.bytes;
+    }
+}
+
+// Enqueue `sweeps` smoothing sweeps on level l; cur tracks which u buffer
+// holds the iterate (weighted Jacobi alternates).
+void relax(gmg_handle h, int l, int sweeps, int& cur) {
+    Level& L = h->lv[l];
+    const int d = h->cfg.d;
+    for (int s = 0; s < sweeps; ++s) {
+        if (h->cfg.smoother == GMG_RBGS) {
+            for (int color = 0; color < 2; ++color)
+                timed(h, K_RB_HALF, l, L.n, false,
+                      [&] { fp64::rb_half(d, L.n, L.u[cur], L.q, color, h->stream); });
+        } else {
+            timed(h, K_WJ, l, L.n, false, [&] {
+                fp64::wj_sweep(d, L.n, L.u[cur], L.u[cur ^ 1], L.q, h->cfg.omega, h->stream);
+            });
+            cur ^= 1;
+        }
+    }
+}
+
+// One cycle of Algorithm 1 followed by the level-0 residual norm, in
+// stream order (captured into the graph).
+gmg_status enqueue_cycle(gmg_handle h) {
+    const gmg_config& c = h->cfg;
+    const int d = c.d;
+    const int L = num_levels(c);
+    std::vector<int> cur(L, 0);
+    h->timed.clear();
+    h->graph_kernels = 0;
+    if (L == 1) {
+        relax(h, 0, c.nu1, cur[0]);
+    } else {
+        for (int l = 0; l + 1 < L; ++l) {
+            relax(h, l, c.nu1, cur[l]);
+            Level& F = h->lv[l];
+            Level& C = h->lv[l + 1];
+            // After a black half sweep the black residual vanishes identically.
+            const bool red_only = c.smoother == GMG_RBGS && c.nu1 > 0;
+            timed(h, K_RESIDUAL, l, F.n, red_only, [&] {
+                fp64::residual(d, F.n, F.u[cur[l]], F.q, F.r, red_only, h->stream);
+            });
+            const bool exact = C.n == 2;
+            timed(h, K_RESTRICT, l, F.n, red_only, [&] {
+                fp64::restrict_fw(d, F.n, F.r, C.q, C.u[0], red_only, exact, h->stream);
+            });
+            cur[l + 1] = 0;
+        }
+        Level& B = h->lv[L - 1];
+        if (B.n > 2) {
+            for (int s = 0; s < c.coarse_sweeps; ++s)
+                for (int color = 0; color < 2; ++color)
+                    timed(h, K_RB_HALF, L - 1, B.n, false,
+                          [&] { fp64::rb_half(d, B.n, B.u[0], B.q, color, h->stream); });
+        }
+        for (int l = L - 2; l >= 0; --l) {
+            Level& F = h->lv[l];
+            Level& C = h->lv[l + 1];
+            timed(h, K_PROLONG, l, F.n, false,
+                  [&] { fp64::prolong_add(d, C.n, C.u[cur[l + 1]], F.u[cur[l]], h->stream); });
+            relax(h, l, c.nu2, cur[l]);
+        }
+    }
+    if (cur[0] != 0) {
+        cudaError_t e = cudaSuccess;
+        timed(h, K_COPY, 0, c.n, false, [&] {
+            e = cudaMemcpyAsync(h->lv[0].u[0], h->lv[0].u[1], sizeof(double) * h->lv[0].nodes,
+                                cudaMemcpyDeviceToDevice, h->stream);
+        });
+        GMG_CUDA_TRY(e);
+    }
+    timed(h, K_RESNORM, 0, c.n, false, [&] {
+        fp64::resnorm(d, c.n, h->lv[0].u[0], h->lv[0].q, h->partial, h->d_res2, h->stream);
+    });
+    h->graph_kernels++;  // resnorm is two kernels (partials, then their sum)
+    GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    GMG_CUDA_TRY(cudaGetLastError());
+    return GMG_OK;
+}
+
+gmg_status ensure_graph(gmg_handle h, double* u) {
+    if (h->graph && h->graph_u == u) return GMG_OK;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->lv[0].u[0] = u;
+    cudaGraph_t g = nullptr;
+    GMG_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    gmg_status st = enqueue_cycle(h);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (st != GMG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        return GMG_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        return GMG_ERR_CUDA;
+    }
+    h->graph_u = u;
+    return GMG_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Prepare q_0 and u's boundary, then the initial residual norm^2.
+gmg_status start(gmg_handle h, const double* f, double* u, double* res0) {
+    GMG_CUDA_TRY(cudaEventRecord(h->ev, h->user_stream));
+    GMG_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev, 0));
+    const gmg_config& c = h->cfg;
+    fp64::prepare(c.d, c.n, f, h->lv[0].q, u, h->stream);
+    fp64::resnorm(c.d, c.n, u, h->lv[0].q, h->partial, h->d_res2, h->stream);
+    h->launches += 3;
+    GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *res0 = std::sqrt(*h->h_res2);
+    if (!std::isfinite(*res0)) {
+        set_error("initial residual norm is not finite (NaN/Inf in f or u)");
+        return GMG_ERR_NONFINITE;
+    }
+    return ensure_graph(h, u);
+}
+
+// Run cycles: until the stopping test (stop = true) or exactly ncycles.
+gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycles, bool stop,
+               int* iters_out, double* relres_out) {
+    gmg_status st = check_device_ptr(f, "f");
+    if (st != GMG_OK) return st;
+    st = check_device_ptr(u, "u");
+    if (st != GMG_OK) return st;
+    DeviceGuard guard(h->device);
+    h->hist.clear();
+    double res0 = 0.0;
+    st = start(h, f, u, &res0);
+    if (st != GMG_OK) return st;
+    double res = res0;
+    int it = 0;
+    const int cap = stop ? h->cfg.maxit : ncycles;
+    while (it < cap && (!stop || res > rtol * res0)) {
+        GMG_CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
+        GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        h->launches += h->graph_kernels;
+        if (h->timing) collect_timing(h);
+        res = std::sqrt(*h->h_res2);
+        ++it;
+        const double rel = res0 > 0.0 ? res / res0 : 0.0;
+        h->hist.push_back(rel);
+        if (!stop && relres_out) relres_out[it - 1] = rel;
+        if (!std::isfinite(res)) {
+            set_error("residual norm became non-finite");
+            if (iters_out) *iters_out = it;
+            return GMG_ERR_NONFINITE;
+        }
+    }
+    if (iters_out) *iters_out = it;
+    if (stop && relres_out) *relres_out = res0 > 0.0 ? res / res0 : 0.0;
+    if (stop && res > rtol * res0) {
+        set_error("maxit reached before the relative residual fell below rtol");
+        return GMG_ERR_NOT_CONVERGED;
+    }
+    return GMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gmg_abi_version(void) { return GMG_ABI_VERSION; }
+
+const char* gmg_last_error(void) { return gmg::last_error().c_str(); }
+
+gmg_status gmg_config_init(gmg_config* cfg, int d, int n) {
+    if (!cfg) {
+        set_error("config is NULL");
+        return GMG_ERR_ARG;
+    }
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->d = d;
+    cfg->n = n;
+    cfg->levels = 0;
+    cfg->smoother = GMG_RBGS;
+    cfg->omega = 0.8;
+    cfg->nu1 = 2;
+    cfg->nu2 = 2;
+    cfg->cycle = GMG_VCYCLE;
+    cfg->precision = GMG_FP64;
+    cfg->maxit = 100;
+    cfg->inner_cycles = 4;
+    cfg->coarse_sweeps = 64;
+    return GMG_OK;
+}
+
+gmg_status gmg_destroy(gmg_handle h) {
+    if (!h) return GMG_OK;
+    DeviceGuard guard(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->h_res2) cudaFreeHost(h->h_res2);
+    if (h->ev) cudaEventDestroy(h->ev);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return GMG_OK;
+}
+
+gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out) {
+    if (!out) {
+        set_error("out is NULL");
+        return GMG_ERR_ARG;
+    }
+    *out = nullptr;
+    gmg_status st = check_cfg(cfg);
+    if (st != GMG_OK) return st;
+    gmg_handle h = new gmg_handle_s();
+    h->cfg = *cfg;
+    h->user_stream = (cudaStream_t)cuda_stream;
+    auto fail = [&](gmg_status s) {
+        gmg_destroy(h);
+        return s;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        set_error("no CUDA device");
+        delete h;
+        return GMG_ERR_CUDA;
+    }
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess) {
+        set_error("stream/event creation failed");
+        return fail(GMG_ERR_CUDA);
+    }
+    const int d = cfg->d;
+    const int L = num_levels(*cfg);
+    h->lv.resize(L);
+    for (int l = 0; l < L; ++l) {
+        Level& v = h->lv[l];
+        v.n = cfg->n >> l;
+        v.nodes = nodes_of(d, v.n);
+        if (l > 0) {
+            if ((st = dev_alloc(h, &v.u[0], v.nodes)) != GMG_OK) return fail(st);
+            if (cfg->smoother == GMG_WJACOBI && (st = dev_alloc(h, &v.u[1], v.nodes)) != GMG_OK)
+                return fail(st);
+        } else if (cfg->smoother == GMG_WJACOBI) {
+            if ((st = dev_alloc(h, &v.u[1], v.nodes)) != GMG_OK) return fail(st);
+        }
+        if ((st = dev_alloc(h, &v.q, v.nodes)) != GMG_OK) return fail(st);
+        if (l + 1 < L && (st = dev_alloc(h, &v.r, v.nodes)) != GMG_OK) return fail(st);
+    }
+    if ((st = dev_alloc(h, &h->partial, fp64::resnorm_partials(d, cfg->n))) != GMG_OK)
+        return fail(st);
+    if ((st = dev_alloc(h, &h->d_res2, 1)) != GMG_OK) return fail(st);
+    if (cudaMallocHost((void**)&h->h_res2, sizeof(double)) != cudaSuccess) {
+        set_error("cudaMallocHost failed");
+        return fail(GMG_ERR_ALLOC);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        set_error("initialisation failed");
+        return fail(GMG_ERR_CUDA);
+    }
+    *out = h;
+    return GMG_OK;
+}
+
+gmg_status gmg_solve(gmg_handle h, const double* f, double* u, double rtol, int* iters_out,
+                     double* relres_out) {
+    if (!h) {
+        set_error("handle is NULL");
+        return GMG_ERR_ARG;
+    }
+    if (!(rtol >= 0.0) || !std::isfinite(rtol)) {
+        set_error("rtol must be finite and >= 0");
+        return GMG_ERR_ARG;
+    }
+    return run(h, f, u, rtol, 0, true, iters_out, relres_out);
+}
+
+gmg_status gmg_cycles(gmg_handle h, const double* f, double* u, int ncycles, double* relres_out) {
+    if (!h) {
+        set_error("handle is NULL");
+        return GMG_ERR_ARG;
+    }
+    if (ncycles < 0) {
+        set_error("ncycles must be >= 0");
+        return GMG_ERR_ARG;
+    }
+    return run(h, f, u, 0.0, ncycles, false, nullptr, relres_out);
+}
+
+gmg_status gmg_solve_host(gmg_handle h, const double* f_host, double* u_host, double rtol,
+                          int* iters_out, double* relres_out) {
+    if (!h) {
+        set_error("handle is NULL");
+        return GMG_ERR_ARG;
+    }
+    if (!f_host || !u_host) {
+        set_error("f_host / u_host is NULL");
+        return GMG_ERR_LAYOUT;
+    }
+    DeviceGuard guard(h->device);
+    const int64_t m = h->lv[0].nodes;
+    gmg_status st;
+    if (!h->f_stage) {
+        if ((st = dev_alloc(h, &h->f_stage, m)) != GMG_OK) return st;
+        if ((st = dev_alloc(h, &h->u_stage, m)) != GMG_OK) return st;
+    }
+    GMG_CUDA_TRY(cudaEventRecord(h->ev, h->user_stream));
+    GMG_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev, 0));
+    GMG_CUDA_TRY(cudaMemcpyAsync(h->f_stage, f_host, sizeof(double) * m, cudaMemcpyHostToDevice,
+                                 h->stream));
+    GMG_CUDA_TRY(cudaMemcpyAsync(h->u_stage, u_host, sizeof(double) * m, cudaMemcpyHostToDevice,
+                                 h->stream));
+    st = run(h, h->f_stage, h->u_stage, rtol, 0, true, iters_out, relres_out);
+    if (st != GMG_OK && st != GMG_ERR_NOT_CONVERGED) return st;
+    GMG_CUDA_TRY(cudaMemcpyAsync(u_host, h->u_stage, sizeof(double) * m, cudaMemcpyDeviceToHost,
+                                 h->stream));
+    GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return st;
+}
+
+gmg_status gmg_set_timing(gmg_handle h, int enable) {
+    if (!h) {
+        set_error("handle is NULL");
+        return GMG_ERR_ARG;
+    }
+    if ((enable != 0) != h->timing) {
+        DeviceGuard guard(h->device);
+        h->timing = enable != 0;
+        if (h->graph) {
+            GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+            h->graph_u = nullptr;
+        }
+    }
+    return GMG_OK;
+}
+
+gmg_status gmg_timing_reset(gmg_handle h) {
+    if (!h) {
+        set_error("handle is NULL");
+        return GMG_ERR_ARG;
+    }
+    h->stats.clear();
+    h->launches = 0;
+    return GMG_OK;
+}
+
+gmg_status gmg_timing_report(gmg_handle h, gmg_kernel_stat* out, int cap, int* count,
+                             int64_t* launches_out) {
+    if (!h || (!out && cap > 0)) {
+        set_error("bad arguments");
+        return GMG_ERR_ARG;
+    }
+    int i = 0;
+    for (auto& kv : h->stats) {
+        if (i < cap) {
+            gmg_kernel_stat& s = out[i];
+            std::memset(&s, 0, sizeof(s));
+            std::snprintf(s.kernel, sizeof(s.kernel), "%s", kKindName[kv.first.first]);
+            s.level = kv.first.second;
+            s.launches = kv.second.launches;
+            s.ms = kv.second.ms;
+            s.dp_ops = kv.second.ops;
+            s.bytes = kv.second.bytes;
+        }
+        ++i;
+    }
+    if (count) *count = i;
+    if (launches_out) *launches_out = h->launches;
+    return GMG_OK;
+}
+
+gmg_status gmg_history(gmg_handle h, double* relres, int cap, int* count) {
+    if (!h || (!relres && cap > 0)) {
+        set_error("bad arguments");
+        return GMG_ERR_ARG;
+    }
+    const int m = (int)h->hist.size();
+    for (int i = 0; i < m && i < cap; ++i) relres[i] = h->hist[i];
+    if (count) *count = m;
+    return GMG_OK;
+}
+
+}  // extern "C"

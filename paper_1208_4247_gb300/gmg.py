@@ -1,0 +1,212 @@
+"""Thin ctypes binding of ``libgmg.so`` (include/gmg.h).
+
+Argument marshalling only: every step of the solve runs in the library's
+CUDA kernels.  Tensors are torch float64 CUDA tensors of shape (n+1,)*d
+(all grid nodes, x fastest); the calls are ordered on torch's current
+stream.  There is no CPU fallback: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libgmg.so")
+
+OK = 0
+ERR_NOT_CONVERGED = 6
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_LAYOUT", 3: "ERR_ALLOC", 4: "ERR_CUDA",
+          5: "ERR_NONFINITE", 6: "ERR_NOT_CONVERGED", 7: "ERR_DEVICE_TIMEOUT",
+          8: "ERR_UNSUPPORTED"}
+SMOOTHERS = {"wjacobi": 0, "rbgs": 1, "learned": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+
+
+class GMGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int), ("levels", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("omega", ctypes.c_double),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("cycle", ctypes.c_int),
+                ("precision", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("inner_cycles", ctypes.c_int), ("coarse_sweeps", ctypes.c_int)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_char * 24), ("level", ctypes.c_int),
+                ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("dp_ops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.c_void_p
+I = ctypes.c_int
+D = ctypes.c_double
+PI = ctypes.POINTER(ctypes.c_int)
+PD = ctypes.POINTER(ctypes.c_double)
+
+# name -> (argtypes, restype); every symbol include/gmg.h declares.
+SIGNATURES = {
+    "gmg_abi_version": ([], I),
+    "gmg_last_error": ([], ctypes.c_char_p),
+    "gmg_config_init": ([ctypes.POINTER(Config), I, I], I),
+    "gmg_create": ([ctypes.POINTER(Config), P, ctypes.POINTER(P)], I),
+    "gmg_solve": ([P, P, P, D, PI, PD], I),
+    "gmg_solve_host": ([P, P, P, D, PI, PD], I),
+    "gmg_cycles": ([P, P, P, I, PD], I),
+    "gmg_history": ([P, PD, I, PI], I),
+    "gmg_destroy": ([P], I),
+    "gmg_set_timing": ([P, I], I),
+    "gmg_timing_report": ([P, ctypes.POINTER(KernelStat), I, PI,
+                           ctypes.POINTER(ctypes.c_int64)], I),
+    "gmg_timing_reset": ([P], I),
+}
+
+
+def lib():
+    """Load libgmg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "paper_1208_4247_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(status: int, allow=()):
+    if status != OK and status not in allow:
+        raise GMGError(status, lib().gmg_last_error().decode())
+    return status
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, name, d, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if tuple(t.shape) != (n + 1,) * d or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with shape {(n + 1,) * d}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """GMG solver handle (gmg_create / gmg_solve / gmg_destroy)."""
+
+    def __init__(self, d: int, n: int, levels: int = 0, smoother: str = "rbgs",
+                 omega: float = 0.8, nu1: int = 2, nu2: int = 2, precision: str = "fp64",
+                 maxit: int = 100, inner_cycles: int = 4, coarse_sweeps: int = 64,
+                 stream=None):
+        self.d, self.n = d, n
+        cfg = Config()
+        _check(lib().gmg_config_init(ctypes.byref(cfg), d, n))
+        cfg.levels = levels
+        cfg.smoother = SMOOTHERS[smoother]
+        cfg.omega = omega
+        cfg.nu1, cfg.nu2 = nu1, nu2
+        cfg.precision = PRECISIONS[precision]
+        cfg.maxit = maxit
+        cfg.inner_cycles = inner_cycles
+        cfg.coarse_sweeps = coarse_sweeps
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        _check(lib().gmg_create(ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def solve(self, f, u, rtol: float = 1e-10):
+        """Returns (cycles, final relative residual, converged)."""
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = _check(lib().gmg_solve(self._h, _dptr(f, "f", self.d, self.n),
+                                    _dptr(u, "u", self.d, self.n), rtol, ctypes.byref(it),
+                                    ctypes.byref(rel)), allow=(ERR_NOT_CONVERGED,))
+        return it.value, rel.value, st == OK
+
+    def solve_host(self, f, u, rtol: float = 1e-10):
+        """f, u: C-contiguous float64 numpy arrays (pinned or pageable host
+        memory); u is overwritten with the solution."""
+        import numpy as np
+        for name, a in (("f", f), ("u", u)):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64
+                    and a.flags["C_CONTIGUOUS"] and a.shape == (self.n + 1,) * self.d):
+                raise ValueError(f"{name} must be a C-contiguous float64 array of shape "
+                                 f"{(self.n + 1,) * self.d}")
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = _check(lib().gmg_solve_host(self._h, ctypes.c_void_p(f.ctypes.data),
+                                         ctypes.c_void_p(u.ctypes.data), rtol,
+                                         ctypes.byref(it), ctypes.byref(rel)),
+                    allow=(ERR_NOT_CONVERGED,))
+        return it.value, rel.value, st == OK
+
+    def cycles(self, f, u, ncycles: int):
+        """Exactly ncycles cycles; returns the relative residual after each."""
+        out = (ctypes.c_double * max(ncycles, 1))()
+        _check(lib().gmg_cycles(self._h, _dptr(f, "f", self.d, self.n),
+                                _dptr(u, "u", self.d, self.n), ncycles, out))
+        return list(out)[:ncycles]
+
+    def history(self):
+        cnt = ctypes.c_int(0)
+        _check(lib().gmg_history(self._h, None, 0, ctypes.byref(cnt)))
+        buf = (ctypes.c_double * max(cnt.value, 1))()
+        _check(lib().gmg_history(self._h, buf, cnt.value, ctypes.byref(cnt)))
+        return list(buf)[:cnt.value]
+
+    def set_timing(self, enable: bool = True):
+        _check(lib().gmg_set_timing(self._h, 1 if enable else 0))
+
+    def timing_reset(self):
+        _check(lib().gmg_timing_reset(self._h))
+
+    def timing_report(self):
+        """Returns (list of per-(kernel, level) dicts, total kernel launches)."""
+        return timing_report(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def timing_report(handle):
+    cnt = ctypes.c_int(0)
+    tot = ctypes.c_int64(0)
+    _check(lib().gmg_timing_report(handle, None, 0, ctypes.byref(cnt), ctypes.byref(tot)))
+    buf = (KernelStat * max(cnt.value, 1))()
+    _check(lib().gmg_timing_report(handle, buf, cnt.value, ctypes.byref(cnt), ctypes.byref(tot)))
+    rows = [dict(kernel=s.kernel.decode(), level=s.level, launches=s.launches, ms=s.ms,
+                 dp_ops=s.dp_ops, bytes=s.bytes) for s in list(buf)[:cnt.value]]
+    return rows, tot.value

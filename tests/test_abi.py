@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and
+loads, exports every symbol include/gmg.h declares, and rejects bad
+configurations before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1208_4247_gb300 import build, gmg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return gmg.lib()
+
+
+def declared_symbols():
+    syms = set()
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if name.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", name)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            syms |= set(re.findall(r"\b(gmg_[a-z0-9_]+)\s*\(", text))
+    return syms
+
+
+def test_every_declared_symbol_is_exported(L):
+    syms = declared_symbols()
+    assert "gmg_solve" in syms and "gmg_create" in syms and "gmg_destroy" in syms
+    for s in sorted(syms):
+        assert hasattr(L, s), s
+    # the binding knows every declared symbol's signature
+    assert syms <= set(gmg.SIGNATURES)
+
+
+def test_abi_version(L):
+    assert L.gmg_abi_version() == 1
+
+
+def test_config_defaults(L):
+    c = gmg.Config()
+    assert L.gmg_config_init(ctypes.byref(c), 3, 256) == 0
+    assert (c.d, c.n, c.levels, c.smoother, c.nu1, c.nu2, c.precision, c.maxit) == \
+        (3, 256, 0, 1, 2, 2, 0, 100)
+    assert c.omega == pytest.approx(0.8)
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("d", 4, 1), ("n", 100, 1), ("n", 1, 1), ("levels", 9, 1), ("smoother", 7, 1),
+    ("smoother", 2, 8), ("omega", 2.5, 1), ("nu1", -1, 1), ("nu2", 17, 1), ("cycle", 1, 1),
+    ("maxit", -3, 1), ("precision", 9, 8),
+])
+def test_bad_config_rejected_before_device_use(L, field, value, status):
+    c = gmg.Config()
+    L.gmg_config_init(ctypes.byref(c), 3, 256)
+    setattr(c, field, value)
+    h = ctypes.c_void_p()
+    assert L.gmg_create(ctypes.byref(c), None, ctypes.byref(h)) == status
+    assert not h.value
+    assert len(L.gmg_last_error()) > 0
+
+
+def test_null_arguments(L):
+    assert L.gmg_create(None, None, None) == 1
+    assert L.gmg_solve(None, None, None, 1e-10, None, None) == 1
+    assert L.gmg_destroy(None) == 0
+    assert L.gmg_config_init(None, 3, 8) == 1
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(gmg, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(gmg, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        gmg.lib()

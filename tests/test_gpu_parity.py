@@ -1,0 +1,225 @@
+"""Parity of the plain FP64 CUDA path with the CPU FP64 oracle.
+
+Per cycle: from an identical iterate, one V-cycle on the GPU and in the oracle
+must agree to ||u_gpu - u_orc|| / ||u_orc|| <= 1e-12 (Euclidean over all
+nodes).  Per solve: identical cycle count to the relative residual 1e-10 and
+matching residual histories.  All calls go through the C ABI.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_4247_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_CYCLE = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1208_4247_gb300 import build
+    build.build()
+    return torch
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def _orc_smoother(name):
+    return oracle.RBGS if name == "rbgs" else oracle.WJACOBI
+
+
+CYCLE_CASES = [
+    # d, n, levels, smoother, omega, nu1, nu2
+    (2, 4, 0, "rbgs", 0.8, 2, 2),
+    (2, 16, 0, "rbgs", 0.8, 2, 2),
+    (2, 64, 0, "wjacobi", 0.8, 2, 2),
+    (2, 256, 0, "wjacobi", 0.8, 2, 2),
+    (2, 256, 0, "rbgs", 0.8, 1, 1),
+    (2, 128, 3, "rbgs", 0.8, 2, 2),
+    (2, 32, 0, "wjacobi", 0.8, 1, 2),
+    (2, 32, 0, "rbgs", 0.8, 0, 2),
+    (2, 32, 0, "rbgs", 0.8, 3, 0),
+    (3, 4, 0, "rbgs", 0.8, 2, 2),
+    (3, 8, 0, "wjacobi", 6 / 7, 1, 1),
+    (3, 32, 0, "rbgs", 0.8, 2, 2),
+    (3, 64, 0, "rbgs", 0.8, 2, 2),
+    (3, 64, 0, "wjacobi", 6 / 7, 2, 2),
+    (3, 64, 2, "rbgs", 0.8, 2, 2),
+    (3, 64, 4, "wjacobi", 0.8, 1, 1),
+    (3, 32, 1, "rbgs", 0.8, 2, 2),
+    (3, 16, 0, "rbgs", 0.8, 0, 1),
+    (3, 128, 0, "rbgs", 0.8, 2, 2),
+]
+
+
+@pytest.mark.parametrize("case", CYCLE_CASES, ids=lambda c: "-".join(map(str, c)))
+def test_cycle_parity(torch_cuda, case):
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n, levels, sm, om, nu1, nu2 = case
+    cs = 8
+    rng = np.random.default_rng(11)
+    f = inputs.rhs_uniform(d, n, 7)
+    u = np.zeros_like(f)
+    u[(slice(1, -1),) * d] = rng.standard_normal((n - 1,) * d)
+    cfg = oracle.make_cfg(d, n, levels, _orc_smoother(sm), om, nu1, nu2, cs)
+    b = oracle.scale_rhs(f)
+    fd = _dev(torch, f)
+    with Solver(d, n, levels=levels, smoother=sm, omega=om, nu1=nu1, nu2=nu2,
+                coarse_sweeps=cs) as S:
+        for c in range(3):
+            ud = _dev(torch, u)
+            rel_gpu = S.cycles(fd, ud, 1)[0]
+            ug = ud.cpu().numpy()
+            uo = u.copy()
+            oracle.vcycle(cfg, b, uo)
+            assert _rel(ug, uo) <= TOL_CYCLE, (c, _rel(ug, uo))
+            rel_orc = oracle.norm2(oracle.residual(b, uo)) / oracle.norm2(oracle.residual(b, u))
+            assert rel_gpu == pytest.approx(rel_orc, rel=1e-6, abs=1e-300)
+            u = ug
+
+
+SOLVE_CASES = [
+    # the 2D 257^2 workload: WJ(4/5) V(2,2), sine + 1e-3 uniform noise
+    (2, 256, "wjacobi", 0.8, 2, 2, "sine_uniform"),
+    (2, 256, "rbgs", 0.8, 2, 2, "uniform"),
+    (3, 64, "rbgs", 0.8, 2, 2, "uniform"),
+    (3, 64, "wjacobi", 6 / 7, 1, 1, "uniform"),
+    (3, 128, "rbgs", 0.8, 1, 1, "uniform"),
+]
+
+
+def _rhs(kind, d, n):
+    if kind == "sine_uniform":
+        return inputs.rhs_sine_plus_uniform(d, n, 1)
+    return inputs.rhs_uniform(d, n, 2)
+
+
+@pytest.mark.parametrize("case", SOLVE_CASES, ids=lambda c: "-".join(map(str, c)))
+def test_solve_parity(torch_cuda, case):
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n, sm, om, nu1, nu2, kind = case
+    f = _rhs(kind, d, n)
+    uo = np.zeros_like(f)
+    cfg = oracle.make_cfg(d, n, 0, _orc_smoother(sm), om, nu1, nu2, 1)
+    it_o, hist_o = oracle.solve(cfg, f, uo, rtol=1e-10, maxit=100)
+    fd = _dev(torch, f)
+    ud = torch.zeros_like(fd)
+    with Solver(d, n, smoother=sm, omega=om, nu1=nu1, nu2=nu2) as S:
+        it_g, rel_g, conv = S.solve(fd, ud, rtol=1e-10)
+        hist_g = np.array(S.history())
+    assert conv and it_g == it_o
+    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-6)
+    ug = ud.cpu().numpy()
+    assert _rel(ug, uo) <= 1e-10
+    # the FP64 residual of the GPU result, computed by the oracle
+    b = oracle.scale_rhs(f)
+    assert oracle.norm2(oracle.residual(b, ug)) / oracle.norm2(b) <= 1e-10
+
+
+def test_full_size_3d_257_rbgs(torch_cuda):
+    """The 3D 257^3 workload (U[-1,1] f, seed 2, RB-GS V(2,2)) at full size:
+    identical cycle count and history, solution within 1e-10 of the oracle's."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 256
+    f = inputs.rhs_uniform(d, n, 2)
+    uo = np.zeros_like(f)
+    it_o, hist_o = oracle.solve(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1), f, uo,
+                                rtol=1e-10, maxit=100)
+    fd = _dev(torch, f)
+    ud = torch.zeros_like(fd)
+    with Solver(d, n) as S:
+        it_g, rel_g, conv = S.solve(fd, ud, rtol=1e-10)
+        hist_g = np.array(S.history())
+    assert conv and it_g == it_o
+    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-6)
+    assert _rel(ud.cpu().numpy(), uo) <= 1e-10
+
+
+def test_solve_host_matches_device(torch_cuda):
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 64
+    f = inputs.rhs_uniform(d, n, 3)
+    uh = np.zeros_like(f)
+    fd = _dev(torch, f)
+    ud = torch.zeros_like(fd)
+    with Solver(d, n) as S:
+        it1, r1, c1 = S.solve(fd, ud)
+        it2, r2, c2 = S.solve_host(f, uh)
+    assert it1 == it2 and c1 and c2
+    assert np.array_equal(ud.cpu().numpy(), uh)
+
+
+def test_zero_rhs_takes_no_cycles(torch_cuda):
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    fd = torch.zeros((17,) * 3, dtype=torch.float64, device="cuda")
+    ud = torch.zeros_like(fd)
+    with Solver(3, 16) as S:
+        it, rel, conv = S.solve(fd, ud)
+    assert it == 0 and conv and rel == 0.0
+
+
+def test_nonfinite_rhs_reported(torch_cuda):
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import GMGError, Solver
+    f = inputs.rhs_uniform(3, 16, 1)
+    f[5, 5, 5] = np.nan
+    fd = _dev(torch, f)
+    ud = torch.zeros_like(fd)
+    with Solver(3, 16) as S:
+        with pytest.raises(GMGError, match="NONFINITE"):
+            S.solve(fd, ud)
+
+
+def test_maxit_reports_not_converged(torch_cuda):
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    fd = _dev(torch, inputs.rhs_uniform(3, 32, 1))
+    ud = torch.zeros_like(fd)
+    with Solver(3, 32, maxit=2) as S:
+        it, rel, conv = S.solve(fd, ud, rtol=1e-10)
+    assert it == 2 and not conv and rel > 1e-10
+
+
+def test_host_pointer_rejected(torch_cuda):
+    import ctypes
+    from paper_1208_4247_gb300 import gmg
+    torch = torch_cuda
+    f = np.zeros((17,) * 3)
+    with gmg.Solver(3, 16) as S:
+        st = gmg.lib().gmg_solve(S._h, ctypes.c_void_p(f.ctypes.data),
+                                 ctypes.c_void_p(f.ctypes.data), 1e-10, None, None)
+    assert st == 2  # GMG_ERR_LAYOUT
+
+
+def test_boundary_written_zero_and_f_boundary_ignored(torch_cuda):
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 2, 32
+    f = inputs.rhs_uniform(d, n, 5)
+    f2 = f.copy()
+    f2[0, :] = 1e3
+    f2[:, -1] = -7.0
+    u = np.full_like(f, 3.0)
+    u[1:-1, 1:-1] = 0.0
+    ua, ub = _dev(torch, u), _dev(torch, u)
+    with Solver(d, n) as S:
+        S.solve(_dev(torch, f), ua)
+        S.solve(_dev(torch, f2), ub)
+    a = ua.cpu().numpy()
+    assert np.array_equal(a, ub.cpu().numpy())
+    assert np.all(a[0, :] == 0) and np.all(a[-1, :] == 0) and np.all(a[:, 0] == 0)
