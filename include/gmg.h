@@ -104,6 +104,11 @@ gmg_status gmg_solve_host(gmg_handle h, const double* f_host, double* u_host, do
 gmg_status gmg_cycles(gmg_handle h, const double* f, double* u, int ncycles,
                       double* relres_out);
 
+/* FP64 residual norm ||h^2 f - A'u||_2 over the interior nodes (Algorithm 3's
+ * res), written to *norm_out (host).  Writes 0 to u's boundary nodes, as
+ * gmg_solve does.  f, u: device pointers.  Synchronises the handle's stream. */
+gmg_status gmg_residual_norm(gmg_handle h, const double* f, double* u, double* norm_out);
+
 /* Relative-residual history of the last solve / cycles call: writes up to
  * cap entries to relres (host), the count to *count. */
 gmg_status gmg_history(gmg_handle h, double* relres, int cap, int* count);

@@ -561,6 +561,29 @@ gmg_status gmg_solve_host(gmg_handle h, const double* f_host, double* u_host, do
     return st;
 }
 
+gmg_status gmg_residual_norm(gmg_handle h, const double* f, double* u, double* norm_out) {
+    if (!h || !norm_out) {
+        set_error("handle / norm_out is NULL");
+        return GMG_ERR_ARG;
+    }
+    gmg_status st = check_device_ptr(f, "f");
+    if (st != GMG_OK) return st;
+    if ((st = check_device_ptr(u, "u")) != GMG_OK) return st;
+    DeviceGuard guard(h->device);
+    GMG_CUDA_TRY(cudaEventRecord(h->ev, h->user_stream));
+    GMG_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev, 0));
+    const gmg_config& c = h->cfg;
+    fp64::prepare(c.d, c.n, f, h->lv[0].q, u, h->stream);
+    fp64::resnorm(c.d, c.n, u, h->lv[0].q, h->partial, h->d_res2, h->stream);
+    h->launches += 3;
+    GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    // sigma = (h^2 f - A'u) / (2d)
+    *norm_out = (2.0 * c.d) * std::sqrt(*h->h_res2);
+    return GMG_OK;
+}
+
 gmg_status gmg_set_timing(gmg_handle h, int enable) {
     if (!h) {
         set_error("handle is NULL");

@@ -63,6 +63,7 @@ SIGNATURES = {
     "gmg_solve_host": ([P, P, P, D, PI, PD], I),
     "gmg_cycles": ([P, P, P, I, PD], I),
     "gmg_history": ([P, PD, I, PI], I),
+    "gmg_residual_norm": ([P, P, P, PD], I),
     "gmg_destroy": ([P], I),
     "gmg_set_timing": ([P, I], I),
     "gmg_timing_report": ([P, ctypes.POINTER(KernelStat), I, PI,
@@ -165,6 +166,13 @@ class Solver:
         _check(lib().gmg_cycles(self._h, _dptr(f, "f", self.d, self.n),
                                 _dptr(u, "u", self.d, self.n), ncycles, out))
         return list(out)[:ncycles]
+
+    def residual_norm(self, f, u):
+        """||h^2 f - A'u||_2 in FP64 (writes 0 to u's boundary nodes)."""
+        out = ctypes.c_double(0.0)
+        _check(lib().gmg_residual_norm(self._h, _dptr(f, "f", self.d, self.n),
+                                       _dptr(u, "u", self.d, self.n), ctypes.byref(out)))
+        return out.value
 
     def history(self):
         cnt = ctypes.c_int(0)

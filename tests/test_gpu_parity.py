@@ -231,3 +231,17 @@ def test_boundary_written_zero_and_f_boundary_ignored(torch_cuda):
     a = ua.cpu().numpy()
     assert np.array_equal(a, ub.cpu().numpy())
     assert np.all(a[0, :] == 0) and np.all(a[-1, :] == 0) and np.all(a[:, 0] == 0)
+
+
+@pytest.mark.parametrize("d,n", [(2, 64), (3, 32), (3, 256)])
+def test_residual_norm_matches_oracle(torch_cuda, d, n):
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    f = inputs.rhs_uniform(d, n, 9)
+    rng = np.random.default_rng(4)
+    u = np.zeros_like(f)
+    u[(slice(1, -1),) * d] = 1e-3 * rng.standard_normal((n - 1,) * d)
+    ref = oracle.norm2(oracle.residual(oracle.scale_rhs(f), u))
+    with Solver(d, n) as S:
+        got = S.residual_norm(_dev(torch, f), _dev(torch, u))
+    assert got == pytest.approx(ref, rel=1e-12)
