@@ -109,6 +109,26 @@ gmg_status gmg_cycles(gmg_handle h, const double* f, double* u, int ncycles,
  * gmg_solve does.  f, u: device pointers.  Synchronises the handle's stream. */
 gmg_status gmg_residual_norm(gmg_handle h, const double* f, double* u, double* norm_out);
 
+/* Allocation-free variant of gmg_residual_norm (the paper has no counterpart;
+ * this is a library service).  For callers that cannot allocate device memory
+ * when they need the residual -- e.g. code running inside a device-allocator
+ * or memory-pool callback, or a real-time loop where cudaMalloc/cudaFree
+ * (which may synchronise the device) are forbidden -- and so cannot create a
+ * gmg_handle.  No handle: d, n as in gmg_config; f, u: device pointers in the
+ * layout above (u is read only, its boundary nodes are taken as 0);
+ * norm_dev: device pointer to one double that receives ||h^2 f - A'u||_2.
+ * Stream-ordered on cuda_stream (a cudaStream_t, NULL = legacy default
+ * stream); no host synchronisation, no allocation of any kind.
+ * Scratch: a fixed 512 KiB static device array (65536 partial sums) that each
+ * GPU loading the library holds until exit; grids needing more partial sums
+ * than that (3D n > 256) are rejected with GMG_ERR_ARG.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it: make that first call before any stream capture.  All calls
+ * share the array, so calls that overlap on the GPU race and must be
+ * serialised by the caller. */
+gmg_status gmg_residual_norm_noalloc(int d, int n, const double* f, const double* u,
+                                     double* norm_dev, void* cuda_stream);
+
 /* Relative-residual history of the last solve / cycles call: writes up to
  * cap entries to relres (host), the count to *count. */
 gmg_status gmg_history(gmg_handle h, double* relres, int cap, int* count);

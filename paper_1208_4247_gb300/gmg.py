@@ -64,6 +64,7 @@ SIGNATURES = {
     "gmg_cycles": ([P, P, P, I, PD], I),
     "gmg_history": ([P, PD, I, PI], I),
     "gmg_residual_norm": ([P, P, P, PD], I),
+    "gmg_residual_norm_noalloc": ([I, I, P, P, P, P], I),
     "gmg_destroy": ([P], I),
     "gmg_set_timing": ([P, I], I),
     "gmg_timing_report": ([P, ctypes.POINTER(KernelStat), I, PI,
