@@ -69,7 +69,10 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.monotonic(), [x.strip() for x in line.split(",")]))
+
+    def mark(self, name):
+        setattr(self, name, time.monotonic())
 
     def __exit__(self, *a):
         if self.proc:
@@ -80,9 +83,13 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        """Samples taken between mark("t0") and mark("t1") (the timed region)."""
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        t0, t1 = getattr(self, "t0", 0.0), getattr(self, "t1", float("inf"))
+        for ts, r in self.rows:
+            if not (t0 <= ts <= t1 + 0.15):
+                continue
             try:
                 sm.append(float(r[1]))
                 mx = float(r[2])
@@ -95,6 +102,80 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def dominant(stats):
+    """Kernel with the largest summed device time; its level-0 record."""
+    by_kernel = {}
+    for s in stats:
+        by_kernel.setdefault(s["kernel"], []).append(s)
+    tot_ms = {k: sum(r["ms"] for r in v) for k, v in by_kernel.items()}
+    dom = max(tot_ms, key=tot_ms.get)
+    recs = sorted(by_kernel[dom], key=lambda r: r["level"])
+    return dom, recs[0], tot_ms[dom] / sum(tot_ms.values())
+
+
+def time_solves(torch, S, f, u, steps, warmup, timing=True):
+    """Warm-up, then `steps` solves from u = 0 bracketed by CUDA events on
+    torch's stream (each solve ends with the library's stream drained)."""
+    S.set_timing(timing)
+    it = rel = None
+    for _ in range(warmup):
+        u.zero_()
+        it, rel, conv = S.solve(f, u, RTOL)
+        assert conv, "warm-up solve did not converge"
+    S.timing_reset()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        u.zero_()
+        it, rel, conv = S.solve(f, u, RTOL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stats, launches = S.timing_report()
+    return e0.elapsed_time(e1) / steps, it, rel, stats, launches
+
+
+def run_forms(torch, args):
+    """The 3D 513^3 workload (3 pi^2 prod sin + 0.01 N(0,1), seed 3), RB-GS
+    V(2,2): plain FP64 cycles vs FP32 and BF16-storage cycles inside FP64
+    iterative refinement, each to relative residual 1e-10."""
+    from paper_1208_4247_gb300 import inputs
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 512
+    dof = (n - 1) ** d
+    f = torch.from_numpy(inputs.rhs_sine_plus_gauss(d, n, 3)).cuda()
+    u = torch.zeros_like(f)
+    pk, _ = peaks()
+    out = {}
+    for name, prec, k in [("fp64_plain", "fp64", 0), ("fp32_ir", "fp32", 5),
+                          ("bf16_ir", "bf16", 2)]:
+        S = Solver(d, n, precision=prec, inner_cycles=max(k, 1))
+        ms, it, rel, stats, launches = time_solves(torch, S, f, u, args.form_steps, 1)
+        S.close()
+        dom, rec, share = dominant(stats)
+        avg_s = rec["ms"] / rec["launches"] * 1e-3
+        alg = sum(r["bytes"] * r["launches"] for r in stats) / args.form_steps
+        out[name] = {"value": dof / (ms * 1e-3), "unit": "DOF/s", "ms_per_step": ms,
+                     "steps": args.form_steps, "outer_steps" if k else "cycles": it,
+                     "inner_cycles_per_step": k or None, "relres": rel,
+                     "solve_alg_gbs": alg / (ms * 1e-3) / 1e9,
+                     "dominant_kernel": f"{dom} (level {rec['level']})",
+                     "dominant_share": share,
+                     "dominant_hbm_gbs": rec["bytes"] / avg_s / 1e9,
+                     "dominant_hbm_frac": rec["bytes"] / avg_s / 1e9 / pk["hbm_gbs"],
+                     "gpu_launches": launches}
+    base = out["fp64_plain"]["ms_per_step"]
+    for v in out.values():
+        v["speedup_vs_fp64_plain"] = base / v["ms_per_step"]
+    del f, u
+    torch.cuda.empty_cache()
+    return {"workload": "3D 513^3 (511^3 = 133.4M unknowns), f = 3 pi^2 prod sin + 0.01 N(0,1) "
+                        "seed 3, RB-GS V(2,2), FW, trilinear, to relative FP64 residual 1e-10",
+            "forms": out}
 
 
 def dist_env():
@@ -173,11 +254,6 @@ def run_ours(args, rank, ws, local):
     S = Solver(D, N)
     S.set_timing(True)
     cycles = None
-    for _ in range(args.warmup):
-        u.zero_()
-        cycles, rel, conv = S.solve(f, u, RTOL)
-        assert conv, "warm-up solve did not converge"
-    S.timing_reset()
 
     def barrier():
         if ws > 1:
@@ -188,13 +264,21 @@ def run_ours(args, rank, ws, local):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            u.zero_()
+            cycles, rel, conv = S.solve(f, u, RTOL)
+            assert conv, "warm-up solve did not converge"
+        S.timing_reset()
+        time.sleep(0.5)  # let the sampler start
         barrier()
+        clk.mark("t0")
         ev0.record(stream)
         for _ in range(args.steps):
             u.zero_()
             cycles, rel, conv = S.solve(f, u, RTOL)
         ev1.record(stream)
         barrier()
+        clk.mark("t1")
     ms_total = ev0.elapsed_time(ev1)
     stats, launches = S.timing_report()
     if ws > 1:
@@ -253,13 +337,21 @@ def run_ours(args, rank, ws, local):
 
     if rank != 0:
         return
+    forms = None
+    if not args.no_forms:
+        forms = run_forms(torch, args)
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        it_o, dt = oracle_solve_timed(f_np, None)
+        times = []
+        while sum(times) < args.cpu_seconds:
+            it_o, dt = oracle_solve_timed(f_np, None)
+            times.append(dt)
+        dt = sum(times) / len(times)
         cpu = {"value": UNKNOWNS / dt, "unit": "DOF/s", "cores": cores(), "kind": "oracle",
-               "sample": f"one full 257^3 solve to 1e-10 ({it_o} cycles, {dt:.1f} s, OpenMP)"}
+               "sample": f"{len(times)} full 257^3 solves to 1e-10 ({it_o} cycles, "
+                         f"{dt:.2f} s each, {sum(times):.1f} s total, OpenMP on all cores)"}
     line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -268,7 +360,7 @@ def run_ours(args, rank, ws, local):
                        "l2": "inputs larger than L2 (u, q, r: 3 x 136 MB at level 0)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks}
+            "gpu_launches": launches, "clocks": clocks, "mixed_precision_513": forms}
     if args.kernels:
         line["kernels"] = stats
     print(json.dumps(line), flush=True)
@@ -277,12 +369,15 @@ def run_ours(args, rank, ws, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels", action="store_true", help="add per-kernel records")
+    ap.add_argument("--no-forms", action="store_true", help="skip the 513^3 precision forms")
+    ap.add_argument("--form-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

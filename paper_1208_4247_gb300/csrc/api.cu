@@ -1,11 +1,14 @@
 // C ABI of the solver (include/gmg.h): handle lifetime, the V-cycle schedule
 // of Algorithm 1 captured once into a CUDA graph, and the stopping loop of
-// Algorithm 3 with every level on the device.
+// Algorithm 3 with every level on the device.  Two forms share the
+// schedule: plain FP64 cycles, and FP32 / BF16 cycles inside FP64 iterative
+// refinement.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -22,6 +25,7 @@ const std::string& last_error() { return g_err; }
 }  // namespace gmg
 
 using namespace gmg;
+using bf16 = __nv_bfloat16;
 
 struct gmg_handle_s {
     gmg_config cfg{};
@@ -29,8 +33,11 @@ struct gmg_handle_s {
     cudaStream_t user_stream = nullptr;
     cudaStream_t stream = nullptr;  // owned, non-blocking; ordered after user_stream per call
     cudaEvent_t ev = nullptr;
-    std::vector<Level> lv;
-    double* u0_tmp = nullptr;  // level-0 ping-pong buffer (weighted Jacobi)
+    // plain form: the whole FP64 hierarchy; refinement forms: level 0 only
+    // (u = the caller's iterate, q = FP64 scaled right-hand side)
+    std::vector<Level<double>> lv;
+    std::vector<Level<float>> lvf;  // FP32 inner hierarchy (GMG_FP32_IR)
+    std::vector<Level<bf16>> lvb;   // BF16 inner hierarchy (GMG_BF16_IR)
     double* partial = nullptr;
     double* d_res2 = nullptr;
     double* h_res2 = nullptr;  // pinned
@@ -41,11 +48,11 @@ struct gmg_handle_s {
     double* u_stage = nullptr;
     std::vector<void*> allocs;
     // launch accounting and optional per-kernel event timing
-    int64_t launches = 0;     // every kernel launch since the last reset
-    int graph_kernels = 0;    // kernels per launch of the cycle graph
+    int64_t launches = 0;   // every kernel launch since the last reset
+    int graph_kernels = 0;  // kernels per launch of the cycle graph
     bool timing = false;
     struct TimedLaunch {
-        int kind, level;
+        int kind, level, prec;
         double ops, bytes;
     };
     std::vector<TimedLaunch> timed;  // timed launches of one graph run, in order
@@ -54,7 +61,7 @@ struct gmg_handle_s {
         int64_t launches = 0;
         double ms = 0.0, ops = 0.0, bytes = 0.0;
     };
-    std::map<std::pair<int, int>, Stat> stats;
+    std::map<std::tuple<int, int, int>, Stat> stats;
 };
 
 namespace {
@@ -106,9 +113,13 @@ gmg_status check_cfg(const gmg_config* c) {
         set_error("cycle must be GMG_VCYCLE");
         return GMG_ERR_ARG;
     }
-    if (c->precision != GMG_FP64) {
-        set_error("precision: only GMG_FP64 is built into gmg_create");
+    if (c->precision != GMG_FP64 && c->precision != GMG_FP32_IR && c->precision != GMG_BF16_IR) {
+        set_error("unknown precision");
         return GMG_ERR_UNSUPPORTED;
+    }
+    if (c->precision != GMG_FP64 && (c->inner_cycles < 1 || c->inner_cycles > 64)) {
+        set_error("inner_cycles must lie in 1..64");
+        return GMG_ERR_ARG;
     }
     if (c->maxit < 0 || c->maxit > 100000) {
         set_error("maxit must lie in 0..100000");
@@ -121,14 +132,16 @@ gmg_status check_cfg(const gmg_config* c) {
     return GMG_OK;
 }
 
-gmg_status dev_alloc(gmg_handle h, double** p, int64_t count) {
-    cudaError_t e = cudaMalloc((void**)p, sizeof(double) * count);
+template <typename T>
+gmg_status dev_alloc(gmg_handle h, T** p, int64_t count) {
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
     if (e != cudaSuccess) {
+        *p = nullptr;
         set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
         return GMG_ERR_ALLOC;
     }
     h->allocs.push_back(*p);
-    e = cudaMemsetAsync(*p, 0, sizeof(double) * count, h->stream);
+    e = cudaMemsetAsync(*p, 0, sizeof(T) * count, h->stream);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
         return GMG_ERR_CUDA;
@@ -157,32 +170,49 @@ gmg_status check_device_ptr(const void* p, const char* name) {
 
 int num_levels(const gmg_config& c) { return c.levels > 0 ? c.levels : ilog2(c.n); }
 
-enum Kind { K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_PREPARE, K_COUNT };
-const char* kKindName[K_COUNT] = {"rb_half", "wj_sweep", "residual", "restrict",
-                                  "prolong_add", "resnorm", "copy", "prepare"};
+enum Kind {
+    K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_OUTER_RES,
+    K_UPDATE, K_MEMSET, K_COUNT
+};
+const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restrict",
+                                  "prolong_add", "resnorm",  "copy",     "outer_residual",
+                                  "update",      "memset"};
+const char* kPrecSuffix[3] = {"", "_f32", "_bf16"};
 
-// Arithmetic model per launch: FP64 pipe instructions the kernel issues and
-// the algorithmic DRAM bytes (every value the operation needs read once,
-// every value it produces written once), both from the level size.
-std::pair<double, double> model(int kind, int d, int n, bool red_only) {
+template <typename T>
+int prec_of();
+template <>
+int prec_of<double>() { return 0; }
+template <>
+int prec_of<float>() { return 1; }
+template <>
+int prec_of<bf16>() { return 2; }
+
+// Arithmetic model per launch: instructions in the kernel's compute
+// precision (FP64 for double storage and for the refinement kernels, FP32
+// otherwise) and algorithmic DRAM bytes (each value the operation needs read
+// once, each value it produces written once) with w bytes per stored value.
+std::pair<double, double> model(int kind, int d, int n, bool red_only, double w) {
     const double N = std::pow((double)(n - 1), d);
     const int nc = n / 2;
     const double Nc = std::pow((double)std::max(nc - 1, 0), d);
     const double cells = std::pow((double)nc, d);
     const bool t = d == 3;
     switch (kind) {
-        case K_RB_HALF: return {N / 2 * (t ? 6 : 4), N / 2 * 24};
-        case K_WJ: return {N * (t ? 8 : 6), N * 24};
+        case K_RB_HALF: return {N / 2 * (t ? 6 : 4), N / 2 * 3 * w};
+        case K_WJ: return {N * (t ? 8 : 6), N * 3 * w};
         case K_RESIDUAL:
-            return red_only ? std::make_pair(N / 2 * (t ? 7 : 5), N * 16)
-                            : std::make_pair(N * (t ? 7 : 5), N * 24);
+            return red_only ? std::make_pair(N / 2 * (t ? 7 : 5), N * 2 * w)
+                            : std::make_pair(N * (t ? 7 : 5), N * 3 * w);
         case K_RESTRICT:
-            return red_only ? std::make_pair(Nc * (t ? 13 : 4), N / 2 * 8 + Nc * 16)
-                            : std::make_pair(Nc * (t ? 27 : 8), N * 8 + Nc * 16);
-        case K_PROLONG: return {cells * (t ? 20 : 8), Nc * 8 + N * 16};
+            return red_only ? std::make_pair(Nc * (t ? 13 : 4), N / 2 * w + Nc * 2 * w)
+                            : std::make_pair(Nc * (t ? 27 : 8), N * w + Nc * 2 * w);
+        case K_PROLONG: return {cells * (t ? 20 : 8), Nc * w + N * 2 * w};
         case K_RESNORM: return {N * (t ? 8 : 6), N * 16};
-        case K_COPY: return {0.0, N * 16};
-        case K_PREPARE: return {N, N * 24};
+        case K_COPY: return {0.0, N * 2 * w};
+        case K_OUTER_RES: return {N * (t ? 8 : 6), N * (16 + w)};
+        case K_UPDATE: return {N, N * (16 + w)};
+        case K_MEMSET: return {0.0, N * w};
     }
     return {0.0, 0.0};
 }
@@ -190,7 +220,7 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only) {
 // Enqueue one kernel (launch() issues it on h->stream), bracketed by event
 // record nodes when timing is on.
 template <class F>
-void timed(gmg_handle h, int kind, int level, int n, bool red_only, F&& launch) {
+void timed(gmg_handle h, int kind, int level, int prec, int n, bool red_only, F&& launch) {
     if (h->timing) {
         const size_t i = h->timed.size();
         while (h->tev.size() < 2 * (i + 1)) {
@@ -201,8 +231,9 @@ void timed(gmg_handle h, int kind, int level, int n, bool red_only, F&& launch) 
         cudaEventRecordWithFlags(h->tev[2 * i], h->stream, cudaEventRecordExternal);
         launch();
         cudaEventRecordWithFlags(h->tev[2 * i + 1], h->stream, cudaEventRecordExternal);
-        auto m = model(kind, h->cfg.d, n, red_only);
-        h->timed.push_back({kind, level, m.first, m.second});
+        const double w = prec == 0 ? 8.0 : prec == 1 ? 4.0 : 2.0;
+        auto m = model(kind, h->cfg.d, n, red_only, w);
+        h->timed.push_back({kind, level, prec, m.first, m.second});
     } else {
         launch();
     }
@@ -218,7 +249,7 @@ void collect_timing(gmg_handle h) {
             continue;
         }
         auto& t = h->timed[i];
-        auto& s = h->stats[{t.kind, t.level}];
+        auto& s = h->stats[{t.kind, t.level, t.prec}];
         s.launches++;
         s.ms += ms;
         s.ops = t.ops;
@@ -228,77 +259,122 @@ void collect_timing(gmg_handle h) {
 
 // Enqueue `sweeps` smoothing sweeps on level l; cur tracks which u buffer
 // holds the iterate (weighted Jacobi alternates).
-void relax(gmg_handle h, int l, int sweeps, int& cur) {
-    Level& L = h->lv[l];
+template <typename T>
+void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur) {
+    Level<T>& L = lv[l];
     const int d = h->cfg.d;
+    const int p = prec_of<T>();
     for (int s = 0; s < sweeps; ++s) {
         if (h->cfg.smoother == GMG_RBGS) {
             for (int color = 0; color < 2; ++color)
-                timed(h, K_RB_HALF, l, L.n, false,
-                      [&] { fp64::rb_half(d, L.n, L.u[cur], L.q, color, h->stream); });
+                timed(h, K_RB_HALF, l, p, L.n, false,
+                      [&] { lk::rb_half<T>(d, L.n, L.u[cur], L.q, color, h->stream); });
         } else {
-            timed(h, K_WJ, l, L.n, false, [&] {
-                fp64::wj_sweep(d, L.n, L.u[cur], L.u[cur ^ 1], L.q, h->cfg.omega, h->stream);
+            timed(h, K_WJ, l, p, L.n, false, [&] {
+                lk::wj_sweep<T>(d, L.n, L.u[cur], L.u[cur ^ 1], L.q, h->cfg.omega, h->stream);
             });
             cur ^= 1;
         }
     }
 }
 
-// One cycle of Algorithm 1 followed by the level-0 residual norm, in
-// stream order (captured into the graph).
-gmg_status enqueue_cycle(gmg_handle h) {
+// One cycle of Algorithm 1 on the hierarchy lv (level-0 iterate lv[0].u[0]
+// in and out), in stream order.
+template <typename T>
+gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
     const gmg_config& c = h->cfg;
     const int d = c.d;
-    const int L = num_levels(c);
+    const int L = (int)lv.size();
+    const int p = prec_of<T>();
     std::vector<int> cur(L, 0);
-    h->timed.clear();
-    h->graph_kernels = 0;
     if (L == 1) {
-        relax(h, 0, c.nu1, cur[0]);
+        relax(h, lv, 0, c.nu1, cur[0]);
     } else {
         for (int l = 0; l + 1 < L; ++l) {
-            relax(h, l, c.nu1, cur[l]);
-            Level& F = h->lv[l];
-            Level& C = h->lv[l + 1];
+            relax(h, lv, l, c.nu1, cur[l]);
+            Level<T>& F = lv[l];
+            Level<T>& C = lv[l + 1];
             // After a black half sweep the black residual vanishes identically.
             const bool red_only = c.smoother == GMG_RBGS && c.nu1 > 0;
-            timed(h, K_RESIDUAL, l, F.n, red_only, [&] {
-                fp64::residual(d, F.n, F.u[cur[l]], F.q, F.r, red_only, h->stream);
+            timed(h, K_RESIDUAL, l, p, F.n, red_only, [&] {
+                lk::residual<T>(d, F.n, F.u[cur[l]], F.q, F.r, red_only, h->stream);
             });
             const bool exact = C.n == 2;
-            timed(h, K_RESTRICT, l, F.n, red_only, [&] {
-                fp64::restrict_fw(d, F.n, F.r, C.q, C.u[0], red_only, exact, h->stream);
+            timed(h, K_RESTRICT, l, p, F.n, red_only, [&] {
+                lk::restrict_fw<T>(d, F.n, F.r, C.q, C.u[0], red_only, exact, h->stream);
             });
             cur[l + 1] = 0;
         }
-        Level& B = h->lv[L - 1];
+        Level<T>& B = lv[L - 1];
         if (B.n > 2) {
             for (int s = 0; s < c.coarse_sweeps; ++s)
                 for (int color = 0; color < 2; ++color)
-                    timed(h, K_RB_HALF, L - 1, B.n, false,
-                          [&] { fp64::rb_half(d, B.n, B.u[0], B.q, color, h->stream); });
+                    timed(h, K_RB_HALF, L - 1, p, B.n, false,
+                          [&] { lk::rb_half<T>(d, B.n, B.u[0], B.q, color, h->stream); });
         }
         for (int l = L - 2; l >= 0; --l) {
-            Level& F = h->lv[l];
-            Level& C = h->lv[l + 1];
-            timed(h, K_PROLONG, l, F.n, false,
-                  [&] { fp64::prolong_add(d, C.n, C.u[cur[l + 1]], F.u[cur[l]], h->stream); });
-            relax(h, l, c.nu2, cur[l]);
+            Level<T>& F = lv[l];
+            Level<T>& C = lv[l + 1];
+            timed(h, K_PROLONG, l, p, F.n, false,
+                  [&] { lk::prolong_add<T>(d, C.n, C.u[cur[l + 1]], F.u[cur[l]], h->stream); });
+            relax(h, lv, l, c.nu2, cur[l]);
         }
     }
     if (cur[0] != 0) {
         cudaError_t e = cudaSuccess;
-        timed(h, K_COPY, 0, c.n, false, [&] {
-            e = cudaMemcpyAsync(h->lv[0].u[0], h->lv[0].u[1], sizeof(double) * h->lv[0].nodes,
+        timed(h, K_COPY, 0, p, c.n, false, [&] {
+            e = cudaMemcpyAsync(lv[0].u[0], lv[0].u[1], sizeof(T) * lv[0].nodes,
                                 cudaMemcpyDeviceToDevice, h->stream);
         });
         GMG_CUDA_TRY(e);
     }
-    timed(h, K_RESNORM, 0, c.n, false, [&] {
-        fp64::resnorm(d, c.n, h->lv[0].u[0], h->lv[0].q, h->partial, h->d_res2, h->stream);
+    return GMG_OK;
+}
+
+// Refinement step: e = 0, k inner cycles on A'e = sigma, u += e, new sigma.
+template <typename T>
+gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
+    const gmg_config& c = h->cfg;
+    const int p = prec_of<T>();
+    cudaError_t e = cudaSuccess;
+    timed(h, K_MEMSET, 0, p, c.n, false, [&] {
+        e = cudaMemsetAsync(in[0].u[0], 0, sizeof(T) * in[0].nodes, h->stream);
     });
-    h->graph_kernels++;  // resnorm is two kernels (partials, then their sum)
+    GMG_CUDA_TRY(e);
+    for (int k = 0; k < c.inner_cycles; ++k) {
+        gmg_status st = enqueue_vcycle<T>(h, in);
+        if (st != GMG_OK) return st;
+    }
+    timed(h, K_UPDATE, 0, p, c.n, false,
+          [&] { mixed::update<T>(c.d, c.n, h->lv[0].u[0], in[0].u[0], h->stream); });
+    timed(h, K_OUTER_RES, 0, p, c.n, false, [&] {
+        mixed::outer_residual<T>(c.d, c.n, h->lv[0].u[0], h->lv[0].q, in[0].q, h->partial,
+                                 h->d_res2, h->stream);
+    });
+    h->graph_kernels++;  // the residual is two kernels (partials, then their sum)
+    return GMG_OK;
+}
+
+// One step of the stopping loop: a plain cycle plus the FP64 norm, or one
+// refinement step; the squared scaled norm lands in h->h_res2.
+gmg_status enqueue_step(gmg_handle h) {
+    const gmg_config& c = h->cfg;
+    h->timed.clear();
+    h->graph_kernels = 0;
+    gmg_status st = GMG_OK;
+    if (c.precision == GMG_FP64) {
+        st = enqueue_vcycle<double>(h, h->lv);
+        if (st != GMG_OK) return st;
+        timed(h, K_RESNORM, 0, 0, c.n, false, [&] {
+            fp64::resnorm(c.d, c.n, h->lv[0].u[0], h->lv[0].q, h->partial, h->d_res2, h->stream);
+        });
+        h->graph_kernels++;  // resnorm is two kernels (partials, then their sum)
+    } else if (c.precision == GMG_FP32_IR) {
+        st = enqueue_refinement<float>(h, h->lvf);
+    } else {
+        st = enqueue_refinement<bf16>(h, h->lvb);
+    }
+    if (st != GMG_OK) return st;
     GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
                                  h->stream));
     GMG_CUDA_TRY(cudaGetLastError());
@@ -314,7 +390,7 @@ gmg_status ensure_graph(gmg_handle h, double* u) {
     h->lv[0].u[0] = u;
     cudaGraph_t g = nullptr;
     GMG_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    gmg_status st = enqueue_cycle(h);
+    gmg_status st = enqueue_step(h);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (st != GMG_OK) {
         if (g) cudaGraphDestroy(g);
@@ -338,22 +414,39 @@ gmg_status ensure_graph(gmg_handle h, double* u) {
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else prev = -1;
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev)
+            cudaSetDevice(dev);
+        else
+            prev = -1;
     }
     ~DeviceGuard() {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
 
-// Prepare q_0 and u's boundary, then the initial residual norm^2.
+// q_0 = h^2 f/(2d), u's boundary = 0, then the initial squared scaled
+// residual norm (and, for refinement, the first inner right-hand side).
+gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
+    const gmg_config& c = h->cfg;
+    fp64::prepare(c.d, c.n, f, h->lv[0].q, u, h->stream);
+    if (c.precision == GMG_FP64)
+        fp64::resnorm(c.d, c.n, u, h->lv[0].q, h->partial, h->d_res2, h->stream);
+    else if (c.precision == GMG_FP32_IR)
+        mixed::outer_residual<float>(c.d, c.n, u, h->lv[0].q, h->lvf[0].q, h->partial, h->d_res2,
+                                     h->stream);
+    else
+        mixed::outer_residual<bf16>(c.d, c.n, u, h->lv[0].q, h->lvb[0].q, h->partial, h->d_res2,
+                                    h->stream);
+    h->launches += 3;
+    GMG_CUDA_TRY(cudaGetLastError());
+    return GMG_OK;
+}
+
 gmg_status start(gmg_handle h, const double* f, double* u, double* res0) {
     GMG_CUDA_TRY(cudaEventRecord(h->ev, h->user_stream));
     GMG_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev, 0));
-    const gmg_config& c = h->cfg;
-    fp64::prepare(c.d, c.n, f, h->lv[0].q, u, h->stream);
-    fp64::resnorm(c.d, c.n, u, h->lv[0].q, h->partial, h->d_res2, h->stream);
-    h->launches += 3;
+    gmg_status st = enqueue_start(h, f, u);
+    if (st != GMG_OK) return st;
     GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
                                  h->stream));
     GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -365,7 +458,7 @@ gmg_status start(gmg_handle h, const double* f, double* u, double* res0) {
     return ensure_graph(h, u);
 }
 
-// Run cycles: until the stopping test (stop = true) or exactly ncycles.
+// Run steps: until the stopping test (stop = true) or exactly ncycles.
 gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycles, bool stop,
                int* iters_out, double* relres_out) {
     gmg_status st = check_device_ptr(f, "f");
@@ -401,6 +494,24 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
     if (stop && res > rtol * res0) {
         set_error("maxit reached before the relative residual fell below rtol");
         return GMG_ERR_NOT_CONVERGED;
+    }
+    return GMG_OK;
+}
+
+template <typename T>
+gmg_status alloc_hierarchy(gmg_handle h, std::vector<Level<T>>& lv, int levels, bool alloc_u0) {
+    const gmg_config& c = h->cfg;
+    gmg_status st;
+    lv.resize(levels);
+    for (int l = 0; l < levels; ++l) {
+        Level<T>& v = lv[l];
+        v.n = c.n >> l;
+        v.nodes = nodes_of(c.d, v.n);
+        if (l > 0 || alloc_u0)
+            if ((st = dev_alloc(h, &v.u[0], v.nodes)) != GMG_OK) return st;
+        if (c.smoother == GMG_WJACOBI && (st = dev_alloc(h, &v.u[1], v.nodes)) != GMG_OK) return st;
+        if ((st = dev_alloc(h, &v.q, v.nodes)) != GMG_OK) return st;
+        if (l + 1 < levels && (st = dev_alloc(h, &v.r, v.nodes)) != GMG_OK) return st;
     }
     return GMG_OK;
 }
@@ -475,23 +586,20 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     }
     const int d = cfg->d;
     const int L = num_levels(*cfg);
-    h->lv.resize(L);
-    for (int l = 0; l < L; ++l) {
-        Level& v = h->lv[l];
-        v.n = cfg->n >> l;
-        v.nodes = nodes_of(d, v.n);
-        if (l > 0) {
-            if ((st = dev_alloc(h, &v.u[0], v.nodes)) != GMG_OK) return fail(st);
-            if (cfg->smoother == GMG_WJACOBI && (st = dev_alloc(h, &v.u[1], v.nodes)) != GMG_OK)
-                return fail(st);
-        } else if (cfg->smoother == GMG_WJACOBI) {
-            if ((st = dev_alloc(h, &v.u[1], v.nodes)) != GMG_OK) return fail(st);
-        }
-        if ((st = dev_alloc(h, &v.q, v.nodes)) != GMG_OK) return fail(st);
-        if (l + 1 < L && (st = dev_alloc(h, &v.r, v.nodes)) != GMG_OK) return fail(st);
+    if (cfg->precision == GMG_FP64) {
+        if ((st = alloc_hierarchy<double>(h, h->lv, L, false)) != GMG_OK) return fail(st);
+    } else {
+        // FP64 level 0: the caller's u and the FP64 scaled right-hand side
+        h->lv.resize(1);
+        h->lv[0].n = cfg->n;
+        h->lv[0].nodes = nodes_of(d, cfg->n);
+        if ((st = dev_alloc(h, &h->lv[0].q, h->lv[0].nodes)) != GMG_OK) return fail(st);
+        st = cfg->precision == GMG_FP32_IR ? alloc_hierarchy<float>(h, h->lvf, L, true)
+                                           : alloc_hierarchy<bf16>(h, h->lvb, L, true);
+        if (st != GMG_OK) return fail(st);
     }
-    if ((st = dev_alloc(h, &h->partial, fp64::resnorm_partials(d, cfg->n))) != GMG_OK)
-        return fail(st);
+    const int np = std::max(fp64::resnorm_partials(d, cfg->n), mixed::outer_partials(d, cfg->n));
+    if ((st = dev_alloc(h, &h->partial, np)) != GMG_OK) return fail(st);
     if ((st = dev_alloc(h, &h->d_res2, 1)) != GMG_OK) return fail(st);
     if (cudaMallocHost((void**)&h->h_res2, sizeof(double)) != cudaSuccess) {
         set_error("cudaMallocHost failed");
@@ -623,8 +731,9 @@ gmg_status gmg_timing_report(gmg_handle h, gmg_kernel_stat* out, int cap, int* c
         if (i < cap) {
             gmg_kernel_stat& s = out[i];
             std::memset(&s, 0, sizeof(s));
-            std::snprintf(s.kernel, sizeof(s.kernel), "%s", kKindName[kv.first.first]);
-            s.level = kv.first.second;
+            std::snprintf(s.kernel, sizeof(s.kernel), "%s%s", kKindName[std::get<0>(kv.first)],
+                          kPrecSuffix[std::get<2>(kv.first)]);
+            s.level = std::get<1>(kv.first);
             s.launches = kv.second.launches;
             s.ms = kv.second.ms;
             s.dp_ops = kv.second.ops;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -15,11 +16,6 @@ namespace gmg {
 void set_error(const std::string& msg);
 const std::string& last_error();
 
-struct Status {
-    gmg_status code = GMG_OK;
-    bool ok() const { return code == GMG_OK; }
-};
-
 #define GMG_CUDA_TRY(expr)                                                              \
     do {                                                                                \
         cudaError_t e_ = (expr);                                                        \
@@ -29,31 +25,50 @@ struct Status {
         }                                                                               \
     } while (0)
 
-// One grid of the hierarchy.  Arrays hold all (n+1)^d nodes, x fastest,
-// boundary entries kept at zero.
+// One grid of a hierarchy in storage type T.  Arrays hold all (n+1)^d
+// nodes, x fastest, boundary entries kept at zero.
+template <typename T>
 struct Level {
     int n = 0;            // intervals per dimension
     int64_t nodes = 0;    // (n+1)^d
-    double* u[2] = {nullptr, nullptr};  // iterate; u[1] = weighted-Jacobi ping-pong partner
-    double* q = nullptr;  // scaled right-hand side q = h^2 f / (2d)
-    double* r = nullptr;  // scaled residual sigma = q + A'-neighbour sum / (2d) - u
+    T* u[2] = {nullptr, nullptr};  // iterate; u[1] = weighted-Jacobi ping-pong partner
+    T* q = nullptr;       // scaled right-hand side q = h^2 f / (2d)
+    T* r = nullptr;       // scaled residual sigma = q + A'-neighbour sum / (2d) - u
 };
 
-// FP64 level kernels (fp64_kernels.cu).  All take interior extents n and
-// work in the scaled variables: q = b / (2d), sigma = (b - A'u) / (2d).
+// Level kernels, explicitly instantiated for double (fp64_kernels.cu) and
+// float / __nv_bfloat16 (mixed_kernels.cu); definitions in level_kernels.cuh.
+namespace lk {
+template <typename T>
+void rb_half(int d, int n, T* u, const T* q, int color, cudaStream_t s);
+template <typename T>
+void wj_sweep(int d, int n, const T* u_in, T* u_out, const T* q, double omega, cudaStream_t s);
+template <typename T>
+void residual(int d, int n, const T* u, const T* q, T* r, bool red_only, cudaStream_t s);
+template <typename T>
+void restrict_fw(int d, int n, const T* r, T* qc, T* uc, bool red_only, bool exact_coarsest,
+                 cudaStream_t s);
+template <typename T>
+void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s);
+}  // namespace lk
+
+// FP64 preparation and stopping-test norm (fp64_kernels.cu).
 namespace fp64 {
 void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s);
-void rb_half(int d, int n, double* u, const double* q, int color, cudaStream_t s);
-void wj_sweep(int d, int n, const double* u_in, double* u_out, const double* q, double omega,
-              cudaStream_t s);
-void residual(int d, int n, const double* u, const double* q, double* r, bool red_only,
-              cudaStream_t s);
-void restrict_fw(int d, int n, const double* r, double* qc, double* uc, bool red_only,
-                 bool exact_coarsest, cudaStream_t s);
-void prolong_add(int d, int nc, const double* uc, double* u, cudaStream_t s);
-int resnorm_partials(int d, int n);  // number of partial sums resnorm writes
+int resnorm_partials(int d, int n);
 void resnorm(int d, int n, const double* u, const double* q, double* partial, double* out,
              cudaStream_t s);
+__global__ void k_sum_partials(const double* partial, int count, double* out);
 }  // namespace fp64
+
+// Outer FP64 kernels of iterative refinement (mixed_kernels.cu).
+namespace mixed {
+int outer_partials(int d, int n);
+template <typename T>
+void outer_residual(int d, int n, const double* u, const double* q, T* q_in, double* partial,
+                    double* out, cudaStream_t s);
+template <typename T>
+void update(int d, int n, double* u, const T* e, cudaStream_t s);
+}  // namespace mixed
 
 }  // namespace gmg

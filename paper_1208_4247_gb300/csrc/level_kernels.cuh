@@ -1,0 +1,338 @@
+// Level kernels of the V-cycle (Algorithm 1), templated on the storage type
+// T (double, float, __nv_bfloat16) with arithmetic in C = double for double
+// storage and float otherwise.
+//
+// Scaled variables: with the unscaled 5/7-point operator A' (section 2.2)
+// and b = h^2 f, each level stores q = b / (2d); the Gauss-Seidel value of a
+// node is q + c * (sum of its 2d neighbours), c = 1/(2d), and the scaled
+// residual is sigma = q + c * sum - u = (b - A'u) / (2d).  Full weighting of
+// b_{l+1} = 4 FW(b - A'u) then reads q_{l+1} = 4 FW(sigma): every transfer
+// weight is a power of two.
+//
+// Instruction counts per node (what bounds the FP64 instantiation on GB300,
+// whose FP64 pipe issues 2 instructions/clock/SM):
+//   red-black half sweep   5 add + 1 fma per updated node
+//   residual               5 add + 1 fma + 1 add
+//   restriction            red nodes only after a black half sweep (the black
+//                          residual is zero in exact arithmetic): 13 ops per
+//                          coarse node in 3D
+//   prolongation+correct   per coarse cell, pair/quad/octet sums shared by
+//                          its 2^d fine nodes: 2.5 ops per fine node in 3D
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "gmg_internal.cuh"
+
+namespace gmg {
+namespace lk {
+
+template <typename T>
+struct Num;
+template <>
+struct Num<double> {
+    using C = double;
+    __device__ static double ld(double v) { return v; }
+    __device__ static double st(double v) { return v; }
+};
+template <>
+struct Num<float> {
+    using C = float;
+    __device__ static float ld(float v) { return v; }
+    __device__ static float st(float v) { return v; }
+};
+template <>
+struct Num<__nv_bfloat16> {
+    using C = float;
+    __device__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+
+__host__ __device__ inline int64_t sy_of(int n) { return (int64_t)n + 1; }
+template <int DIM>
+__host__ __device__ inline int64_t sz_of(int n) {
+    return DIM == 3 ? ((int64_t)n + 1) * (n + 1) : 0;
+}
+
+struct RowLaunch {
+    dim3 grid, block;
+};
+
+// x threads along a row (32..128), rows j over blockIdx.x, planes k over
+// blockIdx.y (3D).
+inline RowLaunch row_launch(int d, int n, int xcount) {
+    int bx = 32;
+    while (bx < xcount && bx < 128) bx *= 2;
+    const int by = 256 / bx;
+    RowLaunch L;
+    L.block = dim3(bx, by, 1);
+    L.grid = dim3((unsigned)((n - 1 + by - 1) / by), d == 3 ? (unsigned)(n - 1) : 1u, 1);
+    return L;
+}
+
+template <int DIM, typename T>
+__device__ inline typename Num<T>::C nbr_sum(const T* u, int64_t p, int64_t sy, int64_t sz) {
+    using N = Num<T>;
+    auto s = N::ld(u[p - 1]) + N::ld(u[p + 1]);
+    s += N::ld(u[p - sy]);
+    s += N::ld(u[p + sy]);
+    if (DIM == 3) {
+        s += N::ld(u[p - sz]);
+        s += N::ld(u[p + sz]);
+    }
+    return s;
+}
+
+// One colour of red-black Gauss-Seidel: nodes with (i+j+k) % 2 == color.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_rb_half(T* __restrict__ u, const T* __restrict__ q, int n,
+                                                 int color) {
+    using N = Num<T>;
+    using C = typename N::C;
+    const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
+    const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
+    const int k = DIM == 3 ? blockIdx.y + 1 : 0;
+    if (j >= n) return;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t row = k * sz + j * sy;
+    const int i0 = 1 + ((1 + j + k + color) & 1);
+    for (int i = i0 + 2 * threadIdx.x; i < n; i += 2 * blockDim.x) {
+        const int64_t p = row + i;
+        u[p] = N::st(fma(c, nbr_sum<DIM>(u, p, sy, sz), N::ld(q[p])));
+    }
+}
+
+// Weighted Jacobi: u_out = u + omega * sigma, all nodes from u_in.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_wj(const T* __restrict__ u, T* __restrict__ uo,
+                                            const T* __restrict__ q, int n, double omega_d) {
+    using N = Num<T>;
+    using C = typename N::C;
+    const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
+    const C omega = C(omega_d);
+    const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
+    const int k = DIM == 3 ? blockIdx.y + 1 : 0;
+    if (j >= n) return;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t row = k * sz + j * sy;
+    for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t p = row + i;
+        const C up = N::ld(u[p]);
+        const C sig = fma(c, nbr_sum<DIM>(u, p, sy, sz), N::ld(q[p])) - up;
+        uo[p] = N::st(fma(omega, sig, up));
+    }
+}
+
+// sigma on all interior nodes, or on red nodes only (black entries of r are
+// never written and never read in that mode).
+template <int DIM, bool RED_ONLY, typename T>
+__global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const T* __restrict__ q,
+                                                  T* __restrict__ r, int n) {
+    using N = Num<T>;
+    using C = typename N::C;
+    const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
+    const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
+    const int k = DIM == 3 ? blockIdx.y + 1 : 0;
+    if (j >= n) return;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t row = k * sz + j * sy;
+    const int step = RED_ONLY ? 2 : 1;
+    const int i0 = RED_ONLY ? 1 + ((1 + j + k) & 1) : 1;
+    for (int i = i0 + step * threadIdx.x; i < n; i += step * blockDim.x) {
+        const int64_t p = row + i;
+        r[p] = N::st(fma(c, nbr_sum<DIM>(u, p, sy, sz), N::ld(q[p])) - N::ld(u[p]));
+    }
+}
+
+// q_c = 4 FW(sigma) at every coarse interior node; u_c = 0 (a fresh coarse
+// iterate) or u_c = q_c when the coarse grid has its single unknown (exact
+// solve u = b/(2d)).  With RED_ONLY the black-node terms (faces and corners
+// in 3D, faces in 2D) are zero and skipped.
+template <int DIM, bool RED_ONLY, typename T>
+__global__ void __launch_bounds__(256) k_restrict(const T* __restrict__ r, T* __restrict__ qc,
+                                                  T* __restrict__ uc, int nc, int exact) {
+    using N = Num<T>;
+    using C = typename N::C;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int K = DIM == 3 ? blockIdx.z + 1 : 0;
+    if (I >= nc || J >= nc) return;
+    const int n = 2 * nc;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t p = (2 * K) * sz + (2 * J) * sy + 2 * I;
+    auto R = [&](int64_t o) { return N::ld(r[p + o]); };
+    C v;
+    if (DIM == 3) {
+        C e = R(-1 - sy) + R(1 - sy);
+        e += R(-1 + sy);
+        e += R(1 + sy);
+        e += R(-1 - sz);
+        e += R(1 - sz);
+        e += R(-sy - sz);
+        e += R(sy - sz);
+        e += R(-1 + sz);
+        e += R(1 + sz);
+        e += R(-sy + sz);
+        e += R(sy + sz);
+        if (RED_ONLY) {
+            v = fma(C(0.125), e, C(0.5) * R(0));
+        } else {
+            C fc = R(-1) + R(1);
+            fc += R(-sy);
+            fc += R(sy);
+            fc += R(-sz);
+            fc += R(sz);
+            C co = R(-1 - sy - sz) + R(1 - sy - sz);
+            co += R(-1 + sy - sz);
+            co += R(1 + sy - sz);
+            co += R(-1 - sy + sz);
+            co += R(1 - sy + sz);
+            co += R(-1 + sy + sz);
+            co += R(1 + sy + sz);
+            v = fma(C(0.0625), co, fma(C(0.125), e, fma(C(0.25), fc, C(0.5) * R(0))));
+        }
+    } else {
+        C co = R(-1 - sy) + R(1 - sy);
+        co += R(-1 + sy);
+        co += R(1 + sy);
+        if (RED_ONLY) {
+            v = fma(C(0.25), co, R(0));
+        } else {
+            C fc = R(-1) + R(1);
+            fc += R(-sy);
+            fc += R(sy);
+            v = fma(C(0.25), co, fma(C(0.5), fc, R(0)));
+        }
+    }
+    const int64_t sc = sy_of(nc);
+    const int64_t P = ((int64_t)K * sc + J) * sc + I;
+    qc[P] = N::st(v);
+    uc[P] = exact ? N::st(v) : N::st(C(0));
+}
+
+// u += P u_c, one thread per coarse cell (I,J,K) in [0, nc-1]^d updating
+// the fine nodes (2I+a, 2J+b, 2K+c), a,b,c in {0,1}, that are interior.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, T* __restrict__ u,
+                                                     int nc) {
+    using N = Num<T>;
+    using C = typename N::C;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = DIM == 3 ? blockIdx.z : 0;
+    if (I >= nc || J >= nc) return;
+    const int n = 2 * nc;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t cy = sy_of(nc), cz = sz_of<DIM>(nc);
+    const int64_t P = K * cz + J * cy + I;
+    const int64_t p = (2 * K) * sz + (2 * J) * sy + 2 * I;
+    const C c000 = N::ld(uc[P]), c100 = N::ld(uc[P + 1]), c010 = N::ld(uc[P + cy]),
+            c110 = N::ld(uc[P + 1 + cy]);
+    const C x00 = c000 + c100;
+    const C x10 = c010 + c110;
+    const C y00 = c000 + c010;
+    const C qxy = x00 + x10;
+    auto add = [&](int64_t o, C w, C v) { u[o] = N::st(fma(w, v, N::ld(u[o]))); };
+    if (DIM == 2) {
+        if (I > 0 && J > 0) u[p] = N::st(N::ld(u[p]) + c000);
+        if (J > 0) add(p + 1, C(0.5), x00);
+        if (I > 0) add(p + sy, C(0.5), y00);
+        add(p + 1 + sy, C(0.25), qxy);
+    } else {
+        const C c001 = N::ld(uc[P + cz]), c101 = N::ld(uc[P + 1 + cz]),
+                c011 = N::ld(uc[P + cy + cz]), c111 = N::ld(uc[P + 1 + cy + cz]);
+        const C x01 = c001 + c101;
+        const C x11 = c011 + c111;
+        const C y01 = c001 + c011;
+        const C z00 = c000 + c001;
+        const C qxz = x00 + x01;
+        const C qyz = y00 + y01;
+        const C oct = qxy + (x01 + x11);
+        if (K > 0) {
+            if (I > 0 && J > 0) u[p] = N::st(N::ld(u[p]) + c000);
+            if (J > 0) add(p + 1, C(0.5), x00);
+            if (I > 0) add(p + sy, C(0.5), y00);
+            add(p + 1 + sy, C(0.25), qxy);
+        }
+        const int64_t pz = p + sz;
+        if (I > 0 && J > 0) add(pz, C(0.5), z00);
+        if (J > 0) add(pz + 1, C(0.25), qxz);
+        if (I > 0) add(pz + sy, C(0.25), qyz);
+        add(pz + 1 + sy, C(0.125), oct);
+    }
+}
+
+// ------------------------------------------------------------- launchers
+
+template <typename T>
+void rb_half(int d, int n, T* u, const T* q, int color, cudaStream_t s) {
+    RowLaunch L = row_launch(d, n, n / 2);
+    if (d == 3)
+        k_rb_half<3, T><<<L.grid, L.block, 0, s>>>(u, q, n, color);
+    else
+        k_rb_half<2, T><<<L.grid, L.block, 0, s>>>(u, q, n, color);
+}
+
+template <typename T>
+void wj_sweep(int d, int n, const T* u_in, T* u_out, const T* q, double omega, cudaStream_t s) {
+    RowLaunch L = row_launch(d, n, n);
+    if (d == 3)
+        k_wj<3, T><<<L.grid, L.block, 0, s>>>(u_in, u_out, q, n, omega);
+    else
+        k_wj<2, T><<<L.grid, L.block, 0, s>>>(u_in, u_out, q, n, omega);
+}
+
+template <typename T>
+void residual(int d, int n, const T* u, const T* q, T* r, bool red_only, cudaStream_t s) {
+    RowLaunch L = row_launch(d, n, red_only ? n / 2 : n);
+    if (d == 3) {
+        if (red_only)
+            k_residual<3, true, T><<<L.grid, L.block, 0, s>>>(u, q, r, n);
+        else
+            k_residual<3, false, T><<<L.grid, L.block, 0, s>>>(u, q, r, n);
+    } else {
+        if (red_only)
+            k_residual<2, true, T><<<L.grid, L.block, 0, s>>>(u, q, r, n);
+        else
+            k_residual<2, false, T><<<L.grid, L.block, 0, s>>>(u, q, r, n);
+    }
+}
+
+template <typename T>
+void restrict_fw(int d, int n, const T* r, T* qc, T* uc, bool red_only, bool exact_coarsest,
+                 cudaStream_t s) {
+    const int nc = n / 2;
+    int bx = 32;
+    while (bx < nc - 1 && bx < 128) bx *= 2;
+    const int by = 256 / bx;
+    dim3 block(bx, by, 1);
+    dim3 grid((nc - 1 + bx - 1) / bx, (nc - 1 + by - 1) / by, d == 3 ? nc - 1 : 1);
+    const int ex = exact_coarsest ? 1 : 0;
+    if (d == 3) {
+        if (red_only)
+            k_restrict<3, true, T><<<grid, block, 0, s>>>(r, qc, uc, nc, ex);
+        else
+            k_restrict<3, false, T><<<grid, block, 0, s>>>(r, qc, uc, nc, ex);
+    } else {
+        if (red_only)
+            k_restrict<2, true, T><<<grid, block, 0, s>>>(r, qc, uc, nc, ex);
+        else
+            k_restrict<2, false, T><<<grid, block, 0, s>>>(r, qc, uc, nc, ex);
+    }
+}
+
+template <typename T>
+void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s) {
+    int bx = 32;
+    while (bx < nc && bx < 128) bx *= 2;
+    const int by = 256 / bx;
+    dim3 block(bx, by, 1);
+    dim3 grid((nc + bx - 1) / bx, (nc + by - 1) / by, d == 3 ? nc : 1);
+    if (d == 3)
+        k_prolong_add<3, T><<<grid, block, 0, s>>>(uc, u, nc);
+    else
+        k_prolong_add<2, T><<<grid, block, 0, s>>>(uc, u, nc);
+}
+
+}  // namespace lk
+}  // namespace gmg

@@ -1,0 +1,117 @@
+// Mixed-precision form: V-cycles in FP32, or in BF16 storage with FP32
+// arithmetic, inside FP64 iterative refinement.  FP64 stays on the GPU for
+// the outer residual (and its norm, the stopping test) and the solution
+// update; the inner cycles solve A'e = b - A'u approximately from e = 0.
+//
+// In the scaled variables the inner right-hand side is the outer scaled
+// residual itself: A'e = b - A'u  <=>  e = sigma + c * (sum of e's
+// neighbours) at the fixed point, so q_inner = sigma rounded to the storage
+// type.
+#include "level_kernels.cuh"
+
+namespace gmg {
+
+namespace lk {
+#define GMG_INSTANTIATE(T)                                                                       \
+    template void rb_half<T>(int, int, T*, const T*, int, cudaStream_t);                         \
+    template void wj_sweep<T>(int, int, const T*, T*, const T*, double, cudaStream_t);           \
+    template void residual<T>(int, int, const T*, const T*, T*, bool, cudaStream_t);             \
+    template void restrict_fw<T>(int, int, const T*, T*, T*, bool, bool, cudaStream_t);          \
+    template void prolong_add<T>(int, int, const T*, T*, cudaStream_t);
+GMG_INSTANTIATE(float)
+GMG_INSTANTIATE(__nv_bfloat16)
+#undef GMG_INSTANTIATE
+}  // namespace lk
+
+namespace mixed {
+namespace {
+
+using lk::sy_of;
+using lk::sz_of;
+
+constexpr int kThreads = 256;
+
+// sigma = q + c * sum - u in FP64 on every interior node, stored to the
+// inner right-hand side in T; partial sums of sigma^2 as in the FP64 norm.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __restrict__ u,
+                                                             const double* __restrict__ q,
+                                                             T* __restrict__ q_in,
+                                                             double* __restrict__ partial, int n) {
+    __shared__ double warp_sums[kThreads / 32];
+    const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
+    double acc = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
+         r += (int64_t)gridDim.x * blockDim.y) {
+        const int j = (int)(r % (n - 1)) + 1;
+        const int k = DIM == 3 ? (int)(r / (n - 1)) + 1 : 0;
+        const int64_t row = k * sz + j * sy;
+        for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+            const int64_t p = row + i;
+            const double sig = fma(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
+            q_in[p] = lk::Num<T>::st((typename lk::Num<T>::C)sig);
+            acc = fma(sig, sig, acc);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((t & 31) == 0) warp_sums[t >> 5] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += warp_sums[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+// u += e over all nodes (e and u are zero on the boundary).
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(double* __restrict__ u, const T* __restrict__ e,
+                                                int64_t nodes) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nodes;
+         p += (int64_t)gridDim.x * blockDim.x)
+        u[p] += (double)lk::Num<T>::ld(e[p]);
+}
+
+}  // namespace
+
+int outer_partials(int d, int n) {
+    int bx = 32;
+    while (bx < n && bx < 128) bx *= 2;
+    const int by = kThreads / bx;
+    const int64_t rows = d == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
+    return (int)std::min<int64_t>((rows + by - 1) / by, 152 * 8);
+}
+
+template <typename T>
+void outer_residual(int d, int n, const double* u, const double* q, T* q_in, double* partial,
+                    double* out, cudaStream_t s) {
+    int bx = 32;
+    while (bx < n && bx < 128) bx *= 2;
+    dim3 block(bx, kThreads / bx, 1);
+    const int blocks = outer_partials(d, n);
+    if (d == 3)
+        k_outer_residual<3, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, n);
+    else
+        k_outer_residual<2, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, n);
+    fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
+}
+
+template <typename T>
+void update(int d, int n, double* u, const T* e, cudaStream_t s) {
+    const int64_t nodes = d == 3 ? (int64_t)(n + 1) * (n + 1) * (n + 1) : (int64_t)(n + 1) * (n + 1);
+    const int blocks = (int)std::min<int64_t>((nodes + 255) / 256, 152 * 16);
+    k_update<T><<<blocks, 256, 0, s>>>(u, e, nodes);
+}
+
+template void outer_residual<float>(int, int, const double*, const double*, float*, double*,
+                                    double*, cudaStream_t);
+template void outer_residual<__nv_bfloat16>(int, int, const double*, const double*,
+                                            __nv_bfloat16*, double*, double*, cudaStream_t);
+template void update<float>(int, int, double*, const float*, cudaStream_t);
+template void update<__nv_bfloat16>(int, int, double*, const __nv_bfloat16*, cudaStream_t);
+
+}  // namespace mixed
+}  // namespace gmg
