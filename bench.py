@@ -150,9 +150,13 @@ def run_forms(torch, args):
     f = torch.from_numpy(inputs.rhs_sine_plus_gauss(d, n, 3)).cuda()
     u = torch.zeros_like(f)
     pk, _ = peaks()
+    from paper_1208_4247_gb300.autotune import tune_inner_cycles
     out = {}
-    for name, prec, k in [("fp64_plain", "fp64", 0), ("fp32_ir", "fp32", 5),
-                          ("bf16_ir", "bf16", 2)]:
+    tuned = {}
+    for prec, ks in (("fp32", (1, 2, 3, 4, 5)), ("bf16", (1, 2, 3))):
+        tuned[prec] = tune_inner_cycles(d, n, f, u, prec, ks=ks)
+    for name, prec, k in [("fp64_plain", "fp64", 0), ("fp32_ir", "fp32", tuned["fp32"][0]),
+                          ("bf16_ir", "bf16", tuned["bf16"][0])]:
         S = Solver(d, n, precision=prec, inner_cycles=max(k, 1))
         ms, it, rel, stats, launches = time_solves(torch, S, f, u, args.form_steps, 1)
         S.close()
@@ -171,11 +175,86 @@ def run_forms(torch, args):
     base = out["fp64_plain"]["ms_per_step"]
     for v in out.values():
         v["speedup_vs_fp64_plain"] = base / v["ms_per_step"]
+    for prec, name in (("fp32", "fp32_ir"), ("bf16", "bf16_ir")):
+        out[name]["autotune_ms_by_inner_cycles"] = tuned[prec][1]
     del f, u
     torch.cuda.empty_cache()
     return {"workload": "3D 513^3 (511^3 = 133.4M unknowns), f = 3 pi^2 prod sin + 0.01 N(0,1) "
                         "seed 3, RB-GS V(2,2), FW, trilinear, to relative FP64 residual 1e-10",
             "forms": out}
+
+
+def run_batch(torch, args):
+    """512 independent solves (seed 4): 2D (2^k+1)^2 k = 6..10 and 3D (2^k+1)^3
+    k = 4..7, f = U[-1,1]; FP32 weighted-Jacobi (4/5) V(1,1) cycles in FP64
+    refinement, one launch per level index over the batch, autotuned inner
+    cycles / tile / CTAs; against the same solves one by one."""
+    from paper_1208_4247_gb300 import inputs
+    from paper_1208_4247_gb300.autotune import tune_batch
+    from paper_1208_4247_gb300.gmg import Batch, Solver
+    mix = inputs.batch_mix(512, 4)
+    dims = [d for d, _ in mix]
+    ns = [n for _, n in mix]
+    dof = sum((n - 1) ** d for d, n in mix)
+    fd = [torch.from_numpy(f).cuda() for f in inputs.batch_rhs(mix, 4)]
+    ud = [torch.zeros_like(f) for f in fd]
+    kw = dict(smoother="wjacobi", omega=0.8, nu1=1, nu2=1, precision="fp32")
+    best, tried = tune_batch(dims, ns, fd, ud, **kw)
+    B = Batch(dims, ns, inner_cycles=best["inner_cycles"], chunk=best["chunk"], ctas=best["ctas"],
+              **kw)
+    B.set_timing(True)
+
+    def run():
+        for u in ud:
+            u.zero_()
+        return B.solve(fd, ud, RTOL)
+
+    run()
+    B.set_timing(True)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(args.form_steps):
+        it, rel, steps, conv = run()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.form_steps
+    stats, launches = B.timing_report()
+    B.close()
+    hist = {}
+    for v in it:
+        hist[v] = hist.get(v, 0) + 1
+    # the same solves one by one (same precision, smoother, sweeps, inner cycles)
+    solvers = [Solver(d, n, smoother="wjacobi", omega=0.8, nu1=1, nu2=1, precision="fp32",
+                      inner_cycles=best["inner_cycles"]) for d, n in mix]
+
+    def one_by_one():
+        for S, f, u in zip(solvers, fd, ud):
+            u.zero_()
+            S.solve(f, u, RTOL)
+
+    one_by_one()
+    torch.cuda.synchronize()
+    e0.record(s)
+    one_by_one()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    for S in solvers:
+        S.close()
+    del fd, ud
+    torch.cuda.empty_cache()
+    dom, rec, share = dominant(stats)
+    return {"workload": "512 solves, seeded mix of 2D (2^k+1)^2 k=6..10 and 3D (2^k+1)^3 k=4..7, "
+                        "f = U[-1,1]; FP32 WJ(4/5) V(1,1) in FP64 refinement",
+            "unknowns": dof, "value": dof / (ms * 1e-3), "unit": "DOF/s", "ms_per_step": ms,
+            "steps": args.form_steps, "batch_steps": steps, "converged": conv,
+            "max_relres": max(rel), "completion_steps_histogram": hist,
+            "autotuned": best, "autotune_tried": [[p, t] for p, t in tried],
+            "one_by_one_ms": ms1, "one_by_one_dof_per_s": dof / (ms1 * 1e-3),
+            "speedup_vs_one_by_one": ms1 / ms, "dominant_kernel": dom,
+            "dominant_share": share, "gpu_launches": launches}
 
 
 def dist_env():
@@ -337,9 +416,10 @@ def run_ours(args, rank, ws, local):
 
     if rank != 0:
         return
-    forms = None
+    forms = batch = None
     if not args.no_forms:
         forms = run_forms(torch, args)
+        batch = run_batch(torch, args)
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -360,7 +440,7 @@ def run_ours(args, rank, ws, local):
                        "l2": "inputs larger than L2 (u, q, r: 3 x 136 MB at level 0)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks, "mixed_precision_513": forms}
+            "gpu_launches": launches, "clocks": clocks, "mixed_precision_513": forms, "batched_512": batch}
     if args.kernels:
         line["kernels"] = stats
     print(json.dumps(line), flush=True)

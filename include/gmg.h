@@ -158,6 +158,41 @@ gmg_status gmg_timing_report(gmg_handle h, gmg_kernel_stat* out, int cap, int* c
 /* Zero the timing records and the launch counter. */
 gmg_status gmg_timing_reset(gmg_handle h);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent solves of uneven sizes (2D and 3D mixed) advanced
+ * together: every step launches one persistent kernel per level index over
+ * the whole batch (work items = chunks of one solve's level grid), so the
+ * coarse levels of the large solves share launches with the fine levels of
+ * the small ones.  Levels are aligned at the coarsest (3^d) grid.  Cycles run
+ * in the inner precision of *common (GMG_FP32_IR or GMG_BF16_IR: FP64 outer
+ * residual, update and norm; GMG_FP64: plain cycles) with its smoother and
+ * sweeps; each solve stops on its own FP64 relative residual (converged
+ * solves are masked on the device).  One refinement step of the whole batch
+ * is one captured CUDA graph. */
+typedef struct gmg_batch_s* gmg_batch;
+
+/* count solves; d[i], n[i] per solve (as in gmg_config); *common gives the
+ * smoother, omega, nu1, nu2, precision, inner_cycles and maxit (its d, n,
+ * levels are ignored: every solve uses all its levels).  chunk: nodes per
+ * work item (0 = 1024); ctas: CTAs per launch (0 = 4 x SM count). */
+gmg_status gmg_batch_create(int count, const int* d, const int* n, const gmg_config* common,
+                            int chunk, int ctas, void* cuda_stream, gmg_batch* out);
+
+/* f[i], u[i]: device pointers of solve i (layout above), u[i] the initial
+ * guess.  iters_out[count] (may be NULL): steps each solve ran;
+ * relres_out[count] (may be NULL): each final relative residual.
+ * *steps_out (may be NULL): batch steps launched.  Returns
+ * GMG_ERR_NOT_CONVERGED if any solve hit maxit. */
+gmg_status gmg_batch_solve(gmg_batch b, const double* const* f, double* const* u, double rtol,
+                           int* iters_out, double* relres_out, int* steps_out);
+
+/* Per-kernel timing of the batch graph, as gmg_set_timing / gmg_timing_report. */
+gmg_status gmg_batch_set_timing(gmg_batch b, int enable);
+gmg_status gmg_batch_timing_report(gmg_batch b, gmg_kernel_stat* out, int cap, int* count,
+                                   int64_t* launches_out);
+
+gmg_status gmg_batch_destroy(gmg_batch b);
+
 /* Release every device and host resource of the handle.  NULL is a no-op. */
 gmg_status gmg_destroy(gmg_handle h);
 

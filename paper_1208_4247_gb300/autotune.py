@@ -1,0 +1,73 @@
+"""Autotuner: picks launch and schedule parameters by timing real solves.
+
+* ``tune_batch`` -- for a batch: inner cycles per refinement step, nodes per
+  work item (the tile) and CTAs per level launch, searched coordinate-wise
+  (cycles, then tile, then CTAs), each candidate timed on the caller's batch.
+* ``tune_inner_cycles`` -- for one solve in a refinement form: inner cycles
+  per outer step.
+
+Timing uses CUDA events on torch's current stream around whole solves from
+u = 0 after one untimed solve per candidate (graph capture, first-touch).
+"""
+from __future__ import annotations
+
+
+def _time(torch, fn, reps=1):
+    fn()  # warm-up: graph capture and first touch
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_batch(dims, ns, fd, ud, rtol=1e-10, ks=(1, 2, 3), chunks=(512, 1024, 2048, 4096),
+               ctas=(152, 304, 608, 1216), **kw):
+    """Returns (best parameter dict, list of (params, ms) tried)."""
+    import torch
+    from .gmg import Batch
+
+    tried = []
+
+    def measure(p):
+        with Batch(dims, ns, inner_cycles=p["inner_cycles"], chunk=p["chunk"], ctas=p["ctas"],
+                   **kw) as B:
+            def run():
+                for u in ud:
+                    u.zero_()
+                _, _, _, conv = B.solve(fd, ud, rtol)
+                assert conv
+            ms = _time(torch, run)
+        tried.append((dict(p), ms))
+        return ms
+
+    best = {"inner_cycles": ks[0], "chunk": 1024, "ctas": 608}
+    for key, values in (("inner_cycles", ks), ("chunk", chunks), ("ctas", ctas)):
+        scores = {}
+        for v in values:
+            p = dict(best)
+            p[key] = v
+            scores[v] = measure(p)
+        best[key] = min(scores, key=scores.get)
+    return best, tried
+
+
+def tune_inner_cycles(d, n, f, u, precision, ks=(1, 2, 3, 4, 5), rtol=1e-10, **kw):
+    """Returns (best k, {k: ms})."""
+    import torch
+    from .gmg import Solver
+
+    out = {}
+    for k in ks:
+        with Solver(d, n, precision=precision, inner_cycles=k, **kw) as S:
+            def run():
+                u.zero_()
+                _, _, conv = S.solve(f, u, rtol)
+                assert conv
+            out[k] = _time(torch, run)
+    return min(out, key=out.get), out

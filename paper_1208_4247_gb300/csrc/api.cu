@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "gmg_internal.cuh"
+#include "timing.cuh"
 
 namespace gmg {
 
@@ -47,21 +48,7 @@ struct gmg_handle_s {
     double* f_stage = nullptr;  // device copies for gmg_solve_host
     double* u_stage = nullptr;
     std::vector<void*> allocs;
-    // launch accounting and optional per-kernel event timing
-    int64_t launches = 0;   // every kernel launch since the last reset
-    int graph_kernels = 0;  // kernels per launch of the cycle graph
-    bool timing = false;
-    struct TimedLaunch {
-        int kind, level, prec;
-        double ops, bytes;
-    };
-    std::vector<TimedLaunch> timed;  // timed launches of one graph run, in order
-    std::vector<cudaEvent_t> tev;    // two events per timed launch
-    struct Stat {
-        int64_t launches = 0;
-        double ms = 0.0, ops = 0.0, bytes = 0.0;
-    };
-    std::map<std::tuple<int, int, int>, Stat> stats;
+    KernelTimer timer;  // launch accounting and optional per-kernel event timing
 };
 
 namespace {
@@ -217,44 +204,15 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
     return {0.0, 0.0};
 }
 
-// Enqueue one kernel (launch() issues it on h->stream), bracketed by event
-// record nodes when timing is on.
+// Enqueue one kernel (launch() issues it on h->stream), timed when timing
+// is on; `kernels` = kernel launches launch() makes.
 template <class F>
-void timed(gmg_handle h, int kind, int level, int prec, int n, bool red_only, F&& launch) {
-    if (h->timing) {
-        const size_t i = h->timed.size();
-        while (h->tev.size() < 2 * (i + 1)) {
-            cudaEvent_t e;
-            cudaEventCreate(&e);
-            h->tev.push_back(e);
-        }
-        cudaEventRecordWithFlags(h->tev[2 * i], h->stream, cudaEventRecordExternal);
-        launch();
-        cudaEventRecordWithFlags(h->tev[2 * i + 1], h->stream, cudaEventRecordExternal);
-        const double w = prec == 0 ? 8.0 : prec == 1 ? 4.0 : 2.0;
-        auto m = model(kind, h->cfg.d, n, red_only, w);
-        h->timed.push_back({kind, level, prec, m.first, m.second});
-    } else {
-        launch();
-    }
-    h->graph_kernels++;
-}
-
-// After a graph run: add each timed launch's device time to its record.
-void collect_timing(gmg_handle h) {
-    for (size_t i = 0; i < h->timed.size(); ++i) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, h->tev[2 * i], h->tev[2 * i + 1]) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        auto& t = h->timed[i];
-        auto& s = h->stats[{t.kind, t.level, t.prec}];
-        s.launches++;
-        s.ms += ms;
-        s.ops = t.ops;
-        s.bytes = t.bytes;
-    }
+void timed(gmg_handle h, int kind, int level, int prec, int n, bool red_only, F&& launch,
+           int kernels = 1) {
+    const double w = prec == 0 ? 8.0 : prec == 1 ? 4.0 : 2.0;
+    auto m = model(kind, h->cfg.d, n, red_only, w);
+    h->timer.run(h->stream, std::string(kKindName[kind]) + kPrecSuffix[prec], level, m.first,
+                 m.second, kernels, launch);
 }
 
 // Enqueue `sweeps` smoothing sweeps on level l; cur tracks which u buffer
@@ -347,11 +305,13 @@ gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
     }
     timed(h, K_UPDATE, 0, p, c.n, false,
           [&] { mixed::update<T>(c.d, c.n, h->lv[0].u[0], in[0].u[0], h->stream); });
-    timed(h, K_OUTER_RES, 0, p, c.n, false, [&] {
-        mixed::outer_residual<T>(c.d, c.n, h->lv[0].u[0], h->lv[0].q, in[0].q, h->partial,
-                                 h->d_res2, h->stream);
-    });
-    h->graph_kernels++;  // the residual is two kernels (partials, then their sum)
+    timed(
+        h, K_OUTER_RES, 0, p, c.n, false,
+        [&] {
+            mixed::outer_residual<T>(c.d, c.n, h->lv[0].u[0], h->lv[0].q, in[0].q, h->partial,
+                                     h->d_res2, h->stream);
+        },
+        2);
     return GMG_OK;
 }
 
@@ -359,16 +319,18 @@ gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
 // refinement step; the squared scaled norm lands in h->h_res2.
 gmg_status enqueue_step(gmg_handle h) {
     const gmg_config& c = h->cfg;
-    h->timed.clear();
-    h->graph_kernels = 0;
+    h->timer.begin_capture();
     gmg_status st = GMG_OK;
     if (c.precision == GMG_FP64) {
         st = enqueue_vcycle<double>(h, h->lv);
         if (st != GMG_OK) return st;
-        timed(h, K_RESNORM, 0, 0, c.n, false, [&] {
-            fp64::resnorm(c.d, c.n, h->lv[0].u[0], h->lv[0].q, h->partial, h->d_res2, h->stream);
-        });
-        h->graph_kernels++;  // resnorm is two kernels (partials, then their sum)
+        timed(
+            h, K_RESNORM, 0, 0, c.n, false,
+            [&] {
+                fp64::resnorm(c.d, c.n, h->lv[0].u[0], h->lv[0].q, h->partial, h->d_res2,
+                              h->stream);
+            },
+            2);
     } else if (c.precision == GMG_FP32_IR) {
         st = enqueue_refinement<float>(h, h->lvf);
     } else {
@@ -437,7 +399,7 @@ gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
     else
         mixed::outer_residual<bf16>(c.d, c.n, u, h->lv[0].q, h->lvb[0].q, h->partial, h->d_res2,
                                     h->stream);
-    h->launches += 3;
+    h->timer.launches += 3;
     GMG_CUDA_TRY(cudaGetLastError());
     return GMG_OK;
 }
@@ -476,8 +438,7 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
     while (it < cap && (!stop || res > rtol * res0)) {
         GMG_CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
         GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
-        h->launches += h->graph_kernels;
-        if (h->timing) collect_timing(h);
+        h->timer.after_graph_run();
         res = std::sqrt(*h->h_res2);
         ++it;
         const double rel = res0 > 0.0 ? res / res0 : 0.0;
@@ -550,7 +511,7 @@ gmg_status gmg_destroy(gmg_handle h) {
     DeviceGuard guard(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
-    for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+    h->timer.destroy();
     for (void* p : h->allocs) cudaFree(p);
     if (h->h_res2) cudaFreeHost(h->h_res2);
     if (h->ev) cudaEventDestroy(h->ev);
@@ -683,7 +644,7 @@ gmg_status gmg_residual_norm(gmg_handle h, const double* f, double* u, double* n
     const gmg_config& c = h->cfg;
     fp64::prepare(c.d, c.n, f, h->lv[0].q, u, h->stream);
     fp64::resnorm(c.d, c.n, u, h->lv[0].q, h->partial, h->d_res2, h->stream);
-    h->launches += 3;
+    h->timer.launches += 3;
     GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
                                  h->stream));
     GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -697,9 +658,9 @@ gmg_status gmg_set_timing(gmg_handle h, int enable) {
         set_error("handle is NULL");
         return GMG_ERR_ARG;
     }
-    if ((enable != 0) != h->timing) {
+    if ((enable != 0) != h->timer.enabled) {
         DeviceGuard guard(h->device);
-        h->timing = enable != 0;
+        h->timer.enabled = enable != 0;
         if (h->graph) {
             GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
             cudaGraphExecDestroy(h->graph);
@@ -715,8 +676,7 @@ gmg_status gmg_timing_reset(gmg_handle h) {
         set_error("handle is NULL");
         return GMG_ERR_ARG;
     }
-    h->stats.clear();
-    h->launches = 0;
+    h->timer.reset();
     return GMG_OK;
 }
 
@@ -726,23 +686,7 @@ gmg_status gmg_timing_report(gmg_handle h, gmg_kernel_stat* out, int cap, int* c
         set_error("bad arguments");
         return GMG_ERR_ARG;
     }
-    int i = 0;
-    for (auto& kv : h->stats) {
-        if (i < cap) {
-            gmg_kernel_stat& s = out[i];
-            std::memset(&s, 0, sizeof(s));
-            std::snprintf(s.kernel, sizeof(s.kernel), "%s%s", kKindName[std::get<0>(kv.first)],
-                          kPrecSuffix[std::get<2>(kv.first)]);
-            s.level = std::get<1>(kv.first);
-            s.launches = kv.second.launches;
-            s.ms = kv.second.ms;
-            s.dp_ops = kv.second.ops;
-            s.bytes = kv.second.bytes;
-        }
-        ++i;
-    }
-    if (count) *count = i;
-    if (launches_out) *launches_out = h->launches;
+    h->timer.report(out, cap, count, launches_out);
     return GMG_OK;
 }
 

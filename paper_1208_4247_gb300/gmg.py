@@ -70,6 +70,12 @@ SIGNATURES = {
     "gmg_timing_report": ([P, ctypes.POINTER(KernelStat), I, PI,
                            ctypes.POINTER(ctypes.c_int64)], I),
     "gmg_timing_reset": ([P], I),
+    "gmg_batch_create": ([I, PI, PI, ctypes.POINTER(Config), I, I, P, ctypes.POINTER(P)], I),
+    "gmg_batch_solve": ([P, ctypes.POINTER(P), ctypes.POINTER(P), D, PI, PD, PI], I),
+    "gmg_batch_set_timing": ([P, I], I),
+    "gmg_batch_timing_report": ([P, ctypes.POINTER(KernelStat), I, PI,
+                                 ctypes.POINTER(ctypes.c_int64)], I),
+    "gmg_batch_destroy": ([P], I),
 }
 
 
@@ -219,3 +225,79 @@ def timing_report(handle):
     rows = [dict(kernel=s.kernel.decode(), level=s.level, launches=s.launches, ms=s.ms,
                  dp_ops=s.dp_ops, bytes=s.bytes) for s in list(buf)[:cnt.value]]
     return rows, tot.value
+
+
+class Batch:
+    """Independent solves of uneven sizes advanced together (gmg_batch_*).
+
+    dims, ns: per-solve d and n.  The inner precision ("fp32" / "bf16"),
+    smoother, sweeps and inner cycles are shared; chunk = nodes per work item,
+    ctas = CTAs per launch (0 = library defaults)."""
+
+    def __init__(self, dims, ns, smoother: str = "wjacobi", omega: float = 0.8, nu1: int = 1,
+                 nu2: int = 1, precision: str = "fp32", inner_cycles: int = 2, maxit: int = 200,
+                 chunk: int = 0, ctas: int = 0, stream=None):
+        self.dims = list(dims)
+        self.ns = list(ns)
+        self.count = len(self.dims)
+        cfg = Config()
+        _check(lib().gmg_config_init(ctypes.byref(cfg), 3, 2))
+        cfg.smoother = SMOOTHERS[smoother]
+        cfg.omega = omega
+        cfg.nu1, cfg.nu2 = nu1, nu2
+        cfg.precision = PRECISIONS[precision]
+        cfg.inner_cycles = inner_cycles
+        cfg.maxit = maxit
+        darr = (ctypes.c_int * self.count)(*self.dims)
+        narr = (ctypes.c_int * self.count)(*self.ns)
+        h = ctypes.c_void_p()
+        _check(lib().gmg_batch_create(self.count, darr, narr, ctypes.byref(cfg), chunk, ctas,
+                                      _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def solve(self, fs, us, rtol: float = 1e-10):
+        """fs, us: lists of float64 CUDA tensors.  Returns (per-solve steps,
+        per-solve relative residuals, batch steps, all converged)."""
+        if len(fs) != self.count or len(us) != self.count:
+            raise ValueError("need one f and one u per solve")
+        fp = (ctypes.c_void_p * self.count)(
+            *[_dptr(f, "f", d, n) for f, d, n in zip(fs, self.dims, self.ns)])
+        up = (ctypes.c_void_p * self.count)(
+            *[_dptr(u, "u", d, n) for u, d, n in zip(us, self.dims, self.ns)])
+        it = (ctypes.c_int * self.count)()
+        rel = (ctypes.c_double * self.count)()
+        steps = ctypes.c_int(0)
+        st = _check(lib().gmg_batch_solve(self._h, fp, up, rtol, it, rel, ctypes.byref(steps)),
+                    allow=(ERR_NOT_CONVERGED,))
+        return list(it), list(rel), steps.value, st == OK
+
+    def set_timing(self, enable: bool = True):
+        _check(lib().gmg_batch_set_timing(self._h, 1 if enable else 0))
+
+    def timing_report(self):
+        cnt = ctypes.c_int(0)
+        tot = ctypes.c_int64(0)
+        _check(lib().gmg_batch_timing_report(self._h, None, 0, ctypes.byref(cnt),
+                                             ctypes.byref(tot)))
+        buf = (KernelStat * max(cnt.value, 1))()
+        _check(lib().gmg_batch_timing_report(self._h, buf, cnt.value, ctypes.byref(cnt),
+                                             ctypes.byref(tot)))
+        return [dict(kernel=s.kernel.decode(), level=s.level, launches=s.launches, ms=s.ms,
+                     dp_ops=s.dp_ops, bytes=s.bytes) for s in list(buf)[:cnt.value]], tot.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gmg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

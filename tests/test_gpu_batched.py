@@ -1,0 +1,108 @@
+"""Batched form: independent solves of uneven sizes (2D and 3D mixed), FP32 /
+BF16-storage cycles in FP64 refinement, one launch per level index over the
+batch.  Each solve must reach an FP64 relative residual <= 1e-10 and lie
+within 1e-9 (relative) of the oracle's FP64 solution."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1208_4247_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1208_4247_gb300 import build
+    build.build()
+    return torch
+
+
+def np_relres(f, u):
+    """FP64 relative residual ||h^2 f - A'u|| / ||h^2 f|| with numpy slicing
+    (u, f on all nodes; boundary of u zero)."""
+    d = f.ndim
+    n = f.shape[0] - 1
+    b = f[(slice(1, -1),) * d] / n ** 2
+    c = (slice(1, -1),) * d
+    au = 2 * d * u[c]
+    for ax in range(d):
+        lo = list(c)
+        hi = list(c)
+        lo[ax] = slice(0, -2)
+        hi[ax] = slice(2, None)
+        au = au - u[tuple(lo)] - u[tuple(hi)]
+    return np.linalg.norm((b - au).ravel()) / np.linalg.norm(b.ravel())
+
+
+SMALL = [(2, 16), (3, 8), (2, 64), (3, 32), (2, 4), (3, 16), (2, 128), (3, 4), (2, 32), (3, 64)]
+
+
+@pytest.mark.parametrize("prec,sm,om,nu,k,chunk", [
+    ("fp32", "wjacobi", 0.8, 1, 2, 0), ("fp32", "rbgs", 0.8, 2, 2, 256),
+    ("bf16", "wjacobi", 0.8, 1, 1, 512), ("fp32", "wjacobi", 0.8, 2, 3, 100),
+])
+def test_small_batch_matches_oracle(torch_cuda, prec, sm, om, nu, k, chunk):
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Batch
+    dims = [d for d, n in SMALL]
+    ns = [n for d, n in SMALL]
+    fs = [inputs.rhs_uniform(d, n, 40 + i) for i, (d, n) in enumerate(SMALL)]
+    fd = [torch.from_numpy(f).cuda() for f in fs]
+    ud = [torch.zeros_like(f) for f in fd]
+    with Batch(dims, ns, smoother=sm, omega=om, nu1=nu, nu2=nu, precision=prec,
+               inner_cycles=k, chunk=chunk, ctas=7) as B:
+        it, rel, steps, conv = B.solve(fd, ud, rtol=1e-10)
+    assert conv and steps == max(it)
+    smo = oracle.RBGS if sm == "rbgs" else oracle.WJACOBI
+    for (d, n), f, u, r in zip(SMALL, fs, ud, rel):
+        ug = u.cpu().numpy()
+        assert r <= 1e-10
+        assert np_relres(f, ug) <= 1e-10
+        uo = np.zeros_like(f)
+        oracle.solve(oracle.make_cfg(d, n, 0, smo, om, 2, 2, 1), f, uo, rtol=1e-13, maxit=100)
+        assert np.linalg.norm(ug - uo) <= 1e-9 * np.linalg.norm(uo)
+
+
+def test_batch_rerun_and_second_rtol(torch_cuda):
+    """A second solve on the same batch handle (new rtol: graph re-captured)
+    restarts from the given u and reaches the looser tolerance in fewer steps."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Batch
+    sizes = [(2, 32), (3, 16), (3, 8)]
+    fd = [torch.from_numpy(inputs.rhs_uniform(d, n, 7 + i)).cuda() for i, (d, n) in enumerate(sizes)]
+    with Batch([d for d, _ in sizes], [n for _, n in sizes]) as B:
+        ud = [torch.zeros_like(f) for f in fd]
+        it1, rel1, s1, c1 = B.solve(fd, ud, rtol=1e-10)
+        ud2 = [torch.zeros_like(f) for f in fd]
+        it2, rel2, s2, c2 = B.solve(fd, ud2, rtol=1e-4)
+    assert c1 and c2 and s2 < s1 and all(r <= 1e-4 for r in rel2)
+
+
+def test_full_batch_512(torch_cuda):
+    """The 512-solve mix (seed 4): every solve's FP64 residual <= 1e-10
+    (numpy), and 6 sampled solves within 1e-9 of the oracle."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Batch
+    mix = inputs.batch_mix(512, 4)
+    fs = inputs.batch_rhs(mix, 4)
+    fd = [torch.from_numpy(f).cuda() for f in fs]
+    ud = [torch.zeros_like(f) for f in fd]
+    with Batch([d for d, _ in mix], [n for _, n in mix], inner_cycles=2) as B:
+        it, rel, steps, conv = B.solve(fd, ud, rtol=1e-10)
+    assert conv
+    us = [u.cpu().numpy() for u in ud]
+    for f, u in zip(fs, us):
+        assert np_relres(f, u) <= 1e-10
+    rng = np.random.default_rng(0)
+    for s in rng.choice(len(mix), 6, replace=False):
+        d, n = mix[s]
+        if (n + 1) ** d > 3e6:
+            continue
+        uo = np.zeros_like(fs[s])
+        oracle.solve(oracle.make_cfg(d, n, 0, oracle.WJACOBI, 0.8, 2, 2, 1), fs[s], uo,
+                     rtol=1e-13, maxit=100)
+        assert np.linalg.norm(us[s] - uo) <= 1e-9 * np.linalg.norm(uo)
