@@ -65,6 +65,11 @@ def lib():
                 ("orc_vcycle", [ctypes.POINTER(Cfg), P, P], I),
                 ("orc_scale_rhs", [I, I, P, P], None),
                 ("orc_solve", [ctypes.POINTER(Cfg), P, P, D, I, P], I),
+                ("orc_conv_fwd", [I, I, P, P, P, P, P], None),
+                ("orc_conv_bwd", [I, I, P, P, P, P, P, P, P], None),
+                ("orc_learned_smooth_error", [I, I, P, P, P], None),
+                ("orc_cgc_error", [I, I, P, I], None),
+                ("orc_learned_loss", [I, I, P, P, P, I], D),
             ]:
                 fn = getattr(L, name)
                 fn.argtypes = args
@@ -168,3 +173,51 @@ def solve(cfg: Cfg, f, u, rtol=1e-10, maxit=100):
     if it < 0:
         raise ValueError("oracle solve: bad configuration")
     return it, hist[:it].copy()
+
+
+HIDDEN = 8
+
+
+def taps(d):
+    return 27 if d == 3 else 9
+
+
+def _pf(a):
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def conv_fwd(W1, W2, x):
+    """Returns (y, z) of the learned smoother's network on grid function x."""
+    d, n = _dn(x)
+    y = np.empty_like(x)
+    z = np.empty((HIDDEN,) + x.shape)
+    lib().orc_conv_fwd(d, n, _pf(W1), _pf(W2), _p(x), _p(z), _p(y))
+    return y, z
+
+
+def conv_bwd(W1, W2, x, gy):
+    """Returns (gx, dW1, dW2) for upstream gradient gy."""
+    d, n = _dn(x)
+    gx = np.empty_like(x)
+    dW1 = np.zeros((HIDDEN, taps(d)))
+    dW2 = np.zeros((HIDDEN, taps(d)))
+    lib().orc_conv_bwd(d, n, _pf(W1), _pf(W2), _p(x), _p(gy), _p(gx), _p(dW1), _p(dW2))
+    return gx, dW1, dW2
+
+
+def learned_smooth_error(W1, W2, e):
+    d, n = _dn(e)
+    lib().orc_learned_smooth_error(d, n, _pf(W1), _pf(W2), _p(e))
+    return e
+
+
+def cgc_error(e, cycles=30):
+    d, n = _dn(e)
+    lib().orc_cgc_error(d, n, _p(e), cycles)
+    return e
+
+
+def learned_loss(W1, W2, e0, coarse_cycles=30):
+    d, n = _dn(e0)
+    return lib().orc_learned_loss(d, n, _pf(W1), _pf(W2), _p(e0), coarse_cycles)

@@ -357,3 +357,187 @@ int orc_solve(const orc_cfg* c, const double* f, double* u, double rtol, int max
     free(r);
     return iter;
 }
+
+/* ------------------------------------------------------- learned smoother
+ *
+ * A per-level convolutional smoother u <- u + N(sigma), sigma = (b - A'u)/(2d)
+ * the scaled residual, N = conv2(ReLU(conv1(sigma))): conv1 maps 1 -> H = 8
+ * channels, conv2 maps 8 -> 1, both 3^d-tap correlations over the interior
+ * nodes with zero padding at the Dirichlet boundary, no biases.  Weights:
+ * W1[c][t], W2[c][t], t = (c3+1)*9 + (b+1)*3 + (a+1) for the tap offset
+ * (a, b, c3) in {-1,0,1}^d (x fastest; 9 taps in 2D).  In error form
+ * (e = u* - u, sigma = A'e/(2d)) one smoothing step is e <- e - N(A'e/(2d)).
+ * The loss is the measured two-grid error contraction
+ *     L = ||S(CG(S(e0)))||^2 / ||e0||^2,
+ * CG(e) = e - P A_c'^{-1} 4 FW(A'e) with the coarse system solved to
+ * round-off. */
+
+#define ORC_HID 8
+
+static inline int ntaps(int d) { return d == 3 ? 27 : 9; }
+static inline void tap_off(int d, int t, int* a, int* b, int* c)
+{
+    *a = t % 3 - 1;
+    *b = (t / 3) % 3 - 1;
+    *c = d == 3 ? t / 9 - 1 : 0;
+}
+
+/* z[ch][p] = sum_t W1[ch][t] x(p + o_t); y[p] = sum_ch sum_t W2[ch][t] relu(z[ch](p + o_t)).
+ * z: ORC_HID arrays of nodes(d,n) (may be NULL: then allocated internally). */
+void orc_conv_fwd(int d, int n, const float* W1, const float* W2, const double* x, double* z,
+                  double* y)
+{
+    int64_t m = nodes(d, n);
+    int T = ntaps(d);
+    double* zz = z ? z : (double*)malloc(sizeof(double) * m * ORC_HID);
+    memset(zz, 0, sizeof(double) * m * ORC_HID);
+    memset(y, 0, sizeof(double) * m);
+    for (int ch = 0; ch < ORC_HID; ++ch)
+        for (int k = kmin(d); k <= kmax(d, n); ++k)
+            for (int j = 1; j < n; ++j)
+                for (int i = 1; i < n; ++i) {
+                    double s = 0.0;
+                    for (int t = 0; t < T; ++t) {
+                        int a, b, c;
+                        tap_off(d, t, &a, &b, &c);
+                        s = s + (double)W1[ch * T + t] * val(x, d, n, i + a, j + b, k + c);
+                    }
+                    zz[ch * m + IDX(n, i, j, k)] = s;
+                }
+    for (int k = kmin(d); k <= kmax(d, n); ++k)
+        for (int j = 1; j < n; ++j)
+            for (int i = 1; i < n; ++i) {
+                double s = 0.0;
+                for (int ch = 0; ch < ORC_HID; ++ch)
+                    for (int t = 0; t < T; ++t) {
+                        int a, b, c;
+                        tap_off(d, t, &a, &b, &c);
+                        double zv = val(zz + ch * m, d, n, i + a, j + b, k + c);
+                        s = s + (double)W2[ch * T + t] * (zv > 0.0 ? zv : 0.0);
+                    }
+                y[IDX(n, i, j, k)] = s;
+            }
+    if (!z) free(zz);
+}
+
+/* Backward of orc_conv_fwd for an upstream gradient gy (interior nodes):
+ * gx = dL/dx, dW1, dW2 (accumulated, arrays of ORC_HID*taps doubles). */
+void orc_conv_bwd(int d, int n, const float* W1, const float* W2, const double* x,
+                  const double* gy, double* gx, double* dW1, double* dW2)
+{
+    int64_t m = nodes(d, n);
+    int T = ntaps(d);
+    double* z = (double*)malloc(sizeof(double) * m * ORC_HID);
+    double* y = (double*)malloc(sizeof(double) * m);
+    double* gz = (double*)calloc(m * ORC_HID, sizeof(double));
+    orc_conv_fwd(d, n, W1, W2, x, z, y);
+    /* dW2[ch][t] = sum_p gy(p) relu(z_ch(p + o_t));  gh_ch(q) = sum_t W2[ch][t] gy(q - o_t) */
+    for (int ch = 0; ch < ORC_HID; ++ch)
+        for (int t = 0; t < T; ++t) {
+            int a, b, c;
+            tap_off(d, t, &a, &b, &c);
+            double s = 0.0;
+            for (int k = kmin(d); k <= kmax(d, n); ++k)
+                for (int j = 1; j < n; ++j)
+                    for (int i = 1; i < n; ++i) {
+                        double zv = val(z + ch * m, d, n, i + a, j + b, k + c);
+                        s = s + gy[IDX(n, i, j, k)] * (zv > 0.0 ? zv : 0.0);
+                    }
+            dW2[ch * T + t] += s;
+        }
+    for (int ch = 0; ch < ORC_HID; ++ch)
+        for (int k = kmin(d); k <= kmax(d, n); ++k)
+            for (int j = 1; j < n; ++j)
+                for (int i = 1; i < n; ++i) {
+                    double s = 0.0;
+                    for (int t = 0; t < T; ++t) {
+                        int a, b, c;
+                        tap_off(d, t, &a, &b, &c);
+                        s = s + (double)W2[ch * T + t] * val(gy, d, n, i - a, j - b, k - c);
+                    }
+                    int64_t p = IDX(n, i, j, k);
+                    gz[ch * m + p] = z[ch * m + p] > 0.0 ? s : 0.0;
+                }
+    /* dW1[ch][t] = sum_p gz_ch(p) x(p + o_t);  gx(q) = sum_ch sum_t W1[ch][t] gz_ch(q - o_t) */
+    for (int ch = 0; ch < ORC_HID; ++ch)
+        for (int t = 0; t < T; ++t) {
+            int a, b, c;
+            tap_off(d, t, &a, &b, &c);
+            double s = 0.0;
+            for (int k = kmin(d); k <= kmax(d, n); ++k)
+                for (int j = 1; j < n; ++j)
+                    for (int i = 1; i < n; ++i)
+                        s = s + gz[ch * m + IDX(n, i, j, k)] * val(x, d, n, i + a, j + b, k + c);
+            dW1[ch * T + t] += s;
+        }
+    memset(gx, 0, sizeof(double) * m);
+    for (int k = kmin(d); k <= kmax(d, n); ++k)
+        for (int j = 1; j < n; ++j)
+            for (int i = 1; i < n; ++i) {
+                double s = 0.0;
+                for (int ch = 0; ch < ORC_HID; ++ch)
+                    for (int t = 0; t < T; ++t) {
+                        int a, b, c;
+                        tap_off(d, t, &a, &b, &c);
+                        s = s + (double)W1[ch * T + t] * val(gz + ch * m, d, n, i - a, j - b, k - c);
+                    }
+                gx[IDX(n, i, j, k)] = s;
+            }
+    free(z);
+    free(y);
+    free(gz);
+}
+
+/* One learned smoothing step in error form: e <- e - N(A'e/(2d)). */
+void orc_learned_smooth_error(int d, int n, const float* W1, const float* W2, double* e)
+{
+    int64_t m = nodes(d, n);
+    double* s = (double*)malloc(sizeof(double) * m);
+    double* y = (double*)malloc(sizeof(double) * m);
+    orc_apply_stencil(d, n, e, s);
+    for (int64_t p = 0; p < m; ++p) s[p] = s[p] / (2.0 * d);
+    orc_conv_fwd(d, n, W1, W2, s, NULL, y);
+    for (int64_t p = 0; p < m; ++p) e[p] = e[p] - y[p];
+    free(s);
+    free(y);
+}
+
+/* Coarse-grid correction in error form with the coarse system solved by
+ * `cycles` red-black V(2,2) cycles from zero: e <- e - P A_c'^{-1} 4 FW(A'e). */
+void orc_cgc_error(int d, int n, double* e, int cycles)
+{
+    int nc = n / 2;
+    int64_t m = nodes(d, n), mc = nodes(d, nc);
+    double* r = (double*)malloc(sizeof(double) * m);
+    double* bc = (double*)malloc(sizeof(double) * mc);
+    double* uc = (double*)calloc(mc, sizeof(double));
+    orc_apply_stencil(d, n, e, r);
+    orc_restrict_fw(d, n, r, bc);
+    orc_cfg c = {d, nc, 0, ORC_RBGS, 0.8, 2, 2, 1};
+    int L = 0;
+    while ((2 << L) <= nc) ++L;
+    c.levels = L;
+    for (int k = 0; k < cycles; ++k) orc_vcycle(&c, bc, uc);
+    double* pu = (double*)calloc(m, sizeof(double));
+    orc_prolong_add(d, nc, uc, pu);
+    for (int64_t p = 0; p < m; ++p) e[p] = e[p] - pu[p];
+    free(r);
+    free(bc);
+    free(uc);
+    free(pu);
+}
+
+/* Two-grid contraction loss ||S(CG(S(e0)))||^2 / ||e0||^2. */
+double orc_learned_loss(int d, int n, const float* W1, const float* W2, const double* e0,
+                        int coarse_cycles)
+{
+    int64_t m = nodes(d, n);
+    double* e = (double*)malloc(sizeof(double) * m);
+    memcpy(e, e0, sizeof(double) * m);
+    orc_learned_smooth_error(d, n, W1, W2, e);
+    orc_cgc_error(d, n, e, coarse_cycles);
+    orc_learned_smooth_error(d, n, W1, W2, e);
+    double num = orc_norm2(d, n, e), den = orc_norm2(d, n, e0);
+    free(e);
+    return (num * num) / (den * den);
+}

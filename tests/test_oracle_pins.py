@@ -258,3 +258,103 @@ def test_solver_reaches_rtol_and_history_monotone():
     b = oracle.scale_rhs(f)
     r = oracle.residual(b, u)
     assert oracle.norm2(r) / oracle.norm2(b) == pytest.approx(hist[-1], rel=1e-9)
+
+
+# ------------------------------------------------------------ learned smoother
+
+def _jacobi_weights(d, omega):
+    """Two-channel weights with relu(x) - relu(-x) = x: the network is omega*x."""
+    T = oracle.taps(d)
+    W1 = np.zeros((oracle.HIDDEN, T), np.float32)
+    W2 = np.zeros((oracle.HIDDEN, T), np.float32)
+    c = T // 2
+    W1[0, c], W1[1, c] = 1.0, -1.0
+    W2[0, c], W2[1, c] = omega, -omega
+    return W1, W2
+
+
+@pytest.mark.parametrize("d,n", [(2, 8), (3, 8)])
+def test_conv_tap_orientation(d, n):
+    """conv1 tap (+1, 0[, 0]) reads x at i+1: y(p) = relu(x(p + e_x)) (zero
+    padding outside the interior)."""
+    T = oracle.taps(d)
+    W1 = np.zeros((oracle.HIDDEN, T), np.float32)
+    W2 = np.zeros((oracle.HIDDEN, T), np.float32)
+    W1[3, T // 2 + 1] = 1.0  # offset (a=+1, b=0, c=0)
+    W2[3, T // 2] = 1.0
+    rng = np.random.default_rng(6)
+    x = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)
+    y, z = oracle.conv_fwd(W1, W2, x)
+    ref = np.zeros_like(x)
+    inner = (slice(1, -1),) * d
+    shifted = np.zeros_like(x)
+    shifted[..., :-1] = x[..., 1:]
+    shifted[..., n - 1] = 0.0
+    ref[inner] = np.maximum(shifted[inner], 0.0)
+    assert np.array_equal(y, ref)
+
+
+@pytest.mark.parametrize("d,n", [(2, 6), (3, 4)])
+def test_conv_backward_matches_finite_differences(d, n):
+    rng = np.random.default_rng(7)
+    T = oracle.taps(d)
+    W1 = rng.standard_normal((oracle.HIDDEN, T)).astype(np.float32)
+    W2 = rng.standard_normal((oracle.HIDDEN, T)).astype(np.float32)
+    x = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)
+    gy = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)
+    gx, dW1, dW2 = oracle.conv_bwd(W1, W2, x, gy)
+    L = lambda W1_, W2_, x_: float(np.sum(gy * oracle.conv_fwd(W1_, W2_, x_)[0]))
+    eps = 1e-6
+    for _ in range(6):
+        p = tuple(rng.integers(1, n, size=d))
+        xp, xm = x.copy(), x.copy()
+        xp[p] += eps
+        xm[p] -= eps
+        assert gx[p] == pytest.approx((L(W1, W2, xp) - L(W1, W2, xm)) / (2 * eps), rel=1e-5, abs=1e-7)
+    # weights are float32: perturb by a float32-representable step
+    for W, dW, which in ((W1, dW1, 0), (W2, dW2, 1)):
+        for _ in range(4):
+            c, t = rng.integers(0, oracle.HIDDEN), rng.integers(0, T)
+            h = np.float32(2.0 ** -10)
+            Wp, Wm = W.copy(), W.copy()
+            Wp[c, t] += h
+            Wm[c, t] -= h
+            args_p = (Wp, W2) if which == 0 else (W1, Wp)
+            args_m = (Wm, W2) if which == 0 else (W1, Wm)
+            fd = (L(*args_p, x) - L(*args_m, x)) / (float(Wp[c, t]) - float(Wm[c, t]))
+            assert dW[c, t] == pytest.approx(fd, rel=1e-4, abs=1e-6)
+
+
+@pytest.mark.parametrize("d,n,omega", [(2, 8, 0.8), (3, 8, 6 / 7)])
+def test_learned_jacobi_weights_equal_dense_weighted_jacobi(d, n, omega):
+    W1, W2 = _jacobi_weights(d, omega)
+    rng = np.random.default_rng(8)
+    e0 = rng.standard_normal((n - 1) ** d)
+    e = dm.from_vec(e0, d, n)
+    oracle.learned_smooth_error(W1, W2, e)
+    ref = dm.wj_iteration_matrix(d, n, float(np.float32(omega))) @ e0
+    np.testing.assert_allclose(dm.to_vec(e), ref, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("d,n", [(2, 16), (3, 8)])
+def test_coarse_grid_correction_equals_dense(d, n):
+    rng = np.random.default_rng(9)
+    e0 = rng.standard_normal((n - 1) ** d)
+    e = dm.from_vec(e0, d, n)
+    oracle.cgc_error(e, cycles=40)
+    A = dm.lap(d, n)
+    Ac = dm.lap(d, n // 2)
+    CG = np.eye(len(e0)) - dm.prolong(d, n // 2) @ np.linalg.solve(Ac, dm.restrict(d, n) @ A)
+    np.testing.assert_allclose(dm.to_vec(e), CG @ e0, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("d,n,omega", [(2, 16, 0.8), (3, 8, 6 / 7)])
+def test_learned_loss_is_two_grid_contraction(d, n, omega):
+    """With the Jacobi weights the loss is ||E e0||^2 / ||e0||^2 for the dense
+    two-grid V(1,1) weighted-Jacobi operator E."""
+    W1, W2 = _jacobi_weights(d, omega)
+    rng = np.random.default_rng(10)
+    e0 = rng.standard_normal((n - 1) ** d)
+    loss = oracle.learned_loss(W1, W2, dm.from_vec(e0, d, n), coarse_cycles=40)
+    E = dm.vcycle_error_matrix(d, n, 2, 0, float(np.float32(omega)), 1, 1, 1000)
+    assert loss == pytest.approx(np.sum((E @ e0) ** 2) / np.sum(e0 ** 2), rel=1e-10)
