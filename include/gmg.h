@@ -158,6 +158,49 @@ gmg_status gmg_timing_report(gmg_handle h, gmg_kernel_stat* out, int cap, int* c
 /* Zero the timing records and the launch counter. */
 gmg_status gmg_timing_reset(gmg_handle h);
 
+/* ------------------------------------------------------- learned smoother
+ * A per-level convolutional smoother u <- u + N(sigma), sigma = (h^2 f - A'u)
+ * / (2d) the scaled residual, N = conv2(ReLU(conv1(sigma))): conv1 maps 1 -> 8
+ * channels, conv2 maps 8 -> 1, both 3^d taps over the interior nodes with zero
+ * padding at the Dirichlet boundary, no biases; BF16 weights (the library
+ * rounds what it is given, round-to-nearest-even), FP32 accumulation.  The
+ * paper has no learned component: this replaces one pre- and one post-
+ * smoothing sweep of its V-cycle (Algorithm 1) on the levels given weights.
+ * Weights: 2 x 8 x T floats (T = 27 in 3D, 9 in 2D), W1[c][t] then W2[c][t],
+ * tap t = (c3+1)*9 + (b+1)*3 + (a+1) for the offset (a, b, c3) in {-1,0,1}^d
+ * (x fastest). */
+#define GMG_LEARNED_HIDDEN 8
+
+/* Use weights (host, layout above; NULL = red-black GS) on `level` of a handle
+ * created with smoother GMG_LEARNED (precision GMG_FP64).  Levels without
+ * weights smooth with red-black GS.  Re-captures the cycle graph. */
+gmg_status gmg_set_learned_weights(gmg_handle h, int level, const float* weights);
+
+/* y = N(x) on a 2D/3D grid of n intervals (x, y: device FP64, all nodes;
+ * x zero on the boundary).  Synchronises cuda_stream. */
+gmg_status gmg_learned_conv(int d, int n, const float* weights, const double* x, double* y,
+                            void* cuda_stream);
+
+/* Two-grid contraction loss L = ||S(CG(S(e0)))||^2 / ||e0||^2 of the error e0
+ * (device FP64, all nodes, zero boundary) on a grid of n intervals, with
+ * S e = e - N(A'e/(2d)) and CG e = e - P A_c'^{-1} 4 FW(A'e), the coarse
+ * system solved by coarse_cycles red-black V(2,2) cycles.  *loss_out: L;
+ * grad_out (host, 2 x 8 x T doubles, may be NULL): dL/dW at the BF16-rounded
+ * weights.  Synchronises cuda_stream. */
+gmg_status gmg_learned_loss_grad(int d, int n, const float* weights, const double* e0,
+                                 int coarse_cycles, double* loss_out, double* grad_out,
+                                 void* cuda_stream);
+
+/* Train the weights on the GPU: `steps` Adam steps (learning rate lr) on the
+ * mean two-grid loss over `batch` error samples per step, each sample the
+ * error left by pair_cycles plain red-black V(1,1) cycles applied to seeded
+ * white noise (seed) on a grid of n intervals.  w_init -> w_out (host, layout
+ * above; FP32 master weights); loss_history (host, `steps` doubles, may be
+ * NULL): the mean loss of each step's batch.  Synchronises cuda_stream. */
+gmg_status gmg_learned_train(int d, int n, int steps, int batch, int pair_cycles,
+                             int coarse_cycles, double lr, uint64_t seed, const float* w_init,
+                             float* w_out, double* loss_history, void* cuda_stream);
+
 /* ---------------------------------------------------------------- batches
  * Many independent solves of uneven sizes (2D and 3D mixed) advanced
  * together: every step launches one persistent kernel per level index over

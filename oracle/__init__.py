@@ -70,6 +70,8 @@ def lib():
                 ("orc_learned_smooth_error", [I, I, P, P, P], None),
                 ("orc_cgc_error", [I, I, P, I], None),
                 ("orc_learned_loss", [I, I, P, P, P, I], D),
+                ("orc_learned_relax", [I, I, P, P, P, P], None),
+                ("orc_vcycle_learned", [ctypes.POINTER(Cfg), P, P, P], I),
             ]:
                 fn = getattr(L, name)
                 fn.argtypes = args
@@ -221,3 +223,19 @@ def cgc_error(e, cycles=30):
 def learned_loss(W1, W2, e0, coarse_cycles=30):
     d, n = _dn(e0)
     return lib().orc_learned_loss(d, n, _pf(W1), _pf(W2), _p(e0), coarse_cycles)
+
+
+def learned_relax(W1, W2, b, u):
+    d, n = _dn(u)
+    lib().orc_learned_relax(d, n, _pf(W1), _pf(W2), _p(b), _p(u))
+    return u
+
+
+def vcycle_learned(cfg: Cfg, weights, b, u):
+    """weights: list (one per level) of float32 arrays (2, 8, T) or None."""
+    arrs = [None if w is None else np.ascontiguousarray(w, dtype=np.float32) for w in weights]
+    ptrs = (ctypes.c_void_p * len(arrs))(*[None if a is None else a.ctypes.data for a in arrs])
+    rc = lib().orc_vcycle_learned(ctypes.byref(cfg), ptrs, _p(b), _p(u))
+    if rc != 0:
+        raise ValueError("oracle learned V-cycle: bad configuration")
+    return u

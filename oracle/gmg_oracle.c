@@ -541,3 +541,64 @@ double orc_learned_loss(int d, int n, const float* W1, const float* W2, const do
     free(e);
     return (num * num) / (den * den);
 }
+
+/* One learned smoothing step on a level: u <- u + N((b - A'u)/(2d)). */
+void orc_learned_relax(int d, int n, const float* W1, const float* W2, const double* b,
+                       double* u)
+{
+    int64_t m = nodes(d, n);
+    double* r = (double*)malloc(sizeof(double) * m);
+    double* y = (double*)malloc(sizeof(double) * m);
+    orc_residual(d, n, b, u, r);
+    for (int64_t p = 0; p < m; ++p) r[p] = r[p] / (2.0 * d);
+    orc_conv_fwd(d, n, W1, W2, r, NULL, y);
+    for (int64_t p = 0; p < m; ++p) u[p] = u[p] + y[p];
+    free(r);
+    free(y);
+}
+
+/* Algorithm 1 with the learned smoother on the levels whose weights are
+ * given: W[l] points at 2 x 8 x taps floats (W1 then W2) or is NULL, in which
+ * case level l relaxes with red-black GS.  Sweeps nu1 / nu2 per level. */
+int orc_vcycle_learned(const orc_cfg* c, const float* const* W, const double* b0, double* u0)
+{
+    int d = c->d, L = c->levels, T = ntaps(d);
+    if (L < 2 || (c->n >> (L - 1)) != 2) return -1;
+    double** b = (double**)calloc(L, sizeof(double*));
+    double** u = (double**)calloc(L, sizeof(double*));
+    double* r = (double*)malloc(sizeof(double) * nodes(d, c->n));
+    b[0] = (double*)b0;
+    u[0] = u0;
+    for (int l = 1; l < L; ++l) {
+        b[l] = (double*)calloc(nodes(d, c->n >> l), sizeof(double));
+        u[l] = (double*)calloc(nodes(d, c->n >> l), sizeof(double));
+    }
+#define ORC_RELAX(l, sweeps)                                                         \
+    for (int s_ = 0; s_ < (sweeps); ++s_) {                                          \
+        if (W[l])                                                                    \
+            orc_learned_relax(d, c->n >> (l), W[l], W[l] + ORC_HID * T, b[l], u[l]); \
+        else                                                                         \
+            orc_rbgs(d, c->n >> (l), b[l], u[l], 1);                                 \
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+        int nl = c->n >> l;
+        ORC_RELAX(l, c->nu1);
+        orc_residual(d, nl, b[l], u[l], r);
+        orc_restrict_fw(d, nl, r, b[l + 1]);
+        memset(u[l + 1], 0, sizeof(double) * nodes(d, nl / 2));
+    }
+    orc_coarse_solve(d, 2, b[L - 1], u[L - 1], 1);
+    for (int l = L - 2; l >= 0; --l) {
+        orc_prolong_add(d, (c->n >> l) / 2, u[l + 1], u[l]);
+        ORC_RELAX(l, c->nu2);
+    }
+#undef ORC_RELAX
+    for (int l = 1; l < L; ++l) {
+        free(b[l]);
+        free(u[l]);
+    }
+    free(b);
+    free(u);
+    free(r);
+    return 0;
+}

@@ -9,6 +9,7 @@
 #include <map>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -49,6 +50,10 @@ struct gmg_handle_s {
     double* u_stage = nullptr;
     std::vector<void*> allocs;
     KernelTimer timer;  // launch accounting and optional per-kernel event timing
+    // learned smoother (GMG_LEARNED): per level BF16-rounded weights on the
+    // device (NULL: red-black GS on that level) and the hidden-layer buffer
+    std::vector<float*> lw, lz;
+    float* lw_scratch = nullptr;
 };
 
 namespace {
@@ -83,10 +88,13 @@ gmg_status check_cfg(const gmg_config* c) {
         set_error("levels must be 0 (all) or 1.." + std::to_string(lmax));
         return GMG_ERR_ARG;
     }
-    if (c->smoother != GMG_WJACOBI && c->smoother != GMG_RBGS) {
-        set_error(c->smoother == GMG_LEARNED ? "learned smoother: use the gmg_learned_* calls"
-                                             : "unknown smoother");
-        return c->smoother == GMG_LEARNED ? GMG_ERR_UNSUPPORTED : GMG_ERR_ARG;
+    if (c->smoother != GMG_WJACOBI && c->smoother != GMG_RBGS && c->smoother != GMG_LEARNED) {
+        set_error("unknown smoother");
+        return GMG_ERR_ARG;
+    }
+    if (c->smoother == GMG_LEARNED && c->precision != GMG_FP64) {
+        set_error("the learned smoother runs in the plain FP64 form only");
+        return GMG_ERR_UNSUPPORTED;
     }
     if (!(c->omega > 0.0 && c->omega < 2.0)) {
         set_error("omega must lie in (0, 2)");
@@ -159,11 +167,11 @@ int num_levels(const gmg_config& c) { return c.levels > 0 ? c.levels : ilog2(c.n
 
 enum Kind {
     K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_OUTER_RES,
-    K_UPDATE, K_MEMSET, K_COUNT
+    K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_COUNT
 };
 const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restrict",
                                   "prolong_add", "resnorm",  "copy",     "outer_residual",
-                                  "update",      "memset"};
+                                  "update",      "memset",   "conv1",    "conv2_update"};
 const char* kPrecSuffix[3] = {"", "_f32", "_bf16"};
 
 template <typename T>
@@ -200,6 +208,8 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
         case K_OUTER_RES: return {N * (t ? 8 : 6), N * (16 + w)};
         case K_UPDATE: return {N, N * (16 + w)};
         case K_MEMSET: return {0.0, N * w};
+        case K_CONV1: return {N * 8 * (t ? 27 : 9), N * (w + 32)};  // FP32 FMAs
+        case K_CONV2: return {N * 8 * (t ? 27 : 9), N * (32 + 2 * w)};
     }
     return {0.0, 0.0};
 }
@@ -215,6 +225,22 @@ void timed(gmg_handle h, int kind, int level, int prec, int n, bool red_only, F&
                  m.second, kernels, launch);
 }
 
+bool learned_level(gmg_handle h, int l) {
+    return h->cfg.smoother == GMG_LEARNED && l < (int)h->lw.size() && h->lw[l];
+}
+
+// One learned smoothing sweep on FP64 level l: sigma = (b - A'u)/(2d),
+// u += conv2(relu(conv1(sigma))).
+void learned_sweep(gmg_handle h, Level<double>& L, int l) {
+    const int d = h->cfg.d;
+    timed(h, K_RESIDUAL, l, 0, L.n, false,
+          [&] { lk::residual<double>(d, L.n, L.u[0], L.q, L.r, false, h->stream); });
+    timed(h, K_CONV1, l, 0, L.n, false,
+          [&] { learned::conv1(d, L.n, L.r, h->lz[l], h->lw[l], h->stream); });
+    timed(h, K_CONV2, l, 0, L.n, false,
+          [&] { learned::conv2(d, L.n, h->lz[l], L.u[0], 1, h->lw[l], h->stream); });
+}
+
 // Enqueue `sweeps` smoothing sweeps on level l; cur tracks which u buffer
 // holds the iterate (weighted Jacobi alternates).
 template <typename T>
@@ -223,7 +249,13 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur)
     const int d = h->cfg.d;
     const int p = prec_of<T>();
     for (int s = 0; s < sweeps; ++s) {
-        if (h->cfg.smoother == GMG_RBGS) {
+        if constexpr (std::is_same<T, double>::value) {
+            if (learned_level(h, l)) {
+                learned_sweep(h, L, l);
+                continue;
+            }
+        }
+        if (h->cfg.smoother == GMG_RBGS || h->cfg.smoother == GMG_LEARNED) {
             for (int color = 0; color < 2; ++color)
                 timed(h, K_RB_HALF, l, p, L.n, false,
                       [&] { lk::rb_half<T>(d, L.n, L.u[cur], L.q, color, h->stream); });
@@ -253,7 +285,9 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
             Level<T>& F = lv[l];
             Level<T>& C = lv[l + 1];
             // After a black half sweep the black residual vanishes identically.
-            const bool red_only = c.smoother == GMG_RBGS && c.nu1 > 0;
+            const bool rb = c.smoother == GMG_RBGS ||
+                            (c.smoother == GMG_LEARNED && !learned_level(h, l));
+            const bool red_only = rb && c.nu1 > 0;
             timed(h, K_RESIDUAL, l, p, F.n, red_only, [&] {
                 lk::residual<T>(d, F.n, F.u[cur[l]], F.q, F.r, red_only, h->stream);
             });
@@ -472,7 +506,8 @@ gmg_status alloc_hierarchy(gmg_handle h, std::vector<Level<T>>& lv, int levels, 
             if ((st = dev_alloc(h, &v.u[0], v.nodes)) != GMG_OK) return st;
         if (c.smoother == GMG_WJACOBI && (st = dev_alloc(h, &v.u[1], v.nodes)) != GMG_OK) return st;
         if ((st = dev_alloc(h, &v.q, v.nodes)) != GMG_OK) return st;
-        if (l + 1 < levels && (st = dev_alloc(h, &v.r, v.nodes)) != GMG_OK) return st;
+        const bool need_r = l + 1 < levels || c.smoother == GMG_LEARNED;
+        if (need_r && (st = dev_alloc(h, &v.r, v.nodes)) != GMG_OK) return st;
     }
     return GMG_OK;
 }
@@ -558,6 +593,11 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
         st = cfg->precision == GMG_FP32_IR ? alloc_hierarchy<float>(h, h->lvf, L, true)
                                            : alloc_hierarchy<bf16>(h, h->lvb, L, true);
         if (st != GMG_OK) return fail(st);
+    }
+    if (cfg->smoother == GMG_LEARNED) {
+        h->lw.assign(L, nullptr);
+        h->lz.assign(L, nullptr);
+        if ((st = dev_alloc(h, &h->lw_scratch, 2 * 8 * 27)) != GMG_OK) return fail(st);
     }
     const int np = std::max(fp64::resnorm_partials(d, cfg->n), mixed::outer_partials(d, cfg->n));
     if ((st = dev_alloc(h, &h->partial, np)) != GMG_OK) return fail(st);
@@ -650,6 +690,45 @@ gmg_status gmg_residual_norm(gmg_handle h, const double* f, double* u, double* n
     GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
     // sigma = (h^2 f - A'u) / (2d)
     *norm_out = (2.0 * c.d) * std::sqrt(*h->h_res2);
+    return GMG_OK;
+}
+
+gmg_status gmg_set_learned_weights(gmg_handle h, int level, const float* weights) {
+    if (!h) {
+        set_error("handle is NULL");
+        return GMG_ERR_ARG;
+    }
+    if (h->cfg.smoother != GMG_LEARNED) {
+        set_error("the handle was not created with smoother GMG_LEARNED");
+        return GMG_ERR_ARG;
+    }
+    if (level < 0 || level >= (int)h->lw.size()) {
+        set_error("level out of range");
+        return GMG_ERR_ARG;
+    }
+    DeviceGuard guard(h->device);
+    GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (!weights) {
+        h->lw[level] = nullptr;
+    } else {
+        gmg_status st;
+        if (!h->lz[level]) {
+            float* z = nullptr;
+            if ((st = dev_alloc(h, &z, 8 * h->lv[level].nodes)) != GMG_OK) return st;
+            h->lz[level] = z;
+        }
+        // keep a device copy per level (the pointer stays valid until destroy)
+        float* w = nullptr;
+        if ((st = dev_alloc(h, &w, 2 * 8 * 27)) != GMG_OK) return st;
+        learned::upload_weights(h->cfg.d, weights, w, h->lw_scratch, h->stream);
+        GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        h->lw[level] = w;
+    }
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+        h->graph_u = nullptr;
+    }
     return GMG_OK;
 }
 

@@ -71,4 +71,14 @@ template <typename T>
 void update(int d, int n, double* u, const T* e, cudaStream_t s);
 }  // namespace mixed
 
+// Learned-smoother network kernels (learned.cu): z = conv1(x) (8 channel
+// planes of (n+1)^d floats), out = / += / -= conv2(relu(z)) for mode 0/1/2.
+// W: 2 x 8 x 3^d BF16-rounded floats on the device.
+namespace learned {
+void conv1(int d, int n, const double* x, float* z, const float* W, cudaStream_t s);
+void conv2(int d, int n, const float* z, double* out, int mode, const float* W, cudaStream_t s);
+// dev = BF16 rounding of the host weights (scratch: 2 x 8 x 3^d device floats)
+void upload_weights(int d, const float* host, float* dev, float* scratch, cudaStream_t s);
+}  // namespace learned
+
 }  // namespace gmg

@@ -1,0 +1,722 @@
+// Learned smoother: a per-level convolutional smoother u <- u + N(sigma),
+// sigma = (b - A'u)/(2d), N = conv2(ReLU(conv1(sigma))) with conv1: 1 -> 8
+// channels and conv2: 8 -> 1 channel, 3^d taps, zero padding at the
+// Dirichlet boundary, no biases, BF16 weights with FP32 accumulation.
+//
+// Training minimises the measured two-grid error contraction
+//     L = ||S(CG(S(e0)))||^2 / ||e0||^2,  S e = e - N(A'e/(2d)),
+//     CG e = e - P A_c'^{-1} 4 FW(A'e),
+// over error samples e0 drawn from plain red-black V(1,1) cycles applied to
+// seeded white noise, with this file's forward and backward kernels and an
+// Adam step, all on the GPU.  The coarse system inside the loss is solved by
+// red-black V(2,2) cycles run to round-off.
+//
+// Weight layout (host and device): 2 x 8 x T floats, W1[c][t] then W2[c][t],
+// tap t = (c3+1)*9 + (b+1)*3 + (a+1) for the offset (a, b, c3) (x fastest);
+// T = 27 in 3D, 9 in 2D.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gmg_internal.cuh"
+#include "level_kernels.cuh"
+
+namespace gmg {
+namespace learned {
+namespace {
+
+constexpr int H = 8;  // hidden channels
+
+using lk::sy_of;
+using lk::sz_of;
+
+template <int DIM>
+constexpr int taps() {
+    return DIM == 3 ? 27 : 9;
+}
+
+template <int DIM>
+__device__ inline int64_t tap_offset(int t, int64_t sy, int64_t sz) {
+    const int a = t % 3 - 1, b = (t / 3) % 3 - 1, c = DIM == 3 ? t / 9 - 1 : 0;
+    return a + b * sy + c * sz;
+}
+
+template <int DIM>
+__device__ inline void load_weights(const float* W, float* ws) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y;
+    for (int i = tid; i < 2 * H * taps<DIM>(); i += nt) ws[i] = W[i];
+    __syncthreads();
+}
+
+// z_c(p) = sum_t W1[c][t] x(p + o_t) on interior nodes (x is zero on the
+// boundary; z's boundary entries are never written and stay zero)
+template <int DIM, typename TI>
+__global__ void __launch_bounds__(256) k_conv1(const TI* __restrict__ x, float* __restrict__ z,
+                                               int n, int64_t zs, const float* __restrict__ W) {
+    constexpr int T = taps<DIM>();
+    __shared__ float ws[2 * H * T];
+    load_weights<DIM>(W, ws);
+    const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
+    const int k = DIM == 3 ? blockIdx.y + 1 : 0;
+    if (j >= n) return;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t row = k * sz + j * sy;
+    for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t p = row + i;
+        float xv[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) xv[t] = (float)x[p + tap_offset<DIM>(t, sy, sz)];
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < T; ++t) acc = fmaf(ws[c * T + t], xv[t], acc);
+            z[c * zs + p] = acc;
+        }
+    }
+}
+
+// y(p) = sum_c sum_t W2[c][t] relu(z_c(p + o_t)); mode 0: out = y,
+// 1: out += y, 2: out -= y (out in FP64)
+template <int DIM, int MODE>
+__global__ void __launch_bounds__(256) k_conv2(const float* __restrict__ z, double* __restrict__ out,
+                                               int n, int64_t zs, const float* __restrict__ W) {
+    constexpr int T = taps<DIM>();
+    __shared__ float ws[2 * H * T];
+    load_weights<DIM>(W, ws);
+    const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
+    const int k = DIM == 3 ? blockIdx.y + 1 : 0;
+    if (j >= n) return;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t row = k * sz + j * sy;
+    const float* w2 = ws + H * T;
+    for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t p = row + i;
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < H; ++c)
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+                acc = fmaf(w2[c * T + t], fmaxf(z[c * zs + p + tap_offset<DIM>(t, sy, sz)], 0.f), acc);
+        if (MODE == 0)
+            out[p] = (double)acc;
+        else if (MODE == 1)
+            out[p] += (double)acc;
+        else
+            out[p] -= (double)acc;
+    }
+}
+
+// gz_c(p) = [z_c(p) > 0] * sum_t W2[c][t] gy(p - o_t)
+template <int DIM>
+__global__ void __launch_bounds__(256) k_conv2_bwd(const double* __restrict__ gy,
+                                                   const float* __restrict__ z,
+                                                   float* __restrict__ gz, int n, int64_t zs,
+                                                   const float* __restrict__ W) {
+    constexpr int T = taps<DIM>();
+    __shared__ float ws[2 * H * T];
+    load_weights<DIM>(W, ws);
+    const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
+    const int k = DIM == 3 ? blockIdx.y + 1 : 0;
+    if (j >= n) return;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t row = k * sz + j * sy;
+    const float* w2 = ws + H * T;
+    for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t p = row + i;
+        float gv[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) gv[t] = (float)gy[p - tap_offset<DIM>(t, sy, sz)];
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < T; ++t) acc = fmaf(w2[c * T + t], gv[t], acc);
+            gz[c * zs + p] = z[c * zs + p] > 0.f ? acc : 0.f;
+        }
+    }
+}
+
+// gx(p) = sum_c sum_t W1[c][t] gz_c(p - o_t)
+template <int DIM>
+__global__ void __launch_bounds__(256) k_conv1_bwd(const float* __restrict__ gz,
+                                                   double* __restrict__ gx, int n, int64_t zs,
+                                                   const float* __restrict__ W) {
+    constexpr int T = taps<DIM>();
+    __shared__ float ws[2 * H * T];
+    load_weights<DIM>(W, ws);
+    const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
+    const int k = DIM == 3 ? blockIdx.y + 1 : 0;
+    if (j >= n) return;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t row = k * sz + j * sy;
+    for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t p = row + i;
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < H; ++c)
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+                acc = fmaf(ws[c * T + t], gz[c * zs + p - tap_offset<DIM>(t, sy, sz)], acc);
+        gx[p] = (double)acc;
+    }
+}
+
+__device__ inline int64_t interior_node(int d, int n, int64_t idx) {
+    const int m = n - 1;
+    const int i = (int)(idx % m) + 1;
+    const int64_t t = idx / m;
+    const int j = (int)(t % m) + 1;
+    const int k = d == 3 ? (int)(t / m) + 1 : 0;
+    return ((int64_t)k * (n + 1) + j) * (n + 1) + i;
+}
+
+// Weight-gradient partials over `rpb` consecutive interior rows, one thread
+// per (channel, tap):  KIND 1: sum_p gz_c(p) x(p + o_t);  KIND 2: sum_p gy(p)
+// relu(z_c(p + o_t)).  FP32 within the block, one double per (block, c, t).
+template <int DIM, int KIND>
+__global__ void __launch_bounds__(256) k_wgrad(const double* __restrict__ dense,
+                                               const float* __restrict__ chan, int n, int64_t zs,
+                                               int rpb, double* __restrict__ partial) {
+    constexpr int T = taps<DIM>();
+    const int ct = threadIdx.x;
+    if (ct >= H * T) return;
+    const int c = ct / T, t = ct % T;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t off = tap_offset<DIM>(t, sy, sz);
+    const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < rows ? r0 + rpb : rows;
+    const float* ch = chan + c * zs;
+    float acc = 0.f;
+    for (int64_t r = r0; r < r1; ++r) {
+        const int j = (int)(r % (n - 1)) + 1;
+        const int k = DIM == 3 ? (int)(r / (n - 1)) + 1 : 0;
+        const int64_t row = k * sz + j * sy;
+        for (int i = 1; i < n; ++i) {
+            const int64_t p = row + i;
+            if (KIND == 1)
+                acc = fmaf(ch[p], (float)dense[p + off], acc);
+            else
+                acc = fmaf((float)dense[p], fmaxf(ch[p + off], 0.f), acc);
+        }
+    }
+    partial[(int64_t)blockIdx.x * (2 * H * T) + (KIND == 1 ? 0 : H * T) + ct] = (double)acc;
+}
+
+// grad[i] += scale * sum_b partial[b][i] (fixed order) for the KIND's half
+__global__ void k_wgrad_reduce(const double* __restrict__ partial, int blocks, int half, int base,
+                               const double* __restrict__ scale_dev, double sign,
+                               double* __restrict__ grad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= half) return;
+    double s = 0.0;
+    for (int b = 0; b < blocks; ++b) s += partial[(int64_t)b * 2 * half + base + i];
+    grad[base + i] += sign * scale_dev[0] * s;
+}
+
+// s = A'e/(2d) = e - c * (sum of neighbours) on interior nodes
+template <int DIM>
+__global__ void __launch_bounds__(256) k_scaled_apply(const double* __restrict__ e,
+                                                      double* __restrict__ s, int n) {
+    const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
+    const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
+    const int k = DIM == 3 ? blockIdx.y + 1 : 0;
+    if (j >= n) return;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t row = k * sz + j * sy;
+    for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t p = row + i;
+        s[p] = e[p] - c * lk::nbr_sum<DIM>(e, p, sy, sz);
+    }
+}
+
+// y = a * x + y over all nodes (a from a device scalar times a constant)
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, int64_t nodes,
+                       double a, const double* __restrict__ a_dev) {
+    const double f = a_dev ? a * a_dev[0] : a;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nodes;
+         p += (int64_t)gridDim.x * blockDim.x)
+        y[p] = fma(f, x[p], y[p]);
+}
+
+// out[0] = sum x^2 (deterministic: fixed grid, fixed trees)
+__global__ void __launch_bounds__(256) k_sumsq_partial(const double* __restrict__ x, int64_t nodes,
+                                                       double* __restrict__ partial) {
+    __shared__ double ws[8];
+    double acc = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nodes;
+         p += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(x[p], x[p], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += ws[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+// scalars: out[0] = op(partials) ; op 0: sum ; 1: 2 / sum (gradient scale) ;
+// 2: acc[0] += sum * inv_den[0] / batch (loss)
+__global__ void k_scalar(const double* __restrict__ partial, int count, int op, double batch,
+                         const double* __restrict__ inv_den, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < count; ++i) s += partial[i];
+    if (op == 0) out[0] = s;
+    if (op == 1) out[0] = 2.0 / s;
+    if (op == 2) out[0] += s * inv_den[0] * 0.5 / batch;
+}
+
+// seeded white noise U[-1,1) on interior nodes (splitmix64 of seed and index)
+__global__ void k_white_noise(double* __restrict__ e, int d, int n, uint64_t seed) {
+    const int64_t m = n - 1;
+    const int64_t total = d == 3 ? m * m * m : m * m;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(idx + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z = z ^ (z >> 31);
+        e[interior_node(d, n, idx)] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+}
+
+// Adam on the master weights; the working copy is their BF16 rounding.
+__global__ void k_adam(float* __restrict__ master, float* __restrict__ work,
+                       const double* __restrict__ grad, double* __restrict__ m1,
+                       double* __restrict__ m2, int count, int step, double lr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double b1 = 0.9, b2 = 0.999, eps = 1e-12;
+    const double g = grad[i];
+    m1[i] = b1 * m1[i] + (1 - b1) * g;
+    m2[i] = b2 * m2[i] + (1 - b2) * g * g;
+    const double mh = m1[i] / (1 - pow(b1, step));
+    const double vh = m2[i] / (1 - pow(b2, step));
+    master[i] = (float)((double)master[i] - lr * mh / (sqrt(vh) + eps));
+    work[i] = __bfloat162float(__float2bfloat16_rn(master[i]));
+}
+
+__global__ void k_round_bf16(const float* __restrict__ in, float* __restrict__ out, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = __bfloat162float(__float2bfloat16_rn(in[i]));
+}
+
+lk::RowLaunch rows(int d, int n) { return lk::row_launch(d, n, n); }
+
+int64_t nodes_of(int d, int n) {
+    const int64_t m = n + 1;
+    return d == 3 ? m * m * m : m * m;
+}
+int64_t interior_of(int d, int n) {
+    const int64_t m = n - 1;
+    return d == 3 ? m * m * m : m * m;
+}
+int flat_blocks(int64_t nodes) { return (int)std::min<int64_t>((nodes + 255) / 256, 152 * 8); }
+
+}  // namespace
+
+// --------------------------------------------------------------- launchers
+
+void conv1(int d, int n, const double* x, float* z, const float* W, cudaStream_t s) {
+    auto L = rows(d, n);
+    const int64_t zs = nodes_of(d, n);
+    if (d == 3)
+        k_conv1<3, double><<<L.grid, L.block, 0, s>>>(x, z, n, zs, W);
+    else
+        k_conv1<2, double><<<L.grid, L.block, 0, s>>>(x, z, n, zs, W);
+}
+
+void conv2(int d, int n, const float* z, double* out, int mode, const float* W, cudaStream_t s) {
+    auto L = rows(d, n);
+    const int64_t zs = nodes_of(d, n);
+    if (d == 3) {
+        if (mode == 0) k_conv2<3, 0><<<L.grid, L.block, 0, s>>>(z, out, n, zs, W);
+        if (mode == 1) k_conv2<3, 1><<<L.grid, L.block, 0, s>>>(z, out, n, zs, W);
+        if (mode == 2) k_conv2<3, 2><<<L.grid, L.block, 0, s>>>(z, out, n, zs, W);
+    } else {
+        if (mode == 0) k_conv2<2, 0><<<L.grid, L.block, 0, s>>>(z, out, n, zs, W);
+        if (mode == 1) k_conv2<2, 1><<<L.grid, L.block, 0, s>>>(z, out, n, zs, W);
+        if (mode == 2) k_conv2<2, 2><<<L.grid, L.block, 0, s>>>(z, out, n, zs, W);
+    }
+}
+
+void upload_weights(int d, const float* host, float* dev, float* scratch, cudaStream_t s) {
+    const int W = 2 * H * (d == 3 ? 27 : 9);
+    cudaMemcpyAsync(scratch, host, sizeof(float) * W, cudaMemcpyHostToDevice, s);
+    k_round_bf16<<<(W + 255) / 256, 256, 0, s>>>(scratch, dev, W);
+}
+
+namespace {
+
+void conv2_bwd(int d, int n, const double* gy, const float* z, float* gz, const float* W,
+               cudaStream_t s) {
+    auto L = rows(d, n);
+    const int64_t zs = nodes_of(d, n);
+    if (d == 3)
+        k_conv2_bwd<3><<<L.grid, L.block, 0, s>>>(gy, z, gz, n, zs, W);
+    else
+        k_conv2_bwd<2><<<L.grid, L.block, 0, s>>>(gy, z, gz, n, zs, W);
+}
+
+void conv1_bwd(int d, int n, const float* gz, double* gx, const float* W, cudaStream_t s) {
+    auto L = rows(d, n);
+    const int64_t zs = nodes_of(d, n);
+    if (d == 3)
+        k_conv1_bwd<3><<<L.grid, L.block, 0, s>>>(gz, gx, n, zs, W);
+    else
+        k_conv1_bwd<2><<<L.grid, L.block, 0, s>>>(gz, gx, n, zs, W);
+}
+
+int wgrad_rpb(int n) { return std::max(1, 2048 / (n - 1)); }
+int wgrad_blocks(int d, int n) {
+    const int64_t rows = d == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
+    return (int)((rows + wgrad_rpb(n) - 1) / wgrad_rpb(n));
+}
+
+// grad += sign * scale * (dW1 from (x, gz), dW2 from (gy, z))
+void wgrad(int d, int n, const double* x, const float* gz, const double* gy, const float* z,
+           double* partial, const double* scale_dev, double sign, double* grad, cudaStream_t s) {
+    const int T = d == 3 ? 27 : 9;
+    const int blocks = wgrad_blocks(d, n), rpb = wgrad_rpb(n);
+    const int64_t zs = nodes_of(d, n);
+    if (d == 3) {
+        k_wgrad<3, 1><<<blocks, 256, 0, s>>>(x, gz, n, zs, rpb, partial);
+        k_wgrad<3, 2><<<blocks, 256, 0, s>>>(gy, z, n, zs, rpb, partial);
+    } else {
+        k_wgrad<2, 1><<<blocks, 256, 0, s>>>(x, gz, n, zs, rpb, partial);
+        k_wgrad<2, 2><<<blocks, 256, 0, s>>>(gy, z, n, zs, rpb, partial);
+    }
+    const int half = H * T;
+    k_wgrad_reduce<<<1, 256, 0, s>>>(partial, blocks, half, 0, scale_dev, sign, grad);
+    k_wgrad_reduce<<<1, 256, 0, s>>>(partial, blocks, half, half, scale_dev, sign, grad);
+}
+
+void scaled_apply(int d, int n, const double* e, double* out, cudaStream_t s) {
+    auto L = rows(d, n);
+    if (d == 3)
+        k_scaled_apply<3><<<L.grid, L.block, 0, s>>>(e, out, n);
+    else
+        k_scaled_apply<2><<<L.grid, L.block, 0, s>>>(e, out, n);
+}
+
+// Work buffers of a training / loss evaluation on one grid.
+struct Trainer {
+    int d = 3, n = 0, T = 27, coarse_cycles = 30, pair_cycles = 1;
+    cudaStream_t s = nullptr;
+    int64_t nodes = 0;
+    double *e0 = nullptr, *e1 = nullptr, *e2 = nullptr, *e3 = nullptr;  // error states
+    double *s1 = nullptr, *s2 = nullptr, *s3 = nullptr;                 // A'e/(2d)
+    double *g = nullptr, *gx = nullptr, *w = nullptr;
+    float *z1 = nullptr, *z3 = nullptr, *gz = nullptr;
+    double *partial = nullptr, *wpart = nullptr, *scal = nullptr;  // scal: [0] 1/||e0||^2*2, [1] loss
+    double* grad = nullptr;
+    std::vector<Level<double>> coarse;  // hierarchy of the n/2 grid (coarse solve)
+    std::vector<Level<double>> pair;    // hierarchy of the n grid (sample generation)
+    std::vector<void*> allocs;
+
+    cudaError_t alloc(void** p, size_t bytes) {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) return e;
+        allocs.push_back(*p);
+        return cudaMemsetAsync(*p, 0, bytes, s);
+    }
+    void release() {
+        for (void* p : allocs) cudaFree(p);
+        allocs.clear();
+    }
+    cudaError_t hierarchy(std::vector<Level<double>>& lv, int nn) {
+        int L = 0;
+        while ((2 << L) <= nn) ++L;
+        lv.resize(L);
+        for (int l = 0; l < L; ++l) {
+            lv[l].n = nn >> l;
+            lv[l].nodes = nodes_of(d, lv[l].n);
+            const size_t b = sizeof(double) * lv[l].nodes;
+            cudaError_t e;
+            if ((e = alloc((void**)&lv[l].u[0], b)) != cudaSuccess) return e;
+            if ((e = alloc((void**)&lv[l].q, b)) != cudaSuccess) return e;
+            if (l + 1 < L && (e = alloc((void**)&lv[l].r, b)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    cudaError_t init(int d_, int n_, int cc, int pc, cudaStream_t st) {
+        d = d_;
+        n = n_;
+        T = d == 3 ? 27 : 9;
+        coarse_cycles = cc;
+        pair_cycles = pc;
+        s = st;
+        nodes = nodes_of(d, n);
+        const size_t b = sizeof(double) * nodes, bz = sizeof(float) * nodes * H;
+        cudaError_t e = cudaSuccess;
+        for (double** p : {&e0, &e1, &e2, &e3, &s1, &s2, &s3, &g, &gx, &w})
+            if (e == cudaSuccess) e = alloc((void**)p, b);
+        for (float** p : {&z1, &z3, &gz})
+            if (e == cudaSuccess) e = alloc((void**)p, bz);
+        if (e == cudaSuccess) e = alloc((void**)&partial, sizeof(double) * 152 * 8);
+        if (e == cudaSuccess)
+            e = alloc((void**)&wpart, sizeof(double) * wgrad_blocks(d, n) * 2 * H * T);
+        if (e == cudaSuccess) e = alloc((void**)&scal, sizeof(double) * 4);
+        if (e == cudaSuccess) e = alloc((void**)&grad, sizeof(double) * 2 * H * T);
+        if (e == cudaSuccess) e = hierarchy(coarse, n / 2);
+        if (e == cudaSuccess) e = hierarchy(pair, n);
+        return e;
+    }
+
+    // RB-GS V(nu,nu) cycle on hierarchy lv (level-0 iterate lv[0].u[0], rhs lv[0].q)
+    void vcycle(std::vector<Level<double>>& lv, int nu) {
+        const int L = (int)lv.size();
+        for (int l = 0; l + 1 < L; ++l) {
+            for (int k = 0; k < nu; ++k)
+                for (int c = 0; c < 2; ++c) lk::rb_half<double>(d, lv[l].n, lv[l].u[0], lv[l].q, c, s);
+            lk::residual<double>(d, lv[l].n, lv[l].u[0], lv[l].q, lv[l].r, nu > 0, s);
+            lk::restrict_fw<double>(d, lv[l].n, lv[l].r, lv[l + 1].q, lv[l + 1].u[0], nu > 0,
+                                    lv[l + 1].n == 2, s);
+        }
+        if (L == 1)
+            for (int k = 0; k < nu; ++k)
+                for (int c = 0; c < 2; ++c) lk::rb_half<double>(d, lv[0].n, lv[0].u[0], lv[0].q, c, s);
+        for (int l = L - 2; l >= 0; --l) {
+            lk::prolong_add<double>(d, lv[l + 1].n, lv[l + 1].u[0], lv[l].u[0], s);
+            for (int k = 0; k < nu; ++k)
+                for (int c = 0; c < 2; ++c) lk::rb_half<double>(d, lv[l].n, lv[l].u[0], lv[l].q, c, s);
+        }
+    }
+
+    // u_c = (2d) A_c'^{-1} q_c with q_c = 4 FW(src) restricted from src (fine)
+    void coarse_solve_of(double* src) {
+        Level<double>& C = coarse[0];
+        // restrict_fw writes q_c and zeroes u_c (or u_c = q_c on a one-unknown grid)
+        lk::restrict_fw<double>(d, n, src, C.q, C.u[0], false, C.n == 2, s);
+        if (C.n > 2)
+            for (int k = 0; k < coarse_cycles; ++k) vcycle(coarse, 2);
+    }
+
+    // e_out = e_in - P u_c (error-form coarse-grid correction), s2 = A'e_in/(2d)
+    void cgc(const double* e_in, double* e_out) {
+        scaled_apply(d, n, e_in, s2, s);
+        coarse_solve_of(s2);
+        cudaMemcpyAsync(e_out, e_in, sizeof(double) * nodes, cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(w, 0, sizeof(double) * nodes, s);
+        lk::prolong_add<double>(d, coarse[0].n, coarse[0].u[0], w, s);
+        k_axpy<<<flat_blocks(nodes), 256, 0, s>>>(e_out, w, nodes, -1.0, nullptr);
+    }
+
+    // g <- g - (A'/(2d)) P u_c' with u_c' = (2d) A_c'^{-1} 4FW(g)
+    void cgc_adjoint(double* gg) {
+        coarse_solve_of(gg);
+        cudaMemsetAsync(w, 0, sizeof(double) * nodes, s);
+        lk::prolong_add<double>(d, coarse[0].n, coarse[0].u[0], w, s);
+        scaled_apply(d, n, w, gx, s);
+        k_axpy<<<flat_blocks(nodes), 256, 0, s>>>(gg, gx, nodes, -1.0, nullptr);
+    }
+
+    // e_out = e_in - N(s_in), s_in = A'e_in/(2d), keeping z
+    void smooth(const double* e_in, double* s_in, float* z, double* e_out, const float* W) {
+        scaled_apply(d, n, e_in, s_in, s);
+        conv1(d, n, s_in, z, W, s);
+        cudaMemcpyAsync(e_out, e_in, sizeof(double) * nodes, cudaMemcpyDeviceToDevice, s);
+        conv2(d, n, z, e_out, 2, W, s);
+    }
+
+    void sumsq(const double* x, int op, double batch) {
+        const int blocks = flat_blocks(nodes);
+        k_sumsq_partial<<<blocks, 256, 0, s>>>(x, nodes, partial);
+        k_scalar<<<1, 32, 0, s>>>(partial, blocks, op, batch, scal, op == 2 ? scal + 1 : scal);
+    }
+
+    // loss (accumulated into scal[1] / batch) and, if want_grad, its
+    // gradient (accumulated into grad / batch) for the sample in e0
+    void loss_grad(const float* W, double batch, bool want_grad) {
+        smooth(e0, s1, z1, e1, W);
+        cgc(e1, e2);
+        smooth(e2, s3, z3, e3, W);
+        sumsq(e0, 1, batch);         // scal[0] = 2 / ||e0||^2
+        sumsq(e3, 2, batch);         // scal[1] += ||e3||^2 / ||e0||^2 / batch
+        if (!want_grad) return;
+        // g3 = 2 e3 / ||e0||^2 (scaled by 1/batch in the weight reduction)
+        cudaMemsetAsync(g, 0, sizeof(double) * nodes, s);
+        k_axpy<<<flat_blocks(nodes), 256, 0, s>>>(g, e3, nodes, 1.0, scal);
+        // post-smoother: dtheta -= J^T g ; g2 = g - (A'/(2d)) J_x^T g
+        conv2_bwd(d, n, g, z3, gz, W, s);
+        wgrad(d, n, s3, gz, g, z3, wpart, scal + 2, -1.0, grad, s);
+        conv1_bwd(d, n, gz, gx, W, s);
+        scaled_apply(d, n, gx, w, s);
+        k_axpy<<<flat_blocks(nodes), 256, 0, s>>>(g, w, nodes, -1.0, nullptr);
+        // coarse-grid correction adjoint
+        cgc_adjoint(g);
+        // pre-smoother weight gradient
+        conv2_bwd(d, n, g, z1, gz, W, s);
+        wgrad(d, n, s1, gz, g, z1, wpart, scal + 2, -1.0, grad, s);
+    }
+
+    // e0 = error after pair_cycles plain RB-GS V(1,1) cycles from white noise
+    void sample(uint64_t seed) {
+        Level<double>& F = pair[0];
+        k_white_noise<<<flat_blocks(interior_of(d, n)), 256, 0, s>>>(F.u[0], d, n, seed);
+        for (int k = 0; k < pair_cycles; ++k) vcycle(pair, 1);
+        cudaMemcpyAsync(e0, F.u[0], sizeof(double) * nodes, cudaMemcpyDeviceToDevice, s);
+    }
+};
+
+gmg_status check_dn(int d, int n) {
+    if (d != 2 && d != 3) {
+        set_error("d must be 2 or 3");
+        return GMG_ERR_ARG;
+    }
+    const int nmax = d == 3 ? 512 : 4096;
+    if (n < 4 || n > nmax || (n & (n - 1))) {
+        set_error("n must be a power of two in [4, " + std::to_string(nmax) + "]");
+        return GMG_ERR_ARG;
+    }
+    return GMG_OK;
+}
+
+}  // namespace
+}  // namespace learned
+}  // namespace gmg
+
+using namespace gmg;
+using namespace gmg::learned;
+
+#define GMG_TRY_CUDA_RELEASE(expr, tr)                                             \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));        \
+            (tr).release();                                                        \
+            return e_ == cudaErrorMemoryAllocation ? GMG_ERR_ALLOC : GMG_ERR_CUDA; \
+        }                                                                          \
+    } while (0)
+
+extern "C" {
+
+gmg_status gmg_learned_conv(int d, int n, const float* weights, const double* x, double* y,
+                            void* cuda_stream) {
+    gmg_status st = check_dn(d, n);
+    if (st != GMG_OK) return st;
+    if (!weights || !x || !y) {
+        set_error("weights, x, y must be non-NULL");
+        return GMG_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int T = d == 3 ? 27 : 9;
+    float *wd = nullptr, *wr = nullptr, *z = nullptr;
+    const int64_t nodes = nodes_of(d, n);
+    GMG_CUDA_TRY(cudaMalloc(&wd, sizeof(float) * 2 * H * T * 2));
+    wr = wd + 2 * H * T;
+    cudaError_t e = cudaMalloc(&z, sizeof(float) * H * nodes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(z, 0, sizeof(float) * H * nodes, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(wd, weights, sizeof(float) * 2 * H * T, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_round_bf16<<<(2 * H * T + 255) / 256, 256, 0, s>>>(wd, wr, 2 * H * T);
+        conv1(d, n, x, z, wr, s);
+        conv2(d, n, z, y, 0, wr, s);
+        e = cudaStreamSynchronize(s);
+    }
+    cudaFree(wd);
+    cudaFree(z);
+    if (e != cudaSuccess) {
+        set_error(std::string("gmg_learned_conv: ") + cudaGetErrorString(e));
+        return GMG_ERR_CUDA;
+    }
+    return GMG_OK;
+}
+
+gmg_status gmg_learned_loss_grad(int d, int n, const float* weights, const double* e0,
+                                 int coarse_cycles, double* loss_out, double* grad_out,
+                                 void* cuda_stream) {
+    gmg_status st = check_dn(d, n);
+    if (st != GMG_OK) return st;
+    if (!weights || !e0 || !loss_out || coarse_cycles < 1) {
+        set_error("weights, e0, loss_out must be non-NULL and coarse_cycles >= 1");
+        return GMG_ERR_ARG;
+    }
+    Trainer tr;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    GMG_TRY_CUDA_RELEASE(tr.init(d, n, coarse_cycles, 0, s), tr);
+    const int W = 2 * H * tr.T;
+    float* wd = nullptr;
+    GMG_TRY_CUDA_RELEASE(tr.alloc((void**)&wd, sizeof(float) * 2 * W), tr);
+    GMG_TRY_CUDA_RELEASE(cudaMemcpyAsync(wd, weights, sizeof(float) * W, cudaMemcpyHostToDevice, s),
+                         tr);
+    k_round_bf16<<<(W + 255) / 256, 256, 0, s>>>(wd, wd + W, W);
+    GMG_TRY_CUDA_RELEASE(cudaMemcpyAsync(tr.e0, e0, sizeof(double) * tr.nodes,
+                                         cudaMemcpyDeviceToDevice, s),
+                         tr);
+    // scal[2] = 1 (the batch scale of the weight-gradient reduction)
+    const double one = 1.0;
+    GMG_TRY_CUDA_RELEASE(cudaMemcpyAsync(tr.scal + 2, &one, sizeof(double), cudaMemcpyHostToDevice, s),
+                         tr);
+    tr.loss_grad(wd + W, 1.0, grad_out != nullptr);
+    double sc[2];
+    GMG_TRY_CUDA_RELEASE(cudaMemcpyAsync(sc, tr.scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, s),
+                         tr);
+    if (grad_out)
+        GMG_TRY_CUDA_RELEASE(cudaMemcpyAsync(grad_out, tr.grad, sizeof(double) * W,
+                                             cudaMemcpyDeviceToHost, s),
+                             tr);
+    GMG_TRY_CUDA_RELEASE(cudaStreamSynchronize(s), tr);
+    *loss_out = sc[1];
+    tr.release();
+    return GMG_OK;
+}
+
+gmg_status gmg_learned_train(int d, int n, int steps, int batch, int pair_cycles, int coarse_cycles,
+                             double lr, uint64_t seed, const float* w_init, float* w_out,
+                             double* loss_history, void* cuda_stream) {
+    gmg_status st = check_dn(d, n);
+    if (st != GMG_OK) return st;
+    if (steps < 1 || steps > 1000000 || batch < 1 || batch > 4096 || pair_cycles < 0 ||
+        pair_cycles > 16 || coarse_cycles < 1 || coarse_cycles > 200 || !(lr > 0.0) || !w_init ||
+        !w_out) {
+        set_error("gmg_learned_train: bad arguments");
+        return GMG_ERR_ARG;
+    }
+    Trainer tr;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    GMG_TRY_CUDA_RELEASE(tr.init(d, n, coarse_cycles, pair_cycles, s), tr);
+    const int W = 2 * H * tr.T;
+    float *master = nullptr, *work = nullptr;
+    double *m1 = nullptr, *m2 = nullptr;
+    GMG_TRY_CUDA_RELEASE(tr.alloc((void**)&master, sizeof(float) * W), tr);
+    GMG_TRY_CUDA_RELEASE(tr.alloc((void**)&work, sizeof(float) * W), tr);
+    GMG_TRY_CUDA_RELEASE(tr.alloc((void**)&m1, sizeof(double) * W), tr);
+    GMG_TRY_CUDA_RELEASE(tr.alloc((void**)&m2, sizeof(double) * W), tr);
+    GMG_TRY_CUDA_RELEASE(cudaMemcpyAsync(master, w_init, sizeof(float) * W, cudaMemcpyHostToDevice, s),
+                         tr);
+    k_round_bf16<<<(W + 255) / 256, 256, 0, s>>>(master, work, W);
+    const double inv_batch = 1.0 / batch;
+    GMG_TRY_CUDA_RELEASE(cudaMemcpyAsync(tr.scal + 2, &inv_batch, sizeof(double),
+                                         cudaMemcpyHostToDevice, s),
+                         tr);
+    std::vector<double> hloss(1);
+    for (int it = 0; it < steps; ++it) {
+        cudaMemsetAsync(tr.grad, 0, sizeof(double) * W, s);
+        cudaMemsetAsync(tr.scal + 1, 0, sizeof(double), s);
+        for (int b = 0; b < batch; ++b) {
+            tr.sample(seed * 1000003ull + (uint64_t)it * 4096ull + (uint64_t)b);
+            tr.loss_grad(work, (double)batch, true);
+        }
+        k_adam<<<(W + 255) / 256, 256, 0, s>>>(master, work, tr.grad, m1, m2, W, it + 1, lr);
+        if (loss_history) {
+            GMG_TRY_CUDA_RELEASE(cudaMemcpyAsync(&loss_history[it], tr.scal + 1, sizeof(double),
+                                                 cudaMemcpyDeviceToHost, s),
+                                 tr);
+        }
+    }
+    GMG_TRY_CUDA_RELEASE(cudaMemcpyAsync(w_out, master, sizeof(float) * W, cudaMemcpyDeviceToHost, s),
+                         tr);
+    GMG_TRY_CUDA_RELEASE(cudaStreamSynchronize(s), tr);
+    tr.release();
+    return GMG_OK;
+}
+
+}  // extern "C"

@@ -76,6 +76,10 @@ SIGNATURES = {
     "gmg_batch_timing_report": ([P, ctypes.POINTER(KernelStat), I, PI,
                                  ctypes.POINTER(ctypes.c_int64)], I),
     "gmg_batch_destroy": ([P], I),
+    "gmg_set_learned_weights": ([P, I, P], I),
+    "gmg_learned_conv": ([I, I, P, P, P, P], I),
+    "gmg_learned_loss_grad": ([I, I, P, P, I, PD, PD, P], I),
+    "gmg_learned_train": ([I, I, I, I, I, I, D, ctypes.c_uint64, P, P, PD, P], I),
 }
 
 
@@ -191,6 +195,17 @@ class Solver:
     def set_timing(self, enable: bool = True):
         _check(lib().gmg_set_timing(self._h, 1 if enable else 0))
 
+    def set_learned_weights(self, level: int, weights):
+        """weights: float32 array (2, 8, 3^d) or None (red-black GS on this level)."""
+        import numpy as np
+        if weights is None:
+            _check(lib().gmg_set_learned_weights(self._h, level, None))
+            return
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        if w.size != 2 * 8 * (27 if self.d == 3 else 9):
+            raise ValueError("weights must hold 2 x 8 x 3^d floats")
+        _check(lib().gmg_set_learned_weights(self._h, level, ctypes.c_void_p(w.ctypes.data)))
+
     def timing_reset(self):
         _check(lib().gmg_timing_reset(self._h))
 
@@ -301,3 +316,61 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ------------------------------------------------------------ learned smoother
+
+def learned_taps(d: int) -> int:
+    return 27 if d == 3 else 9
+
+
+def jacobi_weights(d: int, omega: float):
+    """Weights with relu(x) - relu(-x) = x: the network is omega * sigma
+    (weighted Jacobi), the starting point of training."""
+    import numpy as np
+    T = learned_taps(d)
+    w = np.zeros((2, 8, T), np.float32)
+    w[0, 0, T // 2], w[0, 1, T // 2] = 1.0, -1.0
+    w[1, 0, T // 2], w[1, 1, T // 2] = omega, -omega
+    return w
+
+
+def learned_conv(weights, x):
+    """y = N(x) for a float64 CUDA tensor x (all nodes, zero boundary)."""
+    import numpy as np
+    import torch
+    d = x.dim()
+    n = x.shape[0] - 1
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    y = torch.zeros_like(x)
+    _check(lib().gmg_learned_conv(d, n, ctypes.c_void_p(w.ctypes.data), _dptr(x, "x", d, n),
+                                  _dptr(y, "y", d, n), _stream_ptr(None)))
+    return y
+
+
+def learned_loss_grad(weights, e0, coarse_cycles: int = 30, want_grad: bool = True):
+    """(loss, grad (2, 8, T) float64 or None) of the two-grid contraction."""
+    import numpy as np
+    d = e0.dim()
+    n = e0.shape[0] - 1
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    loss = ctypes.c_double(0.0)
+    g = np.zeros((2, 8, learned_taps(d)))
+    _check(lib().gmg_learned_loss_grad(
+        d, n, ctypes.c_void_p(w.ctypes.data), _dptr(e0, "e0", d, n), coarse_cycles,
+        ctypes.byref(loss), g.ctypes.data_as(PD) if want_grad else None, _stream_ptr(None)))
+    return loss.value, (g if want_grad else None)
+
+
+def learned_train(d: int, n: int, steps: int, batch: int, w_init, lr: float = 1e-3,
+                  pair_cycles: int = 1, coarse_cycles: int = 12, seed: int = 100):
+    """Train on the GPU; returns (weights (2, 8, T) float32, loss history)."""
+    import numpy as np
+    w0 = np.ascontiguousarray(w_init, dtype=np.float32)
+    out = np.zeros_like(w0)
+    hist = np.zeros(steps)
+    _check(lib().gmg_learned_train(d, n, steps, batch, pair_cycles, coarse_cycles, lr, seed,
+                                   ctypes.c_void_p(w0.ctypes.data),
+                                   ctypes.c_void_p(out.ctypes.data), hist.ctypes.data_as(PD),
+                                   _stream_ptr(None)))
+    return out, hist

@@ -51,7 +51,7 @@ def test_config_defaults(L):
 
 @pytest.mark.parametrize("field,value,status", [
     ("d", 4, 1), ("n", 100, 1), ("n", 1, 1), ("levels", 9, 1), ("smoother", 7, 1),
-    ("smoother", 2, 8), ("omega", 2.5, 1), ("nu1", -1, 1), ("nu2", 17, 1), ("cycle", 1, 1),
+    ("omega", 2.5, 1), ("nu1", -1, 1), ("nu2", 17, 1), ("cycle", 1, 1),
     ("maxit", -3, 1), ("precision", 9, 8),
 ])
 def test_bad_config_rejected_before_device_use(L, field, value, status):
@@ -76,3 +76,22 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gmg, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         gmg.lib()
+
+
+def test_learned_smoother_needs_fp64(L):
+    c = gmg.Config()
+    L.gmg_config_init(ctypes.byref(c), 3, 64)
+    c.smoother = 2
+    c.precision = 1
+    h = ctypes.c_void_p()
+    assert L.gmg_create(ctypes.byref(c), None, ctypes.byref(h)) == 8
+    assert b"FP64" in L.gmg_last_error()
+
+
+def test_learned_calls_reject_bad_sizes(L):
+    w = (ctypes.c_float * (2 * 8 * 27))()
+    assert L.gmg_learned_conv(4, 16, w, None, None, None) == 1
+    assert L.gmg_learned_conv(3, 12, w, None, None, None) == 1
+    loss = ctypes.c_double()
+    assert L.gmg_learned_loss_grad(3, 2, w, None, 10, ctypes.byref(loss), None, None) == 1
+    assert L.gmg_learned_train(3, 64, 0, 1, 1, 10, 1e-3, 1, w, w, None, None) == 1

@@ -358,3 +358,27 @@ def test_learned_loss_is_two_grid_contraction(d, n, omega):
     loss = oracle.learned_loss(W1, W2, dm.from_vec(e0, d, n), coarse_cycles=40)
     E = dm.vcycle_error_matrix(d, n, 2, 0, float(np.float32(omega)), 1, 1, 1000)
     assert loss == pytest.approx(np.sum((E @ e0) ** 2) / np.sum(e0 ** 2), rel=1e-10)
+
+
+@pytest.mark.parametrize("d,n,omega", [(2, 16, 0.8), (3, 8, 6 / 7)])
+def test_learned_vcycle_with_jacobi_weights_is_wj_vcycle(d, n, omega):
+    """With the Jacobi weights on every level the learned V-cycle is the
+    weighted-Jacobi V-cycle: equals the dense cycle operator."""
+    W1, W2 = _jacobi_weights(d, omega)
+    w = np.stack([W1, W2])
+    L = oracle.max_levels(n)
+    cfg = oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 1, 1, 1)
+    rng = np.random.default_rng(11)
+    u0 = rng.standard_normal((n - 1) ** d)
+    b = rng.standard_normal((n - 1) ** d)
+    u = dm.from_vec(u0, d, n)
+    oracle.vcycle_learned(cfg, [w] * L, dm.from_vec(b, d, n), u)
+    E = dm.vcycle_error_matrix(d, n, L, 0, float(np.float32(omega)), 1, 1, 1)
+    ref = E @ u0 + (np.eye(len(u0)) - E) @ np.linalg.solve(dm.lap(d, n), b)
+    np.testing.assert_allclose(dm.to_vec(u), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+    # no weights anywhere: the red-black V(1,1) cycle
+    u = dm.from_vec(u0, d, n)
+    oracle.vcycle_learned(cfg, [None] * L, dm.from_vec(b, d, n), u)
+    E = dm.vcycle_error_matrix(d, n, L, 1, 0.8, 1, 1, 1)
+    ref = E @ u0 + (np.eye(len(u0)) - E) @ np.linalg.solve(dm.lap(d, n), b)
+    np.testing.assert_allclose(dm.to_vec(u), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
