@@ -4,7 +4,8 @@
   evaluation of the same (BF16-representable) weights: <= 2e-6 relative
   (about 30 FP32 roundoffs of the largest term);
 * two-grid loss and its gradient: loss within 1e-5, gradient against central
-  finite differences of the oracle's FP64 loss within 2e-3 (FP32 backward);
+  finite differences of the oracle's FP64 loss within 2e-3 relative or
+  3e-4 of the gradient's scale (the backward runs in FP32);
 * one learned V-cycle vs the oracle's learned V-cycle: <= 1e-5 relative;
 * training lowers the loss, the learned cycle solves to an FP64 relative
   residual of 1e-10, and a trained network contracts more per cycle than its
@@ -73,22 +74,28 @@ def test_loss_and_gradient_match_oracle(torch_cuda, d, n):
     assert loss == pytest.approx(lo, rel=1e-5)
 
     def L(wp):
-        wp = wp.astype(np.float32)
         return oracle.learned_loss(wp[0].copy(), wp[1].copy(), e0, 30)
 
-    # directional derivative along a random direction, and single entries
+    # central differences with the float32 displacement actually applied (a
+    # small step keeps them from crossing ReLU kinks): along random directions
+    # and along single weights
     for _ in range(3):
-        v = rng.standard_normal(w.shape).astype(np.float32)
-        h = 1e-3
-        fd = (L(w + h * v) - L(w - h * v)) / (2 * h)
-        assert np.sum(g * v) == pytest.approx(fd, rel=2e-3, abs=1e-6)
+        v = rng.standard_normal(w.shape)
+        wp = (w + 1e-4 * v).astype(np.float32)
+        wm = (w - 1e-4 * v).astype(np.float32)
+        dw = wp.astype(np.float64) - wm.astype(np.float64)
+        pred = np.sum(g * dw)
+        # the backward runs in FP32: its error scales with |g| |dw|, not with
+        # the (cancelling) directional derivative itself
+        assert pred == pytest.approx(L(wp) - L(wm), rel=2e-3,
+                                     abs=3e-4 * np.linalg.norm(g) * np.linalg.norm(dw))
     for _ in range(6):
         idx = tuple(rng.integers(0, s) for s in w.shape)
-        v = np.zeros_like(w)
-        v[idx] = 1.0
-        h = 1e-3
-        fd = (L(w + h * v) - L(w - h * v)) / (2 * h)
-        assert g[idx] == pytest.approx(fd, rel=2e-3, abs=2e-5)
+        wp, wm = w.copy(), w.copy()
+        wp[idx] += np.float32(2.0 ** -12)
+        wm[idx] -= np.float32(2.0 ** -12)
+        fd = (L(wp) - L(wm)) / (float(wp[idx]) - float(wm[idx]))
+        assert g[idx] == pytest.approx(fd, rel=2e-3, abs=3e-4 * np.max(np.abs(g)))
 
 
 @pytest.mark.parametrize("d,n", [(3, 32), (2, 64)])
