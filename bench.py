@@ -257,6 +257,58 @@ def run_batch(torch, args):
             "dominant_share": share, "gpu_launches": launches}
 
 
+def run_learned(torch, args):
+    """3D 257^3 GRF workload (power ~|k|^-2, seed 5): V(1,1) cycles with the
+    learned smoother (trained here on the GPU on 10k error samples from plain
+    V-cycles on 65^3 and 129^3 grids, kept per level only where it beats
+    red-black GS) vs plain FP64 red-black V(1,1) and V(2,2)."""
+    from paper_1208_4247_gb300 import inputs
+    from paper_1208_4247_gb300 import learned_setup as ls
+    from paper_1208_4247_gb300.gmg import Solver, jacobi_weights
+    d, n = 3, 256
+    dof = (n - 1) ** d
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sizes = ((64, args.train_steps65, 8), (128, args.train_steps129, 8))
+    weights, hist = ls.train_weights(d, sizes=sizes)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    f = torch.from_numpy(inputs.rhs_grf(d, n, 5)).cuda()
+    u = torch.zeros_like(f)
+    levels = 8
+    cand = {l: weights[128] if l < 2 else weights[64] for l in range(6)}
+    S = Solver(d, n, smoother="learned", nu1=1, nu2=1)
+    kept, rho_rb, rho_learned, trace = ls.select_levels(S, f, u, cand, levels)
+    for l in kept:
+        S.set_learned_weights(l, jacobi_weights(d, 6.0 / 7.0))
+    rho_untrained = ls.contraction(S, f, u) if kept else None
+    for l in kept:
+        S.set_learned_weights(l, cand[l])
+    out = {"workload": "3D 257^3, f = Gaussian random field (power ~|k|^-2, unit RMS, seed 5), "
+                       "FP64 V(1,1), learned smoother on the kept levels, to relative residual 1e-10",
+           "training": {"pairs": sum(st * b for _, st, b in sizes), "grids": [s_[0] for s_ in sizes],
+                        "seconds": train_s,
+                        "loss_first_last": {str(k): [float(np.mean(v[:10])), float(np.mean(v[-10:]))]
+                                            for k, v in hist.items()}},
+           "levels_kept": kept, "selection_trace": trace,
+           "contraction": {"rbgs_v11": rho_rb, "learned_v11": rho_learned,
+                           "untrained_jacobi_start_v11": rho_untrained}}
+    runs = {}
+    for name, solver in (("learned_v11", S), ("rbgs_v11", Solver(d, n, nu1=1, nu2=1)),
+                         ("rbgs_v22", Solver(d, n, nu1=2, nu2=2))):
+        ms, it, rel, stats, launches = time_solves(torch, solver, f, u, args.form_steps, 1)
+        res = solver.residual_norm(f, u)
+        runs[name] = {"value": dof / (ms * 1e-3), "unit": "DOF/s", "ms_per_step": ms,
+                      "cycles": it, "relres": rel, "fp64_residual_norm": res,
+                      "dominant_kernel": dominant(stats)[0]}
+        solver.close()
+    out["runs"] = runs
+    out["speedup_learned_vs_rbgs_v22"] = runs["rbgs_v22"]["ms_per_step"] / runs["learned_v11"]["ms_per_step"]
+    del f, u
+    torch.cuda.empty_cache()
+    return out
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -416,10 +468,11 @@ def run_ours(args, rank, ws, local):
 
     if rank != 0:
         return
-    forms = batch = None
+    forms = batch = learned = None
     if not args.no_forms:
         forms = run_forms(torch, args)
         batch = run_batch(torch, args)
+        learned = run_learned(torch, args)
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -440,7 +493,8 @@ def run_ours(args, rank, ws, local):
                        "l2": "inputs larger than L2 (u, q, r: 3 x 136 MB at level 0)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks, "mixed_precision_513": forms, "batched_512": batch}
+            "gpu_launches": launches, "clocks": clocks, "mixed_precision_513": forms, "batched_512": batch,
+            "learned_257": learned}
     if args.kernels:
         line["kernels"] = stats
     print(json.dumps(line), flush=True)
@@ -458,6 +512,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the 513^3 precision forms")
     ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--train-steps65", type=int, default=1000)
+    ap.add_argument("--train-steps129", type=int, default=250)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
