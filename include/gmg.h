@@ -173,13 +173,18 @@ gmg_status gmg_timing_reset(gmg_handle h);
 
 /* Use weights (host, layout above; NULL = red-black GS) on `level` of a handle
  * created with smoother GMG_LEARNED (precision GMG_FP64).  Levels without
- * weights smooth with red-black GS.  Re-captures the cycle graph. */
+ * weights smooth with red-black GS.  A learned sweep is the FP64 residual
+ * then the fused tensor-core network (gmg_learned_conv, tensor_cores = 1)
+ * added to u.  Re-captures the cycle graph. */
 gmg_status gmg_set_learned_weights(gmg_handle h, int level, const float* weights);
 
-/* y = N(x) on a 2D/3D grid of n intervals (x, y: device FP64, all nodes;
- * x zero on the boundary).  Synchronises cuda_stream. */
+/* y = N(x) on the interior nodes of a 2D/3D grid of n intervals (x, y:
+ * device FP64, all nodes; x zero on the boundary).  tensor_cores = 0: CUDA-
+ * core kernels with FP32 activations (the training path); 1: the fused
+ * tensor-core kernel the V-cycle uses (BF16 x and hidden activations,
+ * mma.sync m16n8k16, FP32 sums).  Synchronises cuda_stream. */
 gmg_status gmg_learned_conv(int d, int n, const float* weights, const double* x, double* y,
-                            void* cuda_stream);
+                            int tensor_cores, void* cuda_stream);
 
 /* Two-grid contraction loss L = ||S(CG(S(e0)))||^2 / ||e0||^2 of the error e0
  * (device FP64, all nodes, zero boundary) on a grid of n intervals, with

@@ -71,6 +71,8 @@ def lib():
                 ("orc_cgc_error", [I, I, P, I], None),
                 ("orc_learned_loss", [I, I, P, P, P, I], D),
                 ("orc_learned_relax", [I, I, P, P, P, P], None),
+                ("orc_conv_fwd_bf16", [I, I, P, P, P, P], None),
+                ("orc_set_bf16_activations", [I], None),
                 ("orc_vcycle_learned", [ctypes.POINTER(Cfg), P, P, P], I),
             ]:
                 fn = getattr(L, name)
@@ -231,11 +233,22 @@ def learned_relax(W1, W2, b, u):
     return u
 
 
-def vcycle_learned(cfg: Cfg, weights, b, u):
-    """weights: list (one per level) of float32 arrays (2, 8, T) or None."""
+def conv_fwd_bf16(W1, W2, x):
+    """The network with BF16 operands (x and relu(z) rounded to BF16)."""
+    d, n = _dn(x)
+    y = np.empty_like(x)
+    lib().orc_conv_fwd_bf16(d, n, _pf(W1), _pf(W2), _p(x), _p(y))
+    return y
+
+
+def vcycle_learned(cfg: Cfg, weights, b, u, bf16_activations=False):
+    """weights: list (one per level) of float32 arrays (2, 8, T) or None.
+    bf16_activations: evaluate the network with BF16 operands."""
+    lib().orc_set_bf16_activations(1 if bf16_activations else 0)
     arrs = [None if w is None else np.ascontiguousarray(w, dtype=np.float32) for w in weights]
     ptrs = (ctypes.c_void_p * len(arrs))(*[None if a is None else a.ctypes.data for a in arrs])
     rc = lib().orc_vcycle_learned(ctypes.byref(cfg), ptrs, _p(b), _p(u))
+    lib().orc_set_bf16_activations(0)
     if rc != 0:
         raise ValueError("oracle learned V-cycle: bad configuration")
     return u

@@ -542,7 +542,60 @@ double orc_learned_loss(int d, int n, const float* W1, const float* W2, const do
     return (num * num) / (den * den);
 }
 
+/* Round to float (nearest) and then to BF16 (nearest, ties to even). */
+static double bf16(double v)
+{
+    float f = (float)v;
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    b = (b + 0x7FFFu + ((b >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &b, 4);
+    return (double)f;
+}
+
+/* The network with BF16 operands: x and relu(z) rounded to BF16 before each
+ * convolution (the weights are given BF16-representable), exact sums. */
+void orc_conv_fwd_bf16(int d, int n, const float* W1, const float* W2, const double* x,
+                       double* y)
+{
+    int64_t m = nodes(d, n);
+    int T = ntaps(d);
+    double* xr = (double*)malloc(sizeof(double) * m);
+    double* z = (double*)calloc(m * ORC_HID, sizeof(double));
+    for (int64_t p = 0; p < m; ++p) xr[p] = bf16(x[p]);
+    for (int ch = 0; ch < ORC_HID; ++ch)
+        for (int k = kmin(d); k <= kmax(d, n); ++k)
+            for (int j = 1; j < n; ++j)
+                for (int i = 1; i < n; ++i) {
+                    double s = 0.0;
+                    for (int t = 0; t < T; ++t) {
+                        int a, b, c;
+                        tap_off(d, t, &a, &b, &c);
+                        s = s + (double)W1[ch * T + t] * val(xr, d, n, i + a, j + b, k + c);
+                    }
+                    z[ch * m + IDX(n, i, j, k)] = bf16(s > 0.0 ? s : 0.0);
+                }
+    memset(y, 0, sizeof(double) * m);
+    for (int k = kmin(d); k <= kmax(d, n); ++k)
+        for (int j = 1; j < n; ++j)
+            for (int i = 1; i < n; ++i) {
+                double s = 0.0;
+                for (int ch = 0; ch < ORC_HID; ++ch)
+                    for (int t = 0; t < T; ++t) {
+                        int a, b, c;
+                        tap_off(d, t, &a, &b, &c);
+                        s = s + (double)W2[ch * T + t] * val(z + ch * m, d, n, i + a, j + b, k + c);
+                    }
+                y[IDX(n, i, j, k)] = s;
+            }
+    free(xr);
+    free(z);
+}
+
 /* One learned smoothing step on a level: u <- u + N((b - A'u)/(2d)). */
+static int g_bf16_act = 0;
+void orc_set_bf16_activations(int on) { g_bf16_act = on; }
+
 void orc_learned_relax(int d, int n, const float* W1, const float* W2, const double* b,
                        double* u)
 {
@@ -551,7 +604,10 @@ void orc_learned_relax(int d, int n, const float* W1, const float* W2, const dou
     double* y = (double*)malloc(sizeof(double) * m);
     orc_residual(d, n, b, u, r);
     for (int64_t p = 0; p < m; ++p) r[p] = r[p] / (2.0 * d);
-    orc_conv_fwd(d, n, W1, W2, r, NULL, y);
+    if (g_bf16_act)
+        orc_conv_fwd_bf16(d, n, W1, W2, r, y);
+    else
+        orc_conv_fwd(d, n, W1, W2, r, NULL, y);
     for (int64_t p = 0; p < m; ++p) u[p] = u[p] + y[p];
     free(r);
     free(y);

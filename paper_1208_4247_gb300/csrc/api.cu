@@ -171,7 +171,7 @@ enum Kind {
 };
 const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restrict",
                                   "prolong_add", "resnorm",  "copy",     "outer_residual",
-                                  "update",      "memset",   "conv1",    "conv2_update"};
+                                  "update",      "memset",   "conv1",    "conv_tc_update"};
 const char* kPrecSuffix[3] = {"", "_f32", "_bf16"};
 
 template <typename T>
@@ -209,7 +209,7 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
         case K_UPDATE: return {N, N * (16 + w)};
         case K_MEMSET: return {0.0, N * w};
         case K_CONV1: return {N * 8 * (t ? 27 : 9), N * (w + 32)};  // FP32 FMAs
-        case K_CONV2: return {N * 8 * (t ? 27 : 9), N * (32 + 2 * w)};
+        case K_CONV2: return {N * 16 * (t ? 27 : 9), N * 3 * w};  // both convs, u read+write
     }
     return {0.0, 0.0};
 }
@@ -235,10 +235,8 @@ void learned_sweep(gmg_handle h, Level<double>& L, int l) {
     const int d = h->cfg.d;
     timed(h, K_RESIDUAL, l, 0, L.n, false,
           [&] { lk::residual<double>(d, L.n, L.u[0], L.q, L.r, false, h->stream); });
-    timed(h, K_CONV1, l, 0, L.n, false,
-          [&] { learned::conv1(d, L.n, L.r, h->lz[l], h->lw[l], h->stream); });
     timed(h, K_CONV2, l, 0, L.n, false,
-          [&] { learned::conv2(d, L.n, h->lz[l], L.u[0], 1, h->lw[l], h->stream); });
+          [&] { learned::conv_tc(d, L.n, L.r, L.u[0], 1, h->lw[l], h->stream); });
 }
 
 // Enqueue `sweeps` smoothing sweeps on level l; cur tracks which u buffer

@@ -77,6 +77,10 @@ void update(int d, int n, double* u, const T* e, cudaStream_t s);
 namespace learned {
 void conv1(int d, int n, const double* x, float* z, const float* W, cudaStream_t s);
 void conv2(int d, int n, const float* z, double* out, int mode, const float* W, cudaStream_t s);
+// u += N(sigma) (mode 1) or u = N(sigma) (mode 0) with the fused tensor-core
+// kernel (BF16 operands: sigma, weights and hidden activations; FP32 sums)
+void conv_tc(int d, int n, const double* sigma, double* u, int mode, const float* W,
+             cudaStream_t s);
 // dev = BF16 rounding of the host weights (scratch: 2 x 8 x 3^d device floats)
 void upload_weights(int d, const float* host, float* dev, float* scratch, cudaStream_t s);
 }  // namespace learned

@@ -598,7 +598,7 @@ using namespace gmg::learned;
 extern "C" {
 
 gmg_status gmg_learned_conv(int d, int n, const float* weights, const double* x, double* y,
-                            void* cuda_stream) {
+                            int tensor_cores, void* cuda_stream) {
     gmg_status st = check_dn(d, n);
     if (st != GMG_OK) return st;
     if (!weights || !x || !y) {
@@ -617,8 +617,12 @@ gmg_status gmg_learned_conv(int d, int n, const float* weights, const double* x,
         e = cudaMemcpyAsync(wd, weights, sizeof(float) * 2 * H * T, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         k_round_bf16<<<(2 * H * T + 255) / 256, 256, 0, s>>>(wd, wr, 2 * H * T);
-        conv1(d, n, x, z, wr, s);
-        conv2(d, n, z, y, 0, wr, s);
+        if (tensor_cores) {
+            conv_tc(d, n, x, y, 0, wr, s);
+        } else {
+            conv1(d, n, x, z, wr, s);
+            conv2(d, n, z, y, 0, wr, s);
+        }
         e = cudaStreamSynchronize(s);
     }
     cudaFree(wd);
@@ -720,3 +724,196 @@ gmg_status gmg_learned_train(int d, int n, int steps, int batch, int pair_cycles
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Fused tensor-core network for the V-cycle: u += N(sigma) in one kernel.
+//
+// One CTA (8 warps) owns a TX x TY x TZ tile of output nodes.  sigma is
+// staged in shared memory as BF16 on the tile plus a 2-node halo; conv1 runs
+// on the tile plus a 1-node halo as a [16 nodes x 32 taps] x [32 taps x 8
+// channels] product per 16 nodes (two mma.sync m16n8k16 BF16, FP32
+// accumulate, taps 27..31 zero), its ReLU'd result stored channel-last in
+// BF16 (16 bytes per node, zero outside the interior); conv2 runs per 16
+// consecutive output nodes as sum over tap pairs of [16 nodes x (2 taps x 8
+// channels)] x [16 x 8] with ldmatrix gathering each node's 8 channels at
+// the tapped position and only column 0 of the B operand non-zero.  Hidden
+// activations and sigma therefore enter the tensor cores in BF16; weights
+// are BF16; every sum accumulates in FP32.
+namespace gmg {
+namespace learned {
+namespace {
+
+template <int DIM>
+struct TcTile {
+    static constexpr int TX = 16, TY = DIM == 3 ? 8 : 16, TZ = DIM == 3 ? 4 : 1;
+    static constexpr int HZ = DIM == 3 ? 1 : 0;                   // halo in z
+    static constexpr int X1 = TX + 2, Y1 = TY + 2, Z1 = TZ + 2 * HZ;  // halo-1 region
+    static constexpr int X2 = TX + 4, Y2 = TY + 4, Z2 = TZ + 4 * HZ;  // halo-2 region
+    static constexpr int N1 = X1 * Y1 * Z1;
+    static constexpr int N2 = X2 * Y2 * Z2;
+    static constexpr int T = DIM == 3 ? 27 : 9;
+    static constexpr int K1 = (T + 15) / 16;  // conv1 k-steps of 16 taps
+    static constexpr int P2 = (T + 1) / 2;    // conv2 tap pairs
+};
+
+__device__ inline uint32_t pack_bf16(float lo, float hi) {
+    const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return l | (h << 16);
+}
+
+__device__ inline void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ inline void ldmatrix_x4(uint32_t* r, const void* smem_row) {
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(smem_row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+template <int DIM>
+__device__ inline int tap_dx(int t) { return t % 3 - 1; }
+template <int DIM>
+__device__ inline int tap_dy(int t) { return (t / 3) % 3 - 1; }
+template <int DIM>
+__device__ inline int tap_dz(int t) { return DIM == 3 ? t / 9 - 1 : 0; }
+
+// MODE 1: u += N(sigma);  MODE 0: u = N(sigma) (interior nodes)
+template <int DIM, int MODE>
+__global__ void __launch_bounds__(256) k_conv_tc(const double* __restrict__ sigma,
+                                                 double* __restrict__ u, int n,
+                                                 const float* __restrict__ W) {
+    using G = TcTile<DIM>;
+    __shared__ __nv_bfloat16 xs[G::N2];
+    __shared__ __align__(16) uint4 zs[G::N1];  // 8 BF16 channels per node
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int i0 = 1 + G::TX * blockIdx.x, j0 = 1 + G::TY * blockIdx.y,
+              k0 = DIM == 3 ? 1 + G::TZ * blockIdx.z : 0;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    auto inside = [&](int i, int j, int k) {
+        return i >= 1 && i < n && j >= 1 && j < n && (DIM == 2 || (k >= 1 && k < n));
+    };
+    // 1. sigma on the halo-2 region, BF16, zero outside the interior
+    for (int m = threadIdx.x; m < G::N2; m += blockDim.x) {
+        const int hx = m % G::X2, hy = (m / G::X2) % G::Y2, hz = m / (G::X2 * G::Y2);
+        const int i = i0 - 2 + hx, j = j0 - 2 + hy, k = DIM == 3 ? k0 - 2 + hz : 0;
+        const float v = inside(i, j, k) ? (float)sigma[k * sz + j * sy + i] : 0.f;
+        xs[m] = __float2bfloat16_rn(v);
+    }
+    // B operands (weights) in registers
+    uint32_t b1w[G::K1][2];
+#pragma unroll
+    for (int kh = 0; kh < G::K1; ++kh) {
+        const int t0 = 16 * kh + 2 * tig;
+        auto w1 = [&](int t) { return t < G::T ? W[gid * G::T + t] : 0.f; };
+        b1w[kh][0] = pack_bf16(w1(t0), w1(t0 + 1));
+        b1w[kh][1] = pack_bf16(w1(t0 + 8), w1(t0 + 9));
+    }
+    uint32_t b2w[G::P2][2];
+#pragma unroll
+    for (int pp = 0; pp < G::P2; ++pp) {
+        const float* W2 = W + 8 * G::T;
+        const int ta = 2 * pp, tb = 2 * pp + 1;
+        auto w2 = [&](int c, int t) { return (gid == 0 && t < G::T) ? W2[c * G::T + t] : 0.f; };
+        b2w[pp][0] = pack_bf16(w2(2 * tig, ta), w2(2 * tig + 1, ta));
+        b2w[pp][1] = pack_bf16(w2(2 * tig, tb), w2(2 * tig + 1, tb));
+    }
+    __syncthreads();
+    // 2. conv1 on the halo-1 region: groups of 16 nodes, one group per warp turn
+    const int groups1 = (G::N1 + 15) / 16;
+    for (int g = warp; g < groups1; g += 8) {
+        const int r0 = 16 * g + gid, r1 = r0 + 8;
+        auto xsv = [&](int r, int t) -> float {
+            if (r >= G::N1 || t >= G::T) return 0.f;
+            const int hx = r % G::X1, hy = (r / G::X1) % G::Y1, hz = r / (G::X1 * G::Y1);
+            const int m = ((hz + G::HZ + tap_dz<DIM>(t)) * G::Y2 + (hy + 1 + tap_dy<DIM>(t))) * G::X2 +
+                          (hx + 1 + tap_dx<DIM>(t));
+            return __bfloat162float(xs[m]);
+        };
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kh = 0; kh < G::K1; ++kh) {
+            const int t = 16 * kh + 2 * tig;
+            uint32_t a[4];
+            a[0] = pack_bf16(xsv(r0, t), xsv(r0, t + 1));
+            a[1] = pack_bf16(xsv(r1, t), xsv(r1, t + 1));
+            a[2] = pack_bf16(xsv(r0, t + 8), xsv(r0, t + 9));
+            a[3] = pack_bf16(xsv(r1, t + 8), xsv(r1, t + 9));
+            mma_bf16(c, a, b1w[kh][0], b1w[kh][1]);
+        }
+        // relu, BF16, channel-last; zero outside the interior
+        auto store = [&](int r, float v0, float v1) {
+            if (r >= G::N1) return;
+            const int hx = r % G::X1, hy = (r / G::X1) % G::Y1, hz = r / (G::X1 * G::Y1);
+            const bool in = inside(i0 - 1 + hx, j0 - 1 + hy, DIM == 3 ? k0 - 1 + hz : 0);
+            uint32_t* zrow = reinterpret_cast<uint32_t*>(&zs[r]);
+            zrow[tig] = in ? pack_bf16(fmaxf(v0, 0.f), fmaxf(v1, 0.f)) : 0u;
+        };
+        store(r0, c[0], c[1]);
+        store(r1, c[2], c[3]);
+    }
+    __syncthreads();
+    // 3. conv2 on 16-node x-rows of the output tile
+    const int rows2 = G::TY * G::TZ;
+    for (int row = warp; row < rows2; row += 8) {
+        const int oy = row % G::TY, oz = row / G::TY;
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        const int mtx = lane >> 3, rr = lane & 7;  // ldmatrix: this lane's matrix and row
+        const int ox = (mtx & 1) * 8 + rr;
+#pragma unroll
+        for (int pp = 0; pp < G::P2; ++pp) {
+            const int t = 2 * pp + (mtx >> 1);
+            const int tt = t < G::T ? t : G::T / 2;  // padding tap: weight 0, any valid row
+            const int m = ((oz + G::HZ + tap_dz<DIM>(tt)) * G::Y1 + (oy + 1 + tap_dy<DIM>(tt))) * G::X1 +
+                          (ox + 1 + tap_dx<DIM>(tt));
+            uint32_t a[4];
+            ldmatrix_x4(a, &zs[m]);
+            mma_bf16(c, a, b2w[pp][0], b2w[pp][1]);
+        }
+        if (tig == 0) {
+            const int j = j0 + oy, k = DIM == 3 ? k0 + oz : 0;
+            for (int h = 0; h < 2; ++h) {
+                const int i = i0 + gid + 8 * h;
+                if (!inside(i, j, k)) continue;
+                const int64_t p = k * sz + j * sy + i;
+                const double y = (double)c[2 * h];
+                if (MODE == 1)
+                    u[p] += y;
+                else
+                    u[p] = y;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void conv_tc(int d, int n, const double* sigma, double* u, int mode, const float* W,
+             cudaStream_t s) {
+    if (d == 3) {
+        using G = TcTile<3>;
+        dim3 grid((n - 1 + G::TX - 1) / G::TX, (n - 1 + G::TY - 1) / G::TY,
+                  (n - 1 + G::TZ - 1) / G::TZ);
+        if (mode == 1)
+            k_conv_tc<3, 1><<<grid, 256, 0, s>>>(sigma, u, n, W);
+        else
+            k_conv_tc<3, 0><<<grid, 256, 0, s>>>(sigma, u, n, W);
+    } else {
+        using G = TcTile<2>;
+        dim3 grid((n - 1 + G::TX - 1) / G::TX, (n - 1 + G::TY - 1) / G::TY, 1);
+        if (mode == 1)
+            k_conv_tc<2, 1><<<grid, 256, 0, s>>>(sigma, u, n, W);
+        else
+            k_conv_tc<2, 0><<<grid, 256, 0, s>>>(sigma, u, n, W);
+    }
+}
+
+}  // namespace learned
+}  // namespace gmg

@@ -77,7 +77,7 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_int64)], I),
     "gmg_batch_destroy": ([P], I),
     "gmg_set_learned_weights": ([P, I, P], I),
-    "gmg_learned_conv": ([I, I, P, P, P, P], I),
+    "gmg_learned_conv": ([I, I, P, P, P, I, P], I),
     "gmg_learned_loss_grad": ([I, I, P, P, I, PD, PD, P], I),
     "gmg_learned_train": ([I, I, I, I, I, I, D, ctypes.c_uint64, P, P, PD, P], I),
 }
@@ -335,7 +335,7 @@ def jacobi_weights(d: int, omega: float):
     return w
 
 
-def learned_conv(weights, x):
+def learned_conv(weights, x, tensor_cores: bool = False):
     """y = N(x) for a float64 CUDA tensor x (all nodes, zero boundary)."""
     import numpy as np
     import torch
@@ -344,7 +344,8 @@ def learned_conv(weights, x):
     w = np.ascontiguousarray(weights, dtype=np.float32)
     y = torch.zeros_like(x)
     _check(lib().gmg_learned_conv(d, n, ctypes.c_void_p(w.ctypes.data), _dptr(x, "x", d, n),
-                                  _dptr(y, "y", d, n), _stream_ptr(None)))
+                                  _dptr(y, "y", d, n), 1 if tensor_cores else 0,
+                                  _stream_ptr(None)))
     return y
 
 

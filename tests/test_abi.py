@@ -90,8 +90,8 @@ def test_learned_smoother_needs_fp64(L):
 
 def test_learned_calls_reject_bad_sizes(L):
     w = (ctypes.c_float * (2 * 8 * 27))()
-    assert L.gmg_learned_conv(4, 16, w, None, None, None) == 1
-    assert L.gmg_learned_conv(3, 12, w, None, None, None) == 1
+    assert L.gmg_learned_conv(4, 16, w, None, None, 0, None) == 1
+    assert L.gmg_learned_conv(3, 12, w, None, None, 1, None) == 1
     loss = ctypes.c_double()
     assert L.gmg_learned_loss_grad(3, 2, w, None, 10, ctypes.byref(loss), None, None) == 1
     assert L.gmg_learned_train(3, 64, 0, 1, 1, 10, 1e-3, 1, w, w, None, None) == 1

@@ -382,3 +382,24 @@ def test_learned_vcycle_with_jacobi_weights_is_wj_vcycle(d, n, omega):
     E = dm.vcycle_error_matrix(d, n, L, 1, 0.8, 1, 1, 1)
     ref = E @ u0 + (np.eye(len(u0)) - E) @ np.linalg.solve(dm.lap(d, n), b)
     np.testing.assert_allclose(dm.to_vec(u), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("d,n", [(2, 8), (3, 8)])
+def test_bf16_network_with_jacobi_weights(d, n):
+    """BF16 operands: with the Jacobi weights the network returns omega times
+    the BF16 rounding of its input (ties to even), exactly."""
+    W1, W2 = _jacobi_weights(d, 0.75)
+    rng = np.random.default_rng(12)
+    x = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)
+    y = oracle.conv_fwd_bf16(W1, W2, x)
+    xb = x.astype(np.float32).view(np.uint32).astype(np.uint64)
+    xb = (((xb + 0x7FFF + ((xb >> 16) & 1)) >> 16) << 16).astype(np.uint32).view(np.float32)
+    np.testing.assert_array_equal(y, 0.75 * xb.astype(np.float64))
+    # BF16-representable data with small integer weights: identical to the exact network
+    xi = np.round(x * 4) / 4
+    W1i = np.round(rng.standard_normal(W1.shape) * 2).astype(np.float32) / 2
+    W2i = np.round(rng.standard_normal(W2.shape) * 2).astype(np.float32) / 2
+    y1 = oracle.conv_fwd_bf16(W1i, W2i, xi)
+    y2, z = oracle.conv_fwd(W1i, W2i, xi)
+    if np.all(np.abs(z) < 256):  # hidden values stay BF16-representable
+        np.testing.assert_array_equal(y1, y2)
