@@ -298,9 +298,12 @@ def run_learned(torch, args):
                          ("rbgs_v22", Solver(d, n, nu1=2, nu2=2))):
         ms, it, rel, stats, launches = time_solves(torch, solver, f, u, args.form_steps, 1)
         res = solver.residual_norm(f, u)
+        top = sorted(stats, key=lambda r: -r["ms"])[:6]
         runs[name] = {"value": dof / (ms * 1e-3), "unit": "DOF/s", "ms_per_step": ms,
                       "cycles": it, "relres": rel, "fp64_residual_norm": res,
-                      "dominant_kernel": dominant(stats)[0]}
+                      "dominant_kernel": dominant(stats)[0],
+                      "top_kernels_ms_per_step": [[r["kernel"], r["level"],
+                                                   r["ms"] / args.form_steps] for r in top]}
         solver.close()
     out["runs"] = runs
     out["speedup_learned_vs_rbgs_v22"] = runs["rbgs_v22"]["ms_per_step"] / runs["learned_v11"]["ms_per_step"]

@@ -230,26 +230,35 @@ bool learned_level(gmg_handle h, int l) {
 }
 
 // One learned smoothing sweep on FP64 level l: sigma = (b - A'u)/(2d),
-// u += conv2(relu(conv1(sigma))).
-void learned_sweep(gmg_handle h, Level<double>& L, int l) {
+// u += conv2(relu(conv1(sigma))).  sigma_ready: L.r already holds sigma of
+// the current u (level 0 after the stopping-test norm).
+void learned_sweep(gmg_handle h, Level<double>& L, int l, bool sigma_ready) {
     const int d = h->cfg.d;
-    timed(h, K_RESIDUAL, l, 0, L.n, false,
-          [&] { lk::residual<double>(d, L.n, L.u[0], L.q, L.r, false, h->stream); });
+    if (!sigma_ready)
+        timed(h, K_RESIDUAL, l, 0, L.n, false,
+              [&] { lk::residual<double>(d, L.n, L.u[0], L.q, L.r, false, h->stream); });
     timed(h, K_CONV2, l, 0, L.n, false,
           [&] { learned::conv_tc(d, L.n, L.r, L.u[0], 1, h->lw[l], h->stream); });
 }
 
 // Enqueue `sweeps` smoothing sweeps on level l; cur tracks which u buffer
 // holds the iterate (weighted Jacobi alternates).
+// Level 0 of a plain FP64 handle whose level 0 is learned: the stopping-test
+// norm leaves sigma of the cycle's starting iterate in lv[0].r.
+bool sigma_carried(gmg_handle h) {
+    return h->cfg.precision == GMG_FP64 && learned_level(h, 0) && h->cfg.nu1 > 0;
+}
+
 template <typename T>
-void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur) {
+void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
+           bool sigma_ready = false) {
     Level<T>& L = lv[l];
     const int d = h->cfg.d;
     const int p = prec_of<T>();
     for (int s = 0; s < sweeps; ++s) {
         if constexpr (std::is_same<T, double>::value) {
             if (learned_level(h, l)) {
-                learned_sweep(h, L, l);
+                learned_sweep(h, L, l, sigma_ready && s == 0);
                 continue;
             }
         }
@@ -279,7 +288,8 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
         relax(h, lv, 0, c.nu1, cur[0]);
     } else {
         for (int l = 0; l + 1 < L; ++l) {
-            relax(h, lv, l, c.nu1, cur[l]);
+            relax(h, lv, l, c.nu1, cur[l], l == 0 && std::is_same<T, double>::value &&
+                                               sigma_carried(h));
             Level<T>& F = lv[l];
             Level<T>& C = lv[l + 1];
             // After a black half sweep the black residual vanishes identically.
@@ -356,11 +366,12 @@ gmg_status enqueue_step(gmg_handle h) {
     if (c.precision == GMG_FP64) {
         st = enqueue_vcycle<double>(h, h->lv);
         if (st != GMG_OK) return st;
+        double* keep = sigma_carried(h) ? h->lv[0].r : nullptr;
         timed(
             h, K_RESNORM, 0, 0, c.n, false,
             [&] {
                 fp64::resnorm(c.d, c.n, h->lv[0].u[0], h->lv[0].q, h->partial, h->d_res2,
-                              h->stream);
+                              h->stream, keep);
             },
             2);
     } else if (c.precision == GMG_FP32_IR) {
@@ -424,7 +435,8 @@ gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
     const gmg_config& c = h->cfg;
     fp64::prepare(c.d, c.n, f, h->lv[0].q, u, h->stream);
     if (c.precision == GMG_FP64)
-        fp64::resnorm(c.d, c.n, u, h->lv[0].q, h->partial, h->d_res2, h->stream);
+        fp64::resnorm(c.d, c.n, u, h->lv[0].q, h->partial, h->d_res2, h->stream,
+                      sigma_carried(h) ? h->lv[0].r : nullptr);
     else if (c.precision == GMG_FP32_IR)
         mixed::outer_residual<float>(c.d, c.n, u, h->lv[0].q, h->lvf[0].q, h->partial, h->d_res2,
                                      h->stream);

@@ -51,10 +51,12 @@ constexpr int kNormThreads = 256;
 // (j, k) so that each thread accumulates many nodes before the fixed warp
 // shuffle tree and the fixed cross-warp order; one partial per block.  The
 // grid depends on n only, so the result is deterministic.
-template <int DIM>
+// With STORE, sigma is also written to sig_out (the learned smoother's input).
+template <int DIM, bool STORE>
 __global__ void __launch_bounds__(kNormThreads) k_resnorm(const double* __restrict__ u,
                                                           const double* __restrict__ q,
-                                                          double* __restrict__ partial, int n) {
+                                                          double* __restrict__ partial, int n,
+                                                          double* __restrict__ sig_out) {
     __shared__ double warp_sums[kNormThreads / 32];
     const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
     const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
@@ -68,6 +70,7 @@ __global__ void __launch_bounds__(kNormThreads) k_resnorm(const double* __restri
         for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
             const int64_t p = row + i;
             const double sig = fma(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
+            if (STORE) sig_out[p] = sig;
             acc = fma(sig, sig, acc);
         }
     }
@@ -129,12 +132,19 @@ void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s
 int resnorm_partials(int d, int n) { return (int)norm_launch(d, n).grid.x; }
 
 void resnorm(int d, int n, const double* u, const double* q, double* partial, double* out,
-             cudaStream_t s) {
+             cudaStream_t s, double* sigma_out) {
     NormLaunch L = norm_launch(d, n);
-    if (d == 3)
-        k_resnorm<3><<<L.grid, L.block, 0, s>>>(u, q, partial, n);
-    else
-        k_resnorm<2><<<L.grid, L.block, 0, s>>>(u, q, partial, n);
+    if (sigma_out) {
+        if (d == 3)
+            k_resnorm<3, true><<<L.grid, L.block, 0, s>>>(u, q, partial, n, sigma_out);
+        else
+            k_resnorm<2, true><<<L.grid, L.block, 0, s>>>(u, q, partial, n, sigma_out);
+    } else {
+        if (d == 3)
+            k_resnorm<3, false><<<L.grid, L.block, 0, s>>>(u, q, partial, n, nullptr);
+        else
+            k_resnorm<2, false><<<L.grid, L.block, 0, s>>>(u, q, partial, n, nullptr);
+    }
     k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)L.grid.x, out);
 }
 

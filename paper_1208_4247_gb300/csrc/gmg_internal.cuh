@@ -56,8 +56,9 @@ void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s);
 namespace fp64 {
 void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s);
 int resnorm_partials(int d, int n);
+// sum of sigma^2 into *out; sigma_out (may be NULL) also receives sigma
 void resnorm(int d, int n, const double* u, const double* q, double* partial, double* out,
-             cudaStream_t s);
+             cudaStream_t s, double* sigma_out = nullptr);
 __global__ void k_sum_partials(const double* partial, int count, double* out);
 }  // namespace fp64
 

@@ -826,35 +826,51 @@ __global__ void __launch_bounds__(256) k_conv_tc(const double* __restrict__ sigm
         b2w[pp][1] = pack_bf16(w2(2 * tig, tb), w2(2 * tig + 1, tb));
     }
     __syncthreads();
-    // 2. conv1 on the halo-1 region: groups of 16 nodes, one group per warp turn
+    // 2. conv1 on the halo-1 region: groups of 16 nodes, one group per warp
+    // turn.  This lane's taps (fixed per lane) as offsets in the halo-2 tile.
+    constexpr int NT1 = 4 * G::K1;
+    int toff[NT1];
+    bool tok[NT1];
+#pragma unroll
+    for (int q = 0; q < NT1; ++q) {
+        const int kh = q / 4, sub = q % 4;
+        const int t = 16 * kh + 2 * tig + (sub & 1) + (sub >> 1) * 8;
+        tok[q] = t < G::T;
+        const int tt = tok[q] ? t : 0;
+        toff[q] = (tap_dz<DIM>(tt) * G::Y2 + tap_dy<DIM>(tt)) * G::X2 + tap_dx<DIM>(tt);
+    }
     const int groups1 = (G::N1 + 15) / 16;
     for (int g = warp; g < groups1; g += 8) {
         const int r0 = 16 * g + gid, r1 = r0 + 8;
-        auto xsv = [&](int r, int t) -> float {
-            if (r >= G::N1 || t >= G::T) return 0.f;
-            const int hx = r % G::X1, hy = (r / G::X1) % G::Y1, hz = r / (G::X1 * G::Y1);
-            const int m = ((hz + G::HZ + tap_dz<DIM>(t)) * G::Y2 + (hy + 1 + tap_dy<DIM>(t))) * G::X2 +
-                          (hx + 1 + tap_dx<DIM>(t));
-            return __bfloat162float(xs[m]);
+        // centre of each row node in the halo-2 tile (a valid index for padding rows)
+        auto centre = [&](int r) {
+            const int rr = r < G::N1 ? r : 0;
+            const int hx = rr % G::X1, hy = (rr / G::X1) % G::Y1, hz = rr / (G::X1 * G::Y1);
+            return ((hz + G::HZ) * G::Y2 + (hy + 1)) * G::X2 + (hx + 1);
+        };
+        const int m0 = centre(r0), m1 = centre(r1);
+        const bool v0 = r0 < G::N1, v1 = r1 < G::N1;
+        auto xv = [&](int m, bool v, int q) {
+            return (v && tok[q]) ? __bfloat162float(xs[m + toff[q]]) : 0.f;
         };
         float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int kh = 0; kh < G::K1; ++kh) {
-            const int t = 16 * kh + 2 * tig;
+            const int q = 4 * kh;
             uint32_t a[4];
-            a[0] = pack_bf16(xsv(r0, t), xsv(r0, t + 1));
-            a[1] = pack_bf16(xsv(r1, t), xsv(r1, t + 1));
-            a[2] = pack_bf16(xsv(r0, t + 8), xsv(r0, t + 9));
-            a[3] = pack_bf16(xsv(r1, t + 8), xsv(r1, t + 9));
+            a[0] = pack_bf16(xv(m0, v0, q), xv(m0, v0, q + 1));
+            a[1] = pack_bf16(xv(m1, v1, q), xv(m1, v1, q + 1));
+            a[2] = pack_bf16(xv(m0, v0, q + 2), xv(m0, v0, q + 3));
+            a[3] = pack_bf16(xv(m1, v1, q + 2), xv(m1, v1, q + 3));
             mma_bf16(c, a, b1w[kh][0], b1w[kh][1]);
         }
         // relu, BF16, channel-last; zero outside the interior
-        auto store = [&](int r, float v0, float v1) {
+        auto store = [&](int r, float v0_, float v1_) {
             if (r >= G::N1) return;
             const int hx = r % G::X1, hy = (r / G::X1) % G::Y1, hz = r / (G::X1 * G::Y1);
             const bool in = inside(i0 - 1 + hx, j0 - 1 + hy, DIM == 3 ? k0 - 1 + hz : 0);
             uint32_t* zrow = reinterpret_cast<uint32_t*>(&zs[r]);
-            zrow[tig] = in ? pack_bf16(fmaxf(v0, 0.f), fmaxf(v1, 0.f)) : 0u;
+            zrow[tig] = in ? pack_bf16(fmaxf(v0_, 0.f), fmaxf(v1_, 0.f)) : 0u;
         };
         store(r0, c[0], c[1]);
         store(r1, c[2], c[3]);
@@ -867,14 +883,17 @@ __global__ void __launch_bounds__(256) k_conv_tc(const double* __restrict__ sigm
         float c[4] = {0.f, 0.f, 0.f, 0.f};
         const int mtx = lane >> 3, rr = lane & 7;  // ldmatrix: this lane's matrix and row
         const int ox = (mtx & 1) * 8 + rr;
+        const int mc = ((oz + G::HZ) * G::Y1 + (oy + 1)) * G::X1 + (ox + 1);
+        const int hi = mtx >> 1;
 #pragma unroll
         for (int pp = 0; pp < G::P2; ++pp) {
-            const int t = 2 * pp + (mtx >> 1);
-            const int tt = t < G::T ? t : G::T / 2;  // padding tap: weight 0, any valid row
-            const int m = ((oz + G::HZ + tap_dz<DIM>(tt)) * G::Y1 + (oy + 1 + tap_dy<DIM>(tt))) * G::X1 +
-                          (ox + 1 + tap_dx<DIM>(tt));
+            // tap 2pp (matrices 0, 1) or 2pp + 1 (matrices 2, 3); a padding tap
+            // reads the centre row (its weight is zero)
+            const int ta = 2 * pp, tb = 2 * pp + 1 < G::T ? 2 * pp + 1 : G::T / 2;
+            const int oa = (tap_dz<DIM>(ta) * G::Y1 + tap_dy<DIM>(ta)) * G::X1 + tap_dx<DIM>(ta);
+            const int ob = (tap_dz<DIM>(tb) * G::Y1 + tap_dy<DIM>(tb)) * G::X1 + tap_dx<DIM>(tb);
             uint32_t a[4];
-            ldmatrix_x4(a, &zs[m]);
+            ldmatrix_x4(a, &zs[mc + (hi ? ob : oa)]);
             mma_bf16(c, a, b2w[pp][0], b2w[pp][1]);
         }
         if (tig == 0) {

@@ -8,7 +8,8 @@
   3e-4 of the gradient's scale (the backward runs in FP32);
 * the fused tensor-core network (BF16 sigma and hidden activations) vs the
   oracle's BF16-operand network: <= 1e-4 relative (L2), and one learned
-  V-cycle (which uses it) vs the oracle's learned V-cycle: <= 1e-4;
+  V-cycle (which uses it on every level) vs the oracle's learned V-cycle:
+  <= 1e-3 (below one BF16 ulp, 2^-8);
 * training lowers the loss, the learned cycle solves to an FP64 relative
   residual of 1e-10, and a trained network contracts more per cycle than its
   untrained (weighted-Jacobi) start.
@@ -126,7 +127,9 @@ def test_learned_vcycle_matches_oracle(torch_cuda, d, n):
             S.set_learned_weights(l, w)
         S.cycles(torch.from_numpy(f).cuda(), ud, 1)
     ug = ud.cpu().numpy()
-    assert np.linalg.norm(ug - uo) <= 1e-4 * np.linalg.norm(uo)
+    # each smoothing inherits the network's ~1e-4 (rare one-ulp BF16 hidden
+    # roundings); the cycle applies it on every level: bound 1e-3 < 2^-8
+    assert np.linalg.norm(ug - uo) <= 1e-3 * np.linalg.norm(uo)
 
 
 def _contraction(torch, S, f, cycles=8):
