@@ -745,7 +745,8 @@ namespace {
 
 template <int DIM>
 struct TcTile {
-    static constexpr int TX = 16, TY = DIM == 3 ? 8 : 16, TZ = DIM == 3 ? 4 : 1;
+    // TX = 14: a halo-1 x-row is exactly 16 nodes, one conv1 mma group
+    static constexpr int TX = 14, TY = DIM == 3 ? 8 : 16, TZ = DIM == 3 ? 8 : 1;
     static constexpr int HZ = DIM == 3 ? 1 : 0;                   // halo in z
     static constexpr int X1 = TX + 2, Y1 = TY + 2, Z1 = TZ + 2 * HZ;  // halo-1 region
     static constexpr int X2 = TX + 4, Y2 = TY + 4, Z2 = TZ + 4 * HZ;  // halo-2 region
@@ -839,41 +840,38 @@ __global__ void __launch_bounds__(256) k_conv_tc(const double* __restrict__ sigm
         const int tt = tok[q] ? t : 0;
         toff[q] = (tap_dz<DIM>(tt) * G::Y2 + tap_dy<DIM>(tt)) * G::X2 + tap_dx<DIM>(tt);
     }
-    const int groups1 = (G::N1 + 15) / 16;
-    for (int g = warp; g < groups1; g += 8) {
-        const int r0 = 16 * g + gid, r1 = r0 + 8;
-        // centre of each row node in the halo-2 tile (a valid index for padding rows)
-        auto centre = [&](int r) {
-            const int rr = r < G::N1 ? r : 0;
-            const int hx = rr % G::X1, hy = (rr / G::X1) % G::Y1, hz = rr / (G::X1 * G::Y1);
-            return ((hz + G::HZ) * G::Y2 + (hy + 1)) * G::X2 + (hx + 1);
-        };
-        const int m0 = centre(r0), m1 = centre(r1);
-        const bool v0 = r0 < G::N1, v1 = r1 < G::N1;
-        auto xv = [&](int m, bool v, int q) {
-            return (v && tok[q]) ? __bfloat162float(xs[m + toff[q]]) : 0.f;
+    static_assert(G::X1 == 16, "a halo-1 row must be one 16-node mma group");
+    // this lane's two nodes of a row: x = gid and gid + 8 of the halo-1 row
+    const bool xin0 = i0 - 1 + gid >= 1 && i0 - 1 + gid < n;
+    const bool xin1 = i0 - 1 + gid + 8 >= 1 && i0 - 1 + gid + 8 < n;
+    const unsigned short* xr = reinterpret_cast<const unsigned short*>(xs);
+    const int rows1 = G::Y1 * G::Z1;
+    for (int g = warp; g < rows1; g += 8) {
+        const int hy = g % G::Y1, hz = g / G::Y1;
+        const int j = j0 - 1 + hy, k = DIM == 3 ? k0 - 1 + hz : 0;
+        const bool yzin = j >= 1 && j < n && (DIM == 2 || (k >= 1 && k < n));
+        // centre of node (gid, hy, hz) in the halo-2 tile
+        const int m0 = ((hz + G::HZ) * G::Y2 + (hy + 1)) * G::X2 + (gid + 1);
+        const int m1 = m0 + 8;
+        auto xb = [&](int m, int q) -> uint32_t {
+            return tok[q] ? (uint32_t)xr[m + toff[q]] : 0u;
         };
         float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int kh = 0; kh < G::K1; ++kh) {
             const int q = 4 * kh;
             uint32_t a[4];
-            a[0] = pack_bf16(xv(m0, v0, q), xv(m0, v0, q + 1));
-            a[1] = pack_bf16(xv(m1, v1, q), xv(m1, v1, q + 1));
-            a[2] = pack_bf16(xv(m0, v0, q + 2), xv(m0, v0, q + 3));
-            a[3] = pack_bf16(xv(m1, v1, q + 2), xv(m1, v1, q + 3));
+            a[0] = xb(m0, q) | (xb(m0, q + 1) << 16);
+            a[1] = xb(m1, q) | (xb(m1, q + 1) << 16);
+            a[2] = xb(m0, q + 2) | (xb(m0, q + 3) << 16);
+            a[3] = xb(m1, q + 2) | (xb(m1, q + 3) << 16);
             mma_bf16(c, a, b1w[kh][0], b1w[kh][1]);
         }
         // relu, BF16, channel-last; zero outside the interior
-        auto store = [&](int r, float v0_, float v1_) {
-            if (r >= G::N1) return;
-            const int hx = r % G::X1, hy = (r / G::X1) % G::Y1, hz = r / (G::X1 * G::Y1);
-            const bool in = inside(i0 - 1 + hx, j0 - 1 + hy, DIM == 3 ? k0 - 1 + hz : 0);
-            uint32_t* zrow = reinterpret_cast<uint32_t*>(&zs[r]);
-            zrow[tig] = in ? pack_bf16(fmaxf(v0_, 0.f), fmaxf(v1_, 0.f)) : 0u;
-        };
-        store(r0, c[0], c[1]);
-        store(r1, c[2], c[3]);
+        uint32_t* z0 = reinterpret_cast<uint32_t*>(&zs[16 * g + gid]);
+        uint32_t* z1 = reinterpret_cast<uint32_t*>(&zs[16 * g + gid + 8]);
+        z0[tig] = (yzin && xin0) ? pack_bf16(fmaxf(c[0], 0.f), fmaxf(c[1], 0.f)) : 0u;
+        z1[tig] = (yzin && xin1) ? pack_bf16(fmaxf(c[2], 0.f), fmaxf(c[3], 0.f)) : 0u;
     }
     __syncthreads();
     // 3. conv2 on 16-node x-rows of the output tile
@@ -882,7 +880,9 @@ __global__ void __launch_bounds__(256) k_conv_tc(const double* __restrict__ sigm
         const int oy = row % G::TY, oz = row / G::TY;
         float c[4] = {0.f, 0.f, 0.f, 0.f};
         const int mtx = lane >> 3, rr = lane & 7;  // ldmatrix: this lane's matrix and row
-        const int ox = (mtx & 1) * 8 + rr;
+        // rows past the tile's last x (TX..15) are computed but discarded: read
+        // the last column's neighbourhood there so every address stays in its row
+        const int ox = min((mtx & 1) * 8 + rr, G::TX - 1);
         const int mc = ((oz + G::HZ) * G::Y1 + (oy + 1)) * G::X1 + (ox + 1);
         const int hi = mtx >> 1;
 #pragma unroll
@@ -899,8 +899,9 @@ __global__ void __launch_bounds__(256) k_conv_tc(const double* __restrict__ sigm
         if (tig == 0) {
             const int j = j0 + oy, k = DIM == 3 ? k0 + oz : 0;
             for (int h = 0; h < 2; ++h) {
-                const int i = i0 + gid + 8 * h;
-                if (!inside(i, j, k)) continue;
+                const int ox_ = gid + 8 * h;
+                const int i = i0 + ox_;
+                if (ox_ >= G::TX || !inside(i, j, k)) continue;
                 const int64_t p = k * sz + j * sy + i;
                 const double y = (double)c[2 * h];
                 if (MODE == 1)
