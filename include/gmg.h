@@ -206,6 +206,22 @@ gmg_status gmg_learned_train(int d, int n, int steps, int batch, int pair_cycles
                              int coarse_cycles, double lr, uint64_t seed, const float* w_init,
                              float* w_out, double* loss_history, void* cuda_stream);
 
+/* ------------------------------------------------------------ FFT solve
+ * The paper's comparison method (section 2.3): a direct solve of the same FD
+ * system A'u = h^2 f by sine transforms, u = S^-1 diag(1/lambda) S h^2 f with
+ * S the DST-I along every axis and lambda_k = sum_m 4 sin^2(pi k_m / (2n))
+ * the discrete eigenvalues (the paper writes the continuous symbol), each
+ * DST-I done by a length-2n cuFFT D2Z of the odd extension. */
+typedef struct gmg_fft_s* gmg_fft;
+
+/* d = 2 or 3, n a power of two (2D up to 8192, 3D up to 1024); allocates
+ * about 3 (n+1)^d doubles of work space and two cuFFT plans. */
+gmg_status gmg_fft_create(int d, int n, void* cuda_stream, gmg_fft* out);
+/* u = A'^-1 h^2 f on the interior, 0 on the boundary (f, u device pointers,
+ * layout above).  Synchronises the handle's stream. */
+gmg_status gmg_fft_solve(gmg_fft h, const double* f, double* u);
+gmg_status gmg_fft_destroy(gmg_fft h);
+
 /* ---------------------------------------------------------------- batches
  * Many independent solves of uneven sizes (2D and 3D mixed) advanced
  * together: every step launches one persistent kernel per level index over

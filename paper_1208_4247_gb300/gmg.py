@@ -77,6 +77,9 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_int64)], I),
     "gmg_batch_destroy": ([P], I),
     "gmg_set_learned_weights": ([P, I, P], I),
+    "gmg_fft_create": ([I, I, P, ctypes.POINTER(P)], I),
+    "gmg_fft_solve": ([P, P, P], I),
+    "gmg_fft_destroy": ([P], I),
     "gmg_learned_conv": ([I, I, P, P, P, I, P], I),
     "gmg_learned_loss_grad": ([I, I, P, P, I, PD, PD, P], I),
     "gmg_learned_train": ([I, I, I, I, I, I, D, ctypes.c_uint64, P, P, PD, P], I),
@@ -375,3 +378,34 @@ def learned_train(d: int, n: int, steps: int, batch: int, w_init, lr: float = 1e
                                    ctypes.c_void_p(out.ctypes.data), hist.ctypes.data_as(PD),
                                    _stream_ptr(None)))
     return out, hist
+
+
+class FFTSolver:
+    """Direct sine-transform (cuFFT DST-I) solve of the same FD system."""
+
+    def __init__(self, d: int, n: int, stream=None):
+        self.d, self.n = d, n
+        h = ctypes.c_void_p()
+        _check(lib().gmg_fft_create(d, n, _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def solve(self, f, u):
+        _check(lib().gmg_fft_solve(self._h, _dptr(f, "f", self.d, self.n),
+                                   _dptr(u, "u", self.d, self.n)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gmg_fft_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
