@@ -167,11 +167,11 @@ int num_levels(const gmg_config& c) { return c.levels > 0 ? c.levels : ilog2(c.n
 
 enum Kind {
     K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_OUTER_RES,
-    K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_COUNT
+    K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_TAIL, K_COUNT
 };
 const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restrict",
                                   "prolong_add", "resnorm",  "copy",     "outer_residual",
-                                  "update",      "memset",   "conv1",    "conv_tc_update"};
+                                  "update",      "memset",   "conv1",    "conv_tc_update", "tail"};
 const char* kPrecSuffix[3] = {"", "_f32", "_bf16"};
 
 template <typename T>
@@ -210,6 +210,7 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
         case K_MEMSET: return {0.0, N * w};
         case K_CONV1: return {N * 8 * (t ? 27 : 9), N * (w + 32)};  // FP32 FMAs
         case K_CONV2: return {N * 16 * (t ? 27 : 9), N * 3 * w};  // both convs, u read+write
+        case K_TAIL: return {N * (t ? 40 : 30) * 8.0 / 7.0, N * 2 * w};
     }
     return {0.0, 0.0};
 }
@@ -275,6 +276,25 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
     }
 }
 
+// First level handled by the persistent tail kernel (L = none): the first
+// level with n <= 16 (3D) / 64 (2D) whose tail arrays fit in 200 KB of shared
+// memory, below every learned level, leaving at least two tail levels.
+template <typename T>
+int tail_level(gmg_handle h, int L) {
+    const gmg_config& c = h->cfg;
+    const int nmax = c.d == 3 ? 16 : 64;
+    int lo = 0;
+    if (c.smoother == GMG_LEARNED)
+        for (int l = 0; l < L && l < (int)h->lw.size(); ++l)
+            if (h->lw[l]) lo = l + 1;
+    for (int l = lo; l + 1 < L; ++l) {
+        const int n = c.n >> l;
+        if (n <= nmax && tail::smem_bytes(c.d, n, L - l, c.smoother, sizeof(T)) <= 200 * 1024)
+            return l;
+    }
+    return L;
+}
+
 // One cycle of Algorithm 1 on the hierarchy lv (level-0 iterate lv[0].u[0]
 // in and out), in stream order.
 template <typename T>
@@ -284,10 +304,20 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
     const int L = (int)lv.size();
     const int p = prec_of<T>();
     std::vector<int> cur(L, 0);
-    if (L == 1) {
+    const int lt = tail_level<T>(h, L);
+    if (lt == 0) {
+        // the whole hierarchy is small: one persistent launch
+        cudaError_t e = cudaSuccess;
+        timed(h, K_TAIL, 0, p, lv[0].n, false, [&] {
+            e = tail::launch<T>(d, lv[0].n, L, lv[0].u[0], lv[0].q, c.smoother, c.omega, c.nu1,
+                                c.nu2, c.coarse_sweeps, h->stream);
+        });
+        GMG_CUDA_TRY(e);
+    } else if (L == 1) {
         relax(h, lv, 0, c.nu1, cur[0]);
     } else {
-        for (int l = 0; l + 1 < L; ++l) {
+        const int Ldown = lt < L ? lt : L - 1;  // levels smoothed by grid kernels going down
+        for (int l = 0; l < Ldown; ++l) {
             relax(h, lv, l, c.nu1, cur[l], l == 0 && std::is_same<T, double>::value &&
                                                sigma_carried(h));
             Level<T>& F = lv[l];
@@ -305,14 +335,23 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
             });
             cur[l + 1] = 0;
         }
-        Level<T>& B = lv[L - 1];
-        if (B.n > 2) {
-            for (int s = 0; s < c.coarse_sweeps; ++s)
-                for (int color = 0; color < 2; ++color)
-                    timed(h, K_RB_HALF, L - 1, p, B.n, false,
-                          [&] { lk::rb_half<T>(d, B.n, B.u[0], B.q, color, h->stream); });
+        if (lt < L) {
+            cudaError_t e = cudaSuccess;
+            timed(h, K_TAIL, lt, p, lv[lt].n, false, [&] {
+                e = tail::launch<T>(d, lv[lt].n, L - lt, lv[lt].u[0], lv[lt].q, c.smoother,
+                                    c.omega, c.nu1, c.nu2, c.coarse_sweeps, h->stream);
+            });
+            GMG_CUDA_TRY(e);
+        } else {
+            Level<T>& B = lv[L - 1];
+            if (B.n > 2) {
+                for (int s = 0; s < c.coarse_sweeps; ++s)
+                    for (int color = 0; color < 2; ++color)
+                        timed(h, K_RB_HALF, L - 1, p, B.n, false,
+                              [&] { lk::rb_half<T>(d, B.n, B.u[0], B.q, color, h->stream); });
+            }
         }
-        for (int l = L - 2; l >= 0; --l) {
+        for (int l = Ldown - 1; l >= 0; --l) {
             Level<T>& F = lv[l];
             Level<T>& C = lv[l + 1];
             timed(h, K_PROLONG, l, p, F.n, false,

@@ -72,6 +72,15 @@ template <typename T>
 void update(int d, int n, double* u, const T* e, cudaStream_t s);
 }  // namespace mixed
 
+// Persistent single-CTA tail (tail.cu): the V-cycle on levels n_top, n_top/2,
+// ... (levels of them) in shared memory; u_top in/out, q_top in.
+namespace tail {
+size_t smem_bytes(int d, int n_top, int levels, int smoother, size_t elem);
+template <typename T>
+cudaError_t launch(int d, int n_top, int levels, T* u_top, const T* q_top, int smoother,
+                   double omega, int nu1, int nu2, int coarse_sweeps, cudaStream_t s);
+}  // namespace tail
+
 // Learned-smoother network kernels (learned.cu): z = conv1(x) (8 channel
 // planes of (n+1)^d floats), out = / += / -= conv2(relu(z)) for mode 0/1/2.
 // W: 2 x 8 x 3^d BF16-rounded floats on the device.
