@@ -28,7 +28,7 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+    return ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC,-O2",
                    "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, *extra]
 
 

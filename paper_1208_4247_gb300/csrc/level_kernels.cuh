@@ -70,17 +70,18 @@ inline RowLaunch row_launch(int d, int n, int xcount) {
     return L;
 }
 
+// Sum of the 2d axis neighbours as a pair tree, ((x- + x+) + (y- + y+)) +
+// (z- + z+): the same 2d-1 adds as a chain, with a dependency depth of 3.
 template <int DIM, typename T>
 __device__ inline typename Num<T>::C nbr_sum(const T* u, int64_t p, int64_t sy, int64_t sz) {
     using N = Num<T>;
-    auto s = N::ld(u[p - 1]) + N::ld(u[p + 1]);
-    s += N::ld(u[p - sy]);
-    s += N::ld(u[p + sy]);
+    const auto sx = N::ld(u[p - 1]) + N::ld(u[p + 1]);
+    const auto syy = N::ld(u[p - sy]) + N::ld(u[p + sy]);
     if (DIM == 3) {
-        s += N::ld(u[p - sz]);
-        s += N::ld(u[p + sz]);
+        const auto szz = N::ld(u[p - sz]) + N::ld(u[p + sz]);
+        return (sx + syy) + szz;
     }
-    return s;
+    return sx + syy;
 }
 
 // One colour of red-black Gauss-Seidel: nodes with (i+j+k) % 2 == color.

@@ -32,20 +32,33 @@ __device__ inline int64_t nodes_of(int n) {
     return DIM == 3 ? m * m * m : m * m;
 }
 
-// interior node with linear interior index idx -> (node index, i, j, k)
-template <int DIM>
-__device__ inline int64_t inode(int n, int idx, int& i, int& j, int& k) {
-    const int m = n - 1;
+// interior node with linear interior index idx -> (node index, i, j, k);
+// NN, the level's n, is a compile-time constant so the divisions are cheap
+template <int DIM, int NN>
+__device__ inline int64_t inode(int idx, int& i, int& j, int& k) {
+    constexpr int m = NN - 1;
     i = idx % m + 1;
     j = (idx / m) % m + 1;
     k = DIM == 3 ? idx / (m * m) + 1 : 0;
-    return ((int64_t)k * (n + 1) + j) * (n + 1) + i;
+    return ((int64_t)k * (NN + 1) + j) * (NN + 1) + i;
 }
 
-template <int DIM>
-__device__ inline int interior_count(int n) {
-    const int m = n - 1;
-    return DIM == 3 ? m * m * m : m * m;
+template <int DIM, int NN>
+__device__ constexpr int interior_count() {
+    return DIM == 3 ? (NN - 1) * (NN - 1) * (NN - 1) : (NN - 1) * (NN - 1);
+}
+
+// f.template operator()<NN>() for the level size n (a power of two, 2..64)
+template <class F>
+__device__ inline void dispatch_n(int n, F&& f) {
+    switch (n) {
+        case 2: f.template operator()<2>(); break;
+        case 4: f.template operator()<4>(); break;
+        case 8: f.template operator()<8>(); break;
+        case 16: f.template operator()<16>(); break;
+        case 32: f.template operator()<32>(); break;
+        default: f.template operator()<64>(); break;
+    }
 }
 
 template <int DIM, typename T>
@@ -53,13 +66,15 @@ __device__ void rb_half(SLevel<T>& L, int color) {
     using N = Num<T>;
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
-    const int64_t sy = L.n + 1, sz = DIM == 3 ? sy * sy : 0;
-    for (int idx = threadIdx.x; idx < interior_count<DIM>(L.n); idx += blockDim.x) {
-        int i, j, k;
-        const int64_t p = inode<DIM>(L.n, idx, i, j, k);
-        if (((i + j + k) & 1) != color) continue;
-        L.u[p] = N::st(fma(c, lk::nbr_sum<DIM>(L.u, p, sy, sz), N::ld(L.q[p])));
-    }
+    dispatch_n(L.n, [&]<int NN>() {
+        constexpr int64_t sy = NN + 1, sz = DIM == 3 ? sy * sy : 0;
+        for (int idx = threadIdx.x; idx < interior_count<DIM, NN>(); idx += blockDim.x) {
+            int i, j, k;
+            const int64_t p = inode<DIM, NN>(idx, i, j, k);
+            if (((i + j + k) & 1) != color) continue;
+            L.u[p] = N::st(fma(c, lk::nbr_sum<DIM>(L.u, p, sy, sz), N::ld(L.q[p])));
+        }
+    });
     __syncthreads();
 }
 
@@ -69,14 +84,16 @@ __device__ void wj_sweep(SLevel<T>& L, double omega_d) {
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
     const C omega = C(omega_d);
-    const int64_t sy = L.n + 1, sz = DIM == 3 ? sy * sy : 0;
-    for (int idx = threadIdx.x; idx < interior_count<DIM>(L.n); idx += blockDim.x) {
-        int i, j, k;
-        const int64_t p = inode<DIM>(L.n, idx, i, j, k);
-        const C up = N::ld(L.u[p]);
-        const C sig = fma(c, lk::nbr_sum<DIM>(L.u, p, sy, sz), N::ld(L.q[p])) - up;
-        L.u2[p] = N::st(fma(omega, sig, up));
-    }
+    dispatch_n(L.n, [&]<int NN>() {
+        constexpr int64_t sy = NN + 1, sz = DIM == 3 ? sy * sy : 0;
+        for (int idx = threadIdx.x; idx < interior_count<DIM, NN>(); idx += blockDim.x) {
+            int i, j, k;
+            const int64_t p = inode<DIM, NN>(idx, i, j, k);
+            const C up = N::ld(L.u[p]);
+            const C sig = fma(c, lk::nbr_sum<DIM>(L.u, p, sy, sz), N::ld(L.q[p])) - up;
+            L.u2[p] = N::st(fma(omega, sig, up));
+        }
+    });
     __syncthreads();
     T* t = L.u;
     L.u = L.u2;
@@ -100,13 +117,16 @@ __device__ void residual(SLevel<T>& L, bool red_only) {
     using N = Num<T>;
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
-    const int64_t sy = L.n + 1, sz = DIM == 3 ? sy * sy : 0;
-    for (int idx = threadIdx.x; idx < interior_count<DIM>(L.n); idx += blockDim.x) {
-        int i, j, k;
-        const int64_t p = inode<DIM>(L.n, idx, i, j, k);
-        if (red_only && ((i + j + k) & 1)) continue;
-        L.r[p] = N::st(fma(c, lk::nbr_sum<DIM>(L.u, p, sy, sz), N::ld(L.q[p])) - N::ld(L.u[p]));
-    }
+    dispatch_n(L.n, [&]<int NN>() {
+        constexpr int64_t sy = NN + 1, sz = DIM == 3 ? sy * sy : 0;
+        for (int idx = threadIdx.x; idx < interior_count<DIM, NN>(); idx += blockDim.x) {
+            int i, j, k;
+            const int64_t p = inode<DIM, NN>(idx, i, j, k);
+            if (red_only && ((i + j + k) & 1)) continue;
+            L.r[p] = N::st(fma(c, lk::nbr_sum<DIM>(L.u, p, sy, sz), N::ld(L.q[p])) -
+                           N::ld(L.u[p]));
+        }
+    });
     __syncthreads();
 }
 
@@ -117,9 +137,10 @@ __device__ void restrict_fw(SLevel<T>& F, SLevel<T>& Cl, bool red_only) {
     const int nc = Cl.n;
     const int64_t sy = F.n + 1, sz = DIM == 3 ? sy * sy : 0;
     const bool exact = nc == 2;
-    for (int idx = threadIdx.x; idx < interior_count<DIM>(nc); idx += blockDim.x) {
+    dispatch_n(nc, [&]<int NC>() {
+    for (int idx = threadIdx.x; idx < interior_count<DIM, NC>(); idx += blockDim.x) {
         int I, J, K;
-        const int64_t P = inode<DIM>(nc, idx, I, J, K);
+        const int64_t P = inode<DIM, NC>(idx, I, J, K);
         const int64_t p = (2 * K) * sz + (2 * J) * sy + 2 * I;
         auto R = [&](int64_t o) { return N::ld(F.r[p + o]); };
         C v;
@@ -168,6 +189,7 @@ __device__ void restrict_fw(SLevel<T>& F, SLevel<T>& Cl, bool red_only) {
         Cl.q[P] = N::st(v);
         Cl.u[P] = exact ? N::st(v) : N::st(C(0));
     }
+    });
     __syncthreads();
 }
 
@@ -178,11 +200,12 @@ __device__ void prolong_add(SLevel<T>& Cl, SLevel<T>& F) {
     const int nc = Cl.n;
     const int64_t sy = F.n + 1, sz = DIM == 3 ? sy * sy : 0;
     const int64_t cy = nc + 1, cz = DIM == 3 ? cy * cy : 0;
-    const int cells = DIM == 3 ? nc * nc * nc : nc * nc;
     T* u = F.u;
     const T* uc = Cl.u;
+    dispatch_n(nc, [&]<int NC>() {
+    constexpr int cells = DIM == 3 ? NC * NC * NC : NC * NC;
     for (int cell = threadIdx.x; cell < cells; cell += blockDim.x) {
-        const int I = cell % nc, J = (cell / nc) % nc, K = DIM == 3 ? cell / (nc * nc) : 0;
+        const int I = cell % NC, J = (cell / NC) % NC, K = DIM == 3 ? cell / (NC * NC) : 0;
         const int64_t P = K * cz + J * cy + I;
         const int64_t p = (2 * K) * sz + (2 * J) * sy + 2 * I;
         const C c000 = N::ld(uc[P]), c100 = N::ld(uc[P + 1]), c010 = N::ld(uc[P + cy]),
@@ -220,6 +243,7 @@ __device__ void prolong_add(SLevel<T>& Cl, SLevel<T>& F) {
             add(pz + 1 + sy, C(0.125), oct);
         }
     }
+    });
     __syncthreads();
 }
 
