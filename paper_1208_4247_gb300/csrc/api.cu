@@ -167,11 +167,12 @@ int num_levels(const gmg_config& c) { return c.levels > 0 ? c.levels : ilog2(c.n
 
 enum Kind {
     K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_OUTER_RES,
-    K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_TAIL, K_COUNT
+    K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_TAIL, K_RB_FUSED, K_COUNT
 };
 const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restrict",
                                   "prolong_add", "resnorm",  "copy",     "outer_residual",
-                                  "update",      "memset",   "conv1",    "conv_tc_update", "tail"};
+                                  "update",      "memset",   "conv1",    "conv_tc_update", "tail",
+                                  "rb_sweep_fused"};
 const char* kPrecSuffix[3] = {"", "_f32", "_bf16"};
 
 template <typename T>
@@ -211,6 +212,7 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
         case K_CONV1: return {N * 8 * (t ? 27 : 9), N * (w + 32)};  // FP32 FMAs
         case K_CONV2: return {N * 16 * (t ? 27 : 9), N * 3 * w};  // both convs, u read+write
         case K_TAIL: return {N * (t ? 40 : 30) * 8.0 / 7.0, N * 2 * w};
+        case K_RB_FUSED: return {N * (t ? 6 : 4), N * 3 * w};  // read u, q; write u
     }
     return {0.0, 0.0};
 }
@@ -224,6 +226,12 @@ void timed(gmg_handle h, int kind, int level, int prec, int n, bool red_only, F&
     auto m = model(kind, h->cfg.d, n, red_only, w);
     h->timer.run(h->stream, std::string(kKindName[kind]) + kPrecSuffix[prec], level, m.first,
                  m.second, kernels, launch);
+}
+
+// FP32 / BF16 3D red-black: one fused kernel per sweep (ping-pong buffers)
+template <typename T>
+bool use_fused_rb(gmg_handle h) {
+    return !std::is_same<T, double>::value && h->cfg.smoother == GMG_RBGS && h->cfg.d == 3;
 }
 
 bool learned_level(gmg_handle h, int l) {
@@ -260,6 +268,15 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
         if constexpr (std::is_same<T, double>::value) {
             if (learned_level(h, l)) {
                 learned_sweep(h, L, l, sigma_ready && s == 0);
+                continue;
+            }
+        }
+        if constexpr (!std::is_same<T, double>::value) {
+            if (use_fused_rb<T>(h)) {
+                timed(h, K_RB_FUSED, l, p, L.n, false, [&] {
+                    fused::rb_sweep3<T>(L.n, L.u[cur], L.u[cur ^ 1], L.q, h->stream);
+                });
+                cur ^= 1;
                 continue;
             }
         }
@@ -553,7 +570,8 @@ gmg_status alloc_hierarchy(gmg_handle h, std::vector<Level<T>>& lv, int levels, 
         v.nodes = nodes_of(c.d, v.n);
         if (l > 0 || alloc_u0)
             if ((st = dev_alloc(h, &v.u[0], v.nodes)) != GMG_OK) return st;
-        if (c.smoother == GMG_WJACOBI && (st = dev_alloc(h, &v.u[1], v.nodes)) != GMG_OK) return st;
+        const bool pingpong = c.smoother == GMG_WJACOBI || use_fused_rb<T>(h);
+        if (pingpong && (st = dev_alloc(h, &v.u[1], v.nodes)) != GMG_OK) return st;
         if ((st = dev_alloc(h, &v.q, v.nodes)) != GMG_OK) return st;
         const bool need_r = l + 1 < levels || c.smoother == GMG_LEARNED;
         if (need_r && (st = dev_alloc(h, &v.r, v.nodes)) != GMG_OK) return st;
