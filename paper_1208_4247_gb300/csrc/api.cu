@@ -228,10 +228,10 @@ void timed(gmg_handle h, int kind, int level, int prec, int n, bool red_only, F&
                  m.second, kernels, launch);
 }
 
-// FP32 / BF16 3D red-black: one fused kernel per sweep (ping-pong buffers)
+// FP32 3D red-black: one fused kernel per sweep (ping-pong buffers)
 template <typename T>
 bool use_fused_rb(gmg_handle h) {
-    return !std::is_same<T, double>::value && h->cfg.smoother == GMG_RBGS && h->cfg.d == 3;
+    return std::is_same<T, float>::value && h->cfg.smoother == GMG_RBGS && h->cfg.d == 3;
 }
 
 bool learned_level(gmg_handle h, int l) {
@@ -271,10 +271,10 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
                 continue;
             }
         }
-        if constexpr (!std::is_same<T, double>::value) {
+        if constexpr (std::is_same<T, float>::value) {
             if (use_fused_rb<T>(h)) {
                 timed(h, K_RB_FUSED, l, p, L.n, false, [&] {
-                    fused::rb_sweep3<T>(L.n, L.u[cur], L.u[cur ^ 1], L.q, h->stream);
+                    fused::rb_sweep3_f32(L.n, L.u[cur], L.u[cur ^ 1], L.q, h->stream);
                 });
                 cur ^= 1;
                 continue;

@@ -72,11 +72,10 @@ template <typename T>
 void update(int d, int n, double* u, const T* e, cudaStream_t s);
 }  // namespace mixed
 
-// Fused red-black sweep (fused.cu, 3D FP32 / BF16): u_out = one full sweep
-// of u_in (red then black), one pass over memory.
+// Fused red-black sweep (fused.cu, 3D FP32): u_out = one full sweep of u_in
+// (red then black), one pass over memory.
 namespace fused {
-template <typename T>
-void rb_sweep3(int n, const T* uin, T* uout, const T* q, cudaStream_t s);
+void rb_sweep3_f32(int n, const float* uin, float* uout, const float* q, cudaStream_t s);
 }  // namespace fused
 
 // Persistent single-CTA tail (tail.cu): the V-cycle on levels n_top, n_top/2,
