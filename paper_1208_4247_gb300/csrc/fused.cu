@@ -64,15 +64,17 @@ __global__ void __launch_bounds__(NT) k_rb_sweep3_f32(const float* __restrict__ 
                 dst[m] = 0.f;
         }
     };
-    auto half = [&](int k, int color, int lo) {
+    // one colour of plane k over the window region [LO, PX-LO) x [LO, PY-LO)
+    // (LO = 1: tile plus ring, LO = 2: tile); compile-time region width
+    auto half = [&]<int LO>(int k, int color) {
         if (k < 1 || k > n - 1) return;
+        constexpr int W = PX - 2 * LO, HH = PY - 2 * LO;
         float* uc = su[slot(k)];
         const float* um = su[slot(k - 1)];
         const float* up = su[slot(k + 1)];
         const float* qk = sq[qslot(k)];
-        const int w = PX - 2 * lo, h = PY - 2 * lo;
-        for (int t = tid; t < w * h; t += NT) {
-            const int sx = lo + t % w, syy = lo + t / w;
+        for (int t = tid; t < W * HH; t += NT) {
+            const int sx = LO + t % W, syy = LO + t / W;
             const int i = i0 - 2 + sx, j = j0 - 2 + syy;
             if (i < 1 || i > n - 1 || j < 1 || j > n - 1 || ((i + j + k) & 1) != color) continue;
             const int m = syy * PX + sx;
@@ -87,17 +89,17 @@ __global__ void __launch_bounds__(NT) k_rb_sweep3_f32(const float* __restrict__ 
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    half(ks - 1, 0, 2);
+    half.template operator()<2>(ks - 1, 0);
     for (int k = ks; k <= ke; ++k) {
         // plane k+2 and q of k+1 in flight while planes k, k-1 are swept
         fetch(uin, su[slot(k + 2)], k + 2);
         fetch(q, sq[qslot(k + 1)], k + 1);
         cp_async_commit();
         __syncthreads();
-        half(k, 0, 1);  // red, tile + ring
+        half.template operator()<1>(k, 0);  // red, tile + ring
         __syncthreads();
         if (k - 1 >= ks) {
-            half(k - 1, 1, 2);  // black, tile
+            half.template operator()<2>(k - 1, 1);  // black, tile
             __syncthreads();
             const float* done = su[slot(k - 1)];
             for (int m = tid; m < TX * TY; m += NT) {
