@@ -78,7 +78,10 @@ gmg_status gmg_config_init(gmg_config* cfg, int d, int n);
 
 /* Create a solver for *cfg on the current CUDA device.  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream) on which every later call on
- * the handle is ordered.  Allocates the level hierarchy on the device. */
+ * the handle is ordered.  Allocates the level hierarchy on the device.
+ * Environment: GMG_FUSED_RB=1 makes GMG_FP32_IR handles in 3D with red-black
+ * smoothing run each sweep as one fused z-streaming kernel (same results
+ * bit for bit; slower on GB300, see the design notes). */
 gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out);
 
 /* GMGSolve (Algorithm 3, all levels on the device): starting from the initial

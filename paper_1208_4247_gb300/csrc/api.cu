@@ -5,6 +5,7 @@
 // refinement.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -50,6 +51,7 @@ struct gmg_handle_s {
     double* u_stage = nullptr;
     std::vector<void*> allocs;
     KernelTimer timer;  // launch accounting and optional per-kernel event timing
+    bool fused_rb = false;  // GMG_FUSED_RB=1 at create: fused FP32 3D red-black sweeps
     // learned smoother (GMG_LEARNED): per level BF16-rounded weights on the
     // device (NULL: red-black GS on that level) and the hidden-layer buffer
     std::vector<float*> lw, lz;
@@ -228,10 +230,13 @@ void timed(gmg_handle h, int kind, int level, int prec, int n, bool red_only, F&
                  m.second, kernels, launch);
 }
 
-// FP32 3D red-black: one fused kernel per sweep (ping-pong buffers)
+// FP32 3D red-black with GMG_FUSED_RB=1: one fused kernel per sweep
+// (ping-pong buffers).  Off by default: on GB300 the fused kernel is bound by
+// per-node instruction issue and is slower than the two half-sweep kernels.
 template <typename T>
 bool use_fused_rb(gmg_handle h) {
-    return std::is_same<T, float>::value && h->cfg.smoother == GMG_RBGS && h->cfg.d == 3;
+    return std::is_same<T, float>::value && h->fused_rb && h->cfg.smoother == GMG_RBGS &&
+           h->cfg.d == 3;
 }
 
 bool learned_level(gmg_handle h, int l) {
@@ -633,6 +638,7 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     gmg_handle h = new gmg_handle_s();
     h->cfg = *cfg;
     h->user_stream = (cudaStream_t)cuda_stream;
+    if (const char* v = std::getenv("GMG_FUSED_RB")) h->fused_rb = std::strcmp(v, "1") == 0;
     auto fail = [&](gmg_status s) {
         gmg_destroy(h);
         return s;

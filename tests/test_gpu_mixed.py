@@ -100,3 +100,20 @@ def test_full_size_513(torch_cuda, prec, k):
     uo = np.zeros_like(f)
     oracle.solve(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1), f, uo, rtol=1e-12, maxit=60)
     assert _rel(ug, uo) <= 1e-9
+
+
+def test_fused_sweep_equals_two_half_sweeps(torch_cuda, monkeypatch):
+    """GMG_FUSED_RB=1: the fused z-streaming FP32 sweep gives the same V-cycle
+    bit for bit (it performs the same updates in the same order per node)."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 128
+    f = torch.from_numpy(inputs.rhs_uniform(d, n, 6)).cuda()
+    out = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("GMG_FUSED_RB", flag)
+        u = torch.zeros_like(f)
+        with Solver(d, n, precision="fp32", inner_cycles=2) as S:
+            S.cycles(f, u, 2)
+        out.append(u.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
