@@ -243,6 +243,17 @@ def run_batch(torch, args):
     ms1 = e0.elapsed_time(e1)
     for S in solvers:
         S.close()
+    # and one by one in plain FP64 (weighted Jacobi V(1,1))
+    solvers = [Solver(d, n, smoother="wjacobi", omega=0.8, nu1=1, nu2=1) for d, n in mix]
+    one_by_one()
+    torch.cuda.synchronize()
+    e0.record(s)
+    one_by_one()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    for S in solvers:
+        S.close()
     del fd, ud
     torch.cuda.empty_cache()
     dom, rec, share = dominant(stats)
@@ -253,7 +264,8 @@ def run_batch(torch, args):
             "max_relres": max(rel), "completion_steps_histogram": hist,
             "autotuned": best, "autotune_tried": [[p, t] for p, t in tried],
             "one_by_one_ms": ms1, "one_by_one_dof_per_s": dof / (ms1 * 1e-3),
-            "speedup_vs_one_by_one": ms1 / ms, "dominant_kernel": dom,
+            "speedup_vs_one_by_one": ms1 / ms, "one_by_one_fp64_ms": ms64,
+            "speedup_vs_one_by_one_fp64": ms64 / ms, "dominant_kernel": dom,
             "dominant_share": share, "gpu_launches": launches}
 
 
