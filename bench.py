@@ -33,6 +33,10 @@ UNKNOWNS = (N - 1) ** D
 FP64_INST_PER_CLK_SM = 2
 NUM_SMS = 152
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) per launch of the level-0 red-black half sweep of
+# the 257^3 FP64 solve, from one ncu capture of the current kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum: 269.5 MB + 85.8 MB)
+RB_HALF_L0_TRAFFIC = 355.3e6
 
 
 def peaks():
@@ -450,7 +454,9 @@ def run_ours(args, rank, ws, local):
     alg_bytes = sum(r["bytes"] * r["launches"] for r in stats) / args.steps
     roof = {"bound": "alu", "kernel": f"{dom} (level 0)", "achieved": achieved,
             "peak": peak_inst, "unit": "T FP64-pipe inst/s", "frac": achieved / peak_inst,
-            "traffic": None,
+            "traffic": RB_HALF_L0_TRAFFIC if dom == "rb_half" else None,
+            "traffic_unit": "bytes per launch (ncu)",
+            "alg_bytes_per_launch": rec["bytes"],
             "peak_note": "2 FP64 inst/clk/SM x 152 SMs x 2070 MHz (derived, nominal)",
             "kernel_share": tot_ms[dom] / sum(tot_ms.values()),
             "kernel_hbm_gbs": rec["bytes"] / avg_s / 1e9}
