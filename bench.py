@@ -328,6 +328,22 @@ def run_learned(torch, args):
     return out
 
 
+def reduce_max_ms(ms: float, ws: int, device) -> float:
+    """Max of a per-rank time over all ranks (the job's time); identity at N=1."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, ws: int, ms_per_step: float) -> float:
+    """Whole-job throughput: the units all ranks processed / the max time."""
+    return units_per_rank * ws / (ms_per_step * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -431,12 +447,9 @@ def run_ours(args, rank, ws, local):
         clk.mark("t1")
     ms_total = ev0.elapsed_time(ev1)
     stats, launches = S.timing_report()
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = reduce_max_ms(ms_total, ws, dev)
     ms_step = ms_total / args.steps
-    value = UNKNOWNS * ws / (ms_step * 1e-3)
+    value = job_value(UNKNOWNS, ws, ms_step)
 
     # dominant kernel: largest summed device time; achieved = its per-launch
     # FP64 instruction count / its average launch time (level 0 record)

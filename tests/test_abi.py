@@ -95,3 +95,26 @@ def test_learned_calls_reject_bad_sizes(L):
     loss = ctypes.c_double()
     assert L.gmg_learned_loss_grad(3, 2, w, None, 10, ctypes.byref(loss), None, None) == 1
     assert L.gmg_learned_train(3, 64, 0, 1, 1, 10, 1e-3, 1, w, w, None, None) == 1
+
+
+def test_batch_and_fft_reject_bad_arguments(L):
+    c = gmg.Config()
+    L.gmg_config_init(ctypes.byref(c), 3, 16)
+    c.precision = 1
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 2)(3, 2)
+    n = (ctypes.c_int * 2)(16, 100)
+    assert L.gmg_batch_create(2, d, n, ctypes.byref(c), 0, 0, None, ctypes.byref(h)) == 1
+    assert b"solve 1" in L.gmg_last_error()
+    n[1] = 64
+    c.precision = 0
+    assert L.gmg_batch_create(2, d, n, ctypes.byref(c), 0, 0, None, ctypes.byref(h)) == 8
+    c.precision = 1
+    c.smoother, c.nu1, c.nu2 = 0, 1, 2
+    assert L.gmg_batch_create(2, d, n, ctypes.byref(c), 0, 0, None, ctypes.byref(h)) == 8
+    assert L.gmg_batch_solve(None, None, None, 1e-10, None, None, None) == 1
+    assert L.gmg_batch_destroy(None) == 0
+    assert L.gmg_fft_create(3, 100, None, ctypes.byref(h)) == 1
+    assert L.gmg_fft_create(4, 64, None, ctypes.byref(h)) == 1
+    assert L.gmg_fft_solve(None, None, None) == 1
+    assert L.gmg_fft_destroy(None) == 0
