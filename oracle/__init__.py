@@ -74,6 +74,7 @@ def lib():
                 ("orc_conv_fwd_bf16", [I, I, P, P, P, P], None),
                 ("orc_set_bf16_activations", [I], None),
                 ("orc_vcycle_learned", [ctypes.POINTER(Cfg), P, P, P], I),
+                ("orc_fmg", [ctypes.POINTER(Cfg), P, P], I),
             ]:
                 fn = getattr(L, name)
                 fn.argtypes = args
@@ -251,4 +252,13 @@ def vcycle_learned(cfg: Cfg, weights, b, u, bf16_activations=False):
     lib().orc_set_bf16_activations(0)
     if rc != 0:
         raise ValueError("oracle learned V-cycle: bad configuration")
+    return u
+
+
+def fmg(cfg: Cfg, b, u):
+    """FMG-V (Algorithm 2) on b = h^2 f; u (initial content ignored) is
+    overwritten with the result."""
+    rc = lib().orc_fmg(ctypes.byref(cfg), _p(b), _p(u))
+    if rc != 0:
+        raise ValueError("oracle FMG: bad configuration")
     return u

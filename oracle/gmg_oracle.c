@@ -658,3 +658,46 @@ int orc_vcycle_learned(const orc_cfg* c, const float* const* W, const double* b0
     free(r);
     return 0;
 }
+
+/* Full multigrid FMG-V (Algorithm 2): the right-hand side restricted to every
+ * level, b_{l+1} = 4 FW(b_l) (the scaling of the residual restriction); the
+ * coarsest level solved; then for l = L-2 .. 0: u_l = P u_{l+1} (interpolation
+ * of the coarse solution) followed by one V-cycle (Algorithm 1) on levels
+ * l .. L-1 with right-hand side b_l.  The initial u0 is ignored.  Returns 0
+ * or -1. */
+int orc_fmg(const orc_cfg* c, const double* b0, double* u0)
+{
+    int d = c->d, L = c->levels;
+    if (L < 1 || (c->n >> (L - 1)) < 2) return -1;
+    double** b = (double**)calloc(L, sizeof(double*));
+    double** u = (double**)calloc(L, sizeof(double*));
+    b[0] = (double*)b0;
+    u[0] = u0;
+    for (int l = 1; l < L; ++l) {
+        b[l] = (double*)calloc(nodes(d, c->n >> l), sizeof(double));
+        u[l] = (double*)calloc(nodes(d, c->n >> l), sizeof(double));
+    }
+    for (int l = 0; l + 1 < L; ++l) orc_restrict_fw(d, c->n >> l, b[l], b[l + 1]);
+    if (L == 1) {
+        memset(u0, 0, sizeof(double) * nodes(d, c->n));
+        orc_vcycle(c, b0, u0);
+    } else {
+        orc_coarse_solve(d, c->n >> (L - 1), b[L - 1], u[L - 1], c->coarse_sweeps);
+        for (int l = L - 2; l >= 0; --l) {
+            int nl = c->n >> l;
+            memset(u[l], 0, sizeof(double) * nodes(d, nl));
+            orc_prolong_add(d, nl / 2, u[l + 1], u[l]);
+            orc_cfg cl = *c;
+            cl.n = nl;
+            cl.levels = L - l;
+            orc_vcycle(&cl, b[l], u[l]);
+        }
+    }
+    for (int l = 1; l < L; ++l) {
+        free(b[l]);
+        free(u[l]);
+    }
+    free(b);
+    free(u);
+    return 0;
+}

@@ -133,3 +133,26 @@ def from_vec(v: np.ndarray, d: int, n: int) -> np.ndarray:
     a = np.zeros((n + 1,) * d)
     a[(slice(1, -1),) * d] = v.reshape((n - 1,) * d)
     return a
+
+
+def fmg_matrix(d, n, levels, smoother=1, omega=0.8, nu1=2, nu2=2, coarse_sweeps=1):
+    """FMG-V as a linear map u = M b: restricted right-hand sides, exact
+    one-unknown coarsest solve, then per level u_l = P u_{l+1} followed by one
+    V-cycle from that guess: u_l = E_l P u_{l+1} + (I - E_l) A_l^-1 b_l."""
+    A = lap(d, n)
+    if levels == 1:
+        E = vcycle_error_matrix(d, n, 1, smoother, omega, nu1, nu2, coarse_sweeps)
+        return (np.eye(A.shape[0]) - E) @ np.linalg.inv(A)
+    nc = n // 2
+    if levels == 2:
+        Ac = lap(d, nc)
+        if nc == 2:
+            Mc = np.linalg.inv(Ac)
+        else:
+            Sc = np.linalg.matrix_power(rbgs_iteration_matrix(d, nc), coarse_sweeps)
+            Mc = (np.eye(Ac.shape[0]) - Sc) @ np.linalg.inv(Ac)
+    else:
+        Mc = fmg_matrix(d, nc, levels - 1, smoother, omega, nu1, nu2, coarse_sweeps)
+    E = vcycle_error_matrix(d, n, levels, smoother, omega, nu1, nu2, coarse_sweeps)
+    I = np.eye(A.shape[0])
+    return E @ prolong(d, nc) @ Mc @ restrict(d, n) + (I - E) @ np.linalg.inv(A)

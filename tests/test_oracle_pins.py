@@ -403,3 +403,35 @@ def test_bf16_network_with_jacobi_weights(d, n):
     y2, z = oracle.conv_fwd(W1i, W2i, xi)
     if np.all(np.abs(z) < 256):  # hidden values stay BF16-representable
         np.testing.assert_array_equal(y1, y2)
+
+
+@pytest.mark.parametrize("d,n,sm,om,nu1,nu2", [(2, 16, oracle.RBGS, 0.8, 1, 2),
+                                                (2, 16, oracle.WJACOBI, 0.8, 2, 2),
+                                                (3, 8, oracle.RBGS, 0.8, 2, 2)])
+def test_fmg_equals_dense_composition(d, n, sm, om, nu1, nu2):
+    """Algorithm 2 as a linear map of the right-hand side."""
+    L = oracle.max_levels(n)
+    M = dm.fmg_matrix(d, n, L, sm, om, nu1, nu2, 1)
+    rng = np.random.default_rng(13)
+    b = rng.standard_normal((n - 1) ** d)
+    u = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)  # ignored by FMG
+    oracle.fmg(oracle.make_cfg(d, n, 0, sm, om, nu1, nu2, 1), dm.from_vec(b, d, n), u)
+    ref = M @ b
+    assert np.max(np.abs(dm.to_vec(u) - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("d,n,nu,ok", [(2, 256, (1, 2), True), (2, 512, (1, 2), True),
+                                       (3, 32, (3, 3), True), (3, 64, (3, 3), True),
+                                       (3, 32, (1, 2), False), (3, 64, (2, 2), False)])
+def test_fmg_reaches_discretisation_error(d, n, nu, ok):
+    """The paper's FMG-vs-FFT finding (section 5.4): one FMG(1,2) pass reaches
+    the discretisation error in 2D, while 3D needs FMG(3,3); fewer sweeps in 3D
+    leave an error well above it.  Error in the continuous solution, ||.||_h."""
+    from paper_1208_4247_gb300 import inputs
+    ue = inputs.manufactured_u(d, n)
+    f = np.ascontiguousarray(d * np.pi ** 2 * ue)
+    b = oracle.scale_rhs(f)
+    u = np.zeros_like(f)
+    oracle.fmg(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, nu[0], nu[1], 1), b, u)
+    ratio = np.sqrt((1.0 / n) ** d * np.sum((u - ue) ** 2)) / _closed_form_error(d, n)
+    assert (ratio <= 1.2) == ok, ratio
