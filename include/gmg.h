@@ -50,7 +50,7 @@ typedef enum {
 
 typedef enum { GMG_WJACOBI = 0, GMG_RBGS = 1, GMG_LEARNED = 2 } gmg_smoother;
 typedef enum { GMG_FP64 = 0, GMG_FP32_IR = 1, GMG_BF16_IR = 2 } gmg_precision;
-typedef enum { GMG_VCYCLE = 0 } gmg_cycle;
+typedef enum { GMG_VCYCLE = 0, GMG_FMG = 1 } gmg_cycle;
 
 typedef struct {
     int d;             /* 2 or 3 */
@@ -61,7 +61,11 @@ typedef struct {
                           (red = i+j+k even, red before black in pre- and post-smoothing) */
     double omega;      /* weighted-Jacobi weight (ignored by red-black GS) */
     int nu1, nu2;      /* pre- / post-smoothing sweeps (Algorithm 1's mu_f, mu_b), 0..16 */
-    int cycle;         /* gmg_cycle: GMG_VCYCLE */
+    int cycle;         /* gmg_cycle: GMG_VCYCLE, or GMG_FMG: the first cycle of a solve is one
+                          full-multigrid pass (Algorithm 2: the right-hand side restricted
+                          to every level, coarsest solved, then per level interpolation of
+                          the coarse solution and one V-cycle; the initial u is ignored),
+                          the following ones V-cycles (plain FP64, GS or Jacobi only) */
     int precision;     /* gmg_precision: plain FP64, or FP32 / BF16 V-cycles inside
                           FP64 iterative refinement */
     int maxit;         /* cap on V-cycles (FP64) or on outer refinement steps */

@@ -46,6 +46,9 @@ struct gmg_handle_s {
     double* h_res2 = nullptr;  // pinned
     cudaGraphExec_t graph = nullptr;
     const double* graph_u = nullptr;  // level-0 iterate baked into the graph
+    cudaGraphExec_t fmg_graph = nullptr;  // GMG_FMG: the first cycle of a solve
+    int fmg_kernels = 0;
+    std::vector<KernelTimer::Pending> fmg_pending;
     std::vector<double> hist;
     double* f_stage = nullptr;  // device copies for gmg_solve_host
     double* u_stage = nullptr;
@@ -106,9 +109,13 @@ gmg_status check_cfg(const gmg_config* c) {
         set_error("nu1, nu2 must lie in 0..16");
         return GMG_ERR_ARG;
     }
-    if (c->cycle != GMG_VCYCLE) {
-        set_error("cycle must be GMG_VCYCLE");
+    if (c->cycle != GMG_VCYCLE && c->cycle != GMG_FMG) {
+        set_error("cycle must be GMG_VCYCLE or GMG_FMG");
         return GMG_ERR_ARG;
+    }
+    if (c->cycle == GMG_FMG && (c->precision != GMG_FP64 || c->smoother == GMG_LEARNED)) {
+        set_error("GMG_FMG runs in the plain FP64 form with GS or Jacobi smoothing");
+        return GMG_ERR_UNSUPPORTED;
     }
     if (c->precision != GMG_FP64 && c->precision != GMG_FP32_IR && c->precision != GMG_BF16_IR) {
         set_error("unknown precision");
@@ -302,15 +309,16 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
 // level with n <= 16 (3D) / 64 (2D) whose tail arrays fit in 200 KB of shared
 // memory, below every learned level, leaving at least two tail levels.
 template <typename T>
-int tail_level(gmg_handle h, int L) {
+int tail_level(gmg_handle h, const std::vector<Level<T>>& lv) {
     const gmg_config& c = h->cfg;
+    const int L = (int)lv.size();
     const int nmax = c.d == 3 ? 16 : 64;
     int lo = 0;
     if (c.smoother == GMG_LEARNED)
         for (int l = 0; l < L && l < (int)h->lw.size(); ++l)
             if (h->lw[l]) lo = l + 1;
     for (int l = lo; l + 1 < L; ++l) {
-        const int n = c.n >> l;
+        const int n = lv[l].n;
         if (n <= nmax && tail::smem_bytes(c.d, n, L - l, c.smoother, sizeof(T)) <= 200 * 1024)
             return l;
     }
@@ -326,7 +334,7 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
     const int L = (int)lv.size();
     const int p = prec_of<T>();
     std::vector<int> cur(L, 0);
-    const int lt = tail_level<T>(h, L);
+    const int lt = tail_level<T>(h, lv);
     if (lt == 0) {
         // the whole hierarchy is small: one persistent launch
         cudaError_t e = cudaSuccess;
@@ -447,16 +455,59 @@ gmg_status enqueue_step(gmg_handle h) {
     return GMG_OK;
 }
 
-gmg_status ensure_graph(gmg_handle h, double* u) {
-    if (h->graph && h->graph_u == u) return GMG_OK;
-    if (h->graph) {
-        cudaGraphExecDestroy(h->graph);
-        h->graph = nullptr;
+// One full-multigrid pass (Algorithm 2) on the plain FP64 hierarchy, then the
+// FP64 norm: q restricted to every level (4 FW, the residual's scaling), the
+// coarsest solved, then per level u_l = P u_{l+1} and one V-cycle on levels
+// l .. L-1.
+gmg_status enqueue_fmg(gmg_handle h) {
+    const gmg_config& c = h->cfg;
+    std::vector<Level<double>>& lv = h->lv;
+    const int d = c.d, L = (int)lv.size();
+    h->timer.begin_capture();
+    for (int l = 0; l + 1 < L; ++l) {
+        Level<double>& F = lv[l];
+        Level<double>& C = lv[l + 1];
+        timed(h, K_RESTRICT, l, 0, F.n, false, [&] {
+            lk::restrict_fw<double>(d, F.n, F.q, C.q, C.u[0], false, C.n == 2, h->stream);
+        });
     }
-    h->lv[0].u[0] = u;
+    if (L > 1 && lv[L - 1].n > 2) {
+        Level<double>& B = lv[L - 1];
+        for (int s = 0; s < c.coarse_sweeps; ++s)
+            for (int color = 0; color < 2; ++color)
+                timed(h, K_RB_HALF, L - 1, 0, B.n, false,
+                      [&] { lk::rb_half<double>(d, B.n, B.u[0], B.q, color, h->stream); });
+    }
+    cudaError_t e = cudaMemsetAsync(lv[0].u[0], 0, sizeof(double) * lv[0].nodes, h->stream);
+    GMG_CUDA_TRY(e);
+    for (int l = L - 2; l >= 0; --l) {
+        timed(h, K_PROLONG, l, 0, lv[l].n, false, [&] {
+            lk::prolong_add<double>(d, lv[l + 1].n, lv[l + 1].u[0], lv[l].u[0], h->stream);
+        });
+        std::vector<Level<double>> sub(lv.begin() + l, lv.end());
+        gmg_status st = enqueue_vcycle<double>(h, sub);
+        if (st != GMG_OK) return st;
+    }
+    if (L == 1) {
+        gmg_status st = enqueue_vcycle<double>(h, lv);
+        if (st != GMG_OK) return st;
+    }
+    timed(
+        h, K_RESNORM, 0, 0, c.n, false,
+        [&] {
+            fp64::resnorm(c.d, c.n, lv[0].u[0], lv[0].q, h->partial, h->d_res2, h->stream);
+        },
+        2);
+    GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    GMG_CUDA_TRY(cudaGetLastError());
+    return GMG_OK;
+}
+
+gmg_status capture(gmg_handle h, cudaGraphExec_t* out, gmg_status (*enqueue)(gmg_handle)) {
     cudaGraph_t g = nullptr;
     GMG_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    gmg_status st = enqueue_step(h);
+    gmg_status st = enqueue(h);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (st != GMG_OK) {
         if (g) cudaGraphDestroy(g);
@@ -466,13 +517,34 @@ gmg_status ensure_graph(gmg_handle h, double* u) {
         set_error(std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
         return GMG_ERR_CUDA;
     }
-    e = cudaGraphInstantiate(&h->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        h->graph = nullptr;
+        *out = nullptr;
         set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
         return GMG_ERR_CUDA;
     }
+    return GMG_OK;
+}
+
+gmg_status ensure_graph(gmg_handle h, double* u) {
+    if (h->graph && h->graph_u == u) return GMG_OK;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (h->fmg_graph) {
+        cudaGraphExecDestroy(h->fmg_graph);
+        h->fmg_graph = nullptr;
+    }
+    h->lv[0].u[0] = u;
+    gmg_status st;
+    if (h->cfg.cycle == GMG_FMG) {
+        if ((st = capture(h, &h->fmg_graph, enqueue_fmg)) != GMG_OK) return st;
+        h->fmg_kernels = h->timer.graph_kernels;
+        h->fmg_pending = h->timer.pending;
+    }
+    if ((st = capture(h, &h->graph, enqueue_step)) != GMG_OK) return st;
     h->graph_u = u;
     return GMG_OK;
 }
@@ -541,9 +613,19 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
     int it = 0;
     const int cap = stop ? h->cfg.maxit : ncycles;
     while (it < cap && (!stop || res > rtol * res0)) {
-        GMG_CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
+        const bool fmg = it == 0 && h->fmg_graph;
+        GMG_CUDA_TRY(cudaGraphLaunch(fmg ? h->fmg_graph : h->graph, h->stream));
         GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
-        h->timer.after_graph_run();
+        if (fmg) {
+            // the FMG graph's own launch count and (when timing) event pairs
+            std::swap(h->timer.pending, h->fmg_pending);
+            std::swap(h->timer.graph_kernels, h->fmg_kernels);
+            h->timer.after_graph_run();
+            std::swap(h->timer.pending, h->fmg_pending);
+            std::swap(h->timer.graph_kernels, h->fmg_kernels);
+        } else {
+            h->timer.after_graph_run();
+        }
         res = std::sqrt(*h->h_res2);
         ++it;
         const double rel = res0 > 0.0 ? res / res0 : 0.0;
@@ -618,6 +700,7 @@ gmg_status gmg_destroy(gmg_handle h) {
     DeviceGuard guard(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->fmg_graph) cudaGraphExecDestroy(h->fmg_graph);
     h->timer.destroy();
     for (void* p : h->allocs) cudaFree(p);
     if (h->h_res2) cudaFreeHost(h->h_res2);

@@ -22,6 +22,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_LAYOUT", 3: "ERR_ALLOC", 4: "ERR_CUDA",
           8: "ERR_UNSUPPORTED"}
 SMOOTHERS = {"wjacobi": 0, "rbgs": 1, "learned": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+CYCLES = {"v": 0, "fmg": 1}
 
 
 class GMGError(RuntimeError):
@@ -131,7 +132,7 @@ class Solver:
     def __init__(self, d: int, n: int, levels: int = 0, smoother: str = "rbgs",
                  omega: float = 0.8, nu1: int = 2, nu2: int = 2, precision: str = "fp64",
                  maxit: int = 100, inner_cycles: int = 4, coarse_sweeps: int = 64,
-                 stream=None):
+                 cycle: str = "v", stream=None):
         self.d, self.n = d, n
         cfg = Config()
         _check(lib().gmg_config_init(ctypes.byref(cfg), d, n))
@@ -143,6 +144,7 @@ class Solver:
         cfg.maxit = maxit
         cfg.inner_cycles = inner_cycles
         cfg.coarse_sweeps = coarse_sweeps
+        cfg.cycle = CYCLES[cycle]
         self.cfg = cfg
         h = ctypes.c_void_p()
         _check(lib().gmg_create(ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(h)))

@@ -51,7 +51,7 @@ def test_config_defaults(L):
 
 @pytest.mark.parametrize("field,value,status", [
     ("d", 4, 1), ("n", 100, 1), ("n", 1, 1), ("levels", 9, 1), ("smoother", 7, 1),
-    ("omega", 2.5, 1), ("nu1", -1, 1), ("nu2", 17, 1), ("cycle", 1, 1),
+    ("omega", 2.5, 1), ("nu1", -1, 1), ("nu2", 17, 1), ("cycle", 2, 1),
     ("maxit", -3, 1), ("precision", 9, 8),
 ])
 def test_bad_config_rejected_before_device_use(L, field, value, status):
@@ -118,3 +118,12 @@ def test_batch_and_fft_reject_bad_arguments(L):
     assert L.gmg_fft_create(4, 64, None, ctypes.byref(h)) == 1
     assert L.gmg_fft_solve(None, None, None) == 1
     assert L.gmg_fft_destroy(None) == 0
+
+
+def test_fmg_needs_plain_fp64(L):
+    c = gmg.Config()
+    L.gmg_config_init(ctypes.byref(c), 3, 64)
+    c.cycle = 1
+    c.precision = 1
+    h = ctypes.c_void_p()
+    assert L.gmg_create(ctypes.byref(c), None, ctypes.byref(h)) == 8

@@ -245,3 +245,39 @@ def test_residual_norm_matches_oracle(torch_cuda, d, n):
     with Solver(d, n) as S:
         got = S.residual_norm(_dev(torch, f), _dev(torch, u))
     assert got == pytest.approx(ref, rel=1e-12)
+
+
+FMG_CASES = [(2, 64, "rbgs", 0.8, 1, 2), (2, 256, "wjacobi", 0.8, 2, 2), (3, 32, "rbgs", 0.8, 3, 3),
+             (3, 64, "rbgs", 0.8, 2, 2), (3, 16, "wjacobi", 6 / 7, 2, 2)]
+
+
+@pytest.mark.parametrize("case", FMG_CASES, ids=lambda c: "-".join(map(str, c)))
+def test_fmg_pass_and_solve_parity(torch_cuda, case):
+    """GMG_FMG: the first cycle is one FMG pass (Algorithm 2), equal to the
+    oracle's to 1e-12; the solve continues with V-cycles and takes the same
+    number of cycles as the oracle's FMG followed by V-cycles."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n, sm, om, nu1, nu2 = case
+    f = inputs.rhs_uniform(d, n, 8)
+    b = oracle.scale_rhs(f)
+    cfg = oracle.make_cfg(d, n, 0, _orc_smoother(sm), om, nu1, nu2, 1)
+    uo = np.zeros_like(f)
+    oracle.fmg(cfg, b, uo)
+    res0 = oracle.norm2(b)
+    hist_o = [oracle.norm2(oracle.residual(b, uo)) / res0]
+    while hist_o[-1] > 1e-10 and len(hist_o) < 100:
+        oracle.vcycle(cfg, b, uo)
+        hist_o.append(oracle.norm2(oracle.residual(b, uo)) / res0)
+    fd = _dev(torch, f)
+    with Solver(d, n, smoother=sm, omega=om, nu1=nu1, nu2=nu2, cycle="fmg") as S:
+        u1 = torch.full_like(fd, 0.5)  # FMG ignores the initial guess
+        S.cycles(fd, u1, 1)
+        u1o = np.zeros_like(f)
+        oracle.fmg(cfg, b, u1o)
+        assert _rel(u1.cpu().numpy(), u1o) <= TOL_CYCLE
+        ud = torch.zeros_like(fd)
+        it, rel, conv = S.solve(fd, ud, rtol=1e-10)
+        hist_g = np.array(S.history())
+    assert conv and it == len(hist_o)
+    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-6, atol=_floor(d, uo, b))
