@@ -500,6 +500,17 @@ def run_ours(args, rank, ws, local):
            "gmg_speedup_vs_fft": fft_ms / ms_step}
     del uf
 
+    # the paper's FMG (Algorithm 2) as the first cycle, then V(2,2) cycles
+    fmg_runs = {}
+    for nu in (2, 3):
+        Sf = Solver(D, N, nu1=nu, nu2=nu, cycle="fmg")
+        ms_f, it_f, rel_f, _, _ = time_solves(torch, Sf, f, u, args.form_steps,
+                                              max(args.warmup, 1), timing=False)
+        Sf.close()
+        fmg_runs[f"fmg_v{nu}{nu}"] = {"value": UNKNOWNS / (ms_f * 1e-3), "unit": "DOF/s",
+                                      "ms_per_step": ms_f, "cycles": it_f, "relres": rel_f,
+                                      "speedup_vs_plain_v22": ms_step / ms_f}
+
     # end to end through the public API: pinned host f, u; H2D + solve + D2H
     e2e = None
     if not args.no_e2e:
@@ -551,6 +562,7 @@ def run_ours(args, rank, ws, local):
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "cufft_dst_257": fft,
+            "fmg_257": fmg_runs,
             "mixed_precision_513": forms, "batched_512": batch,
             "learned_257": learned}
     if args.kernels:
