@@ -273,6 +273,64 @@ def run_batch(torch, args):
             "dominant_share": share, "gpu_launches": launches}
 
 
+FMG_SWEEPS = ((1, 1), (1, 2), (2, 2), (2, 3), (3, 3))
+
+
+def run_fmg_vs_fft(torch, args):
+    """Section 5.4's comparison at 16M unknowns (2D 4097^2, 3D 257^3): one
+    FMG(nu1, nu2) pass (Algorithm 2) against the direct cuFFT DST-I solve, on
+    the manufactured problem u = prod sin(pi x_m), f = d pi^2 u.  Each pass is
+    timed with CUDA events around the public call (scaling of f, the FMG
+    graph, the residual norm and its host read included); the L2(Omega)
+    error sqrt(h^d sum (u - u*)^2) against the exact u sits beside it; the
+    FFT's error is the discretisation error of the FD system itself."""
+    from paper_1208_4247_gb300 import inputs
+    from paper_1208_4247_gb300.gmg import FFTSolver, Solver
+    stream = torch.cuda.current_stream()
+    steps = max(args.form_steps, 5)
+    out = {}
+    for d, n in ((2, 4096), (3, 256)):
+        ustar = torch.from_numpy(inputs.manufactured_u(d, n)).cuda()
+        f = (d * np.pi ** 2) * ustar
+        u = torch.zeros_like(f)
+        h = 1.0 / n
+
+        def l2err():
+            return float(torch.sqrt(((u - ustar) ** 2).sum() * h ** d))
+
+        def timed(call):
+            for _ in range(max(args.warmup, 1)):
+                call()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / steps
+
+        F = FFTSolver(d, n)
+        fft_ms = timed(lambda: F.solve(f, u))
+        F.close()
+        disc = l2err()
+        rows = {"fft": {"ms": fft_ms, "l2_error": disc}}
+        for nu1, nu2 in FMG_SWEEPS:
+            S = Solver(d, n, nu1=nu1, nu2=nu2, cycle="fmg")
+            ms = timed(lambda: S.cycles(f, u, 1))
+            S.close()
+            e = l2err()
+            rows[f"fmg({nu1},{nu2})"] = {"ms": ms, "l2_error": e,
+                                         "error_over_discretisation": e / disc,
+                                         "speedup_vs_fft": fft_ms / ms}
+        del u, f, ustar
+        torch.cuda.empty_cache()
+        out[f"{d}d_{n + 1}"] = {"unknowns": (n - 1) ** d, "levels": n.bit_length() - 1,
+                                "passes_timed": steps, "rows": rows}
+    return out
+
+
 def run_learned(torch, args):
     """3D 257^3 GRF workload (power ~|k|^-2, seed 5): V(1,1) cycles with the
     learned smoother (trained here on the GPU on 10k error samples from plain
@@ -536,8 +594,9 @@ def run_ours(args, rank, ws, local):
 
     if rank != 0:
         return
-    forms = batch = learned = None
+    forms = batch = learned = fmg_fft = None
     if not args.no_forms:
+        fmg_fft = run_fmg_vs_fft(torch, args)
         forms = run_forms(torch, args)
         batch = run_batch(torch, args)
         learned = run_learned(torch, args)
@@ -562,7 +621,7 @@ def run_ours(args, rank, ws, local):
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "cufft_dst_257": fft,
-            "fmg_257": fmg_runs,
+            "fmg_257": fmg_runs, "fmg_pass_vs_fft": fmg_fft,
             "mixed_precision_513": forms, "batched_512": batch,
             "learned_257": learned}
     if args.kernels:

@@ -281,3 +281,45 @@ def test_fmg_pass_and_solve_parity(torch_cuda, case):
         hist_g = np.array(S.history())
     assert conv and it == len(hist_o)
     np.testing.assert_allclose(hist_g, hist_o, rtol=1e-6, atol=_floor(d, uo, b))
+
+
+def _closed_form_disc_error(d, n):
+    """||u_h - u*||_h for u* = prod sin(pi x_m): u* is an eigenvector of the
+    FD operator with eigenvalue lambda = d (2 - 2 cos(pi h)) / h^2, so the
+    discrete solution is (d pi^2 / lambda) u*, and h^d sum sin^2 = 2^-d."""
+    h = 1.0 / n
+    lam = d * (2.0 - 2.0 * np.cos(np.pi * h)) / h ** 2
+    return abs(d * np.pi ** 2 / lam - 1.0) * 2.0 ** (-d / 2)
+
+
+@pytest.mark.parametrize("d,n,nu,ok", [(2, 4096, (1, 2), True), (3, 256, (3, 3), True),
+                                       (3, 256, (1, 2), False)])
+def test_fmg_pass_discretisation_error_full_size(torch_cuda, d, n, nu, ok):
+    """At the 16M-unknown sizes of the FMG-vs-FFT comparison (section 5.4),
+    one GPU FMG pass reaches the discretisation error (within 1.2x) with
+    FMG(1,2) in 2D and FMG(3,3) in 3D, and not with FMG(1,2) in 3D."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    ue = inputs.manufactured_u(d, n)
+    fd = _dev(torch, d * np.pi ** 2 * ue)
+    ud = torch.zeros_like(fd)
+    with Solver(d, n, nu1=nu[0], nu2=nu[1], cycle="fmg") as S:
+        S.cycles(fd, ud, 1)
+    err = np.sqrt((1.0 / n) ** d * np.sum((ud.cpu().numpy() - ue) ** 2))
+    assert (err / _closed_form_disc_error(d, n) <= 1.2) == ok
+
+
+def test_fmg_pass_parity_full_size(torch_cuda):
+    """One FMG(2,2) pass on the 3D 257^3 workload input (f = U[-1,1], seed 2)
+    equals the oracle's element by element to 1e-12 relative."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 256
+    f = inputs.rhs_uniform(d, n, 2)
+    uo = np.zeros_like(f)
+    oracle.fmg(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1), oracle.scale_rhs(f), uo)
+    fd = _dev(torch, f)
+    ud = torch.zeros_like(fd)
+    with Solver(d, n, cycle="fmg") as S:
+        S.cycles(fd, ud, 1)
+    assert _rel(ud.cpu().numpy(), uo) <= TOL_CYCLE
