@@ -85,7 +85,9 @@ gmg_status gmg_config_init(gmg_config* cfg, int d, int n);
  * the handle is ordered.  Allocates the level hierarchy on the device.
  * Environment: GMG_FUSED_RB=1 makes GMG_FP32_IR handles in 3D with red-black
  * smoothing run each sweep as one fused z-streaming kernel (same results
- * bit for bit; slower on GB300, see the design notes). */
+ * bit for bit; slower on GB300, see the design notes).  GMG_TAIL_N=m sets the
+ * largest level n handled by the single-CTA tail launch (default 8 in 3D,
+ * 32 in 2D; 1 turns the tail off); results are the same bit for bit. */
 gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out);
 
 /* GMGSolve (Algorithm 3, all levels on the device): starting from the initial

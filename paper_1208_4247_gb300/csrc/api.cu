@@ -55,6 +55,7 @@ struct gmg_handle_s {
     std::vector<void*> allocs;
     KernelTimer timer;  // launch accounting and optional per-kernel event timing
     bool fused_rb = false;  // GMG_FUSED_RB=1 at create: fused FP32 3D red-black sweeps
+    int tail_max = 0;       // GMG_TAIL_N at create: largest tail level n (0 = default)
     // learned smoother (GMG_LEARNED): per level BF16-rounded weights on the
     // device (NULL: red-black GS on that level) and the hidden-layer buffer
     std::vector<float*> lw, lz;
@@ -193,9 +194,11 @@ int prec_of<float>() { return 1; }
 template <>
 int prec_of<bf16>() { return 2; }
 
-// Arithmetic model per launch: instructions in the kernel's compute
-// precision (FP64 for double storage and for the refinement kernels, FP32
-// otherwise) and algorithmic DRAM bytes (each value the operation needs read
+// Arithmetic model per launch: the operation's algorithmic instruction count
+// in the kernel's compute precision (FP64 for double storage and for the
+// refinement kernels, FP32 otherwise; a red-black node update counts its
+// 2d-1 adds + 1 fma even where the diagonal walkers share one add between
+// two nodes) and algorithmic DRAM bytes (each value the operation needs read
 // once, each value it produces written once) with w bytes per stored value.
 std::pair<double, double> model(int kind, int d, int n, bool red_only, double w) {
     const double N = std::pow((double)(n - 1), d);
@@ -213,7 +216,9 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
             return red_only ? std::make_pair(Nc * (t ? 13 : 4), N / 2 * w + Nc * 2 * w)
                             : std::make_pair(Nc * (t ? 27 : 8), N * w + Nc * 2 * w);
         case K_PROLONG: return {cells * (t ? 20 : 8), Nc * w + N * 2 * w};
-        case K_RESNORM: return {N * (t ? 8 : 6), N * 16};
+        case K_RESNORM:
+            return red_only ? std::make_pair(N / 2 * (t ? 8 : 6), N * 12)
+                            : std::make_pair(N * (t ? 8 : 6), N * 16);
         case K_COPY: return {0.0, N * 2 * w};
         case K_OUTER_RES: return {N * (t ? 8 : 6), N * (16 + w)};
         case K_UPDATE: return {N, N * (16 + w)};
@@ -306,13 +311,13 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
 }
 
 // First level handled by the persistent tail kernel (L = none): the first
-// level with n <= 16 (3D) / 64 (2D) whose tail arrays fit in 200 KB of shared
+// level with n <= 8 (3D) / 32 (2D) (GMG_TAIL_N overrides) whose tail arrays fit in 200 KB of shared
 // memory, below every learned level, leaving at least two tail levels.
 template <typename T>
 int tail_level(gmg_handle h, const std::vector<Level<T>>& lv) {
     const gmg_config& c = h->cfg;
     const int L = (int)lv.size();
-    const int nmax = c.d == 3 ? 16 : 64;
+    const int nmax = h->tail_max > 0 ? h->tail_max : c.d == 3 ? 8 : 32;
     int lo = 0;
     if (c.smoother == GMG_LEARNED)
         for (int l = 0; l < L && l < (int)h->lw.size(); ++l)
@@ -426,6 +431,14 @@ gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
     return GMG_OK;
 }
 
+// After a plain red-black V-cycle (or FMG pass) the last operation on level 0
+// is a black half sweep, so the stopping-test norm needs the red nodes only.
+bool norm_red_only(gmg_handle h) {
+    const gmg_config& c = h->cfg;
+    return c.precision == GMG_FP64 && c.smoother == GMG_RBGS &&
+           (h->lv.size() > 1 ? c.nu2 > 0 : c.nu1 > 0);
+}
+
 // One step of the stopping loop: a plain cycle plus the FP64 norm, or one
 // refinement step; the squared scaled norm lands in h->h_res2.
 gmg_status enqueue_step(gmg_handle h) {
@@ -437,10 +450,10 @@ gmg_status enqueue_step(gmg_handle h) {
         if (st != GMG_OK) return st;
         double* keep = sigma_carried(h) ? h->lv[0].r : nullptr;
         timed(
-            h, K_RESNORM, 0, 0, c.n, false,
+            h, K_RESNORM, 0, 0, c.n, norm_red_only(h),
             [&] {
                 fp64::resnorm(c.d, c.n, h->lv[0].u[0], h->lv[0].q, h->partial, h->d_res2,
-                              h->stream, keep);
+                              h->stream, keep, norm_red_only(h));
             },
             2);
     } else if (c.precision == GMG_FP32_IR) {
@@ -493,9 +506,10 @@ gmg_status enqueue_fmg(gmg_handle h) {
         if (st != GMG_OK) return st;
     }
     timed(
-        h, K_RESNORM, 0, 0, c.n, false,
+        h, K_RESNORM, 0, 0, c.n, norm_red_only(h),
         [&] {
-            fp64::resnorm(c.d, c.n, lv[0].u[0], lv[0].q, h->partial, h->d_res2, h->stream);
+            fp64::resnorm(c.d, c.n, lv[0].u[0], lv[0].q, h->partial, h->d_res2, h->stream,
+                          nullptr, norm_red_only(h));
         },
         2);
     GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
@@ -722,6 +736,7 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     h->cfg = *cfg;
     h->user_stream = (cudaStream_t)cuda_stream;
     if (const char* v = std::getenv("GMG_FUSED_RB")) h->fused_rb = std::strcmp(v, "1") == 0;
+    if (const char* v = std::getenv("GMG_TAIL_N")) h->tail_max = std::max(0, std::atoi(v));
     auto fail = [&](gmg_status s) {
         gmg_destroy(h);
         return s;

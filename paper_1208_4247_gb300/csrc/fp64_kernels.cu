@@ -1,11 +1,21 @@
 // FP64 kernels of the plain V-cycle: right-hand-side preparation, the
 // stopping-test residual norm (Algorithm 3's res), and the double-precision
 // instantiation of the level kernels (level_kernels.cuh).
+#include <cstdlib>
+
 #include "level_kernels.cuh"
 
 namespace gmg {
 
 namespace lk {
+bool rb_walk_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("GMG_RB_WALK");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 template void rb_half<double>(int, int, double*, const double*, int, cudaStream_t);
 template void wj_sweep<double>(int, int, const double*, double*, const double*, double,
                                cudaStream_t);
@@ -52,7 +62,12 @@ constexpr int kNormThreads = 256;
 // shuffle tree and the fixed cross-warp order; one partial per block.  The
 // grid depends on n only, so the result is deterministic.
 // With STORE, sigma is also written to sig_out (the learned smoother's input).
-template <int DIM, bool STORE>
+// With RED, only red nodes (i + j + k even) are summed: right after a black
+// half sweep every black node holds fma(c, nbr_sum, q) of its unchanged red
+// neighbours, which this kernel recomputes with the same expression, so each
+// black sigma is exactly 0.0 and leaving it out changes the sum only through
+// the order of the red terms.
+template <int DIM, bool STORE, bool RED>
 __global__ void __launch_bounds__(kNormThreads) k_resnorm(const double* __restrict__ u,
                                                           const double* __restrict__ q,
                                                           double* __restrict__ partial, int n,
@@ -67,7 +82,9 @@ __global__ void __launch_bounds__(kNormThreads) k_resnorm(const double* __restri
         const int j = (int)(r % (n - 1)) + 1;
         const int k = DIM == 3 ? (int)(r / (n - 1)) + 1 : 0;
         const int64_t row = k * sz + j * sy;
-        for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const int step = RED ? 2 : 1;
+        const int i0 = RED ? 1 + ((1 + j + k) & 1) : 1;
+        for (int i = i0 + step * threadIdx.x; i < n; i += step * blockDim.x) {
             const int64_t p = row + i;
             const double sig = fma(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
             if (STORE) sig_out[p] = sig;
@@ -89,9 +106,10 @@ struct NormLaunch {
     dim3 grid, block;
 };
 
-NormLaunch norm_launch(int d, int n) {
+NormLaunch norm_launch(int d, int n, bool red_only = false) {
+    const int xcount = red_only ? n / 2 : n;
     int bx = 32;
-    while (bx < n && bx < 128) bx *= 2;
+    while (bx < xcount && bx < 128) bx *= 2;
     const int by = kNormThreads / bx;
     const int64_t rows = d == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
     const int64_t blocks = std::min<int64_t>((rows + by - 1) / by, 152 * 8);
@@ -132,18 +150,23 @@ void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s
 int resnorm_partials(int d, int n) { return (int)norm_launch(d, n).grid.x; }
 
 void resnorm(int d, int n, const double* u, const double* q, double* partial, double* out,
-             cudaStream_t s, double* sigma_out) {
-    NormLaunch L = norm_launch(d, n);
+             cudaStream_t s, double* sigma_out, bool red_only) {
+    NormLaunch L = norm_launch(d, n, red_only && !sigma_out);
     if (sigma_out) {
         if (d == 3)
-            k_resnorm<3, true><<<L.grid, L.block, 0, s>>>(u, q, partial, n, sigma_out);
+            k_resnorm<3, true, false><<<L.grid, L.block, 0, s>>>(u, q, partial, n, sigma_out);
         else
-            k_resnorm<2, true><<<L.grid, L.block, 0, s>>>(u, q, partial, n, sigma_out);
+            k_resnorm<2, true, false><<<L.grid, L.block, 0, s>>>(u, q, partial, n, sigma_out);
+    } else if (red_only) {
+        if (d == 3)
+            k_resnorm<3, false, true><<<L.grid, L.block, 0, s>>>(u, q, partial, n, nullptr);
+        else
+            k_resnorm<2, false, true><<<L.grid, L.block, 0, s>>>(u, q, partial, n, nullptr);
     } else {
         if (d == 3)
-            k_resnorm<3, false><<<L.grid, L.block, 0, s>>>(u, q, partial, n, nullptr);
+            k_resnorm<3, false, false><<<L.grid, L.block, 0, s>>>(u, q, partial, n, nullptr);
         else
-            k_resnorm<2, false><<<L.grid, L.block, 0, s>>>(u, q, partial, n, nullptr);
+            k_resnorm<2, false, false><<<L.grid, L.block, 0, s>>>(u, q, partial, n, nullptr);
     }
     k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)L.grid.x, out);
 }

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(NT) k_rb_sweep3_f32(const float* __restrict__ 
             const int i = i0 - 2 + sx, j = j0 - 2 + syy;
             if (i < 1 || i > n - 1 || j < 1 || j > n - 1 || ((i + j + k) & 1) != color) continue;
             const int m = syy * PX + sx;
-            const float s = ((uc[m - 1] + uc[m + 1]) + (uc[m - PX] + uc[m + PX])) + (um[m] + up[m]);
+            const float s = ((uc[m - 1] + uc[m + 1]) + (uc[m - PX] + um[m])) + (uc[m + PX] + up[m]);
             uc[m] = fmaf(c, s, qk[m]);
         }
     };

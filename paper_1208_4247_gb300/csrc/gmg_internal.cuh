@@ -39,6 +39,10 @@ struct Level {
 // Level kernels, explicitly instantiated for double (fp64_kernels.cu) and
 // float / __nv_bfloat16 (mixed_kernels.cu); definitions in level_kernels.cuh.
 namespace lk {
+// rows per diagonal walker of the FP64 3D half sweep; GMG_RB_WALK=0 turns
+// the walkers off (fp64_kernels.cu reads it once)
+constexpr int kWalk = 4;
+bool rb_walk_enabled();
 template <typename T>
 void rb_half(int d, int n, T* u, const T* q, int color, cudaStream_t s);
 template <typename T>
@@ -56,9 +60,11 @@ void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s);
 namespace fp64 {
 void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s);
 int resnorm_partials(int d, int n);
-// sum of sigma^2 into *out; sigma_out (may be NULL) also receives sigma
+// sum of sigma^2 into *out; sigma_out (may be NULL) also receives sigma;
+// red_only (ignored with sigma_out) sums red nodes only, valid right after a
+// black half sweep of level 0 (black sigma is then exactly zero)
 void resnorm(int d, int n, const double* u, const double* q, double* partial, double* out,
-             cudaStream_t s, double* sigma_out = nullptr);
+             cudaStream_t s, double* sigma_out = nullptr, bool red_only = false);
 __global__ void k_sum_partials(const double* partial, int count, double* out);
 }  // namespace fp64
 

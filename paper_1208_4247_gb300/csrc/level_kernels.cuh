@@ -11,7 +11,8 @@
 //
 // Instruction counts per node (what bounds the FP64 instantiation on GB300,
 // whose FP64 pipe issues 2 instructions/clock/SM):
-//   red-black half sweep   5 add + 1 fma per updated node
+//   red-black half sweep   5 add + 1 fma per updated node (FP64 3D diagonal
+//                          walkers: 4 + 1/kWalk add + 1 fma)
 //   residual               5 add + 1 fma + 1 add
 //   restriction            red nodes only after a black half sweep (the black
 //                          residual is zero in exact arithmetic): 13 ops per
@@ -21,6 +22,8 @@
 #pragma once
 
 #include <cuda_bf16.h>
+
+#include <type_traits>
 
 #include "gmg_internal.cuh"
 
@@ -70,18 +73,21 @@ inline RowLaunch row_launch(int d, int n, int xcount) {
     return L;
 }
 
-// Sum of the 2d axis neighbours as a pair tree, ((x- + x+) + (y- + y+)) +
-// (z- + z+): the same 2d-1 adds as a chain, with a dependency depth of 3.
+// Sum of the 2d axis neighbours as a pair tree: 2D (x- + x+) + (y- + y+),
+// 3D ((x- + x+) + (y- + z-)) + (y+ + z+) -- the same 2d-1 adds as a chain,
+// dependency depth 3.  In 3D the (y+ + z+) pair of node (i, j, k) is the
+// (y- + z-) pair of node (i, j+1, k+1), a node of the same colour, which
+// lets k_rb_half3_walk form each pair once for two nodes.
 template <int DIM, typename T>
 __device__ inline typename Num<T>::C nbr_sum(const T* u, int64_t p, int64_t sy, int64_t sz) {
     using N = Num<T>;
     const auto sx = N::ld(u[p - 1]) + N::ld(u[p + 1]);
-    const auto syy = N::ld(u[p - sy]) + N::ld(u[p + sy]);
     if (DIM == 3) {
-        const auto szz = N::ld(u[p - sz]) + N::ld(u[p + sz]);
-        return (sx + syy) + szz;
+        const auto lo = N::ld(u[p - sy]) + N::ld(u[p - sz]);
+        const auto hi = N::ld(u[p + sy]) + N::ld(u[p + sz]);
+        return (sx + lo) + hi;
     }
-    return sx + syy;
+    return sx + (N::ld(u[p - sy]) + N::ld(u[p + sy]));
 }
 
 // One colour of red-black Gauss-Seidel: nodes with (i+j+k) % 2 == color.
@@ -100,6 +106,68 @@ __global__ void __launch_bounds__(256) k_rb_half(T* __restrict__ u, const T* __r
     for (int i = i0 + 2 * threadIdx.x; i < n; i += 2 * blockDim.x) {
         const int64_t p = row + i;
         u[p] = N::st(fma(c, nbr_sum<DIM>(u, p, sy, sz), N::ld(q[p])));
+    }
+}
+
+// 3D red-black half sweep by diagonal walkers.  The (n-1)^2 interior rows
+// (j, k) form n-1 cyclic diagonals k-1 = (j-1+line) mod (n-1); a walker
+// (one threadIdx.y) takes kWalk consecutive rows (j, k) -> (j+1, k+1) of one
+// diagonal, one red node per x thread and row, and carries the (y+ + z+)
+// pair of each node over as the (y- + z-) pair of the next: 4 adds + 1 fma
+// per node instead of 5 + 1.  Where the diagonal wraps (k: n-1 -> 1) the
+// colour's x offset flips and the pair is formed afresh.  Walkers are
+// numbered segment-major, so the CTAs resident at one time sweep a slab of
+// consecutive j.  Red nodes read only black ones, so the node order does not
+// matter; the operands and their order are nbr_sum's (a + b == b + a), so
+// the result equals k_rb_half's bit for bit.
+// 256 threads, at least 4 CTAs per SM (<= 64 registers): the FP64 pipe needs
+// the warps more than each thread needs registers.
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_rb_half3_walk(T* __restrict__ u, const T* __restrict__ q,
+                                                          int n, int color, int segs) {
+    using N = Num<T>;
+    using C = typename N::C;
+    const C c = C(1.0 / 6.0);
+    const int m = n - 1;
+    const int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    if (w >= (int64_t)m * segs) return;
+    const int seg = (int)(w / m), line = (int)(w % m);
+    int j = 1 + seg * kWalk;
+    const int jend = min(j + kWalk, n);
+    int k = 1 + (j - 1 + line) % m;
+    const int64_t sy = sy_of(n), sz = sz_of<3>(n);
+    while (j < jend) {
+        const int run = min(jend - j, n - k);  // rows before k passes n-1
+        const int i = 1 + ((1 + j + k + color) & 1) + 2 * (int)threadIdx.x;
+        if (i < n) {
+            // every black operand of the run is loaded before the first store
+            // (the compiler cannot reorder loads across stores to u)
+            const int64_t p0 = (int64_t)k * sz + (int64_t)j * sy + i, dp = sy + sz;
+            C xm[kWalk], xp[kWalk], yp[kWalk], zp[kWalk], qv[kWalk];
+            const C ym0 = N::ld(u[p0 - sy]), zm0 = N::ld(u[p0 - sz]);
+#pragma unroll
+            for (int r = 0; r < kWalk; ++r) {
+                if (r < run) {
+                    const int64_t p = p0 + r * dp;
+                    xm[r] = N::ld(u[p - 1]);
+                    xp[r] = N::ld(u[p + 1]);
+                    yp[r] = N::ld(u[p + sy]);
+                    zp[r] = N::ld(u[p + sz]);
+                    qv[r] = N::ld(q[p]);
+                }
+            }
+            C lo = ym0 + zm0;
+#pragma unroll
+            for (int r = 0; r < kWalk; ++r) {
+                if (r < run) {
+                    const C hi = yp[r] + zp[r];
+                    u[p0 + r * dp] = N::st(fma(c, ((xm[r] + xp[r]) + lo) + hi, qv[r]));
+                    lo = hi;
+                }
+            }
+        }
+        j += run;
+        k = 1;  // either the diagonal wrapped or j reached jend
     }
 }
 
@@ -265,8 +333,21 @@ __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, T
 
 // ------------------------------------------------------------- launchers
 
+// FP64 3D levels with 64 <= n <= 512 use the diagonal walkers (one red node
+// per x thread and row, 256 threads) unless GMG_RB_WALK=0 (same results bit
+// for bit).
 template <typename T>
 void rb_half(int d, int n, T* u, const T* q, int color, cudaStream_t s) {
+    if (std::is_same<T, double>::value && d == 3 && n >= 64 && n <= 512 && rb_walk_enabled()) {
+        int bx = 32;
+        while (bx < n / 2) bx *= 2;
+        const int by = 256 / bx;
+        const int segs = (n - 1 + kWalk - 1) / kWalk;
+        const int64_t walkers = (int64_t)(n - 1) * segs;
+        const unsigned blocks = (unsigned)((walkers + by - 1) / by);
+        k_rb_half3_walk<T><<<blocks, dim3(bx, by, 1), 0, s>>>(u, q, n, color, segs);
+        return;
+    }
     RowLaunch L = row_launch(d, n, n / 2);
     if (d == 3)
         k_rb_half<3, T><<<L.grid, L.block, 0, s>>>(u, q, n, color);

@@ -323,3 +323,71 @@ def test_fmg_pass_parity_full_size(torch_cuda):
     with Solver(d, n, cycle="fmg") as S:
         S.cycles(fd, ud, 1)
     assert _rel(ud.cpu().numpy(), uo) <= TOL_CYCLE
+
+
+@pytest.mark.parametrize("d,n,nu1,nu2,cycle", [(3, 128, 2, 2, "v"), (2, 256, 1, 1, "v"),
+                                               (3, 64, 2, 0, "v"), (3, 64, 3, 3, "fmg"),
+                                               (2, 64, 1, 2, "fmg")])
+def test_stopping_norm_equals_full_residual_norm(torch_cuda, d, n, nu1, nu2, cycle):
+    """The stopping-test norm after a red-black cycle sums red nodes only
+    (black sigma is exactly zero after the black half sweep); it must equal
+    the full FP64 residual norm of the same iterate, computed by the oracle,
+    to summation-order rounding."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    f = inputs.rhs_uniform(d, n, 12)
+    b = oracle.scale_rhs(f)
+    fd = _dev(torch, f)
+    ud = torch.zeros_like(fd)
+    with Solver(d, n, nu1=nu1, nu2=nu2, cycle=cycle) as S:
+        rel = S.cycles(fd, ud, 3)
+    ref = oracle.norm2(oracle.residual(b, ud.cpu().numpy())) / oracle.norm2(b)
+    assert rel[-1] == pytest.approx(ref, rel=1e-12)
+
+
+@pytest.mark.parametrize("d,n,sm", [(3, 64, "rbgs"), (2, 256, "wjacobi"), (3, 32, "wjacobi")])
+def test_tail_threshold_is_bitwise_neutral(torch_cuda, monkeypatch, d, n, sm):
+    """GMG_TAIL_N only moves levels between the grid kernels and the
+    single-CTA tail, whose arithmetic is the same node for node: the cycles
+    agree bit for bit for every threshold, tail off (1) included."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    fd = _dev(torch, inputs.rhs_uniform(d, n, 13))
+    outs = []
+    for tn in ("1", "4", "8", "16", "32"):
+        monkeypatch.setenv("GMG_TAIL_N", tn)
+        ud = torch.zeros_like(fd)
+        with Solver(d, n, smoother=sm, omega=0.8) as S:
+            S.cycles(fd, ud, 2)
+        outs.append(ud.cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_walker_sweep_is_bitwise_equal_to_row_sweep(torch_cuda, tmp_path):
+    """The FP64 3D diagonal-walker half sweep (default for n >= 64) against
+    the row kernel (GMG_RB_WALK=0, read once per process, so in a child
+    process): two V(2,2) cycles at 129^3 agree bit for bit."""
+    import os
+    import subprocess
+    import sys
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 128
+    f = inputs.rhs_uniform(d, n, 14)
+    np.save(tmp_path / "f.npy", f)
+    script = (
+        "import numpy as np, torch\n"
+        "from paper_1208_4247_gb300.gmg import Solver\n"
+        f"f = torch.from_numpy(np.load(r'{tmp_path / 'f.npy'}')).cuda()\n"
+        "u = torch.zeros_like(f)\n"
+        f"S = Solver({d}, {n}); S.cycles(f, u, 2); S.close()\n"
+        f"np.save(r'{tmp_path / 'u_rows.npy'}', u.cpu().numpy())\n")
+    env = dict(os.environ, GMG_RB_WALK="0")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", script], check=True, env=env, cwd=root)
+    fd = _dev(torch, f)
+    ud = torch.zeros_like(fd)
+    with Solver(d, n) as S:
+        S.cycles(fd, ud, 2)
+    assert np.array_equal(ud.cpu().numpy(), np.load(tmp_path / "u_rows.npy"))
