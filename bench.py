@@ -619,16 +619,19 @@ def run_ours(args, rank, ws, local):
         S.set_timing(False)
         uh[...] = 0.0
         S.solve_host(fh, uh, RTOL)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        # each call bracketed by its own pair of events (gmg_solve_host returns
+        # with the copies and the solve done); resetting the host initial
+        # guess between calls is host work outside the call and is not timed
+        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
         barrier()
-        e0.record(stream)
-        for _ in range(args.steps):
+        for a, b in pairs:
             uh[...] = 0.0
+            a.record(stream)
             S.solve_host(fh, uh, RTOL)
-        e1.record(stream)
+            b.record(stream)
         barrier()
-        e_ms = e0.elapsed_time(e1) / args.steps
+        e_ms = reduce_max_ms(sum(a.elapsed_time(b) for a, b in pairs), ws, dev) / args.steps
         e2e = {"value": UNKNOWNS * ws / (e_ms * 1e-3), "unit": "DOF/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": 2 * fh.nbytes, "d2h_bytes_per_step": uh.nbytes}
     S.close()

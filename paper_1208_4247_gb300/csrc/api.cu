@@ -215,7 +215,9 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
         case K_RESTRICT:
             return red_only ? std::make_pair(Nc * (t ? 13 : 4), N / 2 * w + Nc * 2 * w)
                             : std::make_pair(Nc * (t ? 27 : 8), N * w + Nc * 2 * w);
-        case K_PROLONG: return {cells * (t ? 20 : 8), Nc * w + N * 2 * w};
+        case K_PROLONG:  // red_only here: black fine nodes only
+            return red_only ? std::make_pair(cells * (t ? 13 : 4), Nc * w + N * w)
+                            : std::make_pair(cells * (t ? 20 : 8), Nc * w + N * 2 * w);
         case K_RESNORM:
             return red_only ? std::make_pair(N / 2 * (t ? 8 : 6), N * 12)
                             : std::make_pair(N * (t ? 8 : 6), N * 16);
@@ -249,6 +251,13 @@ template <typename T>
 bool use_fused_rb(gmg_handle h) {
     return std::is_same<T, float>::value && h->fused_rb && h->cfg.smoother == GMG_RBGS &&
            h->cfg.d == 3;
+}
+
+// The next operation on the level is `sweeps` red-black sweeps starting with
+// a red half sweep (which overwrites every red node without reading it).
+template <typename T>
+bool red_sweep_next(gmg_handle h, int sweeps) {
+    return h->cfg.smoother == GMG_RBGS && sweeps > 0 && !use_fused_rb<T>(h);
 }
 
 bool learned_level(gmg_handle h, int l) {
@@ -389,8 +398,10 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
         for (int l = Ldown - 1; l >= 0; --l) {
             Level<T>& F = lv[l];
             Level<T>& C = lv[l + 1];
-            timed(h, K_PROLONG, l, p, F.n, false,
-                  [&] { lk::prolong_add<T>(d, C.n, C.u[cur[l + 1]], F.u[cur[l]], h->stream); });
+            const bool black = red_sweep_next<T>(h, c.nu2);
+            timed(h, K_PROLONG, l, p, F.n, black, [&] {
+                lk::prolong_add<T>(d, C.n, C.u[cur[l + 1]], F.u[cur[l]], h->stream, black);
+            });
             relax(h, lv, l, c.nu2, cur[l]);
         }
     }
@@ -494,8 +505,9 @@ gmg_status enqueue_fmg(gmg_handle h) {
     cudaError_t e = cudaMemsetAsync(lv[0].u[0], 0, sizeof(double) * lv[0].nodes, h->stream);
     GMG_CUDA_TRY(e);
     for (int l = L - 2; l >= 0; --l) {
-        timed(h, K_PROLONG, l, 0, lv[l].n, false, [&] {
-            lk::prolong_add<double>(d, lv[l + 1].n, lv[l + 1].u[0], lv[l].u[0], h->stream);
+        const bool black = red_sweep_next<double>(h, c.nu1);
+        timed(h, K_PROLONG, l, 0, lv[l].n, black, [&] {
+            lk::prolong_add<double>(d, lv[l + 1].n, lv[l + 1].u[0], lv[l].u[0], h->stream, black);
         });
         std::vector<Level<double>> sub(lv.begin() + l, lv.end());
         gmg_status st = enqueue_vcycle<double>(h, sub);

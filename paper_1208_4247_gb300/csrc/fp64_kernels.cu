@@ -23,7 +23,7 @@ template void residual<double>(int, int, const double*, const double*, double*, 
                                cudaStream_t);
 template void restrict_fw<double>(int, int, const double*, double*, double*, bool, bool,
                                   cudaStream_t);
-template void prolong_add<double>(int, int, const double*, double*, cudaStream_t);
+template void prolong_add<double>(int, int, const double*, double*, cudaStream_t, bool);
 }  // namespace lk
 
 namespace fp64 {
@@ -102,6 +102,34 @@ __global__ void __launch_bounds__(kNormThreads) k_resnorm(const double* __restri
     }
 }
 
+// Red-only norm by the diagonal walkers (3D, 64 <= n <= 512): the same
+// sigma^2 terms as k_resnorm<3, false, true>, summed in walker order; a
+// fixed grid strides over the walkers, so the result is deterministic.
+__global__ void __launch_bounds__(256, 4) k_resnorm3_walk(const double* __restrict__ u,
+                                                          const double* __restrict__ q,
+                                                          double* __restrict__ partial, int n,
+                                                          int segs) {
+    __shared__ double warp_sums[kNormThreads / 32];
+    const double c = 1.0 / 6.0;
+    const int64_t walkers = (int64_t)(n - 1) * segs;
+    double acc = 0.0;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; w < walkers;
+         w += (int64_t)gridDim.x * blockDim.y)
+        lk::walk_nodes(u, n, 0, w, segs, [&](int64_t p, double sum) {
+            const double sig = fma(c, sum, q[p]) - u[p];
+            acc = fma(sig, sig, acc);
+        });
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((t & 31) == 0) warp_sums[t >> 5] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kNormThreads / 32; ++w) s += warp_sums[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
 struct NormLaunch {
     dim3 grid, block;
 };
@@ -151,6 +179,13 @@ int resnorm_partials(int d, int n) { return (int)norm_launch(d, n).grid.x; }
 
 void resnorm(int d, int n, const double* u, const double* q, double* partial, double* out,
              cudaStream_t s, double* sigma_out, bool red_only) {
+    if (red_only && !sigma_out && lk::walk_applies(d, n, sizeof(double))) {
+        const lk::WalkLaunch W = lk::walk_launch(n);
+        const unsigned blocks = std::min<unsigned>(W.blocks, (unsigned)resnorm_partials(d, n));
+        k_resnorm3_walk<<<blocks, W.block, 0, s>>>(u, q, partial, n, W.segs);
+        k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)blocks, out);
+        return;
+    }
     NormLaunch L = norm_launch(d, n, red_only && !sigma_out);
     if (sigma_out) {
         if (d == 3)

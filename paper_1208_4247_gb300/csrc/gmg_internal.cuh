@@ -53,7 +53,9 @@ template <typename T>
 void restrict_fw(int d, int n, const T* r, T* qc, T* uc, bool red_only, bool exact_coarsest,
                  cudaStream_t s);
 template <typename T>
-void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s);
+// black_only: correct the black fine nodes only (valid when a red half sweep
+// follows, which overwrites every red node without reading it)
+void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s, bool black_only = false);
 }  // namespace lk
 
 // FP64 preparation and stopping-test norm (fp64_kernels.cu).

@@ -17,7 +17,7 @@ namespace lk {
     template void wj_sweep<T>(int, int, const T*, T*, const T*, double, cudaStream_t);           \
     template void residual<T>(int, int, const T*, const T*, T*, bool, cudaStream_t);             \
     template void restrict_fw<T>(int, int, const T*, T*, T*, bool, bool, cudaStream_t);          \
-    template void prolong_add<T>(int, int, const T*, T*, cudaStream_t);
+    template void prolong_add<T>(int, int, const T*, T*, cudaStream_t, bool);
 GMG_INSTANTIATE(float)
 GMG_INSTANTIATE(__nv_bfloat16)
 #undef GMG_INSTANTIATE
