@@ -36,7 +36,7 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the level-0 red-black half sweep of
 # the 257^3 FP64 solve, from one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum: 269.5 MB + 85.8 MB)
-RB_HALF_L0_TRAFFIC = 355.3e6
+RB_HALF_L0_TRAFFIC = 356.4e6  # ncu dram read + write of one level-0 walker half sweep, 257^3
 
 
 def peaks():
