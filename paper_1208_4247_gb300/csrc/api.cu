@@ -309,10 +309,10 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
         if (h->cfg.smoother == GMG_RBGS || h->cfg.smoother == GMG_LEARNED) {
             for (int color = 0; color < 2; ++color)
                 timed(h, K_RB_HALF, l, p, L.n, false,
-                      [&] { lk::rb_half<T>(d, L.n, L.u[cur], L.q, color, h->stream); });
+                      [&] { lk::rb_half<T>(d, L.lay, L.u[cur], L.q, color, h->stream); });
         } else {
             timed(h, K_WJ, l, p, L.n, false, [&] {
-                lk::wj_sweep<T>(d, L.n, L.u[cur], L.u[cur ^ 1], L.q, h->cfg.omega, h->stream);
+                lk::wj_sweep<T>(d, L.lay, L.u[cur], L.u[cur ^ 1], L.q, h->cfg.omega, h->stream);
             });
             cur ^= 1;
         }
@@ -353,7 +353,7 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
         // the whole hierarchy is small: one persistent launch
         cudaError_t e = cudaSuccess;
         timed(h, K_TAIL, 0, p, lv[0].n, false, [&] {
-            e = tail::launch<T>(d, lv[0].n, L, lv[0].u[0], lv[0].q, c.smoother, c.omega, c.nu1,
+            e = tail::launch<T>(d, lv[0].lay, L, lv[0].u[0], lv[0].q, c.smoother, c.omega, c.nu1,
                                 c.nu2, c.coarse_sweeps, h->stream);
         });
         GMG_CUDA_TRY(e);
@@ -371,18 +371,18 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
                             (c.smoother == GMG_LEARNED && !learned_level(h, l));
             const bool red_only = rb && c.nu1 > 0;
             timed(h, K_RESIDUAL, l, p, F.n, red_only, [&] {
-                lk::residual<T>(d, F.n, F.u[cur[l]], F.q, F.r, red_only, h->stream);
+                lk::residual<T>(d, F.lay, F.u[cur[l]], F.q, F.r, red_only, h->stream);
             });
             const bool exact = C.n == 2;
             timed(h, K_RESTRICT, l, p, F.n, red_only, [&] {
-                lk::restrict_fw<T>(d, F.n, F.r, C.q, C.u[0], red_only, exact, h->stream);
+                lk::restrict_fw<T>(d, F.lay, C.lay, F.r, C.q, C.u[0], red_only, exact, h->stream);
             });
             cur[l + 1] = 0;
         }
         if (lt < L) {
             cudaError_t e = cudaSuccess;
             timed(h, K_TAIL, lt, p, lv[lt].n, false, [&] {
-                e = tail::launch<T>(d, lv[lt].n, L - lt, lv[lt].u[0], lv[lt].q, c.smoother,
+                e = tail::launch<T>(d, lv[lt].lay, L - lt, lv[lt].u[0], lv[lt].q, c.smoother,
                                     c.omega, c.nu1, c.nu2, c.coarse_sweeps, h->stream);
             });
             GMG_CUDA_TRY(e);
@@ -392,7 +392,7 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
                 for (int s = 0; s < c.coarse_sweeps; ++s)
                     for (int color = 0; color < 2; ++color)
                         timed(h, K_RB_HALF, L - 1, p, B.n, false,
-                              [&] { lk::rb_half<T>(d, B.n, B.u[0], B.q, color, h->stream); });
+                              [&] { lk::rb_half<T>(d, B.lay, B.u[0], B.q, color, h->stream); });
             }
         }
         for (int l = Ldown - 1; l >= 0; --l) {
@@ -400,7 +400,8 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
             Level<T>& C = lv[l + 1];
             const bool black = red_sweep_next<T>(h, c.nu2);
             timed(h, K_PROLONG, l, p, F.n, black, [&] {
-                lk::prolong_add<T>(d, C.n, C.u[cur[l + 1]], F.u[cur[l]], h->stream, black);
+                lk::prolong_add<T>(d, C.lay, F.lay, C.u[cur[l + 1]], F.u[cur[l]], h->stream,
+                                   black);
             });
             relax(h, lv, l, c.nu2, cur[l]);
         }
@@ -431,11 +432,11 @@ gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
         if (st != GMG_OK) return st;
     }
     timed(h, K_UPDATE, 0, p, c.n, false,
-          [&] { mixed::update<T>(c.d, c.n, h->lv[0].u[0], in[0].u[0], h->stream); });
+          [&] { mixed::update<T>(c.d, in[0].lay, h->lv[0].u[0], in[0].u[0], h->stream); });
     timed(
         h, K_OUTER_RES, 0, p, c.n, false,
         [&] {
-            mixed::outer_residual<T>(c.d, c.n, h->lv[0].u[0], h->lv[0].q, in[0].q, h->partial,
+            mixed::outer_residual<T>(c.d, in[0].lay, h->lv[0].u[0], h->lv[0].q, in[0].q, h->partial,
                                      h->d_res2, h->stream);
         },
         2);
@@ -597,10 +598,12 @@ gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
         fp64::resnorm(c.d, c.n, u, h->lv[0].q, h->partial, h->d_res2, h->stream,
                       sigma_carried(h) ? h->lv[0].r : nullptr);
     else if (c.precision == GMG_FP32_IR)
-        mixed::outer_residual<float>(c.d, c.n, u, h->lv[0].q, h->lvf[0].q, h->partial, h->d_res2,
+        mixed::outer_residual<float>(c.d, h->lvf[0].lay, u, h->lv[0].q, h->lvf[0].q, h->partial,
+                                     h->d_res2,
                                      h->stream);
     else
-        mixed::outer_residual<bf16>(c.d, c.n, u, h->lv[0].q, h->lvb[0].q, h->partial, h->d_res2,
+        mixed::outer_residual<bf16>(c.d, h->lvb[0].lay, u, h->lv[0].q, h->lvb[0].q, h->partial,
+                                    h->d_res2,
                                     h->stream);
     h->timer.launches += 3;
     GMG_CUDA_TRY(cudaGetLastError());
@@ -680,7 +683,11 @@ gmg_status alloc_hierarchy(gmg_handle h, std::vector<Level<T>>& lv, int levels, 
     for (int l = 0; l < levels; ++l) {
         Level<T>& v = lv[l];
         v.n = c.n >> l;
-        v.nodes = nodes_of(c.d, v.n);
+        // FP64 levels keep the caller's dense layout; the FP32/BF16 inner
+        // hierarchies are colour-split (dense for the fused FP32 sweep)
+        v.lay = std::is_same<T, double>::value || use_fused_rb<T>(h) ? dense_lay(c.d, v.n)
+                                                                       : split_lay(c.d, v.n);
+        v.nodes = lay_elems(c.d, v.lay);
         if (l > 0 || alloc_u0)
             if ((st = dev_alloc(h, &v.u[0], v.nodes)) != GMG_OK) return st;
         const bool pingpong = c.smoother == GMG_WJACOBI || use_fused_rb<T>(h);
@@ -771,6 +778,7 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
         // FP64 level 0: the caller's u and the FP64 scaled right-hand side
         h->lv.resize(1);
         h->lv[0].n = cfg->n;
+        h->lv[0].lay = dense_lay(d, cfg->n);
         h->lv[0].nodes = nodes_of(d, cfg->n);
         if ((st = dev_alloc(h, &h->lv[0].q, h->lv[0].nodes)) != GMG_OK) return fail(st);
         st = cfg->precision == GMG_FP32_IR ? alloc_hierarchy<float>(h, h->lvf, L, true)

@@ -16,14 +16,15 @@ bool rb_walk_enabled() {
     return on;
 }
 
-template void rb_half<double>(int, int, double*, const double*, int, cudaStream_t);
-template void wj_sweep<double>(int, int, const double*, double*, const double*, double,
+template void rb_half<double>(int, const Lay&, double*, const double*, int, cudaStream_t);
+template void wj_sweep<double>(int, const Lay&, const double*, double*, const double*, double,
                                cudaStream_t);
-template void residual<double>(int, int, const double*, const double*, double*, bool,
+template void residual<double>(int, const Lay&, const double*, const double*, double*, bool,
                                cudaStream_t);
-template void restrict_fw<double>(int, int, const double*, double*, double*, bool, bool,
-                                  cudaStream_t);
-template void prolong_add<double>(int, int, const double*, double*, cudaStream_t, bool);
+template void restrict_fw<double>(int, const Lay&, const Lay&, const double*, double*, double*,
+                                  bool, bool, cudaStream_t);
+template void prolong_add<double>(int, const Lay&, const Lay&, const double*, double*,
+                                  cudaStream_t, bool);
 }  // namespace lk
 
 namespace fp64 {

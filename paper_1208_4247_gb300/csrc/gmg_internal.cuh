@@ -25,6 +25,37 @@ const std::string& last_error();
         }                                                                               \
     } while (0)
 
+// Node addressing of a level array.  Dense (he == 0): node (i, j, k) at
+// k*sz + j*sy + i with sy = n+1, x fastest -- the caller's layout, used by
+// every FP64 array.  Colour-split (he > 0; the FP32/BF16 inner hierarchies):
+// each row stores its even-x nodes first (x/2 at 0..n/2) and its odd-x
+// nodes from offset he ((x-1)/2 at he..he+n/2-1), so the nodes of one colour
+// in a row are contiguous and a half sweep reads and writes only the bytes
+// of the colours it uses; sy is then the padded row stride.
+struct Lay {
+    int n = 0;
+    int he = 0;
+    int64_t sy = 0, sz = 0;
+};
+inline Lay dense_lay(int d, int n) {
+    Lay L;
+    L.n = n;
+    L.sy = n + 1;
+    L.sz = d == 3 ? L.sy * (n + 1) : 0;
+    return L;
+}
+// halves padded to multiples of 8 elements (16 bytes in BF16, 32 in FP32)
+inline Lay split_lay(int d, int n) {
+    Lay L;
+    L.n = n;
+    L.he = (n / 2 + 1 + 7) / 8 * 8;
+    L.sy = L.he + (n / 2 + 7) / 8 * 8;
+    L.sz = d == 3 ? L.sy * (n + 1) : 0;
+    return L;
+}
+// elements of a level array with layout L
+inline int64_t lay_elems(int d, const Lay& L) { return d == 3 ? L.sz * (L.n + 1) : L.sy * (L.n + 1); }
+
 // One grid of a hierarchy in storage type T.  Arrays hold all (n+1)^d
 // nodes, x fastest, boundary entries kept at zero.
 template <typename T>
@@ -34,6 +65,7 @@ struct Level {
     T* u[2] = {nullptr, nullptr};  // iterate; u[1] = weighted-Jacobi ping-pong partner
     T* q = nullptr;       // scaled right-hand side q = h^2 f / (2d)
     T* r = nullptr;       // scaled residual sigma = q + A'-neighbour sum / (2d) - u
+    Lay lay;              // addressing of u, q, r
 };
 
 // Level kernels, explicitly instantiated for double (fp64_kernels.cu) and
@@ -43,19 +75,44 @@ namespace lk {
 // the walkers off (fp64_kernels.cu reads it once)
 constexpr int kWalk = 4;
 bool rb_walk_enabled();
+// Launchers on a level with layout L (restriction: fine F -> coarse C;
+// prolongation: coarse C -> fine F).
 template <typename T>
-void rb_half(int d, int n, T* u, const T* q, int color, cudaStream_t s);
+void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s);
 template <typename T>
-void wj_sweep(int d, int n, const T* u_in, T* u_out, const T* q, double omega, cudaStream_t s);
+void wj_sweep(int d, const Lay& L, const T* u_in, T* u_out, const T* q, double omega,
+              cudaStream_t s);
 template <typename T>
-void residual(int d, int n, const T* u, const T* q, T* r, bool red_only, cudaStream_t s);
+void residual(int d, const Lay& L, const T* u, const T* q, T* r, bool red_only, cudaStream_t s);
 template <typename T>
-void restrict_fw(int d, int n, const T* r, T* qc, T* uc, bool red_only, bool exact_coarsest,
-                 cudaStream_t s);
-template <typename T>
+void restrict_fw(int d, const Lay& F, const Lay& C, const T* r, T* qc, T* uc, bool red_only,
+                 bool exact_coarsest, cudaStream_t s);
 // black_only: correct the black fine nodes only (valid when a red half sweep
 // follows, which overwrites every red node without reading it)
-void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s, bool black_only = false);
+template <typename T>
+void prolong_add(int d, const Lay& C, const Lay& F, const T* uc, T* u, cudaStream_t s,
+                 bool black_only = false);
+
+// The same on dense levels given by n.
+template <typename T>
+inline void rb_half(int d, int n, T* u, const T* q, int color, cudaStream_t s) {
+    rb_half<T>(d, dense_lay(d, n), u, q, color, s);
+}
+template <typename T>
+inline void residual(int d, int n, const T* u, const T* q, T* r, bool red_only, cudaStream_t s) {
+    residual<T>(d, dense_lay(d, n), u, q, r, red_only, s);
+}
+template <typename T>
+inline void restrict_fw(int d, int n, const T* r, T* qc, T* uc, bool red_only,
+                        bool exact_coarsest, cudaStream_t s) {
+    restrict_fw<T>(d, dense_lay(d, n), dense_lay(d, n / 2), r, qc, uc, red_only, exact_coarsest,
+                   s);
+}
+template <typename T>
+inline void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s,
+                        bool black_only = false) {
+    prolong_add<T>(d, dense_lay(d, nc), dense_lay(d, 2 * nc), uc, u, s, black_only);
+}
 }  // namespace lk
 
 // FP64 preparation and stopping-test norm (fp64_kernels.cu).
@@ -73,11 +130,12 @@ __global__ void k_sum_partials(const double* partial, int count, double* out);
 // Outer FP64 kernels of iterative refinement (mixed_kernels.cu).
 namespace mixed {
 int outer_partials(int d, int n);
+// q_in, e: the inner level-0 arrays, layout `in` (dense u, q: FP64, n = in.n)
 template <typename T>
-void outer_residual(int d, int n, const double* u, const double* q, T* q_in, double* partial,
-                    double* out, cudaStream_t s);
+void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q_in,
+                    double* partial, double* out, cudaStream_t s);
 template <typename T>
-void update(int d, int n, double* u, const T* e, cudaStream_t s);
+void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s);
 }  // namespace mixed
 
 // Fused red-black sweep (fused.cu, 3D FP32): u_out = one full sweep of u_in
@@ -90,8 +148,9 @@ void rb_sweep3_f32(int n, const float* uin, float* uout, const float* q, cudaStr
 // ... (levels of them) in shared memory; u_top in/out, q_top in.
 namespace tail {
 size_t smem_bytes(int d, int n_top, int levels, int smoother, size_t elem);
+// top: layout of u_top / q_top in global memory (n_top = top.n)
 template <typename T>
-cudaError_t launch(int d, int n_top, int levels, T* u_top, const T* q_top, int smoother,
+cudaError_t launch(int d, const Lay& top, int levels, T* u_top, const T* q_top, int smoother,
                    double omega, int nu1, int nu2, int coarse_sweeps, cudaStream_t s);
 }  // namespace tail
 

@@ -77,11 +77,13 @@ inline RowLaunch row_launch(int d, int n, int xcount) {
 // 3D ((x- + x+) + (y- + z-)) + (y+ + z+) -- the same 2d-1 adds as a chain,
 // dependency depth 3.  In 3D the (y+ + z+) pair of node (i, j, k) is the
 // (y- + z-) pair of node (i, j+1, k+1), a node of the same colour, which
-// lets k_rb_half3_walk form each pair once for two nodes.
+// lets k_rb_half3_walk form each pair once for two nodes.  xm, xp: offsets
+// of the x-1 and x+1 neighbours (-1, +1 in the dense layout).
 template <int DIM, typename T>
-__device__ inline typename Num<T>::C nbr_sum(const T* u, int64_t p, int64_t sy, int64_t sz) {
+__device__ inline typename Num<T>::C nbr_sum_x(const T* u, int64_t p, int64_t xm, int64_t xp,
+                                               int64_t sy, int64_t sz) {
     using N = Num<T>;
-    const auto sx = N::ld(u[p - 1]) + N::ld(u[p + 1]);
+    const auto sx = N::ld(u[p + xm]) + N::ld(u[p + xp]);
     if (DIM == 3) {
         const auto lo = N::ld(u[p - sy]) + N::ld(u[p - sz]);
         const auto hi = N::ld(u[p + sy]) + N::ld(u[p + sz]);
@@ -89,23 +91,49 @@ __device__ inline typename Num<T>::C nbr_sum(const T* u, int64_t p, int64_t sy, 
     }
     return sx + (N::ld(u[p - sy]) + N::ld(u[p + sy]));
 }
+template <int DIM, typename T>
+__device__ inline typename Num<T>::C nbr_sum(const T* u, int64_t p, int64_t sy, int64_t sz) {
+    return nbr_sum_x<DIM>(u, p, -1, 1, sy, sz);
+}
+
+// Offset of node x = i within its row, and of its x-1 / x+1 neighbours
+// relative to it, for the dense (SPLIT = false) and colour-split layouts.
+template <bool SPLIT>
+__host__ __device__ inline int64_t xo(const Lay& L, int i) {
+    return SPLIT ? ((i & 1) ? L.he + (i >> 1) : (i >> 1)) : i;
+}
+template <bool SPLIT>
+__device__ inline void xnb(const Lay& L, int i, int64_t& xm, int64_t& xp) {
+    if (!SPLIT) {
+        xm = -1;
+        xp = 1;
+    } else if (i & 1) {
+        xm = -L.he;
+        xp = 1 - L.he;
+    } else {
+        xm = L.he - 1;
+        xp = L.he;
+    }
+}
 
 // One colour of red-black Gauss-Seidel: nodes with (i+j+k) % 2 == color.
-template <int DIM, typename T>
-__global__ void __launch_bounds__(256) k_rb_half(T* __restrict__ u, const T* __restrict__ q, int n,
+template <int DIM, bool SPLIT, typename T>
+__global__ void __launch_bounds__(256) k_rb_half(T* __restrict__ u, const T* __restrict__ q, Lay L,
                                                  int color) {
     using N = Num<T>;
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
+    const int n = L.n;
     const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
     const int k = DIM == 3 ? blockIdx.y + 1 : 0;
     if (j >= n) return;
-    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
-    const int64_t row = k * sz + j * sy;
+    const int64_t row = k * L.sz + j * L.sy;
     const int i0 = 1 + ((1 + j + k + color) & 1);
+    int64_t xm, xp;
+    xnb<SPLIT>(L, i0, xm, xp);  // every node of the loop has i0's parity
     for (int i = i0 + 2 * threadIdx.x; i < n; i += 2 * blockDim.x) {
-        const int64_t p = row + i;
-        u[p] = N::st(fma(c, nbr_sum<DIM>(u, p, sy, sz), N::ld(q[p])));
+        const int64_t p = row + xo<SPLIT>(L, i);
+        u[p] = N::st(fma(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])));
     }
 }
 
@@ -244,109 +272,115 @@ inline bool walk_applies(int d, int n, size_t elem) {
 }
 
 // Weighted Jacobi: u_out = u + omega * sigma, all nodes from u_in.
-template <int DIM, typename T>
+template <int DIM, bool SPLIT, typename T>
 __global__ void __launch_bounds__(256) k_wj(const T* __restrict__ u, T* __restrict__ uo,
-                                            const T* __restrict__ q, int n, double omega_d) {
+                                            const T* __restrict__ q, Lay L, double omega_d) {
     using N = Num<T>;
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
     const C omega = C(omega_d);
+    const int n = L.n;
     const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
     const int k = DIM == 3 ? blockIdx.y + 1 : 0;
     if (j >= n) return;
-    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
-    const int64_t row = k * sz + j * sy;
+    const int64_t row = k * L.sz + j * L.sy;
     for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
-        const int64_t p = row + i;
+        const int64_t p = row + xo<SPLIT>(L, i);
+        int64_t xm, xp;
+        xnb<SPLIT>(L, i, xm, xp);
         const C up = N::ld(u[p]);
-        const C sig = fma(c, nbr_sum<DIM>(u, p, sy, sz), N::ld(q[p])) - up;
+        const C sig = fma(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])) - up;
         uo[p] = N::st(fma(omega, sig, up));
     }
 }
 
 // sigma on all interior nodes, or on red nodes only (black entries of r are
 // never written and never read in that mode).
-template <int DIM, bool RED_ONLY, typename T>
+template <int DIM, bool RED_ONLY, bool SPLIT, typename T>
 __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const T* __restrict__ q,
-                                                  T* __restrict__ r, int n) {
+                                                  T* __restrict__ r, Lay L) {
     using N = Num<T>;
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
+    const int n = L.n;
     const int j = blockIdx.x * blockDim.y + threadIdx.y + 1;
     const int k = DIM == 3 ? blockIdx.y + 1 : 0;
     if (j >= n) return;
-    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
-    const int64_t row = k * sz + j * sy;
+    const int64_t row = k * L.sz + j * L.sy;
     const int step = RED_ONLY ? 2 : 1;
     const int i0 = RED_ONLY ? 1 + ((1 + j + k) & 1) : 1;
     for (int i = i0 + step * threadIdx.x; i < n; i += step * blockDim.x) {
-        const int64_t p = row + i;
-        r[p] = N::st(fma(c, nbr_sum<DIM>(u, p, sy, sz), N::ld(q[p])) - N::ld(u[p]));
+        const int64_t p = row + xo<SPLIT>(L, i);
+        int64_t xm, xp;
+        xnb<SPLIT>(L, i, xm, xp);
+        r[p] = N::st(fma(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])) -
+                     N::ld(u[p]));
     }
 }
 
 // q_c = 4 FW(sigma) at every coarse interior node; u_c = 0 (a fresh coarse
 // iterate) or u_c = q_c when the coarse grid has its single unknown (exact
 // solve u = b/(2d)).  With RED_ONLY the black-node terms (faces and corners
-// in 3D, faces in 2D) are zero and skipped.
-template <int DIM, bool RED_ONLY, typename T>
+// in 3D, faces in 2D) are zero and skipped.  F: fine layout, Cl: coarse.
+template <int DIM, bool RED_ONLY, bool SPLIT, typename T>
 __global__ void __launch_bounds__(256) k_restrict(const T* __restrict__ r, T* __restrict__ qc,
-                                                  T* __restrict__ uc, int nc, int exact) {
+                                                  T* __restrict__ uc, Lay F, Lay Cl, int exact) {
     using N = Num<T>;
     using C = typename N::C;
+    const int nc = Cl.n;
     const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
     const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
     const int K = DIM == 3 ? blockIdx.z + 1 : 0;
     if (I >= nc || J >= nc) return;
-    const int n = 2 * nc;
-    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
-    const int64_t p = (2 * K) * sz + (2 * J) * sy + 2 * I;
+    const int64_t sy = F.sy, sz = F.sz;
+    const int64_t p = (2 * K) * sz + (2 * J) * sy + xo<SPLIT>(F, 2 * I);
+    int64_t xm, xp;  // fine x-1, x+1 of the (even) centre 2I
+    xnb<SPLIT>(F, 2 * I, xm, xp);
     auto R = [&](int64_t o) { return N::ld(r[p + o]); };
     C v;
     if (DIM == 3) {
-        C e = R(-1 - sy) + R(1 - sy);
-        e += R(-1 + sy);
-        e += R(1 + sy);
-        e += R(-1 - sz);
-        e += R(1 - sz);
+        C e = R(xm - sy) + R(xp - sy);
+        e += R(xm + sy);
+        e += R(xp + sy);
+        e += R(xm - sz);
+        e += R(xp - sz);
         e += R(-sy - sz);
         e += R(sy - sz);
-        e += R(-1 + sz);
-        e += R(1 + sz);
+        e += R(xm + sz);
+        e += R(xp + sz);
         e += R(-sy + sz);
         e += R(sy + sz);
         if (RED_ONLY) {
             v = fma(C(0.125), e, C(0.5) * R(0));
         } else {
-            C fc = R(-1) + R(1);
+            C fc = R(xm) + R(xp);
             fc += R(-sy);
             fc += R(sy);
             fc += R(-sz);
             fc += R(sz);
-            C co = R(-1 - sy - sz) + R(1 - sy - sz);
-            co += R(-1 + sy - sz);
-            co += R(1 + sy - sz);
-            co += R(-1 - sy + sz);
-            co += R(1 - sy + sz);
-            co += R(-1 + sy + sz);
-            co += R(1 + sy + sz);
+            C co = R(xm - sy - sz) + R(xp - sy - sz);
+            co += R(xm + sy - sz);
+            co += R(xp + sy - sz);
+            co += R(xm - sy + sz);
+            co += R(xp - sy + sz);
+            co += R(xm + sy + sz);
+            co += R(xp + sy + sz);
             v = fma(C(0.0625), co, fma(C(0.125), e, fma(C(0.25), fc, C(0.5) * R(0))));
         }
     } else {
-        C co = R(-1 - sy) + R(1 - sy);
-        co += R(-1 + sy);
-        co += R(1 + sy);
+        C co = R(xm - sy) + R(xp - sy);
+        co += R(xm + sy);
+        co += R(xp + sy);
         if (RED_ONLY) {
             v = fma(C(0.25), co, R(0));
         } else {
-            C fc = R(-1) + R(1);
+            C fc = R(xm) + R(xp);
             fc += R(-sy);
             fc += R(sy);
             v = fma(C(0.25), co, fma(C(0.5), fc, R(0)));
         }
     }
-    const int64_t sc = sy_of(nc);
-    const int64_t P = ((int64_t)K * sc + J) * sc + I;
+    const int64_t P = (int64_t)K * Cl.sz + (int64_t)J * Cl.sy + xo<SPLIT>(Cl, I);
     qc[P] = N::st(v);
     uc[P] = exact ? N::st(v) : N::st(C(0));
 }
@@ -357,22 +391,24 @@ __global__ void __launch_bounds__(256) k_restrict(const T* __restrict__ r, T* __
 // where a red half sweep comes next: it overwrites every red node from its
 // black neighbours without reading the old red value, so the red
 // corrections would never be seen (13 instead of 20 ops per cell in 3D).
-template <int DIM, bool BLACK_ONLY, typename T>
+// Cl: coarse layout, F: fine layout.
+template <int DIM, bool BLACK_ONLY, bool SPLIT, typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, T* __restrict__ u,
-                                                     int nc) {
+                                                     Lay Cl, Lay F) {
     using N = Num<T>;
     using C = typename N::C;
+    const int nc = Cl.n;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int K = DIM == 3 ? blockIdx.z : 0;
     if (I >= nc || J >= nc) return;
-    const int n = 2 * nc;
-    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
-    const int64_t cy = sy_of(nc), cz = sz_of<DIM>(nc);
-    const int64_t P = K * cz + J * cy + I;
-    const int64_t p = (2 * K) * sz + (2 * J) * sy + 2 * I;
-    const C c000 = N::ld(uc[P]), c100 = N::ld(uc[P + 1]), c010 = N::ld(uc[P + cy]),
-            c110 = N::ld(uc[P + 1 + cy]);
+    const int64_t sy = F.sy, sz = F.sz, cy = Cl.sy, cz = Cl.sz;
+    const int64_t Pr = K * cz + J * cy;
+    const int64_t P = Pr + xo<SPLIT>(Cl, I), P1 = Pr + xo<SPLIT>(Cl, I + 1);  // x = I, I+1
+    const int64_t pr = (2 * K) * sz + (2 * J) * sy;
+    const int64_t p = pr + xo<SPLIT>(F, 2 * I), p1 = pr + xo<SPLIT>(F, 2 * I + 1);  // x = 2I, 2I+1
+    const C c000 = N::ld(uc[P]), c100 = N::ld(uc[P1]), c010 = N::ld(uc[P + cy]),
+            c110 = N::ld(uc[P1 + cy]);
     const C x00 = c000 + c100;
     const C x10 = c010 + c110;
     const C y00 = c000 + c010;
@@ -380,12 +416,12 @@ __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, T
     auto add = [&](int64_t o, C w, C v) { u[o] = N::st(fma(w, v, N::ld(u[o]))); };
     if (DIM == 2) {
         if (!BLACK_ONLY && I > 0 && J > 0) u[p] = N::st(N::ld(u[p]) + c000);
-        if (J > 0) add(p + 1, C(0.5), x00);
+        if (J > 0) add(p1, C(0.5), x00);
         if (I > 0) add(p + sy, C(0.5), y00);
-        if (!BLACK_ONLY) add(p + 1 + sy, C(0.25), qxy);
+        if (!BLACK_ONLY) add(p1 + sy, C(0.25), qxy);
     } else {
-        const C c001 = N::ld(uc[P + cz]), c101 = N::ld(uc[P + 1 + cz]),
-                c011 = N::ld(uc[P + cy + cz]), c111 = N::ld(uc[P + 1 + cy + cz]);
+        const C c001 = N::ld(uc[P + cz]), c101 = N::ld(uc[P1 + cz]),
+                c011 = N::ld(uc[P + cy + cz]), c111 = N::ld(uc[P1 + cy + cz]);
         const C x01 = c001 + c101;
         const C x11 = c011 + c111;
         const C y01 = c001 + c011;
@@ -395,71 +431,104 @@ __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, T
         const C oct = qxy + (x01 + x11);
         if (K > 0) {
             if (!BLACK_ONLY && I > 0 && J > 0) u[p] = N::st(N::ld(u[p]) + c000);
-            if (J > 0) add(p + 1, C(0.5), x00);
+            if (J > 0) add(p1, C(0.5), x00);
             if (I > 0) add(p + sy, C(0.5), y00);
-            if (!BLACK_ONLY) add(p + 1 + sy, C(0.25), qxy);
+            if (!BLACK_ONLY) add(p1 + sy, C(0.25), qxy);
         }
-        const int64_t pz = p + sz;
-        if (I > 0 && J > 0) add(pz, C(0.5), z00);
-        if (!BLACK_ONLY && J > 0) add(pz + 1, C(0.25), qxz);
-        if (!BLACK_ONLY && I > 0) add(pz + sy, C(0.25), qyz);
-        add(pz + 1 + sy, C(0.125), oct);
+        if (I > 0 && J > 0) add(p + sz, C(0.5), z00);
+        if (!BLACK_ONLY && J > 0) add(p1 + sz, C(0.25), qxz);
+        if (!BLACK_ONLY && I > 0) add(p + sy + sz, C(0.25), qyz);
+        add(p1 + sy + sz, C(0.125), oct);
     }
 }
 
 // ------------------------------------------------------------- launchers
 
-// FP64 3D levels with 64 <= n <= 512 use the diagonal walkers (one red node
-// per x thread and row, 256 threads) for the half sweeps and the red-only
-// residual unless GMG_RB_WALK=0 (same results bit for bit).
+// FP64 3D dense levels with 64 <= n <= 512 use the diagonal walkers (one red
+// node per x thread and row, 256 threads) for the half sweeps and the
+// red-only residual unless GMG_RB_WALK=0 (same results bit for bit).
 template <typename T>
-void rb_half(int d, int n, T* u, const T* q, int color, cudaStream_t s) {
-    if (walk_applies(d, n, sizeof(T))) {
+void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s) {
+    const int n = L.n;
+    if (L.he == 0 && walk_applies(d, n, sizeof(T))) {
         const WalkLaunch W = walk_launch(n);
         k_rb_half3_walk<T><<<W.blocks, W.block, 0, s>>>(u, q, n, color, W.segs);
         return;
     }
-    RowLaunch L = row_launch(d, n, n / 2);
-    if (d == 3)
-        k_rb_half<3, T><<<L.grid, L.block, 0, s>>>(u, q, n, color);
-    else
-        k_rb_half<2, T><<<L.grid, L.block, 0, s>>>(u, q, n, color);
+    RowLaunch R = row_launch(d, n, n / 2);
+    if (d == 3) {
+        if (L.he)
+            k_rb_half<3, true, T><<<R.grid, R.block, 0, s>>>(u, q, L, color);
+        else
+            k_rb_half<3, false, T><<<R.grid, R.block, 0, s>>>(u, q, L, color);
+    } else {
+        if (L.he)
+            k_rb_half<2, true, T><<<R.grid, R.block, 0, s>>>(u, q, L, color);
+        else
+            k_rb_half<2, false, T><<<R.grid, R.block, 0, s>>>(u, q, L, color);
+    }
 }
 
 template <typename T>
-void wj_sweep(int d, int n, const T* u_in, T* u_out, const T* q, double omega, cudaStream_t s) {
-    RowLaunch L = row_launch(d, n, n);
-    if (d == 3)
-        k_wj<3, T><<<L.grid, L.block, 0, s>>>(u_in, u_out, q, n, omega);
+void wj_sweep(int d, const Lay& L, const T* u_in, T* u_out, const T* q, double omega,
+              cudaStream_t s) {
+    RowLaunch R = row_launch(d, L.n, L.n);
+    if (d == 3) {
+        if (L.he)
+            k_wj<3, true, T><<<R.grid, R.block, 0, s>>>(u_in, u_out, q, L, omega);
+        else
+            k_wj<3, false, T><<<R.grid, R.block, 0, s>>>(u_in, u_out, q, L, omega);
+    } else {
+        if (L.he)
+            k_wj<2, true, T><<<R.grid, R.block, 0, s>>>(u_in, u_out, q, L, omega);
+        else
+            k_wj<2, false, T><<<R.grid, R.block, 0, s>>>(u_in, u_out, q, L, omega);
+    }
+}
+
+template <int DIM, bool SPLIT, typename T>
+void residual_rows(const Lay& L, const T* u, const T* q, T* r, bool red_only, cudaStream_t s) {
+    RowLaunch R = row_launch(DIM, L.n, red_only ? L.n / 2 : L.n);
+    if (red_only)
+        k_residual<DIM, true, SPLIT, T><<<R.grid, R.block, 0, s>>>(u, q, r, L);
     else
-        k_wj<2, T><<<L.grid, L.block, 0, s>>>(u_in, u_out, q, n, omega);
+        k_residual<DIM, false, SPLIT, T><<<R.grid, R.block, 0, s>>>(u, q, r, L);
 }
 
 template <typename T>
-void residual(int d, int n, const T* u, const T* q, T* r, bool red_only, cudaStream_t s) {
-    if (red_only && walk_applies(d, n, sizeof(T))) {
+void residual(int d, const Lay& L, const T* u, const T* q, T* r, bool red_only, cudaStream_t s) {
+    const int n = L.n;
+    if (red_only && L.he == 0 && walk_applies(d, n, sizeof(T))) {
         const WalkLaunch W = walk_launch(n);
         k_residual3_walk<T><<<W.blocks, W.block, 0, s>>>(u, q, r, n, W.segs);
         return;
     }
-    RowLaunch L = row_launch(d, n, red_only ? n / 2 : n);
     if (d == 3) {
-        if (red_only)
-            k_residual<3, true, T><<<L.grid, L.block, 0, s>>>(u, q, r, n);
+        if (L.he)
+            residual_rows<3, true>(L, u, q, r, red_only, s);
         else
-            k_residual<3, false, T><<<L.grid, L.block, 0, s>>>(u, q, r, n);
+            residual_rows<3, false>(L, u, q, r, red_only, s);
     } else {
-        if (red_only)
-            k_residual<2, true, T><<<L.grid, L.block, 0, s>>>(u, q, r, n);
+        if (L.he)
+            residual_rows<2, true>(L, u, q, r, red_only, s);
         else
-            k_residual<2, false, T><<<L.grid, L.block, 0, s>>>(u, q, r, n);
+            residual_rows<2, false>(L, u, q, r, red_only, s);
     }
 }
 
+template <int DIM, bool SPLIT, typename T>
+void restrict_grid(const Lay& F, const Lay& C, const T* r, T* qc, T* uc, bool red_only, int ex,
+                   dim3 grid, dim3 block, cudaStream_t s) {
+    if (red_only)
+        k_restrict<DIM, true, SPLIT, T><<<grid, block, 0, s>>>(r, qc, uc, F, C, ex);
+    else
+        k_restrict<DIM, false, SPLIT, T><<<grid, block, 0, s>>>(r, qc, uc, F, C, ex);
+}
+
 template <typename T>
-void restrict_fw(int d, int n, const T* r, T* qc, T* uc, bool red_only, bool exact_coarsest,
-                 cudaStream_t s) {
-    const int nc = n / 2;
+void restrict_fw(int d, const Lay& F, const Lay& C, const T* r, T* qc, T* uc, bool red_only,
+                 bool exact_coarsest, cudaStream_t s) {
+    const int nc = C.n;
     int bx = 32;
     while (bx < nc - 1 && bx < 128) bx *= 2;
     const int by = 256 / bx;
@@ -467,35 +536,46 @@ void restrict_fw(int d, int n, const T* r, T* qc, T* uc, bool red_only, bool exa
     dim3 grid((nc - 1 + bx - 1) / bx, (nc - 1 + by - 1) / by, d == 3 ? nc - 1 : 1);
     const int ex = exact_coarsest ? 1 : 0;
     if (d == 3) {
-        if (red_only)
-            k_restrict<3, true, T><<<grid, block, 0, s>>>(r, qc, uc, nc, ex);
+        if (F.he)
+            restrict_grid<3, true>(F, C, r, qc, uc, red_only, ex, grid, block, s);
         else
-            k_restrict<3, false, T><<<grid, block, 0, s>>>(r, qc, uc, nc, ex);
+            restrict_grid<3, false>(F, C, r, qc, uc, red_only, ex, grid, block, s);
     } else {
-        if (red_only)
-            k_restrict<2, true, T><<<grid, block, 0, s>>>(r, qc, uc, nc, ex);
+        if (F.he)
+            restrict_grid<2, true>(F, C, r, qc, uc, red_only, ex, grid, block, s);
         else
-            k_restrict<2, false, T><<<grid, block, 0, s>>>(r, qc, uc, nc, ex);
+            restrict_grid<2, false>(F, C, r, qc, uc, red_only, ex, grid, block, s);
     }
 }
 
+template <int DIM, bool SPLIT, typename T>
+void prolong_grid(const Lay& C, const Lay& F, const T* uc, T* u, bool black_only, dim3 grid,
+                  dim3 block, cudaStream_t s) {
+    if (black_only)
+        k_prolong_add<DIM, true, SPLIT, T><<<grid, block, 0, s>>>(uc, u, C, F);
+    else
+        k_prolong_add<DIM, false, SPLIT, T><<<grid, block, 0, s>>>(uc, u, C, F);
+}
+
 template <typename T>
-void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s, bool black_only) {
+void prolong_add(int d, const Lay& C, const Lay& F, const T* uc, T* u, cudaStream_t s,
+                 bool black_only) {
+    const int nc = C.n;
     int bx = 32;
     while (bx < nc && bx < 128) bx *= 2;
     const int by = 256 / bx;
     dim3 block(bx, by, 1);
     dim3 grid((nc + bx - 1) / bx, (nc + by - 1) / by, d == 3 ? nc : 1);
     if (d == 3) {
-        if (black_only)
-            k_prolong_add<3, true, T><<<grid, block, 0, s>>>(uc, u, nc);
+        if (F.he)
+            prolong_grid<3, true>(C, F, uc, u, black_only, grid, block, s);
         else
-            k_prolong_add<3, false, T><<<grid, block, 0, s>>>(uc, u, nc);
+            prolong_grid<3, false>(C, F, uc, u, black_only, grid, block, s);
     } else {
-        if (black_only)
-            k_prolong_add<2, true, T><<<grid, block, 0, s>>>(uc, u, nc);
+        if (F.he)
+            prolong_grid<2, true>(C, F, uc, u, black_only, grid, block, s);
         else
-            k_prolong_add<2, false, T><<<grid, block, 0, s>>>(uc, u, nc);
+            prolong_grid<2, false>(C, F, uc, u, black_only, grid, block, s);
     }
 }
 

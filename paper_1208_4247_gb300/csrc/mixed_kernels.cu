@@ -12,12 +12,13 @@
 namespace gmg {
 
 namespace lk {
-#define GMG_INSTANTIATE(T)                                                                       \
-    template void rb_half<T>(int, int, T*, const T*, int, cudaStream_t);                         \
-    template void wj_sweep<T>(int, int, const T*, T*, const T*, double, cudaStream_t);           \
-    template void residual<T>(int, int, const T*, const T*, T*, bool, cudaStream_t);             \
-    template void restrict_fw<T>(int, int, const T*, T*, T*, bool, bool, cudaStream_t);          \
-    template void prolong_add<T>(int, int, const T*, T*, cudaStream_t, bool);
+#define GMG_INSTANTIATE(T)                                                                      \
+    template void rb_half<T>(int, const Lay&, T*, const T*, int, cudaStream_t);                 \
+    template void wj_sweep<T>(int, const Lay&, const T*, T*, const T*, double, cudaStream_t);   \
+    template void residual<T>(int, const Lay&, const T*, const T*, T*, bool, cudaStream_t);     \
+    template void restrict_fw<T>(int, const Lay&, const Lay&, const T*, T*, T*, bool, bool,     \
+                                 cudaStream_t);                                                 \
+    template void prolong_add<T>(int, const Lay&, const Lay&, const T*, T*, cudaStream_t, bool);
 GMG_INSTANTIATE(float)
 GMG_INSTANTIATE(__nv_bfloat16)
 #undef GMG_INSTANTIATE
@@ -32,14 +33,17 @@ using lk::sz_of;
 constexpr int kThreads = 256;
 
 // sigma = q + c * sum - u in FP64 on every interior node, stored to the
-// inner right-hand side in T; partial sums of sigma^2 as in the FP64 norm.
-template <int DIM, typename T>
+// inner right-hand side in T (layout `in`); partial sums of sigma^2 as in the
+// FP64 norm.
+template <int DIM, bool SPLIT, typename T>
 __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __restrict__ u,
                                                              const double* __restrict__ q,
                                                              T* __restrict__ q_in,
-                                                             double* __restrict__ partial, int n) {
+                                                             double* __restrict__ partial,
+                                                             Lay in) {
     __shared__ double warp_sums[kThreads / 32];
     const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
+    const int n = in.n;
     const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
     const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
     double acc = 0.0;
@@ -48,10 +52,11 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
         const int j = (int)(r % (n - 1)) + 1;
         const int k = DIM == 3 ? (int)(r / (n - 1)) + 1 : 0;
         const int64_t row = k * sz + j * sy;
+        const int64_t row_in = k * in.sz + j * in.sy;
         for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
             const int64_t p = row + i;
             const double sig = fma(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
-            q_in[p] = lk::Num<T>::st((typename lk::Num<T>::C)sig);
+            q_in[row_in + lk::xo<SPLIT>(in, i)] = lk::Num<T>::st((typename lk::Num<T>::C)sig);
             acc = fma(sig, sig, acc);
         }
     }
@@ -66,13 +71,23 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
     }
 }
 
-// u += e over all nodes (e and u are zero on the boundary).
-template <typename T>
+// u += e on the interior nodes (e, layout `in`, is zero on the boundary;
+// so is u).
+template <int DIM, bool SPLIT, typename T>
 __global__ void __launch_bounds__(256) k_update(double* __restrict__ u, const T* __restrict__ e,
-                                                int64_t nodes) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nodes;
-         p += (int64_t)gridDim.x * blockDim.x)
-        u[p] += (double)lk::Num<T>::ld(e[p]);
+                                                Lay in) {
+    const int n = in.n;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
+         r += (int64_t)gridDim.x * blockDim.y) {
+        const int j = (int)(r % (n - 1)) + 1;
+        const int k = DIM == 3 ? (int)(r / (n - 1)) + 1 : 0;
+        const int64_t row = k * sz + j * sy;
+        const int64_t row_in = k * in.sz + j * in.sy;
+        for (int i = 1 + threadIdx.x; i < n; i += blockDim.x)
+            u[row + i] += (double)lk::Num<T>::ld(e[row_in + lk::xo<SPLIT>(in, i)]);
+    }
 }
 
 }  // namespace
@@ -86,32 +101,54 @@ int outer_partials(int d, int n) {
 }
 
 template <typename T>
-void outer_residual(int d, int n, const double* u, const double* q, T* q_in, double* partial,
-                    double* out, cudaStream_t s) {
+void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q_in,
+                    double* partial, double* out, cudaStream_t s) {
+    const int n = in.n;
     int bx = 32;
     while (bx < n && bx < 128) bx *= 2;
     dim3 block(bx, kThreads / bx, 1);
     const int blocks = outer_partials(d, n);
-    if (d == 3)
-        k_outer_residual<3, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, n);
-    else
-        k_outer_residual<2, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, n);
+    if (d == 3) {
+        if (in.he)
+            k_outer_residual<3, true, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, in);
+        else
+            k_outer_residual<3, false, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, in);
+    } else {
+        if (in.he)
+            k_outer_residual<2, true, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, in);
+        else
+            k_outer_residual<2, false, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, in);
+    }
     fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
 }
 
 template <typename T>
-void update(int d, int n, double* u, const T* e, cudaStream_t s) {
-    const int64_t nodes = d == 3 ? (int64_t)(n + 1) * (n + 1) * (n + 1) : (int64_t)(n + 1) * (n + 1);
-    const int blocks = (int)std::min<int64_t>((nodes + 255) / 256, 152 * 16);
-    k_update<T><<<blocks, 256, 0, s>>>(u, e, nodes);
+void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s) {
+    const int n = in.n;
+    int bx = 32;
+    while (bx < n && bx < 128) bx *= 2;
+    dim3 block(bx, 256 / bx, 1);
+    const int64_t rows = d == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
+    const int blocks = (int)std::min<int64_t>((rows + block.y - 1) / block.y, 152 * 16);
+    if (d == 3) {
+        if (in.he)
+            k_update<3, true, T><<<blocks, block, 0, s>>>(u, e, in);
+        else
+            k_update<3, false, T><<<blocks, block, 0, s>>>(u, e, in);
+    } else {
+        if (in.he)
+            k_update<2, true, T><<<blocks, block, 0, s>>>(u, e, in);
+        else
+            k_update<2, false, T><<<blocks, block, 0, s>>>(u, e, in);
+    }
 }
 
-template void outer_residual<float>(int, int, const double*, const double*, float*, double*,
-                                    double*, cudaStream_t);
-template void outer_residual<__nv_bfloat16>(int, int, const double*, const double*,
+template void outer_residual<float>(int, const Lay&, const double*, const double*, float*,
+                                    double*, double*, cudaStream_t);
+template void outer_residual<__nv_bfloat16>(int, const Lay&, const double*, const double*,
                                             __nv_bfloat16*, double*, double*, cudaStream_t);
-template void update<float>(int, int, double*, const float*, cudaStream_t);
-template void update<__nv_bfloat16>(int, int, double*, const __nv_bfloat16*, cudaStream_t);
+template void update<float>(int, const Lay&, double*, const float*, cudaStream_t);
+template void update<__nv_bfloat16>(int, const Lay&, double*, const __nv_bfloat16*, cudaStream_t);
 
 }  // namespace mixed
 }  // namespace gmg

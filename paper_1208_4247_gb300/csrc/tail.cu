@@ -250,8 +250,9 @@ __device__ void prolong_add(SLevel<T>& Cl, SLevel<T>& F) {
 // The V-cycle on levels with n = n_top, n_top/2, ..., n_top >> (levels-1).
 template <int DIM, typename T>
 __global__ void __launch_bounds__(1024) k_tail(T* __restrict__ u_top, const T* __restrict__ q_top,
-                                               int n_top, int levels, int smoother, double omega,
+                                               Lay top, int levels, int smoother, double omega,
                                                int nu1, int nu2, int coarse_sweeps) {
+    const int n_top = top.n;
     extern __shared__ __align__(16) unsigned char smem[];
     SLevel<T> lv[8];
     T* base = reinterpret_cast<T*>(smem);
@@ -275,9 +276,18 @@ __global__ void __launch_bounds__(1024) k_tail(T* __restrict__ u_top, const T* _
     for (int64_t p = threadIdx.x; p < base - reinterpret_cast<T*>(smem); p += blockDim.x)
         reinterpret_cast<T*>(smem)[p] = Num<T>::st(0.f);
     __syncthreads();
+    // global addressing of dense node p of the top level (top's layout)
+    auto gaddr = [&](int64_t p) {
+        const int m = n_top + 1;
+        const int i = (int)(p % m);
+        const int64_t jk = p / m;
+        const int j = (int)(jk % m), k = DIM == 3 ? (int)(jk / m) : 0;
+        return k * top.sz + j * top.sy + (top.he ? lk::xo<true>(top, i) : i);
+    };
     for (int64_t p = threadIdx.x; p < nodes_of<DIM>(n_top); p += blockDim.x) {
-        lv[0].q[p] = q_top[p];
-        lv[0].u[p] = u_top[p];
+        const int64_t g = gaddr(p);
+        lv[0].q[p] = q_top[g];
+        lv[0].u[p] = u_top[g];
     }
     __syncthreads();
     const bool red_only = smoother != GMG_WJACOBI && nu1 > 0;
@@ -299,7 +309,8 @@ __global__ void __launch_bounds__(1024) k_tail(T* __restrict__ u_top, const T* _
         prolong_add<DIM>(lv[l + 1], lv[l]);
         relax<DIM>(lv[l], smoother, omega, nu2);
     }
-    for (int64_t p = threadIdx.x; p < nodes_of<DIM>(n_top); p += blockDim.x) u_top[p] = lv[0].u[p];
+    for (int64_t p = threadIdx.x; p < nodes_of<DIM>(n_top); p += blockDim.x)
+        u_top[gaddr(p)] = lv[0].u[p];
 }
 
 }  // namespace
@@ -315,32 +326,33 @@ size_t smem_bytes(int d, int n_top, int levels, int smoother, size_t elem) {
 }
 
 template <typename T>
-cudaError_t launch(int d, int n_top, int levels, T* u_top, const T* q_top, int smoother,
+cudaError_t launch(int d, const Lay& top, int levels, T* u_top, const T* q_top, int smoother,
                    double omega, int nu1, int nu2, int coarse_sweeps, cudaStream_t s) {
-    const size_t bytes = smem_bytes(d, n_top, levels, smoother, sizeof(T));
+    const size_t bytes = smem_bytes(d, top.n, levels, smoother, sizeof(T));
     cudaError_t e;
     if (d == 3) {
         e = cudaFuncSetAttribute(k_tail<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)bytes);
         if (e != cudaSuccess) return e;
-        k_tail<3, T><<<1, 1024, bytes, s>>>(u_top, q_top, n_top, levels, smoother, omega, nu1,
-                                            nu2, coarse_sweeps);
+        k_tail<3, T><<<1, 1024, bytes, s>>>(u_top, q_top, top, levels, smoother, omega, nu1, nu2,
+                                            coarse_sweeps);
     } else {
         e = cudaFuncSetAttribute(k_tail<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)bytes);
         if (e != cudaSuccess) return e;
-        k_tail<2, T><<<1, 1024, bytes, s>>>(u_top, q_top, n_top, levels, smoother, omega, nu1,
-                                            nu2, coarse_sweeps);
+        k_tail<2, T><<<1, 1024, bytes, s>>>(u_top, q_top, top, levels, smoother, omega, nu1, nu2,
+                                            coarse_sweeps);
     }
     return cudaGetLastError();
 }
 
-template cudaError_t launch<double>(int, int, int, double*, const double*, int, double, int, int,
-                                    int, cudaStream_t);
-template cudaError_t launch<float>(int, int, int, float*, const float*, int, double, int, int, int,
-                                   cudaStream_t);
-template cudaError_t launch<__nv_bfloat16>(int, int, int, __nv_bfloat16*, const __nv_bfloat16*,
-                                           int, double, int, int, int, cudaStream_t);
+template cudaError_t launch<double>(int, const Lay&, int, double*, const double*, int, double,
+                                    int, int, int, cudaStream_t);
+template cudaError_t launch<float>(int, const Lay&, int, float*, const float*, int, double, int,
+                                   int, int, cudaStream_t);
+template cudaError_t launch<__nv_bfloat16>(int, const Lay&, int, __nv_bfloat16*,
+                                           const __nv_bfloat16*, int, double, int, int, int,
+                                           cudaStream_t);
 
 }  // namespace tail
 }  // namespace gmg
