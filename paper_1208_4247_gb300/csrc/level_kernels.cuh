@@ -137,6 +137,108 @@ __global__ void __launch_bounds__(256) k_rb_half(T* __restrict__ u, const T* __r
     }
 }
 
+// Four consecutive elements of a colour-split half row (16-byte aligned for
+// FP32, 8-byte for BF16) as four values of the compute type.
+__device__ inline void ld4(const float* p, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+}
+__device__ inline void ld4(const __nv_bfloat16* p, float* v) {
+    const uint2 a = *reinterpret_cast<const uint2*>(p);
+    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&a.x);
+    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&a.y);
+    v[0] = __low2float(lo);
+    v[1] = __high2float(lo);
+    v[2] = __low2float(hi);
+    v[3] = __high2float(hi);
+}
+__device__ inline void st4(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ inline void st4(__nv_bfloat16* p, const float* v) {
+    uint2 a;
+    *reinterpret_cast<__nv_bfloat162*>(&a.x) = __floats2bfloat162_rn(v[0], v[1]);
+    *reinterpret_cast<__nv_bfloat162*>(&a.y) = __floats2bfloat162_rn(v[2], v[3]);
+    *reinterpret_cast<uint2*>(p) = a;
+}
+
+// One colour of red-black Gauss-Seidel on a colour-split level (FP32 / BF16
+// storage), four nodes per thread: work item w = (row (j, k), group g) holds
+// the nodes of the colour at half-row positions 4g .. 4g+3, whose q, y/z
+// neighbours (same half of the neighbouring rows) and result are one vector
+// each, and whose x neighbours are five consecutive entries of the row's
+// other half.  Same operands in the same order as nbr_sum_x: the results
+// equal k_rb_half's bit for bit.  G = groups per half row.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T* __restrict__ q,
+                                                     Lay L, int color, int G) {
+    using N = Num<T>;
+    const float c = DIM == 3 ? 1.f / 6.f : 0.25f;
+    const int n = L.n, m = n - 1;
+    const int64_t rows = DIM == 3 ? (int64_t)m * m : m;
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= rows * G) return;
+    const int64_t r = w / G;
+    const int g = (int)(w - r * G);
+    const int j = (int)(r % m) + 1, k = DIM == 3 ? (int)(r / m) + 1 : 0;
+    const int par = (color + j + k) & 1;  // x parity of the colour in this row
+    const int x0 = 2 * 4 * g + par;       // x of the group's first node
+    if (x0 > n - 1) return;
+    const int64_t row = k * L.sz + j * L.sy;
+    const int64_t base = row + (par ? L.he : 0) + 4 * g;
+    // other half: x-1 / x+1 of node t are entries t-1+par / t+par of it
+    const int64_t ob = row + (par ? 0 : L.he) + 4 * g;
+    float xo5[5];  // other-half entries 4g-1+par .. 4g+3+par
+    {
+        float v[4];
+        ld4(u + ob, v);
+        if (par) {
+            xo5[0] = v[0];
+            xo5[1] = v[1];
+            xo5[2] = v[2];
+            xo5[3] = v[3];
+            xo5[4] = N::ld(u[ob + 4]);
+        } else {
+            xo5[0] = g > 0 ? N::ld(u[ob - 1]) : 0.f;  // g == 0: x = 0, not updated
+            xo5[1] = v[0];
+            xo5[2] = v[1];
+            xo5[3] = v[2];
+            xo5[4] = v[3];
+        }
+    }
+    float qv[4], ym[4], yp[4], zm[4], zp[4], out[4];
+    ld4(q + base, qv);
+    ld4(u + base - L.sy, ym);
+    ld4(u + base + L.sy, yp);
+    if (DIM == 3) {
+        ld4(u + base - L.sz, zm);
+        ld4(u + base + L.sz, zp);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const float sx = xo5[t] + xo5[t + 1];
+        if (DIM == 3) {
+            const float lo = ym[t] + zm[t];
+            const float hi = yp[t] + zp[t];
+            out[t] = fmaf(c, (sx + lo) + hi, qv[t]);
+        } else {
+            out[t] = fmaf(c, sx + (ym[t] + yp[t]), qv[t]);
+        }
+    }
+    if (x0 >= 1 && x0 + 6 <= n - 1) {
+        st4(u + base, out);
+    } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int x = x0 + 2 * t;
+            if (x >= 1 && x <= n - 1) u[base + t] = N::st(out[t]);
+        }
+    }
+}
+
 // 3D red-black half sweep by diagonal walkers.  The (n-1)^2 interior rows
 // (j, k) form n-1 cyclic diagonals k-1 = (j-1+line) mod (n-1); a walker
 // (one threadIdx.y) takes kWalk consecutive rows (j, k) -> (j+1, k+1) of one
@@ -454,6 +556,18 @@ void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s) {
         const WalkLaunch W = walk_launch(n);
         k_rb_half3_walk<T><<<W.blocks, W.block, 0, s>>>(u, q, n, color, W.segs);
         return;
+    }
+    if constexpr (!std::is_same<T, double>::value) {
+        if (L.he) {
+            const int G = (n / 2 + 1 + 3) / 4;
+            const int64_t items = (int64_t)G * (d == 3 ? (int64_t)(n - 1) * (n - 1) : n - 1);
+            const unsigned blocks = (unsigned)((items + 255) / 256);
+            if (d == 3)
+                k_rb_half_vec<3, T><<<blocks, 256, 0, s>>>(u, q, L, color, G);
+            else
+                k_rb_half_vec<2, T><<<blocks, 256, 0, s>>>(u, q, L, color, G);
+            return;
+        }
     }
     RowLaunch R = row_launch(d, n, n / 2);
     if (d == 3) {
