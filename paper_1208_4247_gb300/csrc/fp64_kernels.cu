@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256, 4) k_resnorm3_walk(const double* __restri
     double acc = 0.0;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; w < walkers;
          w += (int64_t)gridDim.x * blockDim.y)
-        lk::walk_nodes(u, n, 0, w, segs, [&](int64_t p, double sum) {
+        lk::walk_nodes(u, n, 0, w, segs, [&](int64_t p, double sum, int, int, int) {
             const double sig = fma(c, sum, q[p]) - u[p];
             acc = fma(sig, sig, acc);
         });

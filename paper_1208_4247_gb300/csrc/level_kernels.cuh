@@ -302,9 +302,10 @@ __global__ void __launch_bounds__(256, 4) k_rb_half3_walk(T* __restrict__ u, con
 }
 
 // Walker w of the diagonal decomposition above (colour `color`): calls
-// f(p, sum) for each of its nodes p with sum = nbr_sum<3>(u, p) (the same
-// operands in the same order), forming each (y- + z-) pair once per run.
-// For kernels that do not write u (residual, norm).
+// f(p, sum, i, j, k) for each of its nodes p = (i, j, k) with
+// sum = nbr_sum<3>(u, p) (the same operands in the same order), forming each
+// (y- + z-) pair once per run.  For kernels that do not write u (residual,
+// norms).
 template <typename T, class F>
 __device__ inline void walk_nodes(const T* __restrict__ u, int n, int color, int64_t w, int segs,
                                   F&& f) {
@@ -326,7 +327,7 @@ __device__ inline void walk_nodes(const T* __restrict__ u, int n, int color, int
             for (int r = 0; r < run; ++r, p += sy + sz) {
                 const C sx = N::ld(u[p - 1]) + N::ld(u[p + 1]);
                 const C hi = N::ld(u[p + sy]) + N::ld(u[p + sz]);
-                f(p, (sx + lo) + hi);
+                f(p, (sx + lo) + hi, i, j + r, k + r);
                 lo = hi;
             }
         }
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(256, 4) k_residual3_walk(const T* __restrict__
     const C c = C(1.0 / 6.0);
     const int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
     if (w >= (int64_t)(n - 1) * segs) return;
-    walk_nodes(u, n, 0, w, segs, [&](int64_t p, C sum) {
+    walk_nodes(u, n, 0, w, segs, [&](int64_t p, C sum, int, int, int) {
         r[p] = N::st(fma(c, sum, N::ld(q[p])) - N::ld(u[p]));
     });
 }
