@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kNormThreads) k_resnorm(const double* __restri
     }
 }
 
-// Red-only norm by the diagonal walkers (3D, 64 <= n <= 512): the same
+// Red-only norm by the diagonal walkers (3D, 128 <= n <= 512): the same
 // sigma^2 terms as k_resnorm<3, false, true>, summed in walker order; a
 // fixed grid strides over the walkers, so the result is deterministic.
 __global__ void __launch_bounds__(256, 4) k_resnorm3_walk(const double* __restrict__ u,

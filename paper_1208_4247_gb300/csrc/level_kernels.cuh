@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(256, 4) k_residual3_walk(const T* __restrict__
     });
 }
 
-// Launch shape of the walker kernels for a 3D level n (64 <= n <= 512):
+// Launch shape of the walker kernels for a 3D level n (128 <= n <= 512):
 // block (bx, 256/bx) with bx >= n/2 x threads, walkers and CTAs.
 struct WalkLaunch {
     dim3 block;
@@ -370,8 +370,10 @@ inline WalkLaunch walk_launch(int n) {
     L.blocks = (unsigned)((L.walkers + L.block.y - 1) / L.block.y);
     return L;
 }
+// From n = 128 up (at n = 64 the 126 walker CTAs leave SMs idle and the row
+// kernels are faster).
 inline bool walk_applies(int d, int n, size_t elem) {
-    return elem == sizeof(double) && d == 3 && n >= 64 && n <= 512 && rb_walk_enabled();
+    return elem == sizeof(double) && d == 3 && n >= 128 && n <= 512 && rb_walk_enabled();
 }
 
 // Weighted Jacobi: u_out = u + omega * sigma, all nodes from u_in.
@@ -547,7 +549,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, T
 
 // ------------------------------------------------------------- launchers
 
-// FP64 3D dense levels with 64 <= n <= 512 use the diagonal walkers (one red
+// FP64 3D dense levels with 128 <= n <= 512 use the diagonal walkers (one red
 // node per x thread and row, 256 threads) for the half sweeps and the
 // red-only residual unless GMG_RB_WALK=0 (same results bit for bit).
 template <typename T>
