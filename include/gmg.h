@@ -266,6 +266,64 @@ gmg_status gmg_batch_timing_report(gmg_batch b, gmg_kernel_stat* out, int cap, i
 
 gmg_status gmg_batch_destroy(gmg_batch b);
 
+/* ------------------------------------------- the problem statement's names
+ * The solver interface as the problem statement names it (Algorithm 3's
+ * GMGSolve on caller arrays with row pitches, the batched form, and training
+ * and persistence of the learned smoother); wrappers over the calls above. */
+
+/* gmg_solve on arrays with pitches: node (i, j, k) of f and u at
+ * k*strides[2] + j*strides[1] + i (elements; strides[0] must be 1,
+ * strides[1] >= n+1, 3D: strides[2] >= strides[1]*(n+1); strides[2] unused
+ * in 2D).  Dense pitches call gmg_solve directly; any other pitch stages f
+ * and u through dense device copies owned by the handle (one gather each way
+ * and one scatter of u, about 3 (n+1)^d doubles moved twice).  u's boundary
+ * nodes are written as 0, the padding is not touched.  Errors as gmg_solve;
+ * GMG_ERR_LAYOUT for bad strides. */
+gmg_status gmg_solve_strided(gmg_handle h, const double* f, double* u, const int64_t strides[3],
+                             double rtol, int* iters_out, double* relres_out);
+
+/* The batched form from one configuration per solve: cfgs[i].d, cfgs[i].n
+ * give solve i's grid; smoother, omega, nu1, nu2, precision, inner_cycles and
+ * maxit must be the same in every cfgs[i] (else GMG_ERR_ARG).  Default chunk
+ * and CTA count (see gmg_batch_create). */
+gmg_status gmg_create_batched(int count, const gmg_config* cfgs, void* cuda_stream,
+                              gmg_batch* out);
+/* gmg_batch_solve without the per-solve residuals and the step count. */
+gmg_status gmg_solve_batched(gmg_batch b, const double* const* f, double* const* u, double rtol,
+                             int* iters_out);
+
+typedef struct {
+    int n;               /* grid of the training samples (intervals per dimension) */
+    int steps;           /* Adam steps */
+    int batch;           /* error samples per step */
+    int pair_cycles;     /* plain red-black V(1,1) cycles applied to white noise per sample */
+    int coarse_cycles;   /* red-black V(2,2) cycles for the coarse solve of the loss */
+    double lr;           /* Adam learning rate */
+    uint64_t seed;       /* seed of the samples' white noise */
+    double omega_init;   /* start at weighted Jacobi with this omega if w_init is NULL
+                            (<= 0: 6/7 in 3D, 4/5 in 2D) */
+    unsigned level_mask; /* bit l set: install the trained weights on level l */
+} gmg_train_config;
+
+/* Train the learned smoother of h (smoother GMG_LEARNED) with
+ * gmg_learned_train on the handle's dimension and install the result on the
+ * levels of tc->level_mask.  w_init: starting weights (host, layout of
+ * gmg_set_learned_weights) or NULL.  loss_history: tc->steps doubles or
+ * NULL.  Synchronises the handle's stream. */
+gmg_status gmg_smoother_train(gmg_handle h, const gmg_train_config* tc, const float* w_init,
+                              double* loss_history);
+
+/* Persistence of the learned smoother of h (smoother GMG_LEARNED).  Blob
+ * layout, for each level of the handle in order: int32 flag (1: weights
+ * follow, 0: the level smooths with red-black GS), then, if 1, the level's
+ * BF16-rounded weights as 2 x 8 x T floats (layout of
+ * gmg_set_learned_weights).  save: *bytes_out = the blob size; the blob is
+ * written when blob != NULL and cap is large enough (else GMG_ERR_ARG).
+ * load: the blob must match the handle's level count exactly (else
+ * GMG_ERR_ARG, no level changed). */
+gmg_status gmg_smoother_save(gmg_handle h, void* blob, size_t cap, size_t* bytes_out);
+gmg_status gmg_smoother_load(gmg_handle h, const void* blob, size_t bytes);
+
 /* Release every device and host resource of the handle.  NULL is a no-op. */
 gmg_status gmg_destroy(gmg_handle h);
 

@@ -3,7 +3,9 @@
 // Algorithm 3 with every level on the device.  Two forms share the
 // schedule: plain FP64 cycles, and FP32 / BF16 cycles inside FP64 iterative
 // refinement.
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -818,6 +820,47 @@ gmg_status gmg_solve(gmg_handle h, const double* f, double* u, double rtol, int*
     return run(h, f, u, rtol, 0, true, iters_out, relres_out);
 }
 
+gmg_status gmg_solve_strided(gmg_handle h, const double* f, double* u, const int64_t strides[3],
+                             double rtol, int* iters_out, double* relres_out) {
+    if (!h || !strides) {
+        set_error("handle / strides is NULL");
+        return GMG_ERR_ARG;
+    }
+    const int d = h->cfg.d;
+    const int64_t m = h->cfg.n + 1;
+    const int64_t sy = strides[1], sz = d == 3 ? strides[2] : 0;
+    if (strides[0] != 1 || sy < m || (d == 3 && sz < sy * m)) {
+        set_error("strides must be {1, >= n+1, >= strides[1]*(n+1) (3D)} elements");
+        return GMG_ERR_LAYOUT;
+    }
+    if (sy == m && (d == 2 || sz == m * m)) return gmg_solve(h, f, u, rtol, iters_out, relres_out);
+    if (!(rtol >= 0.0) || !std::isfinite(rtol)) {
+        set_error("rtol must be finite and >= 0");
+        return GMG_ERR_ARG;
+    }
+    gmg_status st = check_device_ptr(f, "f");
+    if (st != GMG_OK) return st;
+    if ((st = check_device_ptr(u, "u")) != GMG_OK) return st;
+    DeviceGuard guard(h->device);
+    const int64_t nodes = h->lv[0].nodes;
+    if (!h->f_stage) {
+        if ((st = dev_alloc(h, &h->f_stage, nodes)) != GMG_OK) return st;
+        if ((st = dev_alloc(h, &h->u_stage, nodes)) != GMG_OK) return st;
+    }
+    GMG_CUDA_TRY(cudaEventRecord(h->ev, h->user_stream));
+    GMG_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev, 0));
+    const int64_t dz = d == 3 ? m * m : 0;
+    fp64::copy_strided(d, h->cfg.n, f, sy, sz, h->f_stage, m, dz, h->stream);
+    fp64::copy_strided(d, h->cfg.n, u, sy, sz, h->u_stage, m, dz, h->stream);
+    GMG_CUDA_TRY(cudaGetLastError());
+    st = run(h, h->f_stage, h->u_stage, rtol, 0, true, iters_out, relres_out);
+    if (st != GMG_OK && st != GMG_ERR_NOT_CONVERGED) return st;
+    fp64::copy_strided(d, h->cfg.n, h->u_stage, m, dz, u, sy, sz, h->stream);
+    GMG_CUDA_TRY(cudaGetLastError());
+    GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return st;
+}
+
 gmg_status gmg_cycles(gmg_handle h, const double* f, double* u, int ncycles, double* relres_out) {
     if (!h) {
         set_error("handle is NULL");
@@ -968,6 +1011,127 @@ gmg_status gmg_history(gmg_handle h, double* relres, int cap, int* count) {
     const int m = (int)h->hist.size();
     for (int i = 0; i < m && i < cap; ++i) relres[i] = h->hist[i];
     if (count) *count = m;
+    return GMG_OK;
+}
+
+gmg_status gmg_smoother_train(gmg_handle h, const gmg_train_config* tc, const float* w_init,
+                              double* loss_history) {
+    if (!h || !tc) {
+        set_error("handle / train config is NULL");
+        return GMG_ERR_ARG;
+    }
+    if (h->cfg.smoother != GMG_LEARNED) {
+        set_error("the handle was not created with smoother GMG_LEARNED");
+        return GMG_ERR_ARG;
+    }
+    const int d = h->cfg.d, T = d == 3 ? 27 : 9;
+    std::vector<float> w0(2 * 8 * T, 0.f), w(2 * 8 * T, 0.f);
+    if (w_init) {
+        std::copy(w_init, w_init + 2 * 8 * T, w0.begin());
+    } else {
+        // weighted Jacobi, N(sigma) = omega * sigma (relu(x) - relu(-x) = x)
+        const float om = (float)(tc->omega_init > 0.0 ? tc->omega_init : d == 3 ? 6.0 / 7.0 : 0.8);
+        w0[0 * T + T / 2] = 1.f;
+        w0[1 * T + T / 2] = -1.f;
+        w0[8 * T + 0 * T + T / 2] = om;
+        w0[8 * T + 1 * T + T / 2] = -om;
+    }
+    gmg_status st = gmg_learned_train(d, tc->n, tc->steps, tc->batch, tc->pair_cycles,
+                                      tc->coarse_cycles, tc->lr, tc->seed, w0.data(), w.data(),
+                                      loss_history, (void*)h->user_stream);
+    if (st != GMG_OK) return st;
+    for (int l = 0; l < (int)h->lw.size() && l < 32; ++l)
+        if ((tc->level_mask >> l) & 1u)
+            if ((st = gmg_set_learned_weights(h, l, w.data())) != GMG_OK) return st;
+    return GMG_OK;
+}
+
+gmg_status gmg_smoother_save(gmg_handle h, void* blob, size_t cap, size_t* bytes_out) {
+    if (!h || !bytes_out || (!blob && cap > 0)) {
+        set_error("bad arguments");
+        return GMG_ERR_ARG;
+    }
+    if (h->cfg.smoother != GMG_LEARNED) {
+        set_error("the handle was not created with smoother GMG_LEARNED");
+        return GMG_ERR_ARG;
+    }
+    const int T = h->cfg.d == 3 ? 27 : 9;
+    const size_t wbytes = sizeof(float) * 2 * 8 * T;
+    size_t need = 0;
+    for (float* w : h->lw) need += sizeof(int32_t) + (w ? wbytes : 0);
+    *bytes_out = need;
+    if (!blob) return GMG_OK;
+    if (cap < need) {
+        set_error("blob too small");
+        return GMG_ERR_ARG;
+    }
+    DeviceGuard guard(h->device);
+    GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    unsigned char* p = static_cast<unsigned char*>(blob);
+    for (float* w : h->lw) {
+        const int32_t flag = w ? 1 : 0;
+        std::memcpy(p, &flag, sizeof(flag));
+        p += sizeof(flag);
+        if (w) {
+            GMG_CUDA_TRY(cudaMemcpy(p, w, wbytes, cudaMemcpyDeviceToHost));
+            p += wbytes;
+        }
+    }
+    return GMG_OK;
+}
+
+gmg_status gmg_smoother_load(gmg_handle h, const void* blob, size_t bytes) {
+    if (!h || !blob) {
+        set_error("handle / blob is NULL");
+        return GMG_ERR_ARG;
+    }
+    if (h->cfg.smoother != GMG_LEARNED) {
+        set_error("the handle was not created with smoother GMG_LEARNED");
+        return GMG_ERR_ARG;
+    }
+    const int T = h->cfg.d == 3 ? 27 : 9;
+    const size_t wbytes = sizeof(float) * 2 * 8 * T;
+    // parse the whole blob before changing any level
+    const unsigned char* p = static_cast<const unsigned char*>(blob);
+    const unsigned char* end = p + bytes;
+    std::vector<const float*> ws;
+    for (size_t l = 0; l < h->lw.size(); ++l) {
+        int32_t flag = 0;
+        if (end - p < (ptrdiff_t)sizeof(flag)) {
+            set_error("blob truncated");
+            return GMG_ERR_ARG;
+        }
+        std::memcpy(&flag, p, sizeof(flag));
+        p += sizeof(flag);
+        if (flag != 0 && flag != 1) {
+            set_error("blob: bad level flag");
+            return GMG_ERR_ARG;
+        }
+        if (flag) {
+            if (end - p < (ptrdiff_t)wbytes) {
+                set_error("blob truncated");
+                return GMG_ERR_ARG;
+            }
+            ws.push_back(reinterpret_cast<const float*>(p));
+            p += wbytes;
+        } else {
+            ws.push_back(nullptr);
+        }
+    }
+    if (p != end) {
+        set_error("blob size does not match the handle's levels");
+        return GMG_ERR_ARG;
+    }
+    for (size_t l = 0; l < ws.size(); ++l) {
+        std::vector<float> w;
+        const float* src = ws[l];
+        if (src) {  // the blob need not be float-aligned
+            w.resize(2 * 8 * T);
+            std::memcpy(w.data(), src, wbytes);
+        }
+        gmg_status st = gmg_set_learned_weights(h, (int)l, src ? w.data() : nullptr);
+        if (st != GMG_OK) return st;
+    }
     return GMG_OK;
 }
 

@@ -853,4 +853,33 @@ gmg_status gmg_batch_timing_report(gmg_batch b, gmg_kernel_stat* out, int cap, i
     return GMG_OK;
 }
 
+gmg_status gmg_create_batched(int count, const gmg_config* cfgs, void* cuda_stream,
+                              gmg_batch* out) {
+    if (!out || !cfgs || count < 1 || count > (1 << 20)) {
+        set_error("gmg_create_batched: bad arguments");
+        return GMG_ERR_ARG;
+    }
+    *out = nullptr;
+    const gmg_config& c0 = cfgs[0];
+    std::vector<int> d(count), n(count);
+    for (int i = 0; i < count; ++i) {
+        const gmg_config& c = cfgs[i];
+        if (c.smoother != c0.smoother || c.omega != c0.omega || c.nu1 != c0.nu1 ||
+            c.nu2 != c0.nu2 || c.precision != c0.precision || c.inner_cycles != c0.inner_cycles ||
+            c.maxit != c0.maxit) {
+            set_error("gmg_create_batched: solves differ in smoother, sweeps, precision, "
+                      "inner_cycles or maxit");
+            return GMG_ERR_ARG;
+        }
+        d[i] = c.d;
+        n[i] = c.n;
+    }
+    return gmg_batch_create(count, d.data(), n.data(), &c0, 0, 0, cuda_stream, out);
+}
+
+gmg_status gmg_solve_batched(gmg_batch b, const double* const* f, double* const* u, double rtol,
+                             int* iters_out) {
+    return gmg_batch_solve(b, f, u, rtol, iters_out, nullptr, nullptr);
+}
+
 }  // extern "C"

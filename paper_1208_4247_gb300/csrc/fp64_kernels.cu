@@ -176,6 +176,36 @@ void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s
         k_prepare<2><<<blocks, 256, 0, s>>>(f, q, u, n, scale);
 }
 
+namespace {
+// dst = src on all (n+1)^d nodes, each array with its own row / plane pitch
+template <int DIM>
+__global__ void __launch_bounds__(256) k_copy_strided(const double* __restrict__ src, int64_t ssy,
+                                                      int64_t ssz, double* __restrict__ dst,
+                                                      int64_t dsy, int64_t dsz, int n) {
+    const int64_t m = n + 1;
+    const int64_t rows = DIM == 3 ? m * m : m;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
+         r += (int64_t)gridDim.x * blockDim.y) {
+        const int64_t j = r % m, k = DIM == 3 ? r / m : 0;
+        for (int i = threadIdx.x; i <= n; i += blockDim.x)
+            dst[k * dsz + j * dsy + i] = src[k * ssz + j * ssy + i];
+    }
+}
+}  // namespace
+
+void copy_strided(int d, int n, const double* src, int64_t ssy, int64_t ssz, double* dst,
+                  int64_t dsy, int64_t dsz, cudaStream_t s) {
+    int bx = 32;
+    while (bx < n + 1 && bx < 128) bx *= 2;
+    dim3 block(bx, 256 / bx, 1);
+    const int64_t rows = d == 3 ? (int64_t)(n + 1) * (n + 1) : (n + 1);
+    const unsigned blocks = (unsigned)std::min<int64_t>((rows + block.y - 1) / block.y, 152 * 16);
+    if (d == 3)
+        k_copy_strided<3><<<blocks, block, 0, s>>>(src, ssy, ssz, dst, dsy, dsz, n);
+    else
+        k_copy_strided<2><<<blocks, block, 0, s>>>(src, ssy, ssz, dst, dsy, dsz, n);
+}
+
 int resnorm_partials(int d, int n) { return (int)norm_launch(d, n).grid.x; }
 
 void resnorm(int d, int n, const double* u, const double* q, double* partial, double* out,

@@ -119,6 +119,10 @@ inline void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s,
 namespace fp64 {
 void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s);
 int resnorm_partials(int d, int n);
+// dst = src on every node of a (n+1)^d grid; src / dst row and plane pitches
+// in elements (x contiguous)
+void copy_strided(int d, int n, const double* src, int64_t ssy, int64_t ssz, double* dst,
+                  int64_t dsy, int64_t dsz, cudaStream_t s);
 // sum of sigma^2 into *out; sigma_out (may be NULL) also receives sigma;
 // red_only (ignored with sigma_out) sums red nodes only, valid right after a
 // black half sweep of level 0 (black sigma is then exactly zero)

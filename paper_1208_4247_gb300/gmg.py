@@ -84,7 +84,21 @@ SIGNATURES = {
     "gmg_learned_conv": ([I, I, P, P, P, I, P], I),
     "gmg_learned_loss_grad": ([I, I, P, P, I, PD, PD, P], I),
     "gmg_learned_train": ([I, I, I, I, I, I, D, ctypes.c_uint64, P, P, PD, P], I),
+    "gmg_solve_strided": ([P, P, P, ctypes.POINTER(ctypes.c_int64), D, PI, PD], I),
+    "gmg_create_batched": ([I, P, P, ctypes.POINTER(P)], I),
+    "gmg_solve_batched": ([P, ctypes.POINTER(P), ctypes.POINTER(P), D, PI], I),
+    "gmg_smoother_train": ([P, P, P, PD], I),
+    "gmg_smoother_save": ([P, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], I),
+    "gmg_smoother_load": ([P, P, ctypes.c_size_t], I),
 }
+
+
+class TrainConfig(ctypes.Structure):
+    """gmg_train_config (include/gmg.h)."""
+    _fields_ = [("n", ctypes.c_int), ("steps", ctypes.c_int), ("batch", ctypes.c_int),
+                ("pair_cycles", ctypes.c_int), ("coarse_cycles", ctypes.c_int),
+                ("lr", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("omega_init", ctypes.c_double), ("level_mask", ctypes.c_uint)]
 
 
 def lib():
@@ -158,6 +172,54 @@ class Solver:
                                     _dptr(u, "u", self.d, self.n), rtol, ctypes.byref(it),
                                     ctypes.byref(rel)), allow=(ERR_NOT_CONVERGED,))
         return it.value, rel.value, st == OK
+
+    def solve_strided(self, f, u, rtol: float = 1e-10):
+        """gmg_solve_strided: f, u float64 CUDA tensors of shape (n+1)^d whose
+        x stride is 1 (e.g. views into padded arrays).  Returns as solve."""
+        import torch
+        for name, t in (("f", f), ("u", u)):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+                raise TypeError(f"{name} must be a float64 CUDA tensor")
+            if tuple(t.shape) != (self.n + 1,) * self.d:
+                raise ValueError(f"{name} must have shape {(self.n + 1,) * self.d}")
+        if f.stride() != u.stride():
+            raise ValueError("f and u must have the same strides")
+        st_ = list(reversed(f.stride())) + [0] * (3 - self.d)
+        strides = (ctypes.c_int64 * 3)(*st_)
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = _check(lib().gmg_solve_strided(self._h, ctypes.c_void_p(f.data_ptr()),
+                                            ctypes.c_void_p(u.data_ptr()), strides, rtol,
+                                            ctypes.byref(it), ctypes.byref(rel)),
+                    allow=(ERR_NOT_CONVERGED,))
+        return it.value, rel.value, st == OK
+
+    def smoother_train(self, n: int, steps: int, batch: int = 8, pair_cycles: int = 1,
+                       coarse_cycles: int = 12, lr: float = 3e-3, seed: int = 1,
+                       omega_init: float = 0.0, levels=(0,), w_init=None):
+        """gmg_smoother_train; returns the per-step mean loss (numpy)."""
+        import numpy as np
+        tc = TrainConfig(n, steps, batch, pair_cycles, coarse_cycles, lr, seed, omega_init,
+                         sum(1 << l for l in levels))
+        loss = np.zeros(max(steps, 1), np.float64)
+        w = None if w_init is None else np.ascontiguousarray(w_init, dtype=np.float32)
+        _check(lib().gmg_smoother_train(self._h, ctypes.byref(tc),
+                                        None if w is None else ctypes.c_void_p(w.ctypes.data),
+                                        loss.ctypes.data_as(PD)))
+        return loss[:steps]
+
+    def smoother_save(self) -> bytes:
+        """gmg_smoother_save: the learned smoother of every level as a blob."""
+        size = ctypes.c_size_t(0)
+        _check(lib().gmg_smoother_save(self._h, None, 0, ctypes.byref(size)))
+        buf = ctypes.create_string_buffer(max(size.value, 1))
+        _check(lib().gmg_smoother_save(self._h, buf, size.value, ctypes.byref(size)))
+        return buf.raw[:size.value]
+
+    def smoother_load(self, blob: bytes):
+        """gmg_smoother_load of a blob from smoother_save."""
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().gmg_smoother_load(self._h, buf, len(blob)))
 
     def solve_host(self, f, u, rtol: float = 1e-10):
         """f, u: C-contiguous float64 numpy arrays (pinned or pageable host

@@ -127,3 +127,23 @@ def test_fmg_needs_plain_fp64(L):
     c.precision = 1
     h = ctypes.c_void_p()
     assert L.gmg_create(ctypes.byref(c), None, ctypes.byref(h)) == 8
+
+
+def test_problem_statement_entry_points_reject_bad_arguments(L):
+    """gmg_solve_strided, gmg_create_batched, gmg_smoother_{train,save,load}:
+    argument checks that need no GPU."""
+    st = (ctypes.c_int64 * 3)(1, 20, 400)
+    assert L.gmg_solve_strided(None, None, None, st, 1e-10, None, None) == 1
+    out = ctypes.c_void_p()
+    assert L.gmg_create_batched(0, None, None, ctypes.byref(out)) == 1
+    c = (gmg.Config * 2)()
+    L.gmg_config_init(ctypes.byref(c[0]), 3, 16)
+    L.gmg_config_init(ctypes.byref(c[1]), 2, 64)
+    c[0].precision = c[1].precision = 1
+    c[1].nu1 = 1  # differs from solve 0
+    assert L.gmg_create_batched(2, c, None, ctypes.byref(out)) == 1
+    assert b"differ" in L.gmg_last_error()
+    size = ctypes.c_size_t(0)
+    assert L.gmg_smoother_save(None, None, 0, ctypes.byref(size)) == 1
+    assert L.gmg_smoother_load(None, None, 0) == 1
+    assert L.gmg_smoother_train(None, None, None, None) == 1
