@@ -137,45 +137,53 @@ __global__ void __launch_bounds__(256) k_rb_half(T* __restrict__ u, const T* __r
     }
 }
 
-// Four consecutive elements of a colour-split half row (16-byte aligned for
-// FP32, 8-byte for BF16) as four values of the compute type.
-__device__ inline void ld4(const float* p, float* v) {
+// V consecutive elements of a colour-split half row (16-byte aligned: V = 4
+// for FP32, 8 for BF16) as V values of the compute type.
+__device__ inline void ldv(const float* p, float* v) {
     const float4 a = *reinterpret_cast<const float4*>(p);
     v[0] = a.x;
     v[1] = a.y;
     v[2] = a.z;
     v[3] = a.w;
 }
-__device__ inline void ld4(const __nv_bfloat16* p, float* v) {
-    const uint2 a = *reinterpret_cast<const uint2*>(p);
-    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&a.x);
-    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&a.y);
-    v[0] = __low2float(lo);
-    v[1] = __high2float(lo);
-    v[2] = __low2float(hi);
-    v[3] = __high2float(hi);
+__device__ inline void ldv(const __nv_bfloat16* p, float* v) {
+    const uint4 a = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&w[h]);
+        v[2 * h] = __low2float(b);
+        v[2 * h + 1] = __high2float(b);
+    }
 }
-__device__ inline void st4(float* p, const float* v) {
+__device__ inline void stv(float* p, const float* v) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
-__device__ inline void st4(__nv_bfloat16* p, const float* v) {
-    uint2 a;
-    *reinterpret_cast<__nv_bfloat162*>(&a.x) = __floats2bfloat162_rn(v[0], v[1]);
-    *reinterpret_cast<__nv_bfloat162*>(&a.y) = __floats2bfloat162_rn(v[2], v[3]);
-    *reinterpret_cast<uint2*>(p) = a;
+__device__ inline void stv(__nv_bfloat16* p, const float* v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+        *reinterpret_cast<__nv_bfloat162*>(&w[h]) = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+    *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+template <typename T>
+__host__ __device__ constexpr int vec_of() {
+    return 16 / (int)sizeof(T);
 }
 
 // One colour of red-black Gauss-Seidel on a colour-split level (FP32 / BF16
-// storage), four nodes per thread: work item w = (row (j, k), group g) holds
-// the nodes of the colour at half-row positions 4g .. 4g+3, whose q, y/z
-// neighbours (same half of the neighbouring rows) and result are one vector
-// each, and whose x neighbours are five consecutive entries of the row's
-// other half.  Same operands in the same order as nbr_sum_x: the results
-// equal k_rb_half's bit for bit.  G = groups per half row.
+// storage), V = 16 bytes of nodes per thread: work item w = (row (j, k),
+// group g) holds the nodes of the colour at half-row positions V g .. V g +
+// V-1, whose q, y/z neighbours (same half of the neighbouring rows) and
+// result are one 16-byte vector each, and whose x neighbours are V+1
+// consecutive entries of the row's other half.  Same operands in the same
+// order as nbr_sum_x: the results equal k_rb_half's bit for bit.  G = groups
+// per half row.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T* __restrict__ q,
                                                      Lay L, int color, int G) {
     using N = Num<T>;
+    constexpr int V = vec_of<T>();
     const float c = DIM == 3 ? 1.f / 6.f : 0.25f;
     const int n = L.n, m = n - 1;
     const int64_t rows = DIM == 3 ? (int64_t)m * m : m;
@@ -185,41 +193,34 @@ __global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T*
     const int g = (int)(w - r * G);
     const int j = (int)(r % m) + 1, k = DIM == 3 ? (int)(r / m) + 1 : 0;
     const int par = (color + j + k) & 1;  // x parity of the colour in this row
-    const int x0 = 2 * 4 * g + par;       // x of the group's first node
+    const int x0 = 2 * V * g + par;       // x of the group's first node
     if (x0 > n - 1) return;
     const int64_t row = k * L.sz + j * L.sy;
-    const int64_t base = row + (par ? L.he : 0) + 4 * g;
+    const int64_t base = row + (par ? L.he : 0) + V * g;
     // other half: x-1 / x+1 of node t are entries t-1+par / t+par of it
-    const int64_t ob = row + (par ? 0 : L.he) + 4 * g;
-    float xo5[5];  // other-half entries 4g-1+par .. 4g+3+par
+    const int64_t ob = row + (par ? 0 : L.he) + V * g;
+    float xo[V + 1];  // other-half entries V g - 1 + par .. V g + V - 1 + par
     {
-        float v[4];
-        ld4(u + ob, v);
-        if (par) {
-            xo5[0] = v[0];
-            xo5[1] = v[1];
-            xo5[2] = v[2];
-            xo5[3] = v[3];
-            xo5[4] = N::ld(u[ob + 4]);
-        } else {
-            xo5[0] = g > 0 ? N::ld(u[ob - 1]) : 0.f;  // g == 0: x = 0, not updated
-            xo5[1] = v[0];
-            xo5[2] = v[1];
-            xo5[3] = v[2];
-            xo5[4] = v[3];
-        }
+        float v[V];
+        ldv(u + ob, v);
+#pragma unroll
+        for (int t = 0; t < V; ++t) xo[t + 1 - par] = v[t];
+        if (par)
+            xo[V] = N::ld(u[ob + V]);
+        else
+            xo[0] = g > 0 ? N::ld(u[ob - 1]) : 0.f;  // g == 0: x = 0, not updated
     }
-    float qv[4], ym[4], yp[4], zm[4], zp[4], out[4];
-    ld4(q + base, qv);
-    ld4(u + base - L.sy, ym);
-    ld4(u + base + L.sy, yp);
+    float qv[V], ym[V], yp[V], zm[V], zp[V], out[V];
+    ldv(q + base, qv);
+    ldv(u + base - L.sy, ym);
+    ldv(u + base + L.sy, yp);
     if (DIM == 3) {
-        ld4(u + base - L.sz, zm);
-        ld4(u + base + L.sz, zp);
+        ldv(u + base - L.sz, zm);
+        ldv(u + base + L.sz, zp);
     }
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const float sx = xo5[t] + xo5[t + 1];
+    for (int t = 0; t < V; ++t) {
+        const float sx = xo[t] + xo[t + 1];
         if (DIM == 3) {
             const float lo = ym[t] + zm[t];
             const float hi = yp[t] + zp[t];
@@ -228,11 +229,11 @@ __global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T*
             out[t] = fmaf(c, sx + (ym[t] + yp[t]), qv[t]);
         }
     }
-    if (x0 >= 1 && x0 + 6 <= n - 1) {
-        st4(u + base, out);
+    if (x0 >= 1 && x0 + 2 * (V - 1) <= n - 1) {
+        stv(u + base, out);
     } else {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < V; ++t) {
             const int x = x0 + 2 * t;
             if (x >= 1 && x <= n - 1) u[base + t] = N::st(out[t]);
         }
@@ -562,7 +563,8 @@ void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s) {
     }
     if constexpr (!std::is_same<T, double>::value) {
         if (L.he) {
-            const int G = (n / 2 + 1 + 3) / 4;
+            constexpr int V = vec_of<T>();
+            const int G = (n / 2 + 1 + V - 1) / V;
             const int64_t items = (int64_t)G * (d == 3 ? (int64_t)(n - 1) * (n - 1) : n - 1);
             const unsigned blocks = (unsigned)((items + 255) / 256);
             if (d == 3)
