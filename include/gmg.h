@@ -84,10 +84,14 @@ gmg_status gmg_config_init(gmg_config* cfg, int d, int n);
  * cudaStream_t (NULL = legacy default stream) on which every later call on
  * the handle is ordered.  Allocates the level hierarchy on the device.
  * Environment: GMG_FUSED_RB=1 makes GMG_FP32_IR handles in 3D with red-black
- * smoothing run each sweep as one fused z-streaming kernel (same results
+ * smoothing run each sweep as one fused z-streaming kernel on a dense inner
+ * layout instead of two half sweeps on the colour-split one (same results
  * bit for bit; slower on GB300, see the design notes).  GMG_TAIL_N=m sets the
  * largest level n handled by the single-CTA tail launch (default 8 in 3D,
- * 32 in 2D; 1 turns the tail off); results are the same bit for bit. */
+ * 32 in 2D; 1 turns the tail off); results are the same bit for bit.
+ * GMG_RB_WALK=0 (read once per process) replaces the diagonal-walker FP64 3D
+ * half sweeps, red-only residuals and norms (levels 128 <= n <= 512) by row
+ * kernels; results are the same bit for bit. */
 gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out);
 
 /* GMGSolve (Algorithm 3, all levels on the device): starting from the initial
