@@ -25,6 +25,8 @@ _lib = None
 
 WJACOBI = 0
 RBGS = 1
+MCGS = 3          # the paper's 4-colour (2D) / 8-colour (3D) Gauss-Seidel
+FW, SIMPLEX = 0, 1  # transfer: full weighting + multilinear P, or the paper's R and P
 
 
 def build(force: bool = False) -> str:
@@ -41,7 +43,8 @@ def build(force: bool = False) -> str:
 class Cfg(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int), ("levels", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("omega", ctypes.c_double),
-                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarse_sweeps", ctypes.c_int)]
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarse_sweeps", ctypes.c_int),
+                ("transfer", ctypes.c_int)]
 
 
 def lib():
@@ -75,6 +78,9 @@ def lib():
                 ("orc_set_bf16_activations", [I], None),
                 ("orc_vcycle_learned", [ctypes.POINTER(Cfg), P, P, P], I),
                 ("orc_fmg", [ctypes.POINTER(Cfg), P, P], I),
+                ("orc_mcgs", [I, I, P, P, I, I], None),
+                ("orc_restrict_simplex", [I, I, P, P], None),
+                ("orc_prolong_diag", [I, I, P, P], None),
             ]:
                 fn = getattr(L, name)
                 fn.argtypes = args
@@ -100,9 +106,10 @@ def max_levels(n: int) -> int:
     return int(np.log2(n))
 
 
-def make_cfg(d, n, levels=0, smoother=RBGS, omega=0.8, nu1=2, nu2=2, coarse_sweeps=1) -> Cfg:
+def make_cfg(d, n, levels=0, smoother=RBGS, omega=0.8, nu1=2, nu2=2, coarse_sweeps=1,
+             transfer=FW) -> Cfg:
     return Cfg(d, n, levels if levels > 0 else max_levels(n), smoother, omega, nu1, nu2,
-               coarse_sweeps)
+               coarse_sweeps, transfer)
 
 
 def apply_stencil(u):
@@ -147,6 +154,26 @@ def restrict_fw(r):
 def prolong_add(uc, u):
     d, nc = _dn(uc)
     lib().orc_prolong_add(d, nc, _p(uc), _p(u))
+    return u
+
+
+def mcgs(b, u, sweeps, backward=False):
+    d, n = _dn(u)
+    lib().orc_mcgs(d, n, _p(b), _p(u), sweeps, 1 if backward else 0)
+    return u
+
+
+def restrict_simplex(r):
+    d, n = _dn(r)
+    nc = n // 2
+    bc = np.empty((nc + 1,) * d)
+    lib().orc_restrict_simplex(d, n, _p(r), _p(bc))
+    return bc
+
+
+def prolong_diag(uc, u):
+    d, nc = _dn(uc)
+    lib().orc_prolong_diag(d, nc, _p(uc), _p(u))
     return u
 
 

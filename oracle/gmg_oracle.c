@@ -220,6 +220,78 @@ void orc_prolong_add(int d, int nc, const double* uc, double* u)
             }
 }
 
+/* The paper's own smoother (Remark 1 of section 3.2): Gauss-Seidel in four
+ * colours (2D) or eight (3D), colour (i&1) + 2(j&1) + 4(k&1); each update
+ * solves its own equation, u_p = (b_p + sum of neighbours) / (2d) (eq.
+ * relax_2D).  Forward sweeps take the colours in increasing order, backward
+ * ones in decreasing order (Relax_forward / Relax_backward of Algorithm 1). */
+void orc_mcgs(int d, int n, const double* b, double* u, int sweeps, int backward)
+{
+    int ncol = d == 3 ? 8 : 4;
+    for (int s = 0; s < sweeps; ++s)
+        for (int t = 0; t < ncol; ++t) {
+            int color = backward ? ncol - 1 - t : t;
+#pragma omp parallel for schedule(static)
+            for (int k = kmin(d); k <= kmax(d, n); ++k)
+                for (int j = 1; j < n; ++j)
+                    for (int i = 1; i < n; ++i) {
+                        if ((i & 1) + 2 * (j & 1) + 4 * (k & 1) != color) continue;
+                        int64_t p = IDX(n, i, j, k);
+                        u[p] = (b[p] + nbr_sum(u, d, n, i, j, k)) / (2.0 * d);
+                    }
+        }
+}
+
+/* The paper's prolongation (eq. Prolongation2d and its 3D analogue, linear
+ * interpolation on the triangulation cut along the main diagonal): fine node
+ * 2I + delta, delta in {0,1}^d, gets uc(I) for delta = 0 and
+ * (uc(I) + uc(I + delta)) / 2 otherwise; u += that.  Coarse boundary nodes
+ * carry 0. */
+void orc_prolong_diag(int d, int nc, const double* uc, double* u)
+{
+    int n = 2 * nc;
+#pragma omp parallel for schedule(static)
+    for (int k = kmin(d); k <= kmax(d, n); ++k)
+        for (int j = 1; j < n; ++j)
+            for (int i = 1; i < n; ++i) {
+                int I = i / 2, J = j / 2, K = k / 2;
+                int a = i & 1, bb = j & 1, c = d == 3 ? (k & 1) : 0;
+                double e0 = val(uc, d, nc, I, J, d == 3 ? K : 0);
+                double s;
+                if (a == 0 && bb == 0 && c == 0)
+                    s = e0;
+                else
+                    s = 0.5 * (e0 + val(uc, d, nc, I + a, J + bb, d == 3 ? K + c : 0));
+                u[IDX(n, i, j, k)] = u[IDX(n, i, j, k)] + s;
+            }
+}
+
+/* The paper's restriction (eq. Restriction2d and its 3D analogue: 7 points
+ * in 2D, 15 in 3D), the transpose of the diagonal prolongation over 2^d:
+ * weight 1/2^d at 2I and 1/2^(d+1) at 2I +- delta for every delta in
+ * {0,1}^d other than 0; times the (h_c/h)^2 = 4 of the unscaled form. */
+void orc_restrict_simplex(int d, int n, const double* r, double* bc)
+{
+    int nc = n / 2;
+    memset(bc, 0, sizeof(double) * nodes(d, nc));
+    int dz = d == 3 ? 1 : 0;
+    double w0 = d == 3 ? 0.125 : 0.25;
+#pragma omp parallel for schedule(static)
+    for (int K = kmin(d); K <= kmax(d, nc); ++K)
+        for (int J = 1; J < nc; ++J)
+            for (int I = 1; I < nc; ++I) {
+                double s = w0 * val(r, d, n, 2 * I, 2 * J, 2 * K);
+                for (int c = 0; c <= dz; ++c)
+                    for (int b = 0; b <= 1; ++b)
+                        for (int a = 0; a <= 1; ++a) {
+                            if (a == 0 && b == 0 && c == 0) continue;
+                            s = s + 0.5 * w0 * val(r, d, n, 2 * I + a, 2 * J + b, 2 * K + c);
+                            s = s + 0.5 * w0 * val(r, d, n, 2 * I - a, 2 * J - b, 2 * K - c);
+                        }
+                bc[IDX(nc, I, J, K)] = 4.0 * s;
+            }
+}
+
 /* Coarsest-level solve.  With one unknown (n = 2) the single equation is
  * solved exactly, u = b / (2d) (Remark on the coarsest-level solver).  A
  * coarsest grid with more unknowns (a truncated hierarchy) is solved
@@ -237,24 +309,45 @@ void orc_coarse_solve(int d, int n, const double* b, double* u, int sweeps)
 
 /* ---------------------------------------------------------------- V-cycle */
 
-enum { ORC_WJACOBI = 0, ORC_RBGS = 1 };
+enum { ORC_WJACOBI = 0, ORC_RBGS = 1, ORC_MCGS = 3 };
 
 typedef struct {
     int d;             /* 2 or 3 */
     int n;             /* finest intervals per dimension, a power of two */
     int levels;        /* number of grids, finest = 0 .. coarsest = levels-1 */
-    int smoother;      /* ORC_WJACOBI or ORC_RBGS */
+    int smoother;      /* ORC_WJACOBI, ORC_RBGS or ORC_MCGS */
     double omega;      /* weighted-Jacobi weight */
     int nu1, nu2;      /* pre- and post-smoothing sweeps */
     int coarse_sweeps; /* red-black sweeps when the coarsest grid has > 1 unknown */
+    int transfer;      /* 0: full weighting + multilinear P; 1: the paper's R and P */
 } orc_cfg;
 
-static void relax(const orc_cfg* c, int n, const double* b, double* u, int sweeps)
+/* backward: post-smoothing (Relax_backward), which reverses the colour
+ * order of the multi-colour smoother */
+static void relax(const orc_cfg* c, int n, const double* b, double* u, int sweeps, int backward)
 {
     if (c->smoother == ORC_RBGS)
         orc_rbgs(c->d, n, b, u, sweeps);
+    else if (c->smoother == ORC_MCGS)
+        orc_mcgs(c->d, n, b, u, sweeps, backward);
     else
         orc_wjacobi(c->d, n, b, u, c->omega, sweeps);
+}
+
+static void restrict_(const orc_cfg* c, int n, const double* r, double* bc)
+{
+    if (c->transfer == 1)
+        orc_restrict_simplex(c->d, n, r, bc);
+    else
+        orc_restrict_fw(c->d, n, r, bc);
+}
+
+static void prolong_(const orc_cfg* c, int nc, const double* uc, double* u)
+{
+    if (c->transfer == 1)
+        orc_prolong_diag(c->d, nc, uc, u);
+    else
+        orc_prolong_add(c->d, nc, uc, u);
 }
 
 /* One V-cycle (Algorithm 1) on the right-hand side b0 = h^2 f of the finest
@@ -277,21 +370,21 @@ int orc_vcycle(const orc_cfg* c, const double* b0, double* u0)
     /* down: relax, residual, restrict (Algorithm 1, first loop) */
     for (int l = 0; l + 1 < L; ++l) {
         int nl = c->n >> l;
-        relax(c, nl, b[l], u[l], c->nu1);
+        relax(c, nl, b[l], u[l], c->nu1, 0);
         orc_residual(d, nl, b[l], u[l], r);
-        orc_restrict_fw(d, nl, r, b[l + 1]);
+        restrict_(c, nl, r, b[l + 1]);
         memset(u[l + 1], 0, sizeof(double) * nodes(d, nl / 2));
     }
     /* coarsest level */
     if (L == 1)
-        relax(c, c->n, b[0], u[0], c->nu1);
+        relax(c, c->n, b[0], u[0], c->nu1, 0);
     else
         orc_coarse_solve(d, c->n >> (L - 1), b[L - 1], u[L - 1], c->coarse_sweeps);
     /* up: prolongate-correct, relax (Algorithm 1, second loop, l = L-2..0) */
     for (int l = L - 2; l >= 0; --l) {
         int nl = c->n >> l;
-        orc_prolong_add(d, nl / 2, u[l + 1], u[l]);
-        relax(c, nl, b[l], u[l], c->nu2);
+        prolong_(c, nl / 2, u[l + 1], u[l]);
+        relax(c, nl, b[l], u[l], c->nu2, 1);
     }
     for (int l = 1; l < L; ++l) {
         free(b[l]);
@@ -677,7 +770,7 @@ int orc_fmg(const orc_cfg* c, const double* b0, double* u0)
         b[l] = (double*)calloc(nodes(d, c->n >> l), sizeof(double));
         u[l] = (double*)calloc(nodes(d, c->n >> l), sizeof(double));
     }
-    for (int l = 0; l + 1 < L; ++l) orc_restrict_fw(d, c->n >> l, b[l], b[l + 1]);
+    for (int l = 0; l + 1 < L; ++l) restrict_(c, c->n >> l, b[l], b[l + 1]);
     if (L == 1) {
         memset(u0, 0, sizeof(double) * nodes(d, c->n));
         orc_vcycle(c, b0, u0);
@@ -686,7 +779,7 @@ int orc_fmg(const orc_cfg* c, const double* b0, double* u0)
         for (int l = L - 2; l >= 0; --l) {
             int nl = c->n >> l;
             memset(u[l], 0, sizeof(double) * nodes(d, nl));
-            orc_prolong_add(d, nl / 2, u[l + 1], u[l]);
+            prolong_(c, nl / 2, u[l + 1], u[l]);
             orc_cfg cl = *c;
             cl.n = nl;
             cl.levels = L - l;

@@ -156,3 +156,90 @@ def fmg_matrix(d, n, levels, smoother=1, omega=0.8, nu1=2, nu2=2, coarse_sweeps=
     E = vcycle_error_matrix(d, n, levels, smoother, omega, nu1, nu2, coarse_sweeps)
     I = np.eye(A.shape[0])
     return E @ prolong(d, nc) @ Mc @ restrict(d, n) + (I - E) @ np.linalg.inv(A)
+
+
+def colour_index(d: int, n: int) -> np.ndarray:
+    """The paper's multi-colour index (i mod 2) + 2 (j mod 2) (+ 4 (k mod 2)) of
+    the interior nodes, x-fastest order."""
+    r = np.arange(1, n)
+    grids = np.meshgrid(*([r] * d), indexing="ij")  # slowest axis first
+    c = np.zeros_like(grids[0])
+    for ax, g in enumerate(reversed(grids)):  # x first
+        c = c + (2 ** ax) * (g % 2)
+    return c.reshape(-1)
+
+
+def mcgs_sweep(d: int, n: int, b: np.ndarray, u: np.ndarray, backward: bool) -> np.ndarray:
+    """One multi-colour Gauss-Seidel sweep as a lower-triangular solve in the
+    colour ordering (colours ascending; descending for backward)."""
+    A = lap(d, n)
+    c = colour_index(d, n)
+    cols = range(2 ** d)
+    if backward:
+        cols = reversed(list(cols))
+    perm = np.concatenate([np.where(c == k)[0] for k in cols])
+    Ap = A[np.ix_(perm, perm)]
+    M = np.tril(Ap)
+    rhs = b[perm] - (Ap - M) @ u[perm]
+    up = sla.solve_triangular(M, rhs, lower=True)
+    out = np.empty_like(u)
+    out[perm] = up
+    return out
+
+
+def prolong_diag(d: int, nc: int) -> np.ndarray:
+    """Linear interpolation on the triangulation cut along the main diagonal:
+    fine 2I + delta takes coarse I (delta = 0) or the mean of coarse I and
+    I + delta; coarse boundary values are 0.  Coarse interior -> fine interior."""
+    n = 2 * nc
+    m, mc = n - 1, nc - 1
+    P = np.zeros((m ** d, mc ** d))
+
+    def cidx(c):
+        if any(v < 1 or v > nc - 1 for v in c):
+            return None
+        return sum((c[a] - 1) * mc ** a for a in range(d))  # x fastest
+
+    for f in np.ndindex(*([m] * d)):
+        fi = [v + 1 for v in reversed(f)]  # (x, y, z)
+        row = sum((fi[a] - 1) * m ** a for a in range(d))
+        base = [v // 2 for v in fi]
+        delta = [v % 2 for v in fi]
+        if not any(delta):
+            k = cidx(base)
+            if k is not None:
+                P[row, k] += 1.0
+        else:
+            for c in (base, [base[a] + delta[a] for a in range(d)]):
+                k = cidx(c)
+                if k is not None:
+                    P[row, k] += 0.5
+    return P
+
+
+def restrict_simplex(d: int, n: int) -> np.ndarray:
+    """The paper's restriction stencil times 4: weight 1/2^d at 2I and
+    1/2^(d+1) at 2I +- delta for the 2^d - 1 nonzero delta in {0,1}^d
+    (eq. Restriction2d: (2, 1, 1, 1, 1, 1, 1)/8 in 2D)."""
+    nc = n // 2
+    m, mc = n - 1, nc - 1
+    R = np.zeros((mc ** d, m ** d))
+    w0 = 1.0 / 2 ** d
+
+    def fidx(f):
+        if any(v < 1 or v > n - 1 for v in f):
+            return None
+        return sum((f[a] - 1) * m ** a for a in range(d))
+
+    deltas = [dl for dl in np.ndindex(*([2] * d)) if any(dl)]
+    for c in np.ndindex(*([mc] * d)):
+        ci = [v + 1 for v in reversed(c)]
+        row = sum((ci[a] - 1) * mc ** a for a in range(d))
+        centre = [2 * v for v in ci]
+        R[row, fidx(centre)] += 4.0 * w0
+        for dl in deltas:
+            for sgn in (1, -1):
+                k = fidx([centre[a] + sgn * dl[a] for a in range(d)])
+                if k is not None:
+                    R[row, k] += 4.0 * 0.5 * w0
+    return R

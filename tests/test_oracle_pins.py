@@ -435,3 +435,131 @@ def test_fmg_reaches_discretisation_error(d, n, nu, ok):
     oracle.fmg(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, nu[0], nu[1], 1), b, u)
     ratio = np.sqrt((1.0 / n) ** d * np.sum((u - ue) ** 2)) / _closed_form_error(d, n)
     assert (ratio <= 1.2) == ok, ratio
+
+
+# ------------------------------------------------ the paper's own variant
+# Four-/eight-colour Gauss-Seidel (Remark 1 of section 3.2, reversed colour
+# order in the backward sweeps), the 7-/15-point restriction of eq.
+# Restriction2d and the diagonal-linear prolongation of eq. Prolongation2d.
+
+@pytest.mark.parametrize("d,n", [(2, 8), (2, 16), (3, 8)])
+@pytest.mark.parametrize("backward", [False, True])
+def test_mcgs_is_colour_ordered_triangular_solve(d, n, backward):
+    """One multi-colour sweep equals the Gauss-Seidel triangular solve with
+    the nodes ordered by colour (ascending forward, descending backward)."""
+    rng = np.random.default_rng(2)
+    b = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)
+    u = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)
+    ref = dm.mcgs_sweep(d, n, dm.to_vec(b), dm.to_vec(u), backward)
+    oracle.mcgs(b, u, 1, backward)
+    assert np.max(np.abs(dm.to_vec(u) - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("d,n", [(2, 8), (2, 16), (3, 8)])
+def test_paper_transfer_operators_match_equations(d, n):
+    """The restriction equals the stencil of eq. Restriction2d (and its 15-point
+    3D analogue) times 4, the prolongation the diagonal rule of eq.
+    Prolongation2d, and 4 R = 4 P^T / 2^d holds."""
+    nc = n // 2
+    R = _op_matrix(oracle.restrict_simplex, d, n, nc)
+    P = _op_matrix(lambda uc: oracle.prolong_diag(uc, np.zeros((n + 1,) * d)), d, nc, n)
+    np.testing.assert_allclose(R, dm.restrict_simplex(d, n), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(P, dm.prolong_diag(d, nc), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(R, 4.0 * P.T / 2 ** d, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_diagonal_prolongation_exact_on_linear(d):
+    """Interpolation along the cut diagonals reproduces every linear function
+    wherever its parent coarse nodes are interior (and, unlike the
+    multilinear rule, not the bilinear product x*y)."""
+    nc = 8
+    n = 2 * nc
+    xc = np.arange(nc + 1) / nc
+    xf = np.arange(n + 1) / n
+
+    def grid(x, g):
+        axes = np.meshgrid(*([x] * d), indexing="ij")  # slowest first
+        return np.ascontiguousarray(g(*reversed(axes)))
+
+    lin = lambda x, y, z=0.0: 1.0 + 2.0 * x - y + 0.5 * z
+    out = oracle.prolong_diag(grid(xc, lin), np.zeros((n + 1,) * d))
+    sl = (slice(2, n - 1),) * d
+    np.testing.assert_allclose(out[sl], grid(xf, lin)[sl], rtol=1e-14, atol=1e-14)
+    bil = lambda x, y, z=0.0: x * y
+    out = oracle.prolong_diag(grid(xc, bil), np.zeros((n + 1,) * d))
+    assert np.max(np.abs(out[sl] - grid(xf, bil)[sl])) > 1e-3
+
+
+def _smoother_table():
+    rows = {}
+    with open(os.path.join(GOLDEN, "paper_smoother_table.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                L, wj667, wj8, gs2, gs4 = (int(v) for v in line.split())
+                rows[L] = {"wj667": wj667, "wj8": wj8, "gs2": gs2, "gs4": gs4}
+    return rows
+
+
+def _rb_sweep_order(b, u, order):
+    """Two-colour Gauss-Seidel in the given colour order (numpy, 2D)."""
+    n = u.shape[0] - 1
+    J, I = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    inner = np.zeros_like(u, dtype=bool)
+    inner[1:-1, 1:-1] = True
+    for col in order:
+        m = inner & ((I + J) % 2 == col)
+        s = np.zeros_like(u)
+        s[1:-1, 1:-1] = u[:-2, 1:-1] + u[2:, 1:-1] + u[1:-1, :-2] + u[1:-1, 2:]
+        u[m] = (b[m] + s[m]) / 4.0
+
+
+def _vcycle_rb_reversed(b, u):
+    """V(1,1) with the paper's R and P and two colours, red-black forward and
+    black-red backward (the Relax_forward / Relax_backward pair)."""
+    n = u.shape[0] - 1
+    if n == 2:
+        u[1, 1] = b[1, 1] / 4.0
+        return
+    _rb_sweep_order(b, u, (0, 1))
+    bc = oracle.restrict_simplex(oracle.residual(b, u))
+    uc = np.zeros_like(bc)
+    _vcycle_rb_reversed(bc, uc)
+    oracle.prolong_diag(uc, u)
+    _rb_sweep_order(b, u, (1, 0))
+
+
+@pytest.mark.parametrize("L", [8, 9])
+def test_paper_variant_reproduces_smoother_table(L):
+    """The paper's smoother comparison (golden table): with its R and P,
+    V(1,1) and f = sin(pi x) sin(pi y), the iterations to 1e-6 are 11 for
+    four-colour GS, 16 for two-colour GS with the colour order reversed in
+    the backward sweep, 18 for weighted Jacobi 0.8 -- all as printed -- and
+    21 for weighted Jacobi 2/3 against the printed 22 (the one count that
+    differs, by one cycle).  The same V(1,1) with the colour order kept in
+    both sweeps takes 8 cycles: the table pins the reversed reading."""
+    n = 2 ** L
+    ref = _smoother_table()[L]
+    x = np.arange(n + 1) / n
+    s = np.sin(np.pi * x)
+    s[0] = s[-1] = 0.0
+    f = np.ascontiguousarray(s[:, None] * s[None, :])
+
+    def count(sm, om):
+        u = np.zeros_like(f)
+        it, _ = oracle.solve(oracle.make_cfg(2, n, 0, sm, om, 1, 1, 1, transfer=oracle.SIMPLEX),
+                             f, u, rtol=1e-6, maxit=60)
+        return it
+
+    assert count(oracle.MCGS, 0.8) == ref["gs4"]
+    assert count(oracle.WJACOBI, 0.8) == ref["wj8"]
+    assert abs(count(oracle.WJACOBI, 2.0 / 3.0) - ref["wj667"]) <= 1
+    b = oracle.scale_rhs(f)
+    r0 = oracle.norm2(b)
+    u = np.zeros_like(f)
+    it = 0
+    while oracle.norm2(oracle.residual(b, u)) > 1e-6 * r0 and it < 60:
+        _vcycle_rb_reversed(b, u)
+        it += 1
+    assert it == ref["gs2"]
+    assert count(oracle.RBGS, 0.8) == 8
