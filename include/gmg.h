@@ -48,7 +48,17 @@ typedef enum {
     GMG_ERR_UNSUPPORTED = 8     /* configuration not built in this library */
 } gmg_status;
 
-typedef enum { GMG_WJACOBI = 0, GMG_RBGS = 1, GMG_LEARNED = 2 } gmg_smoother;
+/* GMG_MCGS: the paper's own smoother (Remark 1 of section 3.2): Gauss-Seidel
+ * in four colours (2D) or eight (3D), colour (i&1) + 2(j&1) + 4(k&1), in
+ * increasing colour order in pre-smoothing and decreasing order in
+ * post-smoothing (Relax_forward / Relax_backward of Algorithm 1). */
+typedef enum { GMG_WJACOBI = 0, GMG_RBGS = 1, GMG_LEARNED = 2, GMG_MCGS = 3 } gmg_smoother;
+/* Grid transfers: full weighting + (bi/tri)linear interpolation, or the
+ * paper's own pair -- the 7-point (2D) / 15-point (3D) restriction of eq.
+ * Restriction2d (weight 1/2^d at 2I, 1/2^(d+1) at 2I +- delta, delta in
+ * {0,1}^d nonzero) and the diagonal-linear prolongation of eq.
+ * Prolongation2d (fine 2I + delta takes (e_I + e_{I+delta})/2). */
+typedef enum { GMG_TRANSFER_FW = 0, GMG_TRANSFER_PAPER = 1 } gmg_transfer;
 typedef enum { GMG_FP64 = 0, GMG_FP32_IR = 1, GMG_BF16_IR = 2 } gmg_precision;
 typedef enum { GMG_VCYCLE = 0, GMG_FMG = 1 } gmg_cycle;
 
@@ -72,12 +82,15 @@ typedef struct {
     int inner_cycles;  /* FP32 / BF16 forms: V-cycles per outer refinement step */
     int coarse_sweeps; /* red-black sweeps from zero on a coarsest grid with more than
                           one unknown (truncated hierarchy); unused otherwise */
+    int transfer;      /* gmg_transfer.  GMG_MCGS and GMG_TRANSFER_PAPER run in the plain
+                          FP64 form (V-cycles or FMG), every level on grid kernels */
 } gmg_config;
 
 typedef struct gmg_handle_s* gmg_handle;
 
 /* Fill *cfg with defaults for d, n: all levels, red-black GS, omega = 4/5,
- * V(2,2), plain FP64, maxit 100, 4 inner cycles, 64 coarse sweeps. */
+ * V(2,2), plain FP64, maxit 100, 4 inner cycles, 64 coarse sweeps, full-weighting
+ * transfers. */
 gmg_status gmg_config_init(gmg_config* cfg, int d, int n);
 
 /* Create a solver for *cfg on the current CUDA device.  cuda_stream is a

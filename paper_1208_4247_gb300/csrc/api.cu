@@ -96,9 +96,19 @@ gmg_status check_cfg(const gmg_config* c) {
         set_error("levels must be 0 (all) or 1.." + std::to_string(lmax));
         return GMG_ERR_ARG;
     }
-    if (c->smoother != GMG_WJACOBI && c->smoother != GMG_RBGS && c->smoother != GMG_LEARNED) {
+    if (c->smoother != GMG_WJACOBI && c->smoother != GMG_RBGS && c->smoother != GMG_LEARNED &&
+        c->smoother != GMG_MCGS) {
         set_error("unknown smoother");
         return GMG_ERR_ARG;
+    }
+    if (c->transfer != GMG_TRANSFER_FW && c->transfer != GMG_TRANSFER_PAPER) {
+        set_error("unknown transfer");
+        return GMG_ERR_ARG;
+    }
+    if ((c->smoother == GMG_MCGS || c->transfer == GMG_TRANSFER_PAPER) &&
+        (c->precision != GMG_FP64 || c->smoother == GMG_LEARNED)) {
+        set_error("the paper's smoother and transfers run in the plain FP64 form");
+        return GMG_ERR_UNSUPPORTED;
     }
     if (c->smoother == GMG_LEARNED && c->precision != GMG_FP64) {
         set_error("the learned smoother runs in the plain FP64 form only");
@@ -179,12 +189,14 @@ int num_levels(const gmg_config& c) { return c.levels > 0 ? c.levels : ilog2(c.n
 
 enum Kind {
     K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_OUTER_RES,
-    K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_TAIL, K_RB_FUSED, K_COUNT
+    K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_TAIL, K_RB_FUSED, K_MC_SWEEP, K_RESTRICT_PAPER,
+    K_PROLONG_PAPER, K_COUNT
 };
 const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restrict",
                                   "prolong_add", "resnorm",  "copy",     "outer_residual",
                                   "update",      "memset",   "conv1",    "conv_tc_update", "tail",
-                                  "rb_sweep_fused"};
+                                  "rb_sweep_fused", "mc_sweep", "restrict_paper",
+                                  "prolong_paper"};
 const char* kPrecSuffix[3] = {"", "_f32", "_bf16"};
 
 template <typename T>
@@ -231,6 +243,10 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
         case K_CONV2: return {N * 16 * (t ? 27 : 9), N * 3 * w};  // both convs, u read+write
         case K_TAIL: return {N * (t ? 40 : 30) * 8.0 / 7.0, N * 2 * w};
         case K_RB_FUSED: return {N * (t ? 6 : 4), N * 3 * w};  // read u, q; write u
+        case K_MC_SWEEP:  // one of 2^d colours: the colour's nodes updated
+            return {N / (t ? 8 : 4) * (t ? 6 : 4), N / (t ? 8 : 4) * (t ? 8 : 6) * w};
+        case K_RESTRICT_PAPER: return {Nc * (t ? 16 : 8), N * w + Nc * 2 * w};
+        case K_PROLONG_PAPER: return {cells * (t ? 14 : 6), Nc * w + N * 2 * w};
     }
     return {0.0, 0.0};
 }
@@ -286,13 +302,26 @@ bool sigma_carried(gmg_handle h) {
     return h->cfg.precision == GMG_FP64 && learned_level(h, 0) && h->cfg.nu1 > 0;
 }
 
+// backward: post-smoothing (Relax_backward), which takes the colours of the
+// multi-colour smoother in decreasing order.
 template <typename T>
 void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
-           bool sigma_ready = false) {
+           bool sigma_ready = false, bool backward = false) {
     Level<T>& L = lv[l];
     const int d = h->cfg.d;
     const int p = prec_of<T>();
     for (int s = 0; s < sweeps; ++s) {
+        if constexpr (std::is_same<T, double>::value) {
+            if (h->cfg.smoother == GMG_MCGS) {
+                const int ncol = d == 3 ? 8 : 4;
+                for (int t = 0; t < ncol; ++t) {
+                    const int color = backward ? ncol - 1 - t : t;
+                    timed(h, K_MC_SWEEP, l, p, L.n, false,
+                          [&] { lk::mc_sweep<T>(d, L.lay, L.u[cur], L.q, color, h->stream); });
+                }
+                continue;
+            }
+        }
         if constexpr (std::is_same<T, double>::value) {
             if (learned_level(h, l)) {
                 learned_sweep(h, L, l, sigma_ready && s == 0);
@@ -328,6 +357,7 @@ template <typename T>
 int tail_level(gmg_handle h, const std::vector<Level<T>>& lv) {
     const gmg_config& c = h->cfg;
     const int L = (int)lv.size();
+    if (c.smoother == GMG_MCGS || c.transfer == GMG_TRANSFER_PAPER) return L;  // grid kernels
     const int nmax = h->tail_max > 0 ? h->tail_max : c.d == 3 ? 8 : 32;
     int lo = 0;
     if (c.smoother == GMG_LEARNED)
@@ -369,16 +399,29 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
             Level<T>& F = lv[l];
             Level<T>& C = lv[l + 1];
             // After a black half sweep the black residual vanishes identically.
+            const bool paper = c.transfer == GMG_TRANSFER_PAPER;
             const bool rb = c.smoother == GMG_RBGS ||
                             (c.smoother == GMG_LEARNED && !learned_level(h, l));
-            const bool red_only = rb && c.nu1 > 0;
+            const bool red_only = rb && c.nu1 > 0 && !paper;
             timed(h, K_RESIDUAL, l, p, F.n, red_only, [&] {
                 lk::residual<T>(d, F.lay, F.u[cur[l]], F.q, F.r, red_only, h->stream);
             });
             const bool exact = C.n == 2;
-            timed(h, K_RESTRICT, l, p, F.n, red_only, [&] {
-                lk::restrict_fw<T>(d, F.lay, C.lay, F.r, C.q, C.u[0], red_only, exact, h->stream);
-            });
+            bool done = false;
+            if constexpr (std::is_same<T, double>::value) {
+                if (paper) {
+                    timed(h, K_RESTRICT_PAPER, l, p, F.n, false, [&] {
+                        lk::restrict_paper<T>(d, F.lay, C.lay, F.r, C.q, C.u[0], exact,
+                                              h->stream);
+                    });
+                    done = true;
+                }
+            }
+            if (!done)
+                timed(h, K_RESTRICT, l, p, F.n, red_only, [&] {
+                    lk::restrict_fw<T>(d, F.lay, C.lay, F.r, C.q, C.u[0], red_only, exact,
+                                       h->stream);
+                });
             cur[l + 1] = 0;
         }
         if (lt < L) {
@@ -400,12 +443,24 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
         for (int l = Ldown - 1; l >= 0; --l) {
             Level<T>& F = lv[l];
             Level<T>& C = lv[l + 1];
-            const bool black = red_sweep_next<T>(h, c.nu2);
-            timed(h, K_PROLONG, l, p, F.n, black, [&] {
-                lk::prolong_add<T>(d, C.lay, F.lay, C.u[cur[l + 1]], F.u[cur[l]], h->stream,
-                                   black);
-            });
-            relax(h, lv, l, c.nu2, cur[l]);
+            bool done = false;
+            if constexpr (std::is_same<T, double>::value) {
+                if (c.transfer == GMG_TRANSFER_PAPER) {
+                    timed(h, K_PROLONG_PAPER, l, p, F.n, false, [&] {
+                        lk::prolong_paper<T>(d, C.lay, F.lay, C.u[cur[l + 1]], F.u[cur[l]],
+                                             h->stream);
+                    });
+                    done = true;
+                }
+            }
+            if (!done) {
+                const bool black = red_sweep_next<T>(h, c.nu2);
+                timed(h, K_PROLONG, l, p, F.n, black, [&] {
+                    lk::prolong_add<T>(d, C.lay, F.lay, C.u[cur[l + 1]], F.u[cur[l]], h->stream,
+                                       black);
+                });
+            }
+            relax(h, lv, l, c.nu2, cur[l], false, true);
         }
     }
     if (cur[0] != 0) {
@@ -494,9 +549,15 @@ gmg_status enqueue_fmg(gmg_handle h) {
     for (int l = 0; l + 1 < L; ++l) {
         Level<double>& F = lv[l];
         Level<double>& C = lv[l + 1];
-        timed(h, K_RESTRICT, l, 0, F.n, false, [&] {
-            lk::restrict_fw<double>(d, F.n, F.q, C.q, C.u[0], false, C.n == 2, h->stream);
-        });
+        if (c.transfer == GMG_TRANSFER_PAPER)
+            timed(h, K_RESTRICT_PAPER, l, 0, F.n, false, [&] {
+                lk::restrict_paper<double>(d, F.lay, C.lay, F.q, C.q, C.u[0], C.n == 2,
+                                           h->stream);
+            });
+        else
+            timed(h, K_RESTRICT, l, 0, F.n, false, [&] {
+                lk::restrict_fw<double>(d, F.n, F.q, C.q, C.u[0], false, C.n == 2, h->stream);
+            });
     }
     if (L > 1 && lv[L - 1].n > 2) {
         Level<double>& B = lv[L - 1];
@@ -508,10 +569,18 @@ gmg_status enqueue_fmg(gmg_handle h) {
     cudaError_t e = cudaMemsetAsync(lv[0].u[0], 0, sizeof(double) * lv[0].nodes, h->stream);
     GMG_CUDA_TRY(e);
     for (int l = L - 2; l >= 0; --l) {
-        const bool black = red_sweep_next<double>(h, c.nu1);
-        timed(h, K_PROLONG, l, 0, lv[l].n, black, [&] {
-            lk::prolong_add<double>(d, lv[l + 1].n, lv[l + 1].u[0], lv[l].u[0], h->stream, black);
-        });
+        if (c.transfer == GMG_TRANSFER_PAPER) {
+            timed(h, K_PROLONG_PAPER, l, 0, lv[l].n, false, [&] {
+                lk::prolong_paper<double>(d, lv[l + 1].lay, lv[l].lay, lv[l + 1].u[0],
+                                          lv[l].u[0], h->stream);
+            });
+        } else {
+            const bool black = red_sweep_next<double>(h, c.nu1);
+            timed(h, K_PROLONG, l, 0, lv[l].n, black, [&] {
+                lk::prolong_add<double>(d, lv[l + 1].n, lv[l + 1].u[0], lv[l].u[0], h->stream,
+                                        black);
+            });
+        }
         std::vector<Level<double>> sub(lv.begin() + l, lv.end());
         gmg_status st = enqueue_vcycle<double>(h, sub);
         if (st != GMG_OK) return st;
@@ -727,6 +796,7 @@ gmg_status gmg_config_init(gmg_config* cfg, int d, int n) {
     cfg->maxit = 100;
     cfg->inner_cycles = 4;
     cfg->coarse_sweeps = 64;
+    cfg->transfer = GMG_TRANSFER_FW;
     return GMG_OK;
 }
 

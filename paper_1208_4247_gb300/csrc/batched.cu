@@ -590,6 +590,10 @@ gmg_status gmg_batch_create(int count, const int* d, const int* n, const gmg_con
         set_error("gmg_batch_create: smoother must be weighted Jacobi or red-black GS");
         return GMG_ERR_ARG;
     }
+    if (common->transfer != GMG_TRANSFER_FW) {
+        set_error("gmg_batch_create: the batch uses full-weighting transfers");
+        return GMG_ERR_UNSUPPORTED;
+    }
     if (common->smoother == GMG_WJACOBI && ((common->nu1 + common->nu2) % 2 != 0)) {
         set_error("gmg_batch_create: weighted Jacobi needs nu1 + nu2 even");
         return GMG_ERR_UNSUPPORTED;

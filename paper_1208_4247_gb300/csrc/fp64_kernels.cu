@@ -25,6 +25,11 @@ template void restrict_fw<double>(int, const Lay&, const Lay&, const double*, do
                                   bool, bool, cudaStream_t);
 template void prolong_add<double>(int, const Lay&, const Lay&, const double*, double*,
                                   cudaStream_t, bool);
+template void mc_sweep<double>(int, const Lay&, double*, const double*, int, cudaStream_t);
+template void restrict_paper<double>(int, const Lay&, const Lay&, const double*, double*,
+                                     double*, bool, cudaStream_t);
+template void prolong_paper<double>(int, const Lay&, const Lay&, const double*, double*,
+                                    cudaStream_t);
 }  // namespace lk
 
 namespace fp64 {

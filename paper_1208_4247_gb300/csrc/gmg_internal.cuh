@@ -93,6 +93,16 @@ template <typename T>
 void prolong_add(int d, const Lay& C, const Lay& F, const T* uc, T* u, cudaStream_t s,
                  bool black_only = false);
 
+// The paper's own variant on dense FP64 levels: one colour of the 4/8-colour
+// Gauss-Seidel, the 7/15-point restriction, the diagonal prolongation.
+template <typename T>
+void mc_sweep(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s);
+template <typename T>
+void restrict_paper(int d, const Lay& F, const Lay& C, const T* r, T* qc, T* uc,
+                    bool exact_coarsest, cudaStream_t s);
+template <typename T>
+void prolong_paper(int d, const Lay& C, const Lay& F, const T* uc, T* u, cudaStream_t s);
+
 // The same on dense levels given by n.
 template <typename T>
 inline void rb_half(int d, int n, T* u, const T* q, int color, cudaStream_t s) {

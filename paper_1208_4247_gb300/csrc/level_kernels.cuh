@@ -548,6 +548,97 @@ __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, T
     }
 }
 
+// ------------------------------------------- the paper's own variant
+// (dense levels).  Multi-colour Gauss-Seidel: the nodes of colour
+// (i&1) + 2(j&1) + 4(k&1) = color, one thread per node of the colour's rows.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_mc_sweep(T* __restrict__ u, const T* __restrict__ q,
+                                                  Lay L, int color) {
+    using N = Num<T>;
+    using C = typename N::C;
+    const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
+    const int n = L.n;
+    const int cx = color & 1, cy = (color >> 1) & 1, cz = (color >> 2) & 1;
+    // rows j = jb, jb+2, ... with j = cy (mod 2), j >= 1; planes likewise
+    const int j = (cy ? 1 : 2) + 2 * (int)(blockIdx.x * blockDim.y + threadIdx.y);
+    const int k = DIM == 3 ? (cz ? 1 : 2) + 2 * (int)blockIdx.y : 0;
+    if (j >= n || (DIM == 3 && k >= n)) return;
+    const int64_t row = k * L.sz + j * L.sy;
+    for (int i = (cx ? 1 : 2) + 2 * threadIdx.x; i < n; i += 2 * blockDim.x) {
+        const int64_t p = row + i;
+        u[p] = N::st(fma(c, nbr_sum<DIM>(u, p, L.sy, L.sz), N::ld(q[p])));
+    }
+}
+
+// The paper's restriction (eq. Restriction2d, 15-point analogue in 3D),
+// q_c = 4 R(sigma) with weight 1/2^d at the centre 2I and 1/2^(d+1) at
+// 2I +- delta, delta in {0,1}^d nonzero: the transpose of the diagonal
+// prolongation over 2^d.  u_c = 0, or u_c = q_c on the one-unknown grid.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_restrict_paper(const T* __restrict__ r,
+                                                        T* __restrict__ qc, T* __restrict__ uc,
+                                                        Lay F, Lay Cl, int exact) {
+    using N = Num<T>;
+    using C = typename N::C;
+    const int nc = Cl.n;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y + 1;
+    const int K = DIM == 3 ? blockIdx.z + 1 : 0;
+    if (I >= nc || J >= nc) return;
+    const int64_t sy = F.sy, sz = F.sz;
+    const int64_t p = (2 * K) * sz + (2 * J) * sy + 2 * I;
+    auto R = [&](int64_t o) { return N::ld(r[p + o]); };
+    // pair sums over +-delta, delta = x, y, xy (2D) and z, xz, yz, xyz (3D)
+    C s = (R(-1) + R(1)) + (R(-sy) + R(sy));
+    s += R(-1 - sy) + R(1 + sy);
+    C v;
+    if (DIM == 3) {
+        C t = (R(-sz) + R(sz)) + (R(-1 - sz) + R(1 + sz));
+        t += (R(-sy - sz) + R(sy + sz)) + (R(-1 - sy - sz) + R(1 + sy + sz));
+        v = fma(C(0.25), s + t, C(0.5) * R(0));  // 4 x (1/16, 1/8)
+    } else {
+        v = fma(C(0.5), s, R(0));  // 4 x (1/8, 1/4)
+    }
+    const int64_t P = (int64_t)K * Cl.sz + (int64_t)J * Cl.sy + I;
+    qc[P] = N::st(v);
+    uc[P] = exact ? N::st(v) : N::st(C(0));
+}
+
+// The paper's prolongation (eq. Prolongation2d, 3D analogue), u += P u_c:
+// one thread per coarse cell (I,J,K) in [0, nc-1]^d; fine node 2I + delta
+// gets u_c(I) (delta = 0) or (u_c(I) + u_c(I + delta)) / 2.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256) k_prolong_paper(const T* __restrict__ uc,
+                                                       T* __restrict__ u, Lay Cl, Lay F) {
+    using N = Num<T>;
+    using C = typename N::C;
+    const int nc = Cl.n;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = DIM == 3 ? blockIdx.z : 0;
+    if (I >= nc || J >= nc) return;
+    const int64_t sy = F.sy, sz = F.sz, cy = Cl.sy, cz = Cl.sz;
+    const int64_t P = K * cz + J * cy + I;
+    const int64_t p = (2 * K) * sz + (2 * J) * sy + 2 * I;
+    const C c0 = N::ld(uc[P]);
+    auto add = [&](int64_t o, int64_t co) {
+        u[p + o] = N::st(fma(C(0.5), c0 + N::ld(uc[P + co]), N::ld(u[p + o])));
+    };
+    const int kz = DIM == 3 ? 2 : 1;
+    for (int dz = 0; dz < kz; ++dz) {
+        if (DIM == 3 && dz == 0 && K == 0) continue;  // plane 2K = 0 is boundary
+        const int64_t oz = dz * sz, coz = dz * cz;
+        if (dz == 0) {
+            if (I > 0 && J > 0) u[p] = N::st(N::ld(u[p]) + c0);
+        } else if (I > 0 && J > 0) {
+            add(oz, coz);
+        }
+        if (J > 0) add(oz + 1, coz + 1);
+        if (I > 0) add(oz + sy, coz + cy);
+        add(oz + 1 + sy, coz + 1 + cy);
+    }
+}
+
 // ------------------------------------------------------------- launchers
 
 // FP64 3D dense levels with 128 <= n <= 512 use the diagonal walkers (one red
@@ -696,6 +787,50 @@ void prolong_add(int d, const Lay& C, const Lay& F, const T* uc, T* u, cudaStrea
         else
             prolong_grid<2, false>(C, F, uc, u, black_only, grid, block, s);
     }
+}
+
+template <typename T>
+void mc_sweep(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s) {
+    const int n = L.n;
+    int bx = 32;
+    while (bx < n / 2 && bx < 128) bx *= 2;
+    const int by = 256 / bx;
+    const int rows = n / 2;  // rows of one parity in 1..n-1 (at most n/2)
+    dim3 grid((unsigned)((rows + by - 1) / by), d == 3 ? (unsigned)(n / 2) : 1u, 1);
+    if (d == 3)
+        k_mc_sweep<3, T><<<grid, dim3(bx, by, 1), 0, s>>>(u, q, L, color);
+    else
+        k_mc_sweep<2, T><<<grid, dim3(bx, by, 1), 0, s>>>(u, q, L, color);
+}
+
+template <typename T>
+void restrict_paper(int d, const Lay& F, const Lay& C, const T* r, T* qc, T* uc,
+                    bool exact_coarsest, cudaStream_t s) {
+    const int nc = C.n;
+    int bx = 32;
+    while (bx < nc - 1 && bx < 128) bx *= 2;
+    const int by = 256 / bx;
+    dim3 block(bx, by, 1);
+    dim3 grid((nc - 1 + bx - 1) / bx, (nc - 1 + by - 1) / by, d == 3 ? nc - 1 : 1);
+    const int ex = exact_coarsest ? 1 : 0;
+    if (d == 3)
+        k_restrict_paper<3, T><<<grid, block, 0, s>>>(r, qc, uc, F, C, ex);
+    else
+        k_restrict_paper<2, T><<<grid, block, 0, s>>>(r, qc, uc, F, C, ex);
+}
+
+template <typename T>
+void prolong_paper(int d, const Lay& C, const Lay& F, const T* uc, T* u, cudaStream_t s) {
+    const int nc = C.n;
+    int bx = 32;
+    while (bx < nc && bx < 128) bx *= 2;
+    const int by = 256 / bx;
+    dim3 block(bx, by, 1);
+    dim3 grid((nc + bx - 1) / bx, (nc + by - 1) / by, d == 3 ? nc : 1);
+    if (d == 3)
+        k_prolong_paper<3, T><<<grid, block, 0, s>>>(uc, u, C, F);
+    else
+        k_prolong_paper<2, T><<<grid, block, 0, s>>>(uc, u, C, F);
 }
 
 }  // namespace lk

@@ -20,7 +20,8 @@ ERR_NOT_CONVERGED = 6
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_LAYOUT", 3: "ERR_ALLOC", 4: "ERR_CUDA",
           5: "ERR_NONFINITE", 6: "ERR_NOT_CONVERGED", 7: "ERR_DEVICE_TIMEOUT",
           8: "ERR_UNSUPPORTED"}
-SMOOTHERS = {"wjacobi": 0, "rbgs": 1, "learned": 2}
+SMOOTHERS = {"wjacobi": 0, "rbgs": 1, "learned": 2, "mcgs": 3}
+TRANSFERS = {"fw": 0, "paper": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 CYCLES = {"v": 0, "fmg": 1}
 
@@ -36,7 +37,8 @@ class Config(ctypes.Structure):
                 ("smoother", ctypes.c_int), ("omega", ctypes.c_double),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("cycle", ctypes.c_int),
                 ("precision", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("inner_cycles", ctypes.c_int), ("coarse_sweeps", ctypes.c_int)]
+                ("inner_cycles", ctypes.c_int), ("coarse_sweeps", ctypes.c_int),
+                ("transfer", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -146,13 +148,14 @@ class Solver:
     def __init__(self, d: int, n: int, levels: int = 0, smoother: str = "rbgs",
                  omega: float = 0.8, nu1: int = 2, nu2: int = 2, precision: str = "fp64",
                  maxit: int = 100, inner_cycles: int = 4, coarse_sweeps: int = 64,
-                 cycle: str = "v", stream=None):
+                 cycle: str = "v", transfer: str = "fw", stream=None):
         self.d, self.n = d, n
         cfg = Config()
         _check(lib().gmg_config_init(ctypes.byref(cfg), d, n))
         cfg.levels = levels
         cfg.smoother = SMOOTHERS[smoother]
         cfg.omega = omega
+        cfg.transfer = TRANSFERS[transfer]
         cfg.nu1, cfg.nu2 = nu1, nu2
         cfg.precision = PRECISIONS[precision]
         cfg.maxit = maxit

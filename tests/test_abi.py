@@ -52,7 +52,7 @@ def test_config_defaults(L):
 @pytest.mark.parametrize("field,value,status", [
     ("d", 4, 1), ("n", 100, 1), ("n", 1, 1), ("levels", 9, 1), ("smoother", 7, 1),
     ("omega", 2.5, 1), ("nu1", -1, 1), ("nu2", 17, 1), ("cycle", 2, 1),
-    ("maxit", -3, 1), ("precision", 9, 8),
+    ("maxit", -3, 1), ("precision", 9, 8), ("transfer", 2, 1), ("smoother", 4, 1),
 ])
 def test_bad_config_rejected_before_device_use(L, field, value, status):
     c = gmg.Config()
@@ -147,3 +147,18 @@ def test_problem_statement_entry_points_reject_bad_arguments(L):
     assert L.gmg_smoother_save(None, None, 0, ctypes.byref(size)) == 1
     assert L.gmg_smoother_load(None, None, 0) == 1
     assert L.gmg_smoother_train(None, None, None, None) == 1
+
+
+def test_paper_variant_needs_plain_fp64(L):
+    """The paper's multi-colour smoother and transfers run in the plain FP64
+    form only; the defaults select full weighting."""
+    c = gmg.Config()
+    L.gmg_config_init(ctypes.byref(c), 2, 64)
+    assert c.transfer == 0
+    h = ctypes.c_void_p()
+    for smoother, transfer in ((3, 0), (1, 1)):
+        c.smoother, c.transfer, c.precision = smoother, transfer, 1
+        assert L.gmg_create(ctypes.byref(c), None, ctypes.byref(h)) == 8
+        assert not h.value
+    c.smoother, c.transfer, c.precision = 2, 1, 0
+    assert L.gmg_create(ctypes.byref(c), None, ctypes.byref(h)) == 8
