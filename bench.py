@@ -352,6 +352,74 @@ def run_fmg_vs_fft(torch, args):
     return out
 
 
+# Wall times (s) of the paper's table "Comparison of four different smoothers
+# in 2D on GPU" at L = 12 (GTX 480, FP64, tol 1e-6): context only.
+PAPER_SMOOTHER_L12 = {"wj_0.667": (22, 1.02), "wj_0.8": (19, 0.888), "gs_2colour": (16, 0.682),
+                      "gs_4colour": (11, 0.485)}
+
+
+def run_paper_variant(torch, args):
+    """The paper's own variant (its 4/8-colour Gauss-Seidel with the colour
+    order reversed in post-smoothing, 7/15-point restriction, diagonal-linear
+    prolongation), V(1,1): the smoother comparison at 2D 4097^2 (f = sin sin,
+    tol 1e-6, as the paper's table) and the 3D 257^3 workload input to 1e-10
+    beside the plain red-black V(2,2)."""
+    from paper_1208_4247_gb300 import inputs
+    from paper_1208_4247_gb300.gmg import Solver
+    stream = torch.cuda.current_stream()
+    steps = max(args.form_steps, 3)
+
+    def timed(S, f, u, rtol):
+        for _ in range(max(args.warmup, 1)):
+            u.zero_()
+            S.solve(f, u, rtol)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            u.zero_()
+            it, rel, conv = S.solve(f, u, rtol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, it, rel, conv
+
+    out = {}
+    n = 4096
+    x = np.arange(n + 1) / n
+    sx = np.sin(np.pi * x)
+    sx[0] = sx[-1] = 0.0
+    f = torch.from_numpy(np.ascontiguousarray(sx[:, None] * sx[None, :])).cuda()
+    u = torch.zeros_like(f)
+    rows = {}
+    for name, sm, om, tr in (("wj_0.667", "wjacobi", 2.0 / 3.0, "paper"),
+                             ("wj_0.8", "wjacobi", 0.8, "paper"),
+                             ("gs_2colour_rb", "rbgs", 0.8, "paper"),
+                             ("gs_4colour", "mcgs", 0.8, "paper")):
+        with Solver(2, n, smoother=sm, omega=om, nu1=1, nu2=1, transfer=tr) as S:
+            ms, it, rel, conv = timed(S, f, u, 1e-6)
+        rows[name] = {"ms": ms, "cycles": it, "relres": rel, "converged": conv}
+    out["2d_4097_tol1e-6"] = {"rows": rows, "paper_gtx480_L12": PAPER_SMOOTHER_L12,
+                              "note": "gs_2colour_rb keeps red-black order in both sweeps "
+                                      "(the paper's reverses it: 16 cycles)"}
+    del f, u
+    d, n = 3, 256
+    f = torch.from_numpy(inputs.rhs_uniform(d, n, 2)).cuda()
+    u = torch.zeros_like(f)
+    rows = {}
+    for name, sm, tr, nu in (("gs_8colour_paper_v11", "mcgs", "paper", 1),
+                             ("gs_8colour_paper_v22", "mcgs", "paper", 2),
+                             ("rb_fw_v22", "rbgs", "fw", 2)):
+        with Solver(d, n, smoother=sm, nu1=nu, nu2=nu, transfer=tr) as S:
+            ms, it, rel, conv = timed(S, f, u, 1e-10)
+        rows[name] = {"ms": ms, "cycles": it, "relres": rel, "converged": conv,
+                      "dof_per_s": (n - 1) ** d / (ms * 1e-3)}
+    out["3d_257_tol1e-10"] = rows
+    del f, u
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_learned(torch, args):
     """3D 257^3 GRF workload (power ~|k|^-2, seed 5): V(1,1) cycles with the
     learned smoother (trained here on the GPU on 10k error samples from plain
@@ -639,9 +707,10 @@ def run_ours(args, rank, ws, local):
 
     if rank != 0:
         return
-    forms = batch = learned = fmg_fft = None
+    forms = batch = learned = fmg_fft = paper_variant = None
     if not args.no_forms:
         fmg_fft = run_fmg_vs_fft(torch, args)
+        paper_variant = run_paper_variant(torch, args)
         forms = run_forms(torch, args)
         batch = run_batch(torch, args)
         learned = run_learned(torch, args)
@@ -666,7 +735,7 @@ def run_ours(args, rank, ws, local):
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "cufft_dst_257": fft,
-            "fmg_257": fmg_runs, "fmg_pass_vs_fft": fmg_fft,
+            "fmg_257": fmg_runs, "fmg_pass_vs_fft": fmg_fft, "paper_variant": paper_variant,
             "mixed_precision_513": forms, "batched_512": batch,
             "learned_257": learned}
     if args.kernels:
