@@ -25,7 +25,9 @@
  * dense direct solves, the closed-form discretisation error that the paper's
  * FFT error tables print, brute-force dense two-grid spectral radii, the
  * triangular-solve form of red-black Gauss-Seidel, the adjoint relation
- * FW = P^T / 2^d and exact interpolation of linear functions.
+ * FW = P^T / 2^d and exact interpolation of linear functions; for the paper's
+ * own variant (multi-colour GS, its restriction and prolongation) the same
+ * kinds of dense checks plus the iteration counts of its smoother table.
  */
 #include <math.h>
 #include <stdint.h>
