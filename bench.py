@@ -420,6 +420,33 @@ def run_paper_variant(torch, args):
     return out
 
 
+def run_sweeps(torch, args):
+    """Smoother x sweeps x inner-cycle sweeps of the refinement forms (3D
+    513^3 workload input) and of the batched form (the 512-solve mix, default
+    tile and CTAs): time to 1e-10 for every combination."""
+    from paper_1208_4247_gb300 import inputs
+    from paper_1208_4247_gb300.autotune import sweep_batch, sweep_refinement
+    out = {}
+    d, n = 3, 512
+    f = torch.from_numpy(inputs.rhs_sine_plus_gauss(d, n, 3)).cuda()
+    u = torch.zeros_like(f)
+    sms = (("rbgs", 0.8), ("wjacobi", 6.0 / 7.0))
+    for prec, ks in (("fp32", (1, 2, 3, 4)), ("bf16", (1, 2))):
+        rows, best = sweep_refinement(d, n, f, u, prec, sms, (1, 2, 3), ks=ks)
+        out[f"{prec}_513"] = {"rows": rows, "best": best}
+    del f, u
+    torch.cuda.empty_cache()
+    mix = inputs.batch_mix(512, 4)
+    fd = [torch.from_numpy(x).cuda() for x in inputs.batch_rhs(mix, 4)]
+    ud = [torch.zeros_like(x) for x in fd]
+    rows, best = sweep_batch([a for a, _ in mix], [b for _, b in mix], fd, ud, "fp32",
+                             (("wjacobi", 0.8), ("rbgs", 0.8)), (1, 2), ks=(1, 2, 3))
+    out["batch_512_fp32"] = {"rows": rows, "best": best}
+    del fd, ud
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_learned(torch, args):
     """3D 257^3 GRF workload (power ~|k|^-2, seed 5): V(1,1) cycles with the
     learned smoother (trained here on the GPU on 10k error samples from plain
@@ -714,6 +741,7 @@ def run_ours(args, rank, ws, local):
         forms = run_forms(torch, args)
         batch = run_batch(torch, args)
         learned = run_learned(torch, args)
+    sweeps = run_sweeps(torch, args) if args.sweeps else None
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -736,6 +764,7 @@ def run_ours(args, rank, ws, local):
             "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "cufft_dst_257": fft,
             "fmg_257": fmg_runs, "fmg_pass_vs_fft": fmg_fft, "paper_variant": paper_variant,
+            "sweeps": sweeps,
             "mixed_precision_513": forms, "batched_512": batch,
             "learned_257": learned}
     if args.kernels:
@@ -753,6 +782,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels", action="store_true", help="add per-kernel records")
     ap.add_argument("--no-forms", action="store_true", help="skip the 513^3 precision forms")
+    ap.add_argument("--sweeps", action="store_true",
+                    help="add smoother x sweeps x inner-cycle sweeps of the refinement and batched forms")
     ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--train-steps65", type=int, default=1000)
