@@ -14,6 +14,7 @@
 // Weight layout (host and device): 2 x 8 x T floats, W1[c][t] then W2[c][t],
 // tap t = (c3+1)*9 + (b+1)*3 + (a+1) for the offset (a, b, c3) (x fastest);
 // T = 27 in 3D, 9 in 2D.
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -913,10 +914,220 @@ __global__ void __launch_bounds__(256) k_conv_tc(const double* __restrict__ sigm
     }
 }
 
+// ---------------------------------------------------------------------------
+// z-streaming 3D network: u += N(sigma) with conv2 as a GEMM over taps.
+//
+// A CTA owns a 14 x 14 column of output nodes and a chunk of planes and walks
+// the planes.  Per plane kk (with a one-plane halo on either side of the
+// chunk):
+//  1. conv1 on the 16 x 16 halo-1 nodes of plane kk: per 16-node row a
+//     [16 nodes x 48] x [48 x 8 channels] product, K = 9 (dz, dy) groups x 4
+//     dx slots (dx = -1, 0, +1, one zero-weight slot); sigma (planes kk-1 ..
+//     kk+1) sits in a ring of four BF16 planes stored twice (element e, and
+//     shifted by one), so each A register is one aligned 32-bit load (three
+//     mma.sync m16n8k16 BF16 per row);
+//  2. the ReLU'd accumulators, rounded to BF16, are directly the A operand
+//     of z = h W2 ([16 x 8(16)] x [16 x 32 taps], four mma): z[t][node], the
+//     contribution of the node's hidden vector to tap t, FP32, one plane in
+//     shared memory (zero outside the interior: h is zero there);
+//  3. each thread owns one output column (x, y) and adds plane kk's
+//     contributions to its three open outputs, planes kk+1, kk, kk-1 (taps
+//     dz = -1, 0, +1), in registers; plane kk-1 is then complete: u += y.
+// Sigma of plane kk+2 is fetched into registers while plane kk is computed.
+// The hidden activations and sigma enter the tensor cores in BF16, weights
+// are BF16, every sum is FP32 -- the numerics of k_conv_tc, with the taps of
+// conv2 summed in a different order.
+constexpr int ZS_T = 14;              // output tile (x and y)
+constexpr int ZS_H1 = ZS_T + 2;       // halo-1 width: 16 nodes = one mma row group
+constexpr int ZS_H2 = ZS_T + 4;       // halo-2 rows
+constexpr int ZS_SW = 20;             // smem row stride of a sigma plane (18 + pad)
+constexpr int ZS_SP = ZS_H2 * ZS_SW + 4;  // elements per sigma plane (+4: planes
+                                          // 182 words apart, not a multiple of 32 banks)
+constexpr int ZS_TS = 260;            // floats per tap of the z plane (256 nodes + pad)
+constexpr int ZS_ZP = 27 * ZS_TS;     // floats of the z plane
+constexpr int ZS_PLANES = 16;         // output planes per CTA
+constexpr int ZS_PF = (ZS_SP + 255) / 256;  // sigma elements fetched per thread
+
+constexpr size_t zs_smem_bytes() {
+    return sizeof(float) * ZS_ZP + sizeof(__nv_bfloat16) * 2 * 4 * ZS_SP;
+}
+
+// sigma value of the halo-2 element m of plane k (0 outside the interior)
+__device__ inline float zs_sigma(const double* sigma, int64_t sy, int64_t sz, int n, int i0,
+                                 int j0, int k, int m) {
+    const int x2 = m % ZS_SW, y2 = m / ZS_SW;
+    const int i = i0 - 2 + x2, j = j0 - 2 + y2;
+    if (m >= ZS_SP || x2 >= ZS_H2 || y2 >= ZS_H2 || i < 1 || i >= n || j < 1 || j >= n || k < 1 || k >= n)
+        return 0.f;
+    return (float)sigma[(int64_t)k * sz + (int64_t)j * sy + i];
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 4) k_conv_zs(const double* __restrict__ sigma,
+                                                    double* __restrict__ u, int n,
+                                                    const float* __restrict__ W) {
+    extern __shared__ __align__(16) unsigned char zs_smem[];
+    float* zp = reinterpret_cast<float*>(zs_smem);                         // [27][260]
+    __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(zp + ZS_ZP);      // [4][SP]
+    __nv_bfloat16* sb = sa + 4 * ZS_SP;                                    // shifted copy
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int i0 = 1 + ZS_T * blockIdx.x, j0 = 1 + ZS_T * blockIdx.y;
+    const int k0 = 1 + ZS_PLANES * blockIdx.z;
+    const int kend = min(k0 + ZS_PLANES, n);  // output planes k0 .. kend-1
+    const int64_t sy = (int64_t)n + 1, sz = sy * sy;
+
+    // conv1 B operand: k = 16 kh + (0..15) -> group g = k / 4 (dz, dy), slot
+    // k % 4 (dx = slot - 1; slot 3 and groups >= 9 have weight 0)
+    uint32_t b1w[3][2];
+#pragma unroll
+    for (int kh = 0; kh < 3; ++kh) {
+        auto w1 = [&](int g, int slot) {
+            return (g < 9 && slot < 3) ? W[gid * 27 + 3 * g + slot] : 0.f;
+        };
+        const int g = 4 * kh + (tig >> 1), sl = 2 * (tig & 1);
+        b1w[kh][0] = pack_bf16(w1(g, sl), w1(g, sl + 1));
+        b1w[kh][1] = pack_bf16(w1(g + 2, sl), w1(g + 2, sl + 1));
+    }
+    // z-GEMM B operand: k = channel (8..15 zero), n = tap 8 jn + gid
+    uint32_t b2w[4];
+#pragma unroll
+    for (int jn = 0; jn < 4; ++jn) {
+        const int t = 8 * jn + gid;
+        auto w2 = [&](int c) { return t < 27 ? W[8 * 27 + c * 27 + t] : 0.f; };
+        b2w[jn] = pack_bf16(w2(2 * tig), w2(2 * tig + 1));
+    }
+
+    float pf[ZS_PF];
+    auto fetch = [&](int k) {
+#pragma unroll
+        for (int r = 0; r < ZS_PF; ++r)
+            pf[r] = zs_sigma(sigma, sy, sz, n, i0, j0, k, threadIdx.x + 256 * r);
+    };
+    auto store = [&](int k) {  // the fetched plane k -> ring slot k & 3, both copies
+        __nv_bfloat16* a = sa + (k & 3) * ZS_SP;
+        __nv_bfloat16* b = sb + (k & 3) * ZS_SP;
+#pragma unroll
+        for (int r = 0; r < ZS_PF; ++r) {
+            const int m = threadIdx.x + 256 * r;
+            if (m < ZS_SP) {
+                const __nv_bfloat16 v = __float2bfloat16_rn(pf[r]);
+                a[m] = v;
+                if (m > 0) b[m - 1] = v;
+            }
+        }
+    };
+    for (int k = k0 - 2; k <= k0; ++k) {
+        fetch(k);
+        store(k);
+    }
+    fetch(k0 + 1);
+
+    // this thread's conv1 rows are x = gid, gid + 8 of each 16-node row: the
+    // 32-bit pair of x-adjacent sigma values it reads starts at halo-2
+    // column x (dx = -1, 0) or x + 2 (dx = +1, pad); its parity is gid's
+    const int xoff = (tig & 1) ? 2 : 0;
+    const __nv_bfloat16* src = (gid & 1) ? sb : sa;
+    const int sh = (gid & 1) ? -1 : 0;  // element index in the chosen copy
+    // the output column of this thread and its open sums (planes kk-1, kk, kk+1)
+    const bool owner = threadIdx.x < ZS_T * ZS_T;
+    const int ox = threadIdx.x % ZS_T, oy = threadIdx.x / ZS_T;
+    const bool col_in = owner && i0 + ox < n && j0 + oy < n;
+    float y_prev = 0.f, y_cur = 0.f, y_next = 0.f;
+    for (int kk = k0 - 1; kk <= kend; ++kk) {
+        // u of the output finished this plane, read early (used after conv1)
+        const int64_t po = (int64_t)(kk - 1) * sz + (int64_t)(j0 + oy) * sy + i0 + ox;
+        const bool out = col_in && kk - 1 >= k0;
+        const double u_old = (MODE == 1 && out) ? u[po] : 0.0;
+        __syncthreads();  // sigma planes kk-1 .. kk+1 stored; z plane free
+        for (int ry = warp; ry < ZS_H1; ry += 8) {
+            const int j = j0 - 1 + ry;
+            const bool yk = j >= 1 && j < n && kk >= 1 && kk < n;
+            const int ia = i0 - 1 + gid, ib = ia + 8;
+            const bool ina = yk && ia >= 1 && ia < n, inb = yk && ib >= 1 && ib < n;
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kh = 0; kh < 3; ++kh) {
+                uint32_t a[4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    int g = 4 * kh + (tig >> 1) + 2 * h;
+                    if (g >= 9) g = 4;  // zero-weight group: any in-tile pair
+                    const int dz = g / 3 - 1, dy = g % 3 - 1;
+                    const int e = ((kk + dz) & 3) * ZS_SP + (ry + 1 + dy) * ZS_SW + xoff + sh;
+                    a[2 * h] = *reinterpret_cast<const uint32_t*>(src + e + gid);
+                    a[2 * h + 1] = *reinterpret_cast<const uint32_t*>(src + e + gid + 8);
+                }
+                mma_bf16(c, a, b1w[kh][0], b1w[kh][1]);
+            }
+            uint32_t ah[4];
+            ah[0] = ina ? pack_bf16(fmaxf(c[0], 0.f), fmaxf(c[1], 0.f)) : 0u;
+            ah[1] = inb ? pack_bf16(fmaxf(c[2], 0.f), fmaxf(c[3], 0.f)) : 0u;
+            ah[2] = 0u;
+            ah[3] = 0u;
+#pragma unroll
+            for (int jn = 0; jn < 4; ++jn) {
+                float z[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_bf16(z, ah, b2w[jn], 0u);
+                const int t = 8 * jn + 2 * tig;
+                float* zt = zp + t * ZS_TS + ry * ZS_H1;
+                if (t < 27) {
+                    zt[gid] = z[0];
+                    zt[gid + 8] = z[2];
+                }
+                if (t + 1 < 27) {
+                    zt[ZS_TS + gid] = z[1];
+                    zt[ZS_TS + gid + 8] = z[3];
+                }
+            }
+        }
+        store(kk + 2);  // slot (kk+2) & 3 is not read by this plane's conv1
+        fetch(kk + 3);
+        __syncthreads();  // z plane kk complete
+        if (col_in) {
+            // plane kk's taps: dz = +1 -> output kk-1, 0 -> kk, -1 -> kk+1
+#pragma unroll
+            for (int t = 0; t < 27; ++t) {
+                const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+                const float v = zp[t * ZS_TS + (oy + 1 + dy) * ZS_H1 + ox + 1 + dx];
+                if (dz == 1)
+                    y_prev += v;
+                else if (dz == 0)
+                    y_cur += v;
+                else
+                    y_next += v;
+            }
+            if (out) u[po] = u_old + (double)y_prev;
+        }
+        y_prev = y_cur;
+        y_cur = y_next;
+        y_next = 0.f;
+    }
+}
+
 }  // namespace
+
+// 3D uses the z-streaming kernel unless GMG_CONV_ZS=0 (then the tile kernel;
+// the two agree to FP32 rounding of the conv2 sums).
+bool conv_zs_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("GMG_CONV_ZS");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
 
 void conv_tc(int d, int n, const double* sigma, double* u, int mode, const float* W,
              cudaStream_t s) {
+    if (d == 3 && conv_zs_enabled()) {
+        const size_t bytes = zs_smem_bytes();
+        auto kern = mode == 1 ? k_conv_zs<1> : k_conv_zs<0>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        dim3 grid((n - 1 + ZS_T - 1) / ZS_T, (n - 1 + ZS_T - 1) / ZS_T,
+                  (n - 1 + ZS_PLANES - 1) / ZS_PLANES);
+        kern<<<grid, 256, bytes, s>>>(sigma, u, n, W);
+        return;
+    }
     if (d == 3) {
         using G = TcTile<3>;
         dim3 grid((n - 1 + G::TX - 1) / G::TX, (n - 1 + G::TY - 1) / G::TY,
