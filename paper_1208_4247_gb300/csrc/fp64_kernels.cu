@@ -2,6 +2,7 @@
 // stopping-test residual norm (Algorithm 3's res), and the double-precision
 // instantiation of the level kernels (level_kernels.cuh).
 #include <cstdlib>
+#include <type_traits>
 
 #include "level_kernels.cuh"
 
@@ -136,6 +137,105 @@ __global__ void __launch_bounds__(256, 4) k_resnorm3_walk(const double* __restri
     }
 }
 
+// The stopping-test norm after a red-black cycle fused with the first red
+// half sweep of the next cycle (3D FP64 walkers).  At a red node the sweep's
+// new value fma(c, sum, q) minus the old value is exactly the red-only norm's
+// sigma, so one pass gives both: sigma^2 summed as k_resnorm3_walk sums it
+// (same walkers, grid and order: the same bits) and the node updated as
+// k_rb_half3_walk updates it (the same bits), with the old red value kept in
+// `save` so that a solve that stops on this norm can put it back.  NORM =
+// false: the sweep and the save only.  Every operand of a run is loaded
+// before its first store, as in k_rb_half3_walk.
+template <int N, bool NORM>
+__global__ void __launch_bounds__(256, 4) k_red_ahead3_walk(double* __restrict__ u,
+                                                            const double* __restrict__ q,
+                                                            double* __restrict__ save,
+                                                            double* __restrict__ partial) {
+    // the level size is a template argument: every operand address is one
+    // base plus an immediate offset, which keeps the kernel within 64
+    // registers with four rows of operands in flight
+    constexpr int W = lk::kWalk, m = N - 1, segs = (m + W - 1) / W, walkers = m * segs;
+    constexpr int64_t sy = N + 1, sz = (int64_t)(N + 1) * (N + 1), dp = sy + sz;
+    __shared__ double warp_sums[kNormThreads / 32];
+    const double c = 1.0 / 6.0;
+    double acc = 0.0;
+    for (int w = blockIdx.x * blockDim.y + threadIdx.y; w < walkers; w += gridDim.x * blockDim.y) {
+        const int seg = w / m, line = w % m;
+        int j = 1 + seg * W;
+        const int jend = min(j + W, N);
+        int k = 1 + (j - 1 + line) % m;
+        while (j < jend) {
+            const int run = min(jend - j, N - k);
+            const int i = 1 + ((1 + j + k) & 1) + 2 * (int)threadIdx.x;
+            if (i < N) {
+                const int64_t p0 = (int64_t)k * sz + (int64_t)j * sy + i;
+                const double* up = u + p0;
+                double xm[W], xp[W], yp[W], zp[W], qv[W], uo[W];
+                const double ym0 = up[-sy], zm0 = up[-sz];
+#pragma unroll
+                for (int r = 0; r < W; ++r) {
+                    if (r < run) {
+                        xm[r] = up[r * dp - 1];
+                        xp[r] = up[r * dp + 1];
+                        yp[r] = up[r * dp + sy];
+                        zp[r] = up[r * dp + sz];
+                        qv[r] = q[p0 + r * dp];
+                        uo[r] = up[r * dp];
+                    }
+                }
+                double lo = ym0 + zm0;
+#pragma unroll
+                for (int r = 0; r < W; ++r) {
+                    if (r < run) {
+                        const int64_t p = p0 + r * dp;
+                        const double hi = yp[r] + zp[r];
+                        const double un = fma(c, ((xm[r] + xp[r]) + lo) + hi, qv[r]);
+                        if (NORM) {
+                            const double sig = un - uo[r];
+                            acc = fma(sig, sig, acc);
+                        }
+                        save[p] = uo[r];
+                        u[p] = un;
+                        lo = hi;
+                    }
+                }
+            }
+            j += run;
+            k = 1;
+        }
+    }
+    if (!NORM) return;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((t & 31) == 0) warp_sums[t >> 5] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int v = 0; v < kNormThreads / 32; ++v) s += warp_sums[v];
+        partial[blockIdx.x] = s;
+    }
+}
+
+// u = save on the red interior nodes of a dense 3D level n (undoes
+// k_red_ahead3_walk's sweep).
+__global__ void __launch_bounds__(256) k_red_restore3(double* __restrict__ u,
+                                                      const double* __restrict__ save, int n) {
+    const int half = n / 2;
+    const int64_t m = n - 1, total = m * m * half;
+    const int64_t sy = lk::sy_of(n), sz = lk::sz_of<3>(n);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t / half;
+        const int x = (int)(t - row * half);
+        const int j = 1 + (int)(row % m), k = 1 + (int)(row / m);
+        const int i = 1 + ((1 + j + k) & 1) + 2 * x;
+        if (i < n) {
+            const int64_t p = (int64_t)k * sz + (int64_t)j * sy + i;
+            u[p] = save[p];
+        }
+    }
+}
+
 struct NormLaunch {
     dim3 grid, block;
 };
@@ -212,6 +312,40 @@ void copy_strided(int d, int n, const double* src, int64_t ssy, int64_t ssz, dou
 }
 
 int resnorm_partials(int d, int n) { return (int)norm_launch(d, n).grid.x; }
+
+bool red_ahead_applies(int d, int n) {
+    static const bool on = [] {
+        const char* v = std::getenv("GMG_NORM_AHEAD");
+        return !(v && v[0] == '0');
+    }();
+    return on && lk::walk_applies(d, n, sizeof(double));
+}
+
+void red_ahead(int n, double* u, const double* q, double* save, double* partial, double* out,
+               bool norm, cudaStream_t s) {
+    const lk::WalkLaunch W = lk::walk_launch(n);
+    const unsigned blocks = std::min<unsigned>(W.blocks, (unsigned)resnorm_partials(3, n));
+    auto launch = [&](auto kn) {
+        constexpr int N = decltype(kn)::value;
+        if (norm)
+            k_red_ahead3_walk<N, true><<<blocks, W.block, 0, s>>>(u, q, save, partial);
+        else
+            k_red_ahead3_walk<N, false><<<blocks, W.block, 0, s>>>(u, q, save, nullptr);
+    };
+    if (n == 128)
+        launch(std::integral_constant<int, 128>{});
+    else if (n == 256)
+        launch(std::integral_constant<int, 256>{});
+    else
+        launch(std::integral_constant<int, 512>{});
+    if (norm) k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)blocks, out);
+}
+
+void red_restore(int n, double* u, const double* save, cudaStream_t s) {
+    const int64_t total = (int64_t)(n - 1) * (n - 1) * (n / 2);
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
+    k_red_restore3<<<blocks, 256, 0, s>>>(u, save, n);
+}
 
 void resnorm(int d, int n, const double* u, const double* q, double* partial, double* out,
              cudaStream_t s, double* sigma_out, bool red_only) {

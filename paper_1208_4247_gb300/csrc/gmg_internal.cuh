@@ -139,6 +139,15 @@ void copy_strided(int d, int n, const double* src, int64_t ssy, int64_t ssz, dou
 void resnorm(int d, int n, const double* u, const double* q, double* partial, double* out,
              cudaStream_t s, double* sigma_out = nullptr, bool red_only = false);
 __global__ void k_sum_partials(const double* partial, int count, double* out);
+// The stopping-test norm of a red-black cycle fused with the next cycle's
+// first red half sweep (3D FP64 levels the diagonal walkers take, unless
+// GMG_NORM_AHEAD=0): the red-only norm of u into *out (norm = true) and one
+// red half sweep of u, the old red values kept in save.  red_restore puts
+// them back (u = save on the red interior nodes).
+bool red_ahead_applies(int d, int n);
+void red_ahead(int n, double* u, const double* q, double* save, double* partial, double* out,
+               bool norm, cudaStream_t s);
+void red_restore(int n, double* u, const double* save, cudaStream_t s);
 }  // namespace fp64
 
 // Outer FP64 kernels of iterative refinement (mixed_kernels.cu).
