@@ -104,7 +104,12 @@ gmg_status gmg_config_init(gmg_config* cfg, int d, int n);
  * 32 in 2D; 1 turns the tail off); results are the same bit for bit.
  * GMG_RB_WALK=0 (read once per process) replaces the diagonal-walker FP64 3D
  * half sweeps, red-only residuals and norms (levels 128 <= n <= 512) by row
- * kernels; results are the same bit for bit. */
+ * kernels; results are the same bit for bit.  GMG_NORM_AHEAD=0 (read once
+ * per process) keeps the stopping-test norm of the plain red-black form a
+ * separate kernel instead of fusing it with the next cycle's first red half
+ * sweep (3D levels 128 <= n <= 512; a solve that stops undoes that sweep);
+ * u and the cycle count are the same bit for bit, the norms agree to
+ * rounding. */
 gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out);
 
 /* GMGSolve (Algorithm 3, all levels on the device): starting from the initial

@@ -57,6 +57,9 @@ struct gmg_handle_s {
     std::vector<void*> allocs;
     KernelTimer timer;  // launch accounting and optional per-kernel event timing
     bool fused_rb = false;  // GMG_FUSED_RB=1 at create: fused FP32 3D red-black sweeps
+    // plain red-black form: the stopping-test norm runs fused with the next
+    // cycle's first level-0 red half sweep (norm_ahead_ok)
+    bool ahead = false;
     int tail_max = 0;       // GMG_TAIL_N at create: largest tail level n (0 = default)
     // learned smoother (GMG_LEARNED): per level BF16-rounded weights on the
     // device (NULL: red-black GS on that level) and the hidden-layer buffer
@@ -190,13 +193,13 @@ int num_levels(const gmg_config& c) { return c.levels > 0 ? c.levels : ilog2(c.n
 enum Kind {
     K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_OUTER_RES,
     K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_TAIL, K_RB_FUSED, K_MC_SWEEP, K_RESTRICT_PAPER,
-    K_PROLONG_PAPER, K_COUNT
+    K_PROLONG_PAPER, K_NORM_AHEAD, K_COUNT
 };
 const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restrict",
                                   "prolong_add", "resnorm",  "copy",     "outer_residual",
                                   "update",      "memset",   "conv1",    "conv_tc_update", "tail",
                                   "rb_sweep_fused", "mc_sweep", "restrict_paper",
-                                  "prolong_paper"};
+                                  "prolong_paper", "resnorm_red_sweep"};
 const char* kPrecSuffix[3] = {"", "_f32", "_bf16"};
 
 template <typename T>
@@ -247,6 +250,8 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
             return {N / (t ? 8 : 4) * (t ? 6 : 4), N / (t ? 8 : 4) * (t ? 8 : 6) * w};
         case K_RESTRICT_PAPER: return {Nc * (t ? 16 : 8), N * w + Nc * 2 * w};
         case K_PROLONG_PAPER: return {cells * (t ? 14 : 6), Nc * w + N * 2 * w};
+        case K_NORM_AHEAD:  // red nodes: sigma^2 and the update; read u, q (red); write u, save
+            return {N / 2 * (t ? 8 : 6), N * 2.5 * w};
     }
     return {0.0, 0.0};
 }
@@ -304,9 +309,11 @@ bool sigma_carried(gmg_handle h) {
 
 // backward: post-smoothing (Relax_backward), which takes the colours of the
 // multi-colour smoother in decreasing order.
+// first_red_done: the first red half sweep already ran (fused with the
+// previous step's stopping-test norm).
 template <typename T>
 void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
-           bool sigma_ready = false, bool backward = false) {
+           bool sigma_ready = false, bool backward = false, bool first_red_done = false) {
     Level<T>& L = lv[l];
     const int d = h->cfg.d;
     const int p = prec_of<T>();
@@ -338,7 +345,7 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
             }
         }
         if (h->cfg.smoother == GMG_RBGS || h->cfg.smoother == GMG_LEARNED) {
-            for (int color = 0; color < 2; ++color)
+            for (int color = first_red_done && s == 0 ? 1 : 0; color < 2; ++color)
                 timed(h, K_RB_HALF, l, p, L.n, false,
                       [&] { lk::rb_half<T>(d, L.lay, L.u[cur], L.q, color, h->stream); });
         } else {
@@ -372,9 +379,10 @@ int tail_level(gmg_handle h, const std::vector<Level<T>>& lv) {
 }
 
 // One cycle of Algorithm 1 on the hierarchy lv (level-0 iterate lv[0].u[0]
-// in and out), in stream order.
+// in and out), in stream order.  first_red_done: the cycle's first level-0
+// red half sweep already ran (fp64::red_ahead); it starts with the black one.
 template <typename T>
-gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
+gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_red_done = false) {
     const gmg_config& c = h->cfg;
     const int d = c.d;
     const int L = (int)lv.size();
@@ -390,12 +398,13 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv) {
         });
         GMG_CUDA_TRY(e);
     } else if (L == 1) {
-        relax(h, lv, 0, c.nu1, cur[0]);
+        relax(h, lv, 0, c.nu1, cur[0], false, false, first_red_done);
     } else {
         const int Ldown = lt < L ? lt : L - 1;  // levels smoothed by grid kernels going down
         for (int l = 0; l < Ldown; ++l) {
-            relax(h, lv, l, c.nu1, cur[l], l == 0 && std::is_same<T, double>::value &&
-                                               sigma_carried(h));
+            relax(h, lv, l, c.nu1, cur[l],
+                  l == 0 && std::is_same<T, double>::value && sigma_carried(h), false,
+                  l == 0 && first_red_done);
             Level<T>& F = lv[l];
             Level<T>& C = lv[l + 1];
             // After a black half sweep the black residual vanishes identically.
@@ -508,13 +517,44 @@ bool norm_red_only(gmg_handle h) {
            (h->lv.size() > 1 ? c.nu2 > 0 : c.nu1 > 0);
 }
 
+// The red-only stopping-test norm and the next cycle's first level-0 red half
+// sweep read the same operands, and the sweep's change at a red node is that
+// norm's sigma: one fused pass (fp64::red_ahead) does both, the cycle graph
+// starts with its first black half sweep, and a solve that stops puts the
+// red nodes back (fp64::red_restore) -- u and the norm history are those of
+// the unfused schedule.  Plain FP64 red-black with grid kernels on level 0,
+// pre-smoothing, and a level-0 size the diagonal walkers take.
+bool norm_ahead_ok(gmg_handle h) {
+    const gmg_config& c = h->cfg;
+    return c.precision == GMG_FP64 && c.smoother == GMG_RBGS && c.nu1 > 0 && h->lv.size() > 1 &&
+           norm_red_only(h) && fp64::red_ahead_applies(c.d, c.n) &&
+           tail_level<double>(h, h->lv) > 0;
+}
+
+// The fused norm of the step's (or FMG pass's) result plus the next red half
+// sweep; the squared scaled norm lands in h->d_res2.
+void enqueue_norm_ahead(gmg_handle h) {
+    const gmg_config& c = h->cfg;
+    Level<double>& L0 = h->lv[0];
+    timed(
+        h, K_NORM_AHEAD, 0, 0, c.n, true,
+        [&] {
+            fp64::red_ahead(c.n, L0.u[0], L0.q, L0.r, h->partial, h->d_res2, true, h->stream);
+        },
+        2);
+}
+
 // One step of the stopping loop: a plain cycle plus the FP64 norm, or one
 // refinement step; the squared scaled norm lands in h->h_res2.
 gmg_status enqueue_step(gmg_handle h) {
     const gmg_config& c = h->cfg;
     h->timer.begin_capture();
     gmg_status st = GMG_OK;
-    if (c.precision == GMG_FP64) {
+    if (c.precision == GMG_FP64 && h->ahead) {
+        st = enqueue_vcycle<double>(h, h->lv, true);
+        if (st != GMG_OK) return st;
+        enqueue_norm_ahead(h);
+    } else if (c.precision == GMG_FP64) {
         st = enqueue_vcycle<double>(h, h->lv);
         if (st != GMG_OK) return st;
         double* keep = sigma_carried(h) ? h->lv[0].r : nullptr;
@@ -589,13 +629,16 @@ gmg_status enqueue_fmg(gmg_handle h) {
         gmg_status st = enqueue_vcycle<double>(h, lv);
         if (st != GMG_OK) return st;
     }
-    timed(
-        h, K_RESNORM, 0, 0, c.n, norm_red_only(h),
-        [&] {
-            fp64::resnorm(c.d, c.n, lv[0].u[0], lv[0].q, h->partial, h->d_res2, h->stream,
-                          nullptr, norm_red_only(h));
-        },
-        2);
+    if (h->ahead)
+        enqueue_norm_ahead(h);
+    else
+        timed(
+            h, K_RESNORM, 0, 0, c.n, norm_red_only(h),
+            [&] {
+                fp64::resnorm(c.d, c.n, lv[0].u[0], lv[0].q, h->partial, h->d_res2, h->stream,
+                              nullptr, norm_red_only(h));
+            },
+            2);
     GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
                                  h->stream));
     GMG_CUDA_TRY(cudaGetLastError());
@@ -665,10 +708,16 @@ struct DeviceGuard {
 gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
     const gmg_config& c = h->cfg;
     fp64::prepare(c.d, c.n, f, h->lv[0].q, u, h->stream);
-    if (c.precision == GMG_FP64)
+    if (c.precision == GMG_FP64) {
         fp64::resnorm(c.d, c.n, u, h->lv[0].q, h->partial, h->d_res2, h->stream,
                       sigma_carried(h) ? h->lv[0].r : nullptr);
-    else if (c.precision == GMG_FP32_IR)
+        if (h->ahead && c.cycle != GMG_FMG) {
+            // the first cycle's first red half sweep (its result is undone if
+            // the solve stops before the first cycle)
+            fp64::red_ahead(c.n, u, h->lv[0].q, h->lv[0].r, nullptr, nullptr, false, h->stream);
+            h->timer.launches += 1;
+        }
+    } else if (c.precision == GMG_FP32_IR)
         mixed::outer_residual<float>(c.d, h->lvf[0].lay, u, h->lv[0].q, h->lvf[0].q, h->partial,
                                      h->d_res2,
                                      h->stream);
@@ -712,6 +761,17 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
     double res = res0;
     int it = 0;
     const int cap = stop ? h->cfg.maxit : ncycles;
+    // with the fused norm a red half sweep of a cycle that does not run is
+    // pending on u whenever the loop ends: undo it
+    auto finish = [&]() -> gmg_status {
+        if (h->ahead && (it > 0 || !h->fmg_graph)) {
+            fp64::red_restore(h->cfg.n, u, h->lv[0].r, h->stream);
+            h->timer.launches += 1;
+            GMG_CUDA_TRY(cudaGetLastError());
+            GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        }
+        return GMG_OK;
+    };
     while (it < cap && (!stop || res > rtol * res0)) {
         const bool fmg = it == 0 && h->fmg_graph;
         GMG_CUDA_TRY(cudaGraphLaunch(fmg ? h->fmg_graph : h->graph, h->stream));
@@ -732,11 +792,13 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
         h->hist.push_back(rel);
         if (!stop && relres_out) relres_out[it - 1] = rel;
         if (!std::isfinite(res)) {
-            set_error("residual norm became non-finite");
             if (iters_out) *iters_out = it;
+            if ((st = finish()) != GMG_OK) return st;
+            set_error("residual norm became non-finite");
             return GMG_ERR_NONFINITE;
         }
     }
+    if ((st = finish()) != GMG_OK) return st;
     if (iters_out) *iters_out = it;
     if (stop && relres_out) *relres_out = res0 > 0.0 ? res / res0 : 0.0;
     if (stop && res > rtol * res0) {
@@ -873,6 +935,7 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
         set_error("initialisation failed");
         return fail(GMG_ERR_CUDA);
     }
+    h->ahead = norm_ahead_ok(h);
     *out = h;
     return GMG_OK;
 }

@@ -140,14 +140,17 @@ __global__ void __launch_bounds__(256, 4) k_resnorm3_walk(const double* __restri
 // The stopping-test norm after a red-black cycle fused with the first red
 // half sweep of the next cycle (3D FP64 walkers).  At a red node the sweep's
 // new value fma(c, sum, q) minus the old value is exactly the red-only norm's
-// sigma, so one pass gives both: sigma^2 summed as k_resnorm3_walk sums it
-// (same walkers, grid and order: the same bits) and the node updated as
-// k_rb_half3_walk updates it (the same bits), with the old red value kept in
-// `save` so that a solve that stops on this norm can put it back.  NORM =
-// false: the sweep and the save only.  Every operand of a run is loaded
-// before its first store, as in k_rb_half3_walk.
+// sigma, so one pass gives both: the sigma^2 terms of k_resnorm3_walk (the
+// same bits, summed in another fixed order: deterministic) and the node
+// updated as k_rb_half3_walk updates it (the same bits), with the old red
+// value kept in `save` so that a solve that stops on this norm can put it
+// back.  NORM = false: the sweep and the save only.  Every operand of a run
+// is loaded before its first store, as in k_rb_half3_walk.
+// 256 threads, 3 CTAs per SM: the sixth operand row (the old red value) does
+// not fit in 64 registers without spills, and this beats 4 CTAs with spills
+// (257^3 and 513^3 solves).
 template <int N, bool NORM>
-__global__ void __launch_bounds__(256, 4) k_red_ahead3_walk(double* __restrict__ u,
+__global__ void __launch_bounds__(256, 3) k_red_ahead3_walk(double* __restrict__ u,
                                                             const double* __restrict__ q,
                                                             double* __restrict__ save,
                                                             double* __restrict__ partial) {
@@ -323,8 +326,10 @@ bool red_ahead_applies(int d, int n) {
 
 void red_ahead(int n, double* u, const double* q, double* save, double* partial, double* out,
                bool norm, cudaStream_t s) {
+    // two waves of 3 resident CTAs per SM stride over the walkers; the
+    // partial sums (one per CTA) fit the resnorm buffer (resnorm_partials)
     const lk::WalkLaunch W = lk::walk_launch(n);
-    const unsigned blocks = std::min<unsigned>(W.blocks, (unsigned)resnorm_partials(3, n));
+    const unsigned blocks = std::min<unsigned>(W.blocks, 152u * 3 * 2);
     auto launch = [&](auto kn) {
         constexpr int N = decltype(kn)::value;
         if (norm)

@@ -393,6 +393,69 @@ def test_walker_sweep_is_bitwise_equal_to_row_sweep(torch_cuda, tmp_path):
     assert np.array_equal(ud.cpu().numpy(), np.load(tmp_path / "u_rows.npy"))
 
 
+def test_fused_stopping_norm_matches_unfused_schedule(torch_cuda, tmp_path):
+    """The stopping-test norm fused with the next cycle's first red half sweep
+    (default for 3D FP64 levels of 128..512) against the separate norm kernel
+    (GMG_NORM_AHEAD=0, in a child process): V-cycle and FMG solves, a solve
+    that hits maxit, a fixed cycle count and zero cycles from a random initial
+    guess leave u bit for bit equal, with the same cycle counts and norm
+    histories (the two norms sum the same terms in different orders)."""
+    import os
+    import subprocess
+    import sys
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 128
+    f = inputs.rhs_uniform(d, n, 15)
+    rng = np.random.default_rng(16)
+    u0 = np.zeros_like(f)
+    u0[1:-1, 1:-1, 1:-1] = rng.standard_normal((n - 1,) * d)
+    np.save(tmp_path / "f.npy", f)
+    np.save(tmp_path / "u0.npy", u0)
+    # (label, Solver kwargs, action): action "solve" or an int cycle count
+    cases = [("v", {}, "solve"), ("fmg", {"cycle": "fmg"}, "solve"),
+             ("maxit", {"maxit": 3}, "solve"), ("fixed", {}, 4), ("zero", {}, 0),
+             ("v11", {"nu1": 1, "nu2": 1}, "solve")]
+    script = (
+        "import numpy as np, torch, json\n"
+        "from paper_1208_4247_gb300.gmg import Solver\n"
+        f"f = torch.from_numpy(np.load(r'{tmp_path / 'f.npy'}')).cuda()\n"
+        f"u0 = np.load(r'{tmp_path / 'u0.npy'}')\n"
+        f"cases = {cases!r}\n"
+        "out = {}\n"
+        "for label, kw, act in cases:\n"
+        "    u = torch.from_numpy(u0.copy()).cuda()\n"
+        f"    S = Solver({d}, {n}, **kw)\n"
+        "    r = S.solve(f, u, rtol=1e-10) if act == 'solve' else S.cycles(f, u, act)\n"
+        "    out[label] = [list(r) if act != 'solve' else [r[0], r[2]], S.history()]\n"
+        "    S.close()\n"
+        f"    np.save(r'{tmp_path}/u_' + label + '.npy', u.cpu().numpy())\n"
+        f"json.dump(out, open(r'{tmp_path / 'ref.json'}', 'w'))\n")
+    env = dict(os.environ, GMG_NORM_AHEAD="0")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", script], check=True, env=env, cwd=root)
+    import json
+    ref = json.load(open(tmp_path / "ref.json"))
+    fd = _dev(torch, f)
+    for label, kw, act in cases:
+        ud = _dev(torch, u0)
+        with Solver(d, n, **kw) as S:
+            r = S.solve(fd, ud, rtol=1e-10) if act == "solve" else S.cycles(fd, ud, act)
+            hist = S.history()
+        res = list(r) if act != "solve" else [r[0], r[2]]
+        want_res, want_hist = ref[label]
+        if act == "solve":
+            assert res == want_res, label
+        else:
+            np.testing.assert_allclose(res, want_res, rtol=1e-13, err_msg=label)
+        assert len(hist) == len(want_hist), label
+        np.testing.assert_allclose(hist, want_hist, rtol=1e-13, err_msg=label)
+        assert np.array_equal(ud.cpu().numpy(), np.load(tmp_path / f"u_{label}.npy")), label
+    # zero cycles: the interior is the initial guess, bit for bit
+    uz = np.load(tmp_path / "u_zero.npy")
+    assert np.array_equal(uz[1:-1, 1:-1, 1:-1], u0[1:-1, 1:-1, 1:-1])
+
+
 @pytest.mark.parametrize("d,n,expect,tol", [(3, 256, 4.4371e-6, 1e-4), (3, 512, 1.1093e-6, 1e-4),
                                             (2, 256, 6.2750e-6, 1e-4), (2, 4096, 2.4511e-8, 1e-3)])
 def test_converged_solve_reproduces_discretisation_error(torch_cuda, d, n, expect, tol):
