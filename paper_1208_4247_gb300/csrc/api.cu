@@ -708,15 +708,17 @@ struct DeviceGuard {
 gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
     const gmg_config& c = h->cfg;
     fp64::prepare(c.d, c.n, f, h->lv[0].q, u, h->stream);
-    if (c.precision == GMG_FP64) {
+    if (c.precision == GMG_FP64 && h->ahead && c.cycle != GMG_FMG) {
+        // the first norm in two colour halves: the black one from u_0, then
+        // the red one fused with the first cycle's first red half sweep
+        // (undone if the solve stops before the first cycle)
+        fp64::resnorm_black(c.n, u, h->lv[0].q, h->partial, h->d_res2 + 1, h->stream);
+        fp64::red_ahead(c.n, u, h->lv[0].q, h->lv[0].r, h->partial, h->d_res2, true, h->stream,
+                        h->d_res2 + 1);
+        h->timer.launches += 2;
+    } else if (c.precision == GMG_FP64) {
         fp64::resnorm(c.d, c.n, u, h->lv[0].q, h->partial, h->d_res2, h->stream,
                       sigma_carried(h) ? h->lv[0].r : nullptr);
-        if (h->ahead && c.cycle != GMG_FMG) {
-            // the first cycle's first red half sweep (its result is undone if
-            // the solve stops before the first cycle)
-            fp64::red_ahead(c.n, u, h->lv[0].q, h->lv[0].r, nullptr, nullptr, false, h->stream);
-            h->timer.launches += 1;
-        }
     } else if (c.precision == GMG_FP32_IR)
         mixed::outer_residual<float>(c.d, h->lvf[0].lay, u, h->lv[0].q, h->lvf[0].q, h->partial,
                                      h->d_res2,
@@ -926,7 +928,7 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     }
     const int np = std::max(fp64::resnorm_partials(d, cfg->n), mixed::outer_partials(d, cfg->n));
     if ((st = dev_alloc(h, &h->partial, np)) != GMG_OK) return fail(st);
-    if ((st = dev_alloc(h, &h->d_res2, 1)) != GMG_OK) return fail(st);
+    if ((st = dev_alloc(h, &h->d_res2, 2)) != GMG_OK) return fail(st);
     if (cudaMallocHost((void**)&h->h_res2, sizeof(double)) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         return fail(GMG_ERR_ALLOC);

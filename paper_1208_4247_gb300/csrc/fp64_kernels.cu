@@ -44,20 +44,23 @@ using lk::sz_of;
 template <int DIM>
 __global__ void __launch_bounds__(256) k_prepare(const double* __restrict__ f, double* __restrict__ q,
                                                  double* __restrict__ u, int n, double scale) {
+    // rows (j, k) of (n+1) nodes, x contiguous (no per-node index division)
     const int64_t m = sy_of(n);
-    const int64_t nodes = DIM == 3 ? m * m * m : m * m;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nodes;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(p % m);
-        const int64_t t = p / m;
-        const int j = (int)(t % m);
-        const int k = DIM == 3 ? (int)(t / m) : 1;
-        const bool inner = i > 0 && i < n && j > 0 && j < n && k > 0 && k < (DIM == 3 ? n : 2);
-        if (inner) {
-            q[p] = scale * f[p];
-        } else {
-            q[p] = 0.0;
-            u[p] = 0.0;
+    const int64_t rows = DIM == 3 ? m * m : m;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
+         r += (int64_t)gridDim.x * blockDim.y) {
+        const int j = (int)(r % m);
+        const int k = DIM == 3 ? (int)(r / m) : 1;
+        const bool row_inner = j > 0 && j < n && k > 0 && k < (DIM == 3 ? n : 2);
+        const int64_t base = r * m;
+        for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+            const int64_t p = base + i;
+            if (row_inner && i > 0 && i < n) {
+                q[p] = scale * f[p];
+            } else {
+                q[p] = 0.0;
+                u[p] = 0.0;
+            }
         }
     }
 }
@@ -109,20 +112,21 @@ __global__ void __launch_bounds__(kNormThreads) k_resnorm(const double* __restri
     }
 }
 
-// Red-only norm by the diagonal walkers (3D, 128 <= n <= 512): the same
-// sigma^2 terms as k_resnorm<3, false, true>, summed in walker order; a
-// fixed grid strides over the walkers, so the result is deterministic.
+// One-colour norm by the diagonal walkers (3D, 128 <= n <= 512).  Colour 0
+// (red): the same sigma^2 terms as k_resnorm<3, false, true>, summed in
+// walker order.  Colour 1 (black): the black half of a solve's first norm.
+// A fixed grid strides over the walkers, so the result is deterministic.
 __global__ void __launch_bounds__(256, 4) k_resnorm3_walk(const double* __restrict__ u,
                                                           const double* __restrict__ q,
                                                           double* __restrict__ partial, int n,
-                                                          int segs) {
+                                                          int segs, int color) {
     __shared__ double warp_sums[kNormThreads / 32];
     const double c = 1.0 / 6.0;
     const int64_t walkers = (int64_t)(n - 1) * segs;
     double acc = 0.0;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; w < walkers;
          w += (int64_t)gridDim.x * blockDim.y)
-        lk::walk_nodes(u, n, 0, w, segs, [&](int64_t p, double sum, int, int, int) {
+        lk::walk_nodes(u, n, color, w, segs, [&](int64_t p, double sum, int, int, int) {
             const double sig = fma(c, sum, q[p]) - u[p];
             acc = fma(sig, sig, acc);
         });
@@ -239,6 +243,25 @@ __global__ void __launch_bounds__(256) k_red_restore3(double* __restrict__ u,
     }
 }
 
+// out = (plus ? *plus : 0) + the sum of count partials, in k_sum_partials'
+// order.
+__global__ void __launch_bounds__(1024) k_sum_partials_plus(const double* __restrict__ partial,
+                                                            int count,
+                                                            const double* __restrict__ plus,
+                                                            double* __restrict__ out) {
+    __shared__ double warp_sums[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) acc += partial[i];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += warp_sums[w];
+        out[0] = plus ? plus[0] + t : t;
+    }
+}
+
 struct NormLaunch {
     dim3 grid, block;
 };
@@ -276,12 +299,15 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict_
 void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s) {
     const double h = 1.0 / n;
     const double scale = h * h / (2.0 * d);
-    const int64_t nodes = d == 3 ? (int64_t)(n + 1) * (n + 1) * (n + 1) : (int64_t)(n + 1) * (n + 1);
-    const int blocks = (int)std::min<int64_t>((nodes + 255) / 256, 152 * 16);
+    int bx = 32;
+    while (bx < n + 1 && bx < 256) bx *= 2;
+    const dim3 block(bx, 256 / bx, 1);
+    const int64_t rows = d == 3 ? (int64_t)(n + 1) * (n + 1) : (int64_t)(n + 1);
+    const int blocks = (int)std::min<int64_t>((rows + block.y - 1) / block.y, 152 * 16);
     if (d == 3)
-        k_prepare<3><<<blocks, 256, 0, s>>>(f, q, u, n, scale);
+        k_prepare<3><<<blocks, block, 0, s>>>(f, q, u, n, scale);
     else
-        k_prepare<2><<<blocks, 256, 0, s>>>(f, q, u, n, scale);
+        k_prepare<2><<<blocks, block, 0, s>>>(f, q, u, n, scale);
 }
 
 namespace {
@@ -325,7 +351,7 @@ bool red_ahead_applies(int d, int n) {
 }
 
 void red_ahead(int n, double* u, const double* q, double* save, double* partial, double* out,
-               bool norm, cudaStream_t s) {
+               bool norm, cudaStream_t s, const double* plus) {
     // two waves of 3 resident CTAs per SM stride over the walkers; the
     // partial sums (one per CTA) fit the resnorm buffer (resnorm_partials)
     const lk::WalkLaunch W = lk::walk_launch(n);
@@ -343,7 +369,15 @@ void red_ahead(int n, double* u, const double* q, double* save, double* partial,
         launch(std::integral_constant<int, 256>{});
     else
         launch(std::integral_constant<int, 512>{});
-    if (norm) k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)blocks, out);
+    if (norm) k_sum_partials_plus<<<1, 1024, 0, s>>>(partial, (int)blocks, plus, out);
+}
+
+void resnorm_black(int n, const double* u, const double* q, double* partial, double* out,
+                   cudaStream_t s) {
+    const lk::WalkLaunch W = lk::walk_launch(n);
+    const unsigned blocks = std::min<unsigned>(W.blocks, (unsigned)resnorm_partials(3, n));
+    k_resnorm3_walk<<<blocks, W.block, 0, s>>>(u, q, partial, n, W.segs, 1);
+    k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)blocks, out);
 }
 
 void red_restore(int n, double* u, const double* save, cudaStream_t s) {
@@ -357,7 +391,7 @@ void resnorm(int d, int n, const double* u, const double* q, double* partial, do
     if (red_only && !sigma_out && lk::walk_applies(d, n, sizeof(double))) {
         const lk::WalkLaunch W = lk::walk_launch(n);
         const unsigned blocks = std::min<unsigned>(W.blocks, (unsigned)resnorm_partials(d, n));
-        k_resnorm3_walk<<<blocks, W.block, 0, s>>>(u, q, partial, n, W.segs);
+        k_resnorm3_walk<<<blocks, W.block, 0, s>>>(u, q, partial, n, W.segs, 0);
         k_sum_partials<<<1, 1024, 0, s>>>(partial, (int)blocks, out);
         return;
     }

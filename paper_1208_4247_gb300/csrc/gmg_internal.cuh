@@ -141,12 +141,16 @@ void resnorm(int d, int n, const double* u, const double* q, double* partial, do
 __global__ void k_sum_partials(const double* partial, int count, double* out);
 // The stopping-test norm of a red-black cycle fused with the next cycle's
 // first red half sweep (3D FP64 levels the diagonal walkers take, unless
-// GMG_NORM_AHEAD=0): the red-only norm of u into *out (norm = true) and one
-// red half sweep of u, the old red values kept in save.  red_restore puts
-// them back (u = save on the red interior nodes).
+// GMG_NORM_AHEAD=0): the red-only norm of u into *out (norm = true; plus
+// (may be NULL): *out = *plus + that norm) and one red half sweep of u, the
+// old red values kept in save.  red_restore puts them back (u = save on the
+// red interior nodes).  resnorm_black: the black nodes' sigma^2 sum (the
+// other half of a first norm whose red half red_ahead sums).
 bool red_ahead_applies(int d, int n);
 void red_ahead(int n, double* u, const double* q, double* save, double* partial, double* out,
-               bool norm, cudaStream_t s);
+               bool norm, cudaStream_t s, const double* plus = nullptr);
+void resnorm_black(int n, const double* u, const double* q, double* partial, double* out,
+                   cudaStream_t s);
 void red_restore(int n, double* u, const double* save, cudaStream_t s);
 }  // namespace fp64
 
