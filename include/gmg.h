@@ -118,8 +118,11 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
  * than maxit cycles have run.  f, u: device pointers (layout above).
  * iters_out (may be NULL): cycles run.  relres_out (may be NULL): final
  * relative residual.  Returns GMG_ERR_NOT_CONVERGED with a valid u when
- * maxit stops the loop.  Synchronises the handle's stream once per cycle to
- * read the residual norm. */
+ * maxit stops the loop.  The stopping test runs on the device: the cycles
+ * after the first run as one graph launch whose while node repeats a cycle
+ * and its norm until the test fails, and the host synchronises once per
+ * solve (once per cycle while per-kernel timing is on, or with
+ * GMG_DEVICE_LOOP=0 at create; results are the same bit for bit). */
 gmg_status gmg_solve(gmg_handle h, const double* f, double* u, double rtol,
                      int* iters_out, double* relres_out);
 

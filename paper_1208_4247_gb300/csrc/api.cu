@@ -32,6 +32,18 @@ const std::string& last_error() { return g_err; }
 using namespace gmg;
 using bf16 = __nv_bfloat16;
 
+namespace gmg {
+// Device side of the stopping loop (Algorithm 3's test after each cycle):
+// parameters written by the host before the loop graph runs, the cycle
+// count and the relative residual history written by the device.
+struct LoopState {
+    double res0, rtol, res;  // initial and latest ||h^2 f - A'u|| (scaled), rtol
+    int cap, stop, it, pad;  // cycle cap; stop on rtol; cycles run so far
+    double hist[1];          // [cap]: relative residual after each cycle
+};
+constexpr size_t kLoopHeader = offsetof(LoopState, hist);
+}  // namespace gmg
+
 struct gmg_handle_s {
     gmg_config cfg{};
     int device = 0;
@@ -49,6 +61,15 @@ struct gmg_handle_s {
     cudaGraphExec_t graph = nullptr;
     const double* graph_u = nullptr;  // level-0 iterate baked into the graph
     cudaGraphExec_t fmg_graph = nullptr;  // GMG_FMG: the first cycle of a solve
+    // while-node graph around one step: the stopping test runs on the device
+    // (k_loop_test), one launch and one sync per solve (timing off only)
+    cudaGraphExec_t loop_graph = nullptr;
+    cudaGraphConditionalHandle loop_cond = 0;
+    int loop_kernels = 0;         // kernel launches per loop iteration
+    int loop_cap = 0;             // history capacity of d_loop
+    LoopState* d_loop = nullptr;
+    LoopState* h_loop = nullptr;  // pinned
+    bool device_loop = true;      // GMG_DEVICE_LOOP=0 at create: host loop
     int fmg_kernels = 0;
     std::vector<KernelTimer::Pending> fmg_pending;
     std::vector<double> hist;
@@ -545,8 +566,9 @@ void enqueue_norm_ahead(gmg_handle h) {
 }
 
 // One step of the stopping loop: a plain cycle plus the FP64 norm, or one
-// refinement step; the squared scaled norm lands in h->h_res2.
-gmg_status enqueue_step(gmg_handle h) {
+// refinement step; the squared scaled norm lands in h->d_res2 (enqueue_step:
+// and is copied to h->h_res2).
+gmg_status enqueue_step_kernels(gmg_handle h) {
     const gmg_config& c = h->cfg;
     h->timer.begin_capture();
     gmg_status st = GMG_OK;
@@ -571,10 +593,79 @@ gmg_status enqueue_step(gmg_handle h) {
         st = enqueue_refinement<bf16>(h, h->lvb);
     }
     if (st != GMG_OK) return st;
+    GMG_CUDA_TRY(cudaGetLastError());
+    return GMG_OK;
+}
+
+gmg_status enqueue_step(gmg_handle h) {
+    gmg_status st = enqueue_step_kernels(h);
+    if (st != GMG_OK) return st;
     GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
                                  h->stream));
     GMG_CUDA_TRY(cudaGetLastError());
     return GMG_OK;
+}
+
+// The stopping test of Algorithm 3 after a cycle, on the device: it counts
+// the cycle, records res / res0, and lets the while node run another cycle
+// while it < cap, res is finite and (unless stop is off) res > rtol * res0
+// (the host loop's test, in the same FP64 operations).
+}  // namespace
+namespace gmg {
+__global__ void k_loop_test(const double* __restrict__ res2, LoopState* __restrict__ st,
+                            cudaGraphConditionalHandle cond) {
+    const int it = st->it + 1;
+    st->it = it;
+    const double res = sqrt(res2[0]);
+    st->res = res;
+    st->hist[it - 1] = st->res0 > 0.0 ? res / st->res0 : 0.0;
+    const bool more = it < st->cap && isfinite(res) && (!st->stop || res > st->rtol * st->res0);
+    cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+}  // namespace gmg
+namespace {
+
+// The loop graph: a while node whose body is one step (a cycle and its FP64
+// norm) followed by k_loop_test.  On failure the handle keeps the host loop.
+void build_loop_graph(gmg_handle h) {
+    cudaGraph_t g = nullptr;
+    cudaGraph_t body = nullptr;
+    bool capturing = false;
+    auto give_up = [&] {
+        if (capturing) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(h->stream, &tmp);
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        h->loop_graph = nullptr;
+    };
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return give_up();
+    if (cudaGraphConditionalHandleCreate(&h->loop_cond, g, 1, cudaGraphCondAssignDefault) !=
+        cudaSuccess)
+        return give_up();
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h->loop_cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) return give_up();
+    body = np.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return give_up();
+    capturing = true;
+    const int step_kernels = h->timer.graph_kernels;
+    h->timer.begin_capture();
+    if (enqueue_step_kernels(h) != GMG_OK) return give_up();
+    k_loop_test<<<1, 1, 0, h->stream>>>(h->d_res2, h->d_loop, h->loop_cond);
+    h->loop_kernels = h->timer.graph_kernels + 1;
+    h->timer.graph_kernels = step_kernels;
+    capturing = false;
+    if (cudaStreamEndCapture(h->stream, &body) != cudaSuccess) return give_up();
+    if (cudaGraphInstantiate(&h->loop_graph, g, 0) != cudaSuccess) return give_up();
+    cudaGraphDestroy(g);
 }
 
 // One full-multigrid pass (Algorithm 2) on the plain FP64 hierarchy, then the
@@ -678,6 +769,10 @@ gmg_status ensure_graph(gmg_handle h, double* u) {
         cudaGraphExecDestroy(h->fmg_graph);
         h->fmg_graph = nullptr;
     }
+    if (h->loop_graph) {
+        cudaGraphExecDestroy(h->loop_graph);
+        h->loop_graph = nullptr;
+    }
     h->lv[0].u[0] = u;
     gmg_status st;
     if (h->cfg.cycle == GMG_FMG) {
@@ -686,6 +781,7 @@ gmg_status ensure_graph(gmg_handle h, double* u) {
         h->fmg_pending = h->timer.pending;
     }
     if ((st = capture(h, &h->graph, enqueue_step)) != GMG_OK) return st;
+    if (h->device_loop && h->d_loop && !h->timer.enabled) build_loop_graph(h);
     h->graph_u = u;
     return GMG_OK;
 }
@@ -776,6 +872,37 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
     };
     while (it < cap && (!stop || res > rtol * res0)) {
         const bool fmg = it == 0 && h->fmg_graph;
+        if (!fmg && h->loop_graph && !h->timer.enabled && cap <= h->loop_cap) {
+            // the remaining cycles in one launch, the test on the device
+            LoopState* L = h->h_loop;
+            L->res0 = res0;
+            L->rtol = rtol;
+            L->res = res;
+            L->cap = cap;
+            L->stop = stop ? 1 : 0;
+            L->it = it;
+            GMG_CUDA_TRY(
+                cudaMemcpyAsync(h->d_loop, L, kLoopHeader, cudaMemcpyHostToDevice, h->stream));
+            GMG_CUDA_TRY(cudaGraphLaunch(h->loop_graph, h->stream));
+            GMG_CUDA_TRY(cudaMemcpyAsync(L, h->d_loop, kLoopHeader + sizeof(double) * cap,
+                                         cudaMemcpyDeviceToHost, h->stream));
+            GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+            const int it0 = it;
+            it = L->it;
+            h->timer.launches += (int64_t)(it - it0) * h->loop_kernels;
+            for (int k = it0; k < it; ++k) {
+                h->hist.push_back(L->hist[k]);
+                if (!stop && relres_out) relres_out[k] = L->hist[k];
+            }
+            res = L->res;
+            if (!std::isfinite(res)) {
+                if (iters_out) *iters_out = it;
+                if ((st = finish()) != GMG_OK) return st;
+                set_error("residual norm became non-finite");
+                return GMG_ERR_NONFINITE;
+            }
+            break;
+        }
         GMG_CUDA_TRY(cudaGraphLaunch(fmg ? h->fmg_graph : h->graph, h->stream));
         GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
         if (fmg) {
@@ -870,6 +997,8 @@ gmg_status gmg_destroy(gmg_handle h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->fmg_graph) cudaGraphExecDestroy(h->fmg_graph);
+    if (h->loop_graph) cudaGraphExecDestroy(h->loop_graph);
+    if (h->h_loop) cudaFreeHost(h->h_loop);
     h->timer.destroy();
     for (void* p : h->allocs) cudaFree(p);
     if (h->h_res2) cudaFreeHost(h->h_res2);
@@ -892,6 +1021,7 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     h->user_stream = (cudaStream_t)cuda_stream;
     if (const char* v = std::getenv("GMG_FUSED_RB")) h->fused_rb = std::strcmp(v, "1") == 0;
     if (const char* v = std::getenv("GMG_TAIL_N")) h->tail_max = std::max(0, std::atoi(v));
+    if (const char* v = std::getenv("GMG_DEVICE_LOOP")) h->device_loop = std::strcmp(v, "0") != 0;
     auto fail = [&](gmg_status s) {
         gmg_destroy(h);
         return s;
@@ -930,6 +1060,13 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     if ((st = dev_alloc(h, &h->partial, np)) != GMG_OK) return fail(st);
     if ((st = dev_alloc(h, &h->d_res2, 2)) != GMG_OK) return fail(st);
     if (cudaMallocHost((void**)&h->h_res2, sizeof(double)) != cudaSuccess) {
+        set_error("cudaMallocHost failed");
+        return fail(GMG_ERR_ALLOC);
+    }
+    h->loop_cap = std::max(cfg->maxit, 1);
+    const size_t loop_bytes = kLoopHeader + sizeof(double) * h->loop_cap;
+    if ((st = dev_alloc(h, (char**)&h->d_loop, (int64_t)loop_bytes)) != GMG_OK) return fail(st);
+    if (cudaMallocHost((void**)&h->h_loop, loop_bytes) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         return fail(GMG_ERR_ALLOC);
     }

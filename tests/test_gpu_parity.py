@@ -456,6 +456,54 @@ def test_fused_stopping_norm_matches_unfused_schedule(torch_cuda, tmp_path):
     assert np.array_equal(uz[1:-1, 1:-1, 1:-1], u0[1:-1, 1:-1, 1:-1])
 
 
+def test_device_stopping_loop_matches_host_loop(torch_cuda, tmp_path):
+    """The stopping loop on the device (a while node around one cycle and
+    its norm, the test in a one-thread kernel; default with timing off)
+    against the host loop (GMG_DEVICE_LOOP=0, in a child process): plain,
+    FMG, refinement and 2D Jacobi solves, a solve that hits maxit, fixed and
+    zero cycle counts give the same u, cycle counts and relative-residual
+    histories bit for bit."""
+    import json
+    import os
+    import subprocess
+    import sys
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    # (label, d, n, Solver kwargs, action: "solve" or a cycle count)
+    cases = [("v3", 3, 128, {}, "solve"), ("fmg3", 3, 128, {"cycle": "fmg"}, "solve"),
+             ("maxit", 3, 128, {"maxit": 3}, "solve"), ("fixed", 3, 64, {}, 5),
+             ("zero", 3, 64, {}, 0), ("fp32", 3, 64, {"precision": "fp32"}, "solve"),
+             ("wj2", 2, 256, {"smoother": "wjacobi", "omega": 0.8}, "solve")]
+    for label, d, n, kw, act in cases:
+        np.save(tmp_path / f"f_{label}.npy", inputs.rhs_uniform(d, n, 40))
+    script = (
+        "import numpy as np, torch, json\n"
+        "from paper_1208_4247_gb300.gmg import Solver\n"
+        f"cases = {cases!r}\n"
+        "out = {}\n"
+        "for label, d, n, kw, act in cases:\n"
+        f"    f = torch.from_numpy(np.load(r'{tmp_path}/f_' + label + '.npy')).cuda()\n"
+        "    u = torch.zeros_like(f)\n"
+        "    S = Solver(d, n, **kw)\n"
+        "    r = S.solve(f, u, rtol=1e-10) if act == 'solve' else S.cycles(f, u, act)\n"
+        "    out[label] = [list(r), S.history()]\n"
+        "    S.close()\n"
+        f"    np.save(r'{tmp_path}/u_' + label + '.npy', u.cpu().numpy())\n"
+        f"json.dump(out, open(r'{tmp_path / 'ref.json'}', 'w'))\n")
+    env = dict(os.environ, GMG_DEVICE_LOOP="0")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", script], check=True, env=env, cwd=root)
+    ref = json.load(open(tmp_path / "ref.json"))
+    for label, d, n, kw, act in cases:
+        fd = _dev(torch, np.load(tmp_path / f"f_{label}.npy"))
+        ud = torch.zeros_like(fd)
+        with Solver(d, n, **kw) as S:
+            r = S.solve(fd, ud, rtol=1e-10) if act == "solve" else S.cycles(fd, ud, act)
+            hist = S.history()
+        assert [list(r), hist] == ref[label], label
+        assert np.array_equal(ud.cpu().numpy(), np.load(tmp_path / f"u_{label}.npy")), label
+
+
 @pytest.mark.parametrize("d,n,expect,tol", [(3, 256, 4.4371e-6, 1e-4), (3, 512, 1.1093e-6, 1e-4),
                                             (2, 256, 6.2750e-6, 1e-4), (2, 4096, 2.4511e-8, 1e-3)])
 def test_converged_solve_reproduces_discretisation_error(torch_cuda, d, n, expect, tol):
