@@ -535,6 +535,61 @@ def oracle_solve_timed(f, cores_note):
     return it, dt
 
 
+ORACLE_CORES_SCRIPT = r"""
+import json, time
+import numpy as np
+import oracle
+from paper_1208_4247_gb300 import inputs
+oracle.build()
+out = {}
+f = inputs.rhs_sine_plus_uniform(2, 256, 1)
+cfg = oracle.make_cfg(2, 256, 0, oracle.WJACOBI, 0.8, 2, 2, 1)
+u = np.zeros_like(f)
+t0 = time.perf_counter()
+it, hist = oracle.solve(cfg, f, u, 1e-10, 100)
+out["2d_257_wj"] = {"s_per_solve": time.perf_counter() - t0, "cycles": it}
+for key, n, seed in (("3d_257_rb", 256, 2), ("3d_513_rb", 512, 3)):
+    f = inputs.rhs_uniform(3, n, seed) if n == 256 else inputs.rhs_sine_plus_gauss(3, n, seed)
+    b = oracle.scale_rhs(f)
+    u = np.zeros_like(f)
+    cfg = oracle.make_cfg(3, n, 0, oracle.RBGS, 0.8, 2, 2, 1)
+    t0 = time.perf_counter()
+    oracle.vcycle(cfg, b, u)
+    out[key] = {"s_per_cycle": time.perf_counter() - t0}
+print(json.dumps(out))
+"""
+
+
+def run_oracle_cores(cycles_257, cycles_513):
+    """The CPU oracle on all host cores and on one core (OpenMP threads set in
+    a child process): the 2D 257^2 weighted-Jacobi V(2,2) workload as a full
+    solve; 3D 257^3 and 513^3 red-black V(2,2) as one timed V-cycle each,
+    converted to DOF/s to 1e-10 with the cycle counts of the same solves on
+    the GPU (the oracle takes the same counts: parity tests)."""
+    import subprocess
+    out = {}
+    for label, threads in (("all_cores", cores()), ("one_core", 1)):
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        r = subprocess.run([sys.executable, "-c", ORACLE_CORES_SCRIPT], env=env,
+                           capture_output=True, text=True, cwd=os.path.dirname(os.path.abspath(__file__)))
+        if r.returncode != 0:
+            out[label] = {"error": r.stderr.strip().splitlines()[-1] if r.stderr else "failed"}
+            continue
+        m = json.loads(r.stdout.strip().splitlines()[-1])
+        w = m["2d_257_wj"]
+        out[label] = {
+            "threads": threads,
+            "2d_257_wj_v22": {"dof_per_s": 255 ** 2 / w["s_per_solve"], "s": w["s_per_solve"],
+                              "cycles": w["cycles"], "sample": "one full solve"},
+            "3d_257_rb_v22": {"dof_per_s": 255 ** 3 / (m["3d_257_rb"]["s_per_cycle"] * cycles_257),
+                              "s_per_cycle": m["3d_257_rb"]["s_per_cycle"], "cycles": cycles_257,
+                              "sample": "one V-cycle (no norm), times the cycle count"},
+            "3d_513_rb_v22": {"dof_per_s": 511 ** 3 / (m["3d_513_rb"]["s_per_cycle"] * cycles_513),
+                              "s_per_cycle": m["3d_513_rb"]["s_per_cycle"], "cycles": cycles_513,
+                              "sample": "one V-cycle (no norm), times the cycle count"}}
+    return out
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -754,6 +809,8 @@ def run_ours(args, rank, ws, local):
         cpu = {"value": UNKNOWNS / dt, "unit": "DOF/s", "cores": cores(), "kind": "oracle",
                "sample": f"{len(times)} full 257^3 solves to 1e-10 ({it_o} cycles, "
                          f"{dt:.2f} s each, {sum(times):.1f} s total, OpenMP on all cores)"}
+        c513 = (forms or {}).get("forms", {}).get("fp64_plain", {}).get("cycles") or 11
+        cpu["by_cores"] = run_oracle_cores(cycles, c513)
     line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
