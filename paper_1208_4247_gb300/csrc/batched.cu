@@ -101,13 +101,18 @@ __device__ inline float nsum(const T* u, int64_t p, int64_t sy, int64_t sz, bool
 __device__ inline int64_t off_u(const BLevel& L, int which) { return which ? L.u1 : L.u0; }
 
 // smoothing sweep on the items' interior nodes: weighted Jacobi (src -> dst)
-// or one colour of red-black Gauss-Seidel (in place, src == dst).  (Loading
-// four nodes' operands before their stores measured slower here: 93 vs 82 ms
-// of sweeps in the 512-solve batch.)
+// or one colour of red-black Gauss-Seidel (in place, src == dst).  pool_in
+// and pool_out are the same pool: what a launch reads through pool_in (the
+// src iterate, or the other colour, and q) is never written during the
+// launch, so the two may be declared not to alias, which lets the compiler
+// issue a node's loads ahead of the previous node's store.  (Loading four
+// nodes' operands ahead by hand measured slower: 93 vs 82 ms of sweeps.)
 template <typename T>
 __global__ void __launch_bounds__(256) k_smooth(const Item* __restrict__ items, int nitems,
                                                 const BSolve* __restrict__ sv,
-                                                const BLevel* __restrict__ lv, T* pool,
+                                                const BLevel* __restrict__ lv,
+                                                const T* __restrict__ pool_in,
+                                                T* __restrict__ pool_out,
                                                 const int* __restrict__ active, int src, int dst,
                                                 int color, float omega) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -117,9 +122,9 @@ __global__ void __launch_bounds__(256) k_smooth(const Item* __restrict__ items, 
         const bool three = L.d == 3;
         const float c = three ? 1.f / 6.f : 0.25f;
         const int64_t sy = L.n + 1, sz = three ? sy * sy : 0;
-        const T* u = pool + off_u(L, src);
-        T* uo = pool + off_u(L, dst);
-        const T* q = pool + L.q;
+        const T* u = pool_in + off_u(L, src);
+        T* uo = pool_out + off_u(L, dst);
+        const T* q = pool_in + L.q;
         for (int t = threadIdx.x; t < w.count; t += blockDim.x) {
             int i, j, k;
             const int64_t p = node_of(L, (uint32_t)(w.start + t), i, j, k);
@@ -135,11 +140,14 @@ __global__ void __launch_bounds__(256) k_smooth(const Item* __restrict__ items, 
     }
 }
 
-// r = sigma on the items' interior nodes
+// r = sigma on the items' interior nodes (pool_in / pool_out: the same pool,
+// as in k_smooth; u and q are not written during the launch)
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual(const Item* __restrict__ items, int nitems,
                                                   const BSolve* __restrict__ sv,
-                                                  const BLevel* __restrict__ lv, T* pool,
+                                                  const BLevel* __restrict__ lv,
+                                                  const T* __restrict__ pool_in,
+                                                  T* __restrict__ pool_out,
                                                   const int* __restrict__ active, int src) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const Item w = items[it];
@@ -148,9 +156,9 @@ __global__ void __launch_bounds__(256) k_residual(const Item* __restrict__ items
         const bool three = L.d == 3;
         const float c = three ? 1.f / 6.f : 0.25f;
         const int64_t sy = L.n + 1, sz = three ? sy * sy : 0;
-        const T* u = pool + off_u(L, src);
-        const T* q = pool + L.q;
-        T* r = pool + L.r;
+        const T* u = pool_in + off_u(L, src);
+        const T* q = pool_in + L.q;
+        T* r = pool_out + L.r;
         for (int t = threadIdx.x; t < w.count; t += blockDim.x) {
             const int64_t p = node_of(L, (uint32_t)(w.start + t));
             r[p] = Num<T>::st(fmaf(c, nsum(u, p, sy, sz, three), Num<T>::ld(q[p])) -
@@ -160,11 +168,14 @@ __global__ void __launch_bounds__(256) k_residual(const Item* __restrict__ items
 }
 
 // q_c = 4 FW(r) on the items' coarse interior nodes (item level = fine
-// level); u_c = 0, or u_c = q_c on a one-unknown coarsest grid
+// level); u_c = 0, or u_c = q_c on a one-unknown coarsest grid.  pool_in /
+// pool_out: the same pool, as in k_smooth (r is not written here).
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(const Item* __restrict__ items, int nitems,
                                                   const BSolve* __restrict__ sv,
-                                                  const BLevel* __restrict__ lv, T* pool,
+                                                  const BLevel* __restrict__ lv,
+                                                  const T* __restrict__ pool_in,
+                                                  T* __restrict__ pool_out,
                                                   const int* __restrict__ active) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const Item w = items[it];
@@ -174,7 +185,7 @@ __global__ void __launch_bounds__(256) k_restrict(const Item* __restrict__ items
         const bool three = F.d == 3;
         const int64_t sy = F.n + 1, sz = three ? sy * sy : 0;
         const int64_t cy = C.n + 1, cz = three ? cy * cy : 0;
-        const T* r = pool + F.r;
+        const T* r = pool_in + F.r;
         for (int t = threadIdx.x; t < w.count; t += blockDim.x) {
             int I, J, K;
             const int64_t P = node_of(C, (uint32_t)(w.start + t), I, J, K);
@@ -189,8 +200,8 @@ __global__ void __launch_bounds__(256) k_restrict(const Item* __restrict__ items
                         const float wgt = (three ? 0.5f : 1.f) * ldexpf(1.f, -odd);
                         v = fmaf(wgt, Num<T>::ld(r[p + dz * sz + dy * sy + dx]), v);
                     }
-            T* qc = pool + C.q;
-            T* uc = pool + C.u0;
+            T* qc = pool_out + C.q;
+            T* uc = pool_out + C.u0;
             qc[P] = Num<T>::st(v);
             uc[P] = C.n == 2 ? Num<T>::st(v) : Num<T>::st(0.f);
         }
@@ -512,15 +523,15 @@ gmg_status enqueue_step(gmg_batch b, double rtol2) {
                     launch_op<T>(b, "b_rb_half", g, r, 1.5 * w, 3.0, nn,
                                  [&](int grid, const Item* it, int ni) {
                                      k_smooth<T><<<grid, 256, 0, b->stream>>>(
-                                         it, ni, b->ds, b->dl, pool, b->active, cur[g], cur[g],
-                                         color, omega);
+                                         it, ni, b->ds, b->dl, pool, pool, b->active, cur[g],
+                                         cur[g], color, omega);
                                  });
             } else {
                 launch_op<T>(b, "b_wj_sweep", g, r, 3 * w, 8.0, nn,
                              [&](int grid, const Item* it, int ni) {
                                  k_smooth<T><<<grid, 256, 0, b->stream>>>(
-                                     it, ni, b->ds, b->dl, pool, b->active, cur[g], cur[g] ^ 1, -1,
-                                     omega);
+                                     it, ni, b->ds, b->dl, pool, pool, b->active, cur[g],
+                                     cur[g] ^ 1, -1, omega);
                              });
                 cur[g] ^= 1;
             }
@@ -534,14 +545,14 @@ gmg_status enqueue_step(gmg_batch b, double rtol2) {
             const int64_t nn = range_nodes(b, b->fine[g]);
             launch_op<T>(b, "b_residual", g, b->fine[g], 3 * w, 7.0, nn,
                          [&](int grid, const Item* it, int ni) {
-                             k_residual<T><<<grid, 256, 0, b->stream>>>(it, ni, b->ds, b->dl, pool,
-                                                                        b->active, cur[g]);
+                             k_residual<T><<<grid, 256, 0, b->stream>>>(
+                                 it, ni, b->ds, b->dl, pool, pool, b->active, cur[g]);
                          });
             const int64_t nc = range_nodes(b, b->coarse[g]);
             launch_op<T>(b, "b_restrict", g, b->coarse[g], 10 * w, 27.0, nc,
                          [&](int grid, const Item* it, int ni) {
                              k_restrict<T><<<grid, 256, 0, b->stream>>>(it, ni, b->ds, b->dl,
-                                                                        pool, b->active);
+                                                                        pool, pool, b->active);
                          });
             cur[g - 1] = 0;
         }
