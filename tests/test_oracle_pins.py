@@ -160,6 +160,10 @@ def test_vcycle_equals_dense_cycle(case):
     (2, 32, oracle.RBGS, 0.8, 1, 0.074),
     (2, 32, oracle.RBGS, 0.8, 2, 0.041),
     (3, 8, oracle.RBGS, 0.8, 2, None),
+    (3, 16, oracle.RBGS, 0.8, 1, 0.183),
+    (3, 16, oracle.RBGS, 0.8, 2, 0.076),
+    (3, 16, oracle.WJACOBI, 6.0 / 7.0, 1, 0.495),
+    (3, 16, oracle.WJACOBI, 0.8, 1, 0.523),
 ])
 def test_two_grid_contraction(d, n, sm, om, nu, rho_ref):
     """Brute-force two-grid spectral radius vs the oracle's asymptotic
