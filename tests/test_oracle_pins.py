@@ -187,6 +187,33 @@ def test_two_grid_contraction(d, n, sm, om, nu, rho_ref):
     assert rate == pytest.approx(rho, rel=0.02)
 
 
+@pytest.mark.parametrize("d,ns,sm,om,nu,ntg", [
+    (2, (64, 128, 256), oracle.RBGS, 0.8, 1, 16),
+    (2, (64, 128, 256), oracle.WJACOBI, 0.8, 2, 16),
+    (3, (16, 32, 64), oracle.RBGS, 0.8, 2, 8),
+    (3, (16, 32, 64), oracle.WJACOBI, 6.0 / 7.0, 1, 8),
+])
+def test_vcycle_contraction_is_h_independent(d, ns, sm, om, nu, ntg):
+    """The multigrid property for the full-depth V-cycle (down to 3^d): its
+    asymptotic contraction stays within 3% as h halves (a coarse level with
+    the wrong scaling or transfer breaks this), and it lies near the
+    brute-force two-grid factor of a small grid (between 0.95x and 2x)."""
+    E = dm.vcycle_error_matrix(d, ntg, 2, sm, om, nu, nu, 200)
+    rho_tg = max(abs(np.linalg.eigvals(E)))
+    rates = []
+    for n in ns:
+        cfg = oracle.make_cfg(d, n, 0, sm, om, nu, nu, 1)
+        u = dm.from_vec(np.random.default_rng(4).standard_normal((n - 1) ** d), d, n)
+        b = np.zeros_like(u)
+        norms = []
+        for _ in range(40):
+            oracle.vcycle(cfg, b, u)
+            norms.append(np.linalg.norm(u))
+        rates.append((norms[-1] / norms[-11]) ** 0.1)
+    assert max(rates) <= 1.03 * min(rates), rates
+    assert all(0.95 * rho_tg <= r <= 2.0 * rho_tg for r in rates), (rho_tg, rates)
+
+
 @pytest.mark.parametrize("d,n,sm,om", [
     (2, 16, oracle.RBGS, 0.8), (2, 16, oracle.WJACOBI, 0.8),
     (3, 8, oracle.RBGS, 0.8), (3, 8, oracle.WJACOBI, 6.0 / 7.0),
