@@ -638,3 +638,43 @@ def test_paper_variant_reproduces_smoother_table(L):
             it += 1
         assert it == ref["gs2"]
         assert count(oracle.RBGS, 0.8) == 8
+
+
+def _mcgs_error_matrix(d, n, backward):
+    """Error propagation of one multi-colour sweep (b = 0), column by column."""
+    m = (n - 1) ** d
+    return np.array([dm.mcgs_sweep(d, n, np.zeros(m), e, backward) for e in np.eye(m)]).T
+
+
+def _paper_vcycle_error(d, n, nu1, nu2):
+    """Algorithm 1 with the paper's smoother and transfers, as a dense matrix:
+    forward multi-colour sweeps down, backward sweeps up, R of eq.
+    Restriction2d (x 4), P of eq. Prolongation2d, coarse iterates from zero,
+    the one-unknown coarsest grid solved exactly."""
+    if n == 2:
+        return np.zeros((1, 1))
+    nc = n // 2
+    A = dm.lap(d, n)
+    Ac = dm.lap(d, nc)
+    Ec = _paper_vcycle_error(d, nc, nu1, nu2)
+    Bc = (np.eye(Ac.shape[0]) - Ec) @ np.linalg.inv(Ac)
+    CG = np.eye(A.shape[0]) - dm.prolong_diag(d, nc) @ Bc @ dm.restrict_simplex(d, n) @ A
+    Sf = np.linalg.matrix_power(_mcgs_error_matrix(d, n, False), nu1)
+    Sb = np.linalg.matrix_power(_mcgs_error_matrix(d, n, True), nu2)
+    return Sb @ CG @ Sf
+
+
+@pytest.mark.parametrize("d,n,nu1,nu2", [(2, 8, 1, 1), (2, 16, 2, 1), (3, 8, 1, 2)])
+def test_paper_variant_vcycle_equals_dense_cycle(d, n, nu1, nu2):
+    """The paper's variant of Algorithm 1 (full depth) as a linear map:
+    u1 = E u0 + (I - E) A'^-1 b with E composed from the dense operators."""
+    rng = np.random.default_rng(9)
+    E = _paper_vcycle_error(d, n, nu1, nu2)
+    A = dm.lap(d, n)
+    u0 = rng.standard_normal((n - 1) ** d)
+    b = rng.standard_normal((n - 1) ** d)
+    ref = E @ u0 + (np.eye(len(u0)) - E) @ np.linalg.solve(A, b)
+    cfg = oracle.make_cfg(d, n, 0, oracle.MCGS, 0.8, nu1, nu2, 1, transfer=oracle.SIMPLEX)
+    u = dm.from_vec(u0, d, n)
+    oracle.vcycle(cfg, dm.from_vec(b, d, n), u)
+    assert np.max(np.abs(dm.to_vec(u) - ref)) <= 1e-12 * np.max(np.abs(ref))
