@@ -22,12 +22,15 @@
  *     written, one rounding per operation, no fused multiply-add.
  *
  * Pins (tests/test_oracle_pins.py): sine eigenpairs of A' (section 2.2),
- * dense direct solves, the closed-form discretisation error that the paper's
- * FFT error tables print, brute-force dense two-grid spectral radii, the
- * triangular-solve form of red-black Gauss-Seidel, the adjoint relation
- * FW = P^T / 2^d and exact interpolation of linear functions; for the paper's
- * own variant (multi-colour GS, its restriction and prolongation) the same
- * kinds of dense checks plus the iteration counts of its smoother table.
+ * dense direct solves, sine-transform (DST-I) direct solves at full workload
+ * sizes, the closed-form discretisation error that the paper's FFT error
+ * tables print, brute-force dense two-grid spectral radii (2D and 3D), the
+ * h-independence of the full V-cycle's contraction, the triangular-solve form
+ * of red-black Gauss-Seidel, the adjoint relation FW = P^T / 2^d and exact
+ * interpolation of linear functions; for the paper's own variant (multi-colour
+ * GS, its restriction and prolongation) the same kinds of dense checks, its
+ * whole V-cycle as a dense composition, and the iteration counts of its
+ * smoother table.
  */
 #include <math.h>
 #include <stdint.h>
