@@ -93,9 +93,14 @@ typedef struct gmg_handle_s* gmg_handle;
  * transfers. */
 gmg_status gmg_config_init(gmg_config* cfg, int d, int n);
 
-/* Create a solver for *cfg on the current CUDA device.  cuda_stream is a
- * cudaStream_t (NULL = legacy default stream) on which every later call on
- * the handle is ordered.  Allocates the level hierarchy on the device.
+/* Create a solver for *cfg on the current CUDA device: the grid hierarchy of
+ * Algorithm 1 (n, n/2, ..., down to the 3^d grid or cfg->levels grids;
+ * section 3.1) with its per-level arrays.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream) on which every later call on the handle is
+ * ordered.  Allocates the level hierarchy on the device; *out receives the
+ * handle, owned by the caller until gmg_destroy.  Errors: GMG_ERR_ARG for a
+ * bad configuration (before any device work), GMG_ERR_ALLOC when device
+ * memory runs out (nothing is left allocated), GMG_ERR_CUDA otherwise.
  * Environment: GMG_FUSED_RB=1 makes GMG_FP32_IR handles in 3D with red-black
  * smoothing run each sweep as one fused z-streaming kernel on a dense inner
  * layout instead of two half sweeps on the colour-split one (same results
@@ -126,8 +131,9 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
 gmg_status gmg_solve(gmg_handle h, const double* f, double* u, double rtol,
                      int* iters_out, double* relres_out);
 
-/* As gmg_solve, but f and u are HOST pointers: f and the initial u are copied
- * to device buffers owned by the handle, the solve runs, u is copied back. */
+/* Algorithm 3 as gmg_solve, but f and u are HOST pointers: f and the initial
+ * u are copied to device buffers owned by the handle, the solve runs, u is
+ * copied back.  Errors as gmg_solve. */
 gmg_status gmg_solve_host(gmg_handle h, const double* f_host, double* u_host, double rtol,
                           int* iters_out, double* relres_out);
 
@@ -163,8 +169,10 @@ gmg_status gmg_residual_norm(gmg_handle h, const double* f, double* u, double* n
 gmg_status gmg_residual_norm_noalloc(int d, int n, const double* f, const double* u,
                                      double* norm_dev, void* cuda_stream);
 
-/* Relative-residual history of the last solve / cycles call: writes up to
- * cap entries to relres (host), the count to *count. */
+/* Relative-residual history of the last solve / cycles call (Algorithm 3's
+ * res / res_0 after each cycle): writes up to cap entries to relres (host),
+ * the count to *count (count may be NULL).  GMG_ERR_ARG for a NULL handle or
+ * a NULL relres with cap > 0. */
 gmg_status gmg_history(gmg_handle h, double* relres, int cap, int* count);
 
 /* Per-kernel device timing (diagnostics, the paper's per-function and
@@ -189,7 +197,7 @@ typedef struct {
 gmg_status gmg_timing_report(gmg_handle h, gmg_kernel_stat* out, int cap, int* count,
                              int64_t* launches_out);
 
-/* Zero the timing records and the launch counter. */
+/* Zero the timing records and the launch counter (section 5.3 profiles). */
 gmg_status gmg_timing_reset(gmg_handle h);
 
 /* ------------------------------------------------------- learned smoother
@@ -212,7 +220,8 @@ gmg_status gmg_timing_reset(gmg_handle h);
  * added to u.  Re-captures the cycle graph. */
 gmg_status gmg_set_learned_weights(gmg_handle h, int level, const float* weights);
 
-/* y = N(x) on the interior nodes of a 2D/3D grid of n intervals (x, y:
+/* No counterpart in the paper (the learned smoother above).
+ * y = N(x) on the interior nodes of a 2D/3D grid of n intervals (x, y:
  * device FP64, all nodes; x zero on the boundary).  tensor_cores = 0: CUDA-
  * core kernels with FP32 activations (the training path); 1: the fused
  * tensor-core kernel the V-cycle uses (BF16 x and hidden activations,
@@ -220,7 +229,8 @@ gmg_status gmg_set_learned_weights(gmg_handle h, int level, const float* weights
 gmg_status gmg_learned_conv(int d, int n, const float* weights, const double* x, double* y,
                             int tensor_cores, void* cuda_stream);
 
-/* Two-grid contraction loss L = ||S(CG(S(e0)))||^2 / ||e0||^2 of the error e0
+/* No counterpart in the paper (the learned smoother's training loss).
+ * Two-grid contraction loss L = ||S(CG(S(e0)))||^2 / ||e0||^2 of the error e0
  * (device FP64, all nodes, zero boundary) on a grid of n intervals, with
  * S e = e - N(A'e/(2d)) and CG e = e - P A_c'^{-1} 4 FW(A'e), the coarse
  * system solved by coarse_cycles red-black V(2,2) cycles.  *loss_out: L;
@@ -230,7 +240,8 @@ gmg_status gmg_learned_loss_grad(int d, int n, const float* weights, const doubl
                                  int coarse_cycles, double* loss_out, double* grad_out,
                                  void* cuda_stream);
 
-/* Train the weights on the GPU: `steps` Adam steps (learning rate lr) on the
+/* No counterpart in the paper (training of the learned smoother).
+ * Train the weights on the GPU: `steps` Adam steps (learning rate lr) on the
  * mean two-grid loss over `batch` error samples per step, each sample the
  * error left by pair_cycles plain red-black V(1,1) cycles applied to seeded
  * white noise (seed) on a grid of n intervals.  w_init -> w_out (host, layout
@@ -251,9 +262,12 @@ typedef struct gmg_fft_s* gmg_fft;
 /* d = 2 or 3, n a power of two (2D up to 8192, 3D up to 1024); allocates
  * about 3 (n+1)^d doubles of work space and two cuFFT plans. */
 gmg_status gmg_fft_create(int d, int n, void* cuda_stream, gmg_fft* out);
-/* u = A'^-1 h^2 f on the interior, 0 on the boundary (f, u device pointers,
- * layout above).  Synchronises the handle's stream. */
+/* Section 2.3: u = A'^-1 h^2 f on the interior, 0 on the boundary (f, u
+ * device pointers, layout above).  Synchronises the handle's stream.
+ * Errors: GMG_ERR_ARG for NULL arguments, GMG_ERR_CUDA for a failed
+ * transform or launch. */
 gmg_status gmg_fft_solve(gmg_fft h, const double* f, double* u);
+/* Release the plans and work space of h.  NULL is a no-op. */
 gmg_status gmg_fft_destroy(gmg_fft h);
 
 /* ---------------------------------------------------------------- batches
@@ -266,7 +280,8 @@ gmg_status gmg_fft_destroy(gmg_fft h);
  * residual, update and norm; GMG_FP64: plain cycles) with its smoother and
  * sweeps; each solve stops on its own FP64 relative residual (converged
  * solves are masked on the device).  One refinement step of the whole batch
- * is one captured CUDA graph. */
+ * is one captured CUDA graph.  No counterpart in the paper: each solve runs
+ * Algorithms 1 and 3, the batching is this library's. */
 typedef struct gmg_batch_s* gmg_batch;
 
 /* count solves; d[i], n[i] per solve (as in gmg_config); *common gives the
@@ -284,11 +299,13 @@ gmg_status gmg_batch_create(int count, const int* d, const int* n, const gmg_con
 gmg_status gmg_batch_solve(gmg_batch b, const double* const* f, double* const* u, double rtol,
                            int* iters_out, double* relres_out, int* steps_out);
 
-/* Per-kernel timing of the batch graph, as gmg_set_timing / gmg_timing_report. */
+/* Per-kernel timing of the batch graph, as gmg_set_timing / gmg_timing_report
+ * (section 5.3 profiles). */
 gmg_status gmg_batch_set_timing(gmg_batch b, int enable);
 gmg_status gmg_batch_timing_report(gmg_batch b, gmg_kernel_stat* out, int cap, int* count,
                                    int64_t* launches_out);
 
+/* Release every device and host resource of the batch.  NULL is a no-op. */
 gmg_status gmg_batch_destroy(gmg_batch b);
 
 /* ------------------------------------------- the problem statement's names
@@ -349,13 +366,16 @@ gmg_status gmg_smoother_train(gmg_handle h, const gmg_train_config* tc, const fl
 gmg_status gmg_smoother_save(gmg_handle h, void* blob, size_t cap, size_t* bytes_out);
 gmg_status gmg_smoother_load(gmg_handle h, const void* blob, size_t bytes);
 
-/* Release every device and host resource of the handle.  NULL is a no-op. */
+/* Release every device and host resource of the handle.  NULL is a no-op.
+ * (A library service; no counterpart in the paper.) */
 gmg_status gmg_destroy(gmg_handle h);
 
-/* Message of the calling thread's last failed call ("" if none). */
+/* Message of the calling thread's last failed call ("" if none); owned by
+ * the library, valid until that thread's next call.  A library service; no
+ * counterpart in the paper. */
 const char* gmg_last_error(void);
 
-/* Version of this ABI (GMG_ABI_VERSION). */
+/* Version of this ABI (GMG_ABI_VERSION).  A library service. */
 int gmg_abi_version(void);
 #define GMG_ABI_VERSION 1
 
