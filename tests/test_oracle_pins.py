@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import dense_mg as dm
+from paper_1208_4247_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -298,14 +299,12 @@ def test_closed_form_matches_paper_fft_table():
         assert e == pytest.approx(cf, rel=4e-3 if d == 2 else 6e-4), (d, L)
 
 
-@pytest.mark.parametrize("d,Ls", [(2, [6, 7, 8, 9]), (3, [4, 5, 6])])
+@pytest.mark.parametrize("d,Ls", [(2, [6, 7, 8, 9]), (3, [4, 5, 6, 7])])
 def test_discretisation_error_closed_form_and_order(d, Ls):
     """GMG solved to 1e-12 reproduces the closed-form error; O(h^2)."""
     errs = []
     for L in Ls:
         n = 2 ** L
-        ue = oracle_u = None
-        from paper_1208_4247_gb300 import inputs
         ue = inputs.manufactured_u(d, n)
         f = np.ascontiguousarray(d * np.pi ** 2 * ue)
         u = np.zeros_like(f)
@@ -317,6 +316,21 @@ def test_discretisation_error_closed_form_and_order(d, Ls):
     ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
     for r in ratios:
         assert r == pytest.approx(4.0, rel=0.02)
+
+
+def test_discretisation_error_at_257_cubed():
+    """At the 257^3 workload grid the converged oracle reproduces the closed
+    form and the paper's FFT error for L = 8 (4.437e-6).  rtol is 1e-11: the
+    FP64 residual floor of this grid is about 1e-12."""
+    d, n = 3, 256
+    ue = inputs.manufactured_u(d, n)
+    f = np.ascontiguousarray(d * np.pi ** 2 * ue)
+    u = np.zeros_like(f)
+    oracle.solve(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1), f, u, rtol=1e-11, maxit=50)
+    err = np.sqrt((1.0 / n) ** d * np.sum((u - ue) ** 2))
+    assert err == pytest.approx(_closed_form_error(d, n), rel=1e-6)
+    paper = [e for dd, L, e in _golden() if (dd, L) == (3, 8)]
+    assert paper and err == pytest.approx(paper[0], rel=6e-4)
 
 
 def test_solver_reaches_rtol_and_history_monotone():
