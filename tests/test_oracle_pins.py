@@ -334,7 +334,6 @@ def test_discretisation_error_at_257_cubed():
 
 
 def test_solver_reaches_rtol_and_history_monotone():
-    from paper_1208_4247_gb300 import inputs
     n = 64
     f = inputs.rhs_uniform(3, n, 2)
     u = np.zeros_like(f)
@@ -514,7 +513,6 @@ def test_fmg_reaches_discretisation_error(d, n, nu, ok):
     """The paper's FMG-vs-FFT finding (section 5.4): one FMG(1,2) pass reaches
     the discretisation error in 2D, while 3D needs FMG(3,3); fewer sweeps in 3D
     leave an error well above it.  Error in the continuous solution, ||.||_h."""
-    from paper_1208_4247_gb300 import inputs
     ue = inputs.manufactured_u(d, n)
     f = np.ascontiguousarray(d * np.pi ** 2 * ue)
     b = oracle.scale_rhs(f)
