@@ -157,13 +157,19 @@ gmg_status gmg_residual_norm(gmg_handle h, const double* f, double* u, double* n
  * gmg_handle.  No handle: d, n as in gmg_config; f, u: device pointers in the
  * layout above (u is read only, its boundary nodes are taken as 0);
  * norm_dev: device pointer to one double that receives ||h^2 f - A'u||_2.
- * Stream-ordered on cuda_stream (a cudaStream_t, NULL = legacy default
- * stream); no host synchronisation, no allocation of any kind.
+ * The call runs on the current CUDA device: f, u and norm_dev must be 8-byte
+ * aligned device memory of that device (or managed memory), else
+ * GMG_ERR_LAYOUT before anything is launched.  Stream-ordered on cuda_stream
+ * (a cudaStream_t, NULL = legacy default stream); no host synchronisation,
+ * no allocation of any kind.  The result equals gmg_residual_norm's to
+ * rounding (its own summation order).
  * Scratch: a fixed 512 KiB static device array (65536 partial sums) that each
  * GPU loading the library holds until exit; grids needing more partial sums
- * than that (3D n > 256) are rejected with GMG_ERR_ARG.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and
- * caches it: make that first call before any stream capture.  All calls
+ * than that (3D n > 256) are rejected with GMG_ERR_ARG.  Every call looks up
+ * the array's device address on the current device (cudaGetSymbolAddress,
+ * which allocates nothing, so the address stays right after a
+ * cudaDeviceReset); the first call on a device may load the library's device
+ * code there, so make that first call before any stream capture.  All calls
  * share the array, so calls that overlap on the GPU race and must be
  * serialised by the caller. */
 gmg_status gmg_residual_norm_noalloc(int d, int n, const double* f, const double* u,

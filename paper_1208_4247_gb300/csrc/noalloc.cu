@@ -13,44 +13,39 @@
 // Scratch: g_partials, a file-scope __device__ array of kMaxPartials doubles
 // (512 KiB) that every GPU which loads this library holds until the process
 // exits.  Host code cannot use the symbol g_partials as a device address
-// (on the host it names a host-side shadow), so the first call on each
-// device looks up the real address with cudaGetSymbolAddress, with that
-// device current, and caches it.  Make that first call before any stream
+// (on the host it names a host-side shadow), so every call looks up the real
+// address on the current device with cudaGetSymbolAddress (a lookup that
+// allocates nothing).  Looking it up on every call rather than caching it
+// keeps the address right after the caller resets the device
+// (cudaDeviceReset reloads the module).  The first call on a device may load
+// the library's device code there: make that first call before any stream
 // capture.  Every call shares the one array and keeps the last call's
 // contents: each call writes every partial sum it later reads, so nothing
 // has to start at zero, but calls whose kernels overlap on the GPU (other
 // streams, other host threads) race on the array and must be serialised by
 // the caller.
+//
+// The kernels are this file's own: one block per 256/x rows, no grid-stride
+// loop, neighbours summed left to right.  The result agrees with the handle
+// path's gmg_residual_norm to rounding (a different summation order), not
+// bit for bit.
 #include <cmath>
-#include <mutex>
 #include <string>
+#include <utility>
 
 #include "gmg_internal.cuh"
 
 namespace {
 
 constexpr int kMaxPartials = 65536;
-constexpr int kMaxDevices = 64;
-
 __device__ __align__(256) double g_partials[kMaxPartials];
 
-std::mutex g_mu;
-double* g_partials_addr[kMaxDevices] = {};
-
-// Device address of g_partials on the current device (looked up once).
+// Device address of g_partials on the current device.
 cudaError_t partials_address(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_partials_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_partials);
-        if (e != cudaSuccess) return e;
-        g_partials_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_partials_addr[dev];
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 
@@ -58,8 +53,8 @@ struct Shape {
     dim3 grid, block;
 };
 
-// The launch shape of the handle path's residual-norm kernel: 256 threads,
-// x along a row (32..128 threads), one block per 256/x rows of a plane.
+// Launch shape: 256 threads, x along a row (32..128 threads), one block per
+// 256/x rows of a plane, so one partial sum per block.
 Shape shape(int d, int n) {
     int bx = 32;
     while (bx < n && bx < 128) bx *= 2;
@@ -72,7 +67,7 @@ Shape shape(int d, int n) {
 
 // Partial sums of sigma^2, sigma = q + c * (sum of neighbours) - u with
 // q = h^2 f / (2d) formed on the fly; boundary neighbours read as 0 whatever
-// u holds there.  One partial per block, same order as the handle path.
+// u holds there.  One partial per block.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_resnorm_static(const double* __restrict__ f,
                                                         const double* __restrict__ u,
@@ -129,13 +124,37 @@ __global__ void __launch_bounds__(1024) k_finish_static(const double* __restrict
     }
 }
 
-bool device_pointer(const void* p) {
+// GMG_OK if p is 8-byte aligned device (or managed) memory usable on the
+// current device; GMG_ERR_LAYOUT with a message otherwise.  Nothing is
+// launched before every pointer has passed.
+gmg_status check_pointer(const void* p, const char* name) {
+    if (!p) {
+        gmg::set_error(std::string(name) + " is NULL");
+        return GMG_ERR_LAYOUT;
+    }
+    if (reinterpret_cast<uintptr_t>(p) % alignof(double) != 0) {
+        gmg::set_error(std::string(name) + " is not 8-byte aligned");
+        return GMG_ERR_LAYOUT;
+    }
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        gmg::set_error(std::string(name) + " is not a device pointer");
+        return GMG_ERR_LAYOUT;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return GMG_OK;
+    if (a.type != cudaMemoryTypeDevice) {
+        gmg::set_error(std::string(name) + " is not a device pointer");
+        return GMG_ERR_LAYOUT;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || a.device != dev) {
+        cudaGetLastError();
+        gmg::set_error(std::string(name) + " lives on device " + std::to_string(a.device) +
+                       ", not on the current device " + std::to_string(dev));
+        return GMG_ERR_LAYOUT;
+    }
+    return GMG_OK;
 }
 
 }  // namespace
@@ -160,13 +179,11 @@ extern "C" gmg_status gmg_residual_norm_noalloc(int d, int n, const double* f, c
                   " (largest grids: 3D n = 256, 2D n = 16384); use gmg_residual_norm");
         return GMG_ERR_ARG;
     }
-    if (!f || !u || !norm_dev) {
-        set_error("f, u and norm_dev must be non-NULL device pointers");
-        return GMG_ERR_LAYOUT;
-    }
-    if (!device_pointer(f) || !device_pointer(u) || !device_pointer(norm_dev)) {
-        set_error("f, u and norm_dev must be device pointers");
-        return GMG_ERR_LAYOUT;
+    for (const auto& [p, name] : {std::pair<const void*, const char*>{f, "f"},
+                                  {u, "u"},
+                                  {norm_dev, "norm_dev"}}) {
+        const gmg_status st = check_pointer(p, name);
+        if (st != GMG_OK) return st;
     }
     double* partial = nullptr;
     cudaError_t e = partials_address(&partial);

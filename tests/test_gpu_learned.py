@@ -34,10 +34,10 @@ def torch_cuda():
 
 
 def bf16_round(w):
-    """Round-to-nearest-even to BF16, returned as float32."""
-    a = np.ascontiguousarray(w, np.float32).view(np.uint32).astype(np.uint64)
-    a = ((a + 0x7FFF + ((a >> 16) & 1)) >> 16) << 16
-    return a.astype(np.uint32).view(np.float32).reshape(np.shape(w))
+    """Round-to-nearest-even to BF16 (torch's CPU conversion), as float32."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(w, np.float32))
+    return t.to(torch.bfloat16).to(torch.float32).numpy().reshape(np.shape(w))
 
 
 def random_weights(d, rng, scale=0.3):

@@ -470,17 +470,25 @@ def test_learned_vcycle_with_jacobi_weights_is_wj_vcycle(d, n, omega):
     np.testing.assert_allclose(dm.to_vec(u), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
 
 
+def _bf16_torch(x):
+    """BF16 rounding by an implementation outside the oracle: torch's CPU
+    conversions double -> float32 -> bfloat16 (round to nearest, ties to
+    even), widened back to float64."""
+    torch = pytest.importorskip("torch")
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+    return t.to(torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+
+
 @pytest.mark.parametrize("d,n", [(2, 8), (3, 8)])
 def test_bf16_network_with_jacobi_weights(d, n):
     """BF16 operands: with the Jacobi weights the network returns omega times
-    the BF16 rounding of its input (ties to even), exactly."""
+    the BF16 rounding of its input (ties to even), exactly; the rounding is
+    torch's conversion, not a formula of this project."""
     W1, W2 = _jacobi_weights(d, 0.75)
     rng = np.random.default_rng(12)
     x = dm.from_vec(rng.standard_normal((n - 1) ** d), d, n)
     y = oracle.conv_fwd_bf16(W1, W2, x)
-    xb = x.astype(np.float32).view(np.uint32).astype(np.uint64)
-    xb = (((xb + 0x7FFF + ((xb >> 16) & 1)) >> 16) << 16).astype(np.uint32).view(np.float32)
-    np.testing.assert_array_equal(y, 0.75 * xb.astype(np.float64))
+    np.testing.assert_array_equal(y, 0.75 * _bf16_torch(x))
     # BF16-representable data with small integer weights: identical to the exact network
     xi = np.round(x * 4) / 4
     W1i = np.round(rng.standard_normal(W1.shape) * 2).astype(np.float32) / 2
@@ -489,6 +497,33 @@ def test_bf16_network_with_jacobi_weights(d, n):
     y2, z = oracle.conv_fwd(W1i, W2i, xi)
     if np.all(np.abs(z) < 256):  # hidden values stay BF16-representable
         np.testing.assert_array_equal(y1, y2)
+
+
+def test_bf16_network_rounding_ties():
+    """Round-to-nearest-even cases written out by hand (BF16 keeps 8
+    significant bits: spacing 2^-7 on [1, 2)): exact ties go to the even
+    neighbour, values above a tie go up, and a double just above a tie that
+    float32 rounds onto the tie goes to even (double -> float -> BF16)."""
+    d, n = 2, 4
+    W1, W2 = _jacobi_weights(d, 0.75)
+    vals = np.array([
+        [1 + 2.0 ** -8, 1.0],                          # tie, even neighbour below
+        [1 + 3 * 2.0 ** -8, 1 + 2.0 ** -6],            # tie, even neighbour above
+        [-(1 + 2.0 ** -8), -1.0],                      # negative tie
+        [1 + 2.0 ** -8 + 2.0 ** -20, 1 + 2.0 ** -7],   # above the tie in float32
+        [1 + 2.0 ** -8 + 2.0 ** -40, 1.0],             # onto the tie in float32
+        [3 + 2.0 ** -7, 3.0],                          # tie at spacing 2^-6 on [2, 4)
+        [0.5 + 3 * 2.0 ** -9, 0.5 + 2.0 ** -7],        # tie, spacing 2^-8 on [1/2, 1)
+        [2.0 ** -130, 2.0 ** -130],                    # subnormal in float32, exact in BF16
+        [-0.0, 0.0],
+    ])
+    x = np.zeros((n + 1, n + 1))
+    for idx, (v, want) in enumerate(vals):
+        x[:] = 0.0
+        x[2, 2] = v
+        y = oracle.conv_fwd_bf16(W1, W2, x)
+        assert y[2, 2] == 0.75 * want, (idx, v, y[2, 2], want)
+        assert y[2, 2] == 0.75 * _bf16_torch(np.array([v]))[0], idx
 
 
 @pytest.mark.parametrize("d,n,sm,om,nu1,nu2", [(2, 16, oracle.RBGS, 0.8, 1, 2),
