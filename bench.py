@@ -468,7 +468,7 @@ def run_learned(torch, args):
     levels = 8
     cand = {l: weights[128] if l < 2 else weights[64] for l in range(6)}
     S = Solver(d, n, smoother="learned", nu1=1, nu2=1)
-    kept, rho_rb, rho_learned, trace = ls.select_levels(S, f, u, cand, levels)
+    kept, rho_rb, rho_learned = ls.select_levels(S, f, u, cand, levels)
     for l in kept:
         S.set_learned_weights(l, jacobi_weights(d, 6.0 / 7.0))
     rho_untrained = ls.contraction(S, f, u) if kept else None
@@ -480,7 +480,7 @@ def run_learned(torch, args):
                         "seconds": train_s,
                         "loss_first_last": {str(k): [float(np.mean(v[:10])), float(np.mean(v[-10:]))]
                                             for k, v in hist.items()}},
-           "levels_kept": kept, "selection_trace": trace,
+           "levels_kept": kept,
            "contraction": {"rbgs_v11": rho_rb, "learned_v11": rho_learned,
                            "untrained_jacobi_start_v11": rho_untrained}}
     runs = {}

@@ -350,16 +350,43 @@ typedef struct {
     uint64_t seed;       /* seed of the samples' white noise */
     double omega_init;   /* start at weighted Jacobi with this omega if w_init is NULL
                             (<= 0: 6/7 in 3D, 4/5 in 2D) */
-    unsigned level_mask; /* bit l set: install the trained weights on level l */
+    unsigned level_mask; /* bit l set: the trained weights are a candidate for level l */
+    const double* select_f; /* NULL: install the trained weights on every level of
+                               level_mask.  Else a device f (layout above) of the target
+                               problem: keep them on a level only where they lower the
+                               measured contraction (gmg_smoother_select, 8 cycles, skip 2);
+                               every other level smooths with red-black GS */
 } gmg_train_config;
 
 /* Train the learned smoother of h (smoother GMG_LEARNED) with
  * gmg_learned_train on the handle's dimension and install the result on the
- * levels of tc->level_mask.  w_init: starting weights (host, layout of
+ * levels of tc->level_mask (with tc->select_f: on those of them where it
+ * beats red-black GS, see gmg_smoother_select).  w_init: starting weights (host, layout of
  * gmg_set_learned_weights) or NULL.  loss_history: tc->steps doubles or
  * NULL.  Synchronises the handle's stream. */
 gmg_status gmg_smoother_train(gmg_handle h, const gmg_train_config* tc, const float* w_init,
                               double* loss_history);
+
+/* The learned smoother's fallback (no counterpart in the paper; red-black GS,
+ * the smoother of Algorithm 1's relax steps, is what it falls back to).  On
+ * the target problem f (device, layout above) measure the V-cycle
+ * contraction rho = (r_{cycles-1} / r_skip)^(1 / (cycles-1-skip)), r_c the
+ * relative residual after cycle c+1 of a solve from u = 0, first with
+ * red-black GS on every level, then level by level from the finest (l = 0
+ * .. count-1): candidates[l] (host weights, layout of gmg_set_learned_weights;
+ * NULL = no candidate) is installed and kept only if rho falls below the best
+ * so far, else that level goes back to red-black GS.  Levels >= count smooth
+ * with red-black GS.  When no level keeps its weights, the cycle is the
+ * red-black one of the same handle.  kept_mask_out (may be NULL): bit l set
+ * for each level that kept its weights; rho_base_out, rho_out (may be NULL):
+ * the contraction with red-black GS everywhere and with the kept weights.
+ * Uses a work array owned by the handle (allocated on first use); f is only
+ * read.  Synchronises the handle's stream.  Errors: GMG_ERR_ARG (handle not
+ * GMG_LEARNED, count outside [0, levels], skip < 0, cycles < skip + 2),
+ * GMG_ERR_LAYOUT (f not a device pointer), else as gmg_cycles. */
+gmg_status gmg_smoother_select(gmg_handle h, const double* f, const float* const* candidates,
+                               int count, int cycles, int skip, unsigned* kept_mask_out,
+                               double* rho_base_out, double* rho_out);
 
 /* Persistence of the learned smoother of h (smoother GMG_LEARNED).  Blob
  * layout, for each level of the handle in order: int32 flag (1: weights
@@ -383,7 +410,7 @@ const char* gmg_last_error(void);
 
 /* Version of this ABI (GMG_ABI_VERSION).  A library service. */
 int gmg_abi_version(void);
-#define GMG_ABI_VERSION 1
+#define GMG_ABI_VERSION 2
 
 #ifdef __cplusplus
 }

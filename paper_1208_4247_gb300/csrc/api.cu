@@ -5,6 +5,7 @@
 // refinement.
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <cstddef>
 #include <cstdio>
 #include <cstdlib>
@@ -1312,9 +1313,86 @@ gmg_status gmg_smoother_train(gmg_handle h, const gmg_train_config* tc, const fl
                                       tc->coarse_cycles, tc->lr, tc->seed, w0.data(), w.data(),
                                       loss_history, (void*)h->user_stream);
     if (st != GMG_OK) return st;
+    if (tc->select_f) {
+        // the fallback: keep the trained weights only where they lower the
+        // measured contraction on the caller's problem
+        std::vector<const float*> cand(h->lw.size(), nullptr);
+        for (int l = 0; l < (int)cand.size() && l < 32; ++l)
+            if ((tc->level_mask >> l) & 1u) cand[l] = w.data();
+        return gmg_smoother_select(h, tc->select_f, cand.data(), (int)cand.size(), 8, 2,
+                                   nullptr, nullptr, nullptr);
+    }
     for (int l = 0; l < (int)h->lw.size() && l < 32; ++l)
         if ((tc->level_mask >> l) & 1u)
             if ((st = gmg_set_learned_weights(h, l, w.data())) != GMG_OK) return st;
+    return GMG_OK;
+}
+
+gmg_status gmg_smoother_select(gmg_handle h, const double* f, const float* const* candidates,
+                               int count, int cycles, int skip, unsigned* kept_mask_out,
+                               double* rho_base_out, double* rho_out) {
+    if (!h || (!candidates && count > 0)) {
+        set_error("handle / candidates is NULL");
+        return GMG_ERR_ARG;
+    }
+    if (h->cfg.smoother != GMG_LEARNED) {
+        set_error("the handle was not created with smoother GMG_LEARNED");
+        return GMG_ERR_ARG;
+    }
+    if (count < 0 || count > (int)h->lw.size() || count > 32) {
+        set_error("count must be in [0, levels of the handle] (at most 32)");
+        return GMG_ERR_ARG;
+    }
+    if (skip < 0 || cycles < skip + 2 || cycles > 1000) {
+        set_error("need 0 <= skip and skip + 2 <= cycles <= 1000");
+        return GMG_ERR_ARG;
+    }
+    gmg_status st = check_device_ptr(f, "f");
+    if (st != GMG_OK) return st;
+    DeviceGuard guard(h->device);
+    const int64_t m = h->lv[0].nodes;
+    if (!h->f_stage) {
+        if ((st = dev_alloc(h, &h->f_stage, m)) != GMG_OK) return st;
+        if ((st = dev_alloc(h, &h->u_stage, m)) != GMG_OK) return st;
+    }
+    std::vector<double> rel(cycles);
+    // geometric mean of the residual reduction of cycles skip+1 .. cycles-1
+    // of a solve from u = 0
+    auto contraction = [&](double* rho) -> gmg_status {
+        GMG_CUDA_TRY(cudaEventRecord(h->ev, h->user_stream));
+        GMG_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev, 0));
+        GMG_CUDA_TRY(cudaMemsetAsync(h->u_stage, 0, sizeof(double) * m, h->stream));
+        GMG_CUDA_TRY(cudaEventRecord(h->ev, h->stream));
+        GMG_CUDA_TRY(cudaStreamWaitEvent(h->user_stream, h->ev, 0));
+        gmg_status s = run(h, f, h->u_stage, 0.0, cycles, false, nullptr, rel.data());
+        if (s != GMG_OK) return s;
+        const double a = rel[cycles - 1], b = rel[skip];
+        *rho = (b > 0.0 && a >= 0.0) ? std::pow(a / b, 1.0 / (cycles - 1 - skip))
+                                     : std::numeric_limits<double>::infinity();
+        if (!std::isfinite(*rho)) *rho = std::numeric_limits<double>::infinity();
+        return GMG_OK;
+    };
+    for (int l = 0; l < (int)h->lw.size(); ++l)
+        if ((st = gmg_set_learned_weights(h, l, nullptr)) != GMG_OK) return st;
+    double base = 0.0;
+    if ((st = contraction(&base)) != GMG_OK) return st;
+    double best = base;
+    unsigned kept = 0;
+    for (int l = 0; l < count; ++l) {
+        if (!candidates[l]) continue;
+        if ((st = gmg_set_learned_weights(h, l, candidates[l])) != GMG_OK) return st;
+        double rho = 0.0;
+        if ((st = contraction(&rho)) != GMG_OK) return st;
+        if (rho < best) {
+            best = rho;
+            kept |= 1u << l;
+        } else if ((st = gmg_set_learned_weights(h, l, nullptr)) != GMG_OK) {
+            return st;
+        }
+    }
+    if (kept_mask_out) *kept_mask_out = kept;
+    if (rho_base_out) *rho_base_out = base;
+    if (rho_out) *rho_out = best;
     return GMG_OK;
 }
 

@@ -90,6 +90,7 @@ SIGNATURES = {
     "gmg_create_batched": ([I, P, P, ctypes.POINTER(P)], I),
     "gmg_solve_batched": ([P, ctypes.POINTER(P), ctypes.POINTER(P), D, PI], I),
     "gmg_smoother_train": ([P, P, P, PD], I),
+    "gmg_smoother_select": ([P, P, P, I, I, I, ctypes.POINTER(ctypes.c_uint), PD, PD], I),
     "gmg_smoother_save": ([P, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], I),
     "gmg_smoother_load": ([P, P, ctypes.c_size_t], I),
 }
@@ -100,7 +101,8 @@ class TrainConfig(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("steps", ctypes.c_int), ("batch", ctypes.c_int),
                 ("pair_cycles", ctypes.c_int), ("coarse_cycles", ctypes.c_int),
                 ("lr", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("omega_init", ctypes.c_double), ("level_mask", ctypes.c_uint)]
+                ("omega_init", ctypes.c_double), ("level_mask", ctypes.c_uint),
+                ("select_f", ctypes.c_void_p)]
 
 
 def lib():
@@ -199,17 +201,43 @@ class Solver:
 
     def smoother_train(self, n: int, steps: int, batch: int = 8, pair_cycles: int = 1,
                        coarse_cycles: int = 12, lr: float = 3e-3, seed: int = 1,
-                       omega_init: float = 0.0, levels=(0,), w_init=None):
-        """gmg_smoother_train; returns the per-step mean loss (numpy)."""
+                       omega_init: float = 0.0, levels=(0,), w_init=None, select_f=None):
+        """gmg_smoother_train; returns the per-step mean loss (numpy).
+        select_f (float64 CUDA tensor of the target problem, optional): keep
+        the trained weights only on levels where they beat red-black GS."""
         import numpy as np
+        sf = None if select_f is None else _dptr(select_f, "select_f", self.d, self.n)
         tc = TrainConfig(n, steps, batch, pair_cycles, coarse_cycles, lr, seed, omega_init,
-                         sum(1 << l for l in levels))
+                         sum(1 << l for l in levels), sf)
         loss = np.zeros(max(steps, 1), np.float64)
         w = None if w_init is None else np.ascontiguousarray(w_init, dtype=np.float32)
         _check(lib().gmg_smoother_train(self._h, ctypes.byref(tc),
                                         None if w is None else ctypes.c_void_p(w.ctypes.data),
                                         loss.ctypes.data_as(PD)))
         return loss[:steps]
+
+    def smoother_select(self, f, candidates, cycles: int = 8, skip: int = 2):
+        """gmg_smoother_select: candidates {level: weights (2, 8, 3^d) float32}.
+        Returns (kept levels, contraction with red-black GS everywhere,
+        contraction with the kept weights)."""
+        import numpy as np
+        count = max(candidates) + 1 if candidates else 0
+        keep = [None] * count
+        ptrs = (ctypes.c_void_p * max(count, 1))()
+        for l, w in candidates.items():
+            a = np.ascontiguousarray(w, dtype=np.float32)
+            if a.size != 2 * 8 * (27 if self.d == 3 else 9):
+                raise ValueError("weights must hold 2 x 8 x 3^d floats")
+            keep[l] = a
+            ptrs[l] = a.ctypes.data
+        mask = ctypes.c_uint(0)
+        rb = ctypes.c_double(0.0)
+        rho = ctypes.c_double(0.0)
+        _check(lib().gmg_smoother_select(self._h, _dptr(f, "f", self.d, self.n), ptrs, count,
+                                         cycles, skip, ctypes.byref(mask), ctypes.byref(rb),
+                                         ctypes.byref(rho)))
+        del keep
+        return [l for l in range(32) if (mask.value >> l) & 1], rb.value, rho.value
 
     def smoother_save(self) -> bytes:
         """gmg_smoother_save: the learned smoother of every level as a blob."""

@@ -5,9 +5,10 @@ Gauss-Seidel (the fallback).
 * ``train_weights`` -- the two-grid contraction training of the library
   (gmg_learned_train) on a 65^3 then a 129^3 grid, started from weighted
   Jacobi (omega = 6/7) weights.
-* ``select_levels`` -- greedy per-level choice on the target problem: level
-  by level from the finest, the learned weights are kept if the measured
-  V-cycle contraction (geometric mean over a few cycles) improves.
+* ``select_levels`` -- the library's per-level fallback on the target
+  problem (gmg_smoother_select): level by level from the finest, the learned
+  weights are kept if the measured V-cycle contraction (geometric mean over a
+  few cycles) improves, else the level smooths with red-black GS.
 """
 from __future__ import annotations
 
@@ -35,20 +36,8 @@ def contraction(S, f, u, cycles=8, skip=2):
 
 
 def select_levels(S, f, u, candidates, levels):
-    """candidates: {level: weights}.  Sets the kept weights on S and returns
-    (kept levels, contraction before, contraction after, trace)."""
-    for l in range(levels):
-        S.set_learned_weights(l, None)
-    base = contraction(S, f, u)
-    best = base
-    kept, trace = [], []
-    for l in sorted(candidates):
-        S.set_learned_weights(l, candidates[l])
-        rho = contraction(S, f, u)
-        trace.append((l, rho))
-        if rho < best:
-            best = rho
-            kept.append(l)
-        else:
-            S.set_learned_weights(l, None)
-    return kept, base, best, trace
+    """candidates: {level: weights}.  The library's fallback rule
+    (gmg_smoother_select): sets the kept weights on S and returns (kept
+    levels, contraction before, contraction after)."""
+    del u, levels  # the library measures on its own work array, every level
+    return S.smoother_select(f, candidates)

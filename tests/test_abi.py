@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_abi_version(L):
-    assert L.gmg_abi_version() == 1
+    assert L.gmg_abi_version() == 2
 
 
 def test_config_defaults(L):
@@ -95,6 +95,7 @@ def test_learned_calls_reject_bad_sizes(L):
     loss = ctypes.c_double()
     assert L.gmg_learned_loss_grad(3, 2, w, None, 10, ctypes.byref(loss), None, None) == 1
     assert L.gmg_learned_train(3, 64, 0, 1, 1, 10, 1e-3, 1, w, w, None, None) == 1
+    assert L.gmg_smoother_select(None, None, None, 0, 8, 2, None, None, None) == 1
 
 
 def test_batch_and_fft_reject_bad_arguments(L):

@@ -168,3 +168,73 @@ def test_training_lowers_loss_and_beats_untrained_start(torch_cuda):
     uo = np.zeros_like(fn)
     oracle.solve(oracle.make_cfg(3, nn, 0, oracle.RBGS, 0.8, 2, 2, 1), fn, uo, 1e-13, 100)
     assert np.linalg.norm(ug - uo) <= 1e-9 * np.linalg.norm(uo)
+
+
+def _blob_levels(blob, nlev, T):
+    """Levels whose flag is 1 in a gmg_smoother_save blob."""
+    import struct
+    kept, off = [], 0
+    for l in range(nlev):
+        flag = struct.unpack_from("<i", blob, off)[0]
+        off += 4
+        if flag:
+            kept.append(l)
+            off += 4 * 2 * 8 * T
+    assert off == len(blob)
+    return kept
+
+
+def test_trained_smoother_gains_over_red_black(torch_cuda):
+    """What the trained network gains over the method without it: trained on
+    the GPU (65^3 error samples), installed through the library's fallback
+    rule on a 65^3 GRF problem, the learned V(1,1) cycle contracts the
+    residual faster than the red-black V(1,1) cycle on the same problem, and
+    the solve still reaches the oracle's FP64 solution."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 64
+    f = torch.from_numpy(inputs.rhs_grf(d, n, 5)).cuda()
+    L = oracle.max_levels(n)
+    with Solver(d, n, nu1=1, nu2=1) as R:
+        rho_rb = _contraction(torch, R, f)
+    with Solver(d, n, smoother="learned", nu1=1, nu2=1) as S:
+        S.smoother_train(n, steps=300, batch=8, coarse_cycles=12, lr=2e-3, seed=100,
+                         levels=range(L - 2), select_f=f)
+        kept = _blob_levels(S.smoother_save(), L, 27)
+        rho_l = _contraction(torch, S, f)
+        u = torch.zeros_like(f)
+        it, rel, conv = S.solve(f, u, 1e-10)
+    assert 0 in kept, kept
+    assert rho_l < 0.9 * rho_rb, (rho_l, rho_rb)
+    assert conv
+    fn = f.cpu().numpy()
+    ug = u.cpu().numpy()
+    b = oracle.scale_rhs(fn)
+    assert oracle.norm2(oracle.residual(b, ug)) / oracle.norm2(b) <= 1e-10
+    uo = np.zeros_like(fn)
+    oracle.solve(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1), fn, uo, 1e-13, 100)
+    assert np.linalg.norm(ug - uo) <= 1e-9 * np.linalg.norm(uo)
+
+
+def test_poor_weights_fall_back_to_red_black(torch_cuda):
+    """Finite but poor weights (weighted Jacobi, omega = 0.3) on every level:
+    the fallback rejects every level, and the cycle is then the red-black
+    V(1,1) cycle bit for bit."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver, jacobi_weights
+    d, n = 3, 64
+    f = torch.from_numpy(inputs.rhs_grf(d, n, 5)).cuda()
+    L = oracle.max_levels(n)
+    w = jacobi_weights(d, 0.3)
+    rng = np.random.default_rng(8)
+    u0 = torch.from_numpy(interior_noise(d, n, rng)).cuda()
+    with Solver(d, n, smoother="learned", nu1=1, nu2=1) as S:
+        kept, rho_rb, rho = S.smoother_select(f, {l: w for l in range(L)})
+        assert kept == [] and rho == rho_rb
+        assert _blob_levels(S.smoother_save(), L, 27) == []
+        ul = u0.clone()
+        S.cycles(f, ul, 3)
+    with Solver(d, n, nu1=1, nu2=1) as R:
+        ur = u0.clone()
+        R.cycles(f, ur, 3)
+    assert torch.equal(ul, ur)

@@ -79,15 +79,28 @@ def test_refinement_reaches_fp64_accuracy(torch_cuda, prec, k, d, n, sm, om, nu)
     assert _rel(ug, uo) <= 1e-9
 
 
-@pytest.mark.parametrize("prec,k", [("fp32", 5), ("bf16", 2)])
-def test_full_size_513(torch_cuda, prec, k):
-    """The 3D 513^3 workload (3 pi^2 prod sin + 0.01 N(0,1), seed 3), RB-GS
-    V(2,2) inner cycles: FP64 residual <= 1e-10 and error vs the oracle's
-    FP64 solution <= 1e-9."""
+@pytest.fixture(scope="module")
+def oracle_513():
+    """f of the 3D 513^3 workload (3 pi^2 prod sin + 0.01 N(0,1), seed 3) and
+    the oracle's FP64 solution (RB-GS V(2,2) to 1e-12), computed once."""
+    d, n = 3, 512
+    f = inputs.rhs_sine_plus_gauss(d, n, 3)
+    uo = np.zeros_like(f)
+    oracle.solve(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1), f, uo, rtol=1e-12, maxit=60)
+    return f, uo
+
+
+# k = 3 (FP32) and k = 1 (BF16) are the inner-cycle counts the benchmark's
+# autotuner picks on this workload; k = 5 / 2 are the neighbours it rejects
+@pytest.mark.parametrize("prec,k", [("fp32", 3), ("bf16", 1), ("fp32", 5), ("bf16", 2)])
+def test_full_size_513(torch_cuda, oracle_513, prec, k):
+    """The 3D 513^3 workload, RB-GS V(2,2) inner cycles: FP64 residual
+    <= 1e-10 and error vs the oracle's FP64 solution <= 1e-9 (globally and
+    node by node)."""
     torch = torch_cuda
     from paper_1208_4247_gb300.gmg import Solver
     d, n = 3, 512
-    f = inputs.rhs_sine_plus_gauss(d, n, 3)
+    f, uo = oracle_513
     fd = _dev(torch, f)
     ud = torch.zeros_like(fd)
     with Solver(d, n, precision=prec, inner_cycles=k) as S:
@@ -97,9 +110,8 @@ def test_full_size_513(torch_cuda, prec, k):
     del ud, fd
     b = oracle.scale_rhs(f)
     assert oracle.norm2(oracle.residual(b, ug)) / oracle.norm2(b) <= 1e-10
-    uo = np.zeros_like(f)
-    oracle.solve(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1), f, uo, rtol=1e-12, maxit=60)
     assert _rel(ug, uo) <= 1e-9
+    assert np.max(np.abs(ug - uo)) <= 1e-9 * np.max(np.abs(uo))
 
 
 def test_fused_sweep_equals_two_half_sweeps(torch_cuda, monkeypatch):

@@ -2,7 +2,8 @@
 
 Per cycle: from an identical iterate, one V-cycle on the GPU and in the oracle
 must agree to ||u_gpu - u_orc|| / ||u_orc|| <= 1e-12 (Euclidean over all
-nodes).  Per solve: identical cycle count to the relative residual 1e-10 and
+nodes) and, node by node, max |u_gpu - u_orc| <= 1e-12 max |u_orc| (so a
+wrong tile edge cannot hide under a global norm).  Per solve: identical cycle count to the relative residual 1e-10 and
 matching residual histories.  All calls go through the C ABI.
 """
 import numpy as np
@@ -32,6 +33,15 @@ def _dev(torch, a):
 
 def _rel(a, b):
     return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def _max_rel(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def _check_cycle(c, ug, uo):
+    assert _rel(ug, uo) <= TOL_CYCLE, (c, _rel(ug, uo))
+    assert _max_rel(ug, uo) <= TOL_CYCLE, (c, _max_rel(ug, uo))
 
 
 def _orc_smoother(name):
@@ -83,9 +93,41 @@ def test_cycle_parity(torch_cuda, case):
             ug = ud.cpu().numpy()
             uo = u.copy()
             oracle.vcycle(cfg, b, uo)
-            assert _rel(ug, uo) <= TOL_CYCLE, (c, _rel(ug, uo))
+            _check_cycle(c, ug, uo)
             rel_orc = oracle.norm2(oracle.residual(b, uo)) / oracle.norm2(oracle.residual(b, u))
             assert rel_gpu == pytest.approx(rel_orc, rel=1e-6, abs=1e-300)
+            u = ug
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_cycle_parity_full_size(torch_cuda, n):
+    """The benchmarked plain FP64 workloads at full size (3D 257^3: U[-1,1]
+    seed 2; 3D 513^3: 3 pi^2 prod sin + 0.01 N(0,1) seed 3; RB-GS V(2,2)):
+    three cycles from a seeded random iterate, each from the same input on
+    both sides, node by node within 1e-12 of the oracle.  These sizes run the
+    diagonal-walker half sweeps, the z-walking transfers and the norm fused
+    with the next red half sweep."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d = 3
+    f = inputs.rhs_uniform(d, n, 2) if n == 256 else inputs.rhs_sine_plus_gauss(d, n, 3)
+    rng = np.random.default_rng(29)
+    u = np.zeros_like(f)
+    u[(slice(1, -1),) * d] = rng.standard_normal((n - 1,) * d)
+    cfg = oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1)
+    b = oracle.scale_rhs(f)
+    fd = _dev(torch, f)
+    with Solver(d, n) as S:
+        for c in range(3):
+            ud = _dev(torch, u)
+            rel_gpu = S.cycles(fd, ud, 1)[0]
+            ug = ud.cpu().numpy()
+            del ud
+            uo = u.copy()
+            oracle.vcycle(cfg, b, uo)
+            _check_cycle(c, ug, uo)
+            rel_orc = oracle.norm2(oracle.residual(b, uo)) / oracle.norm2(oracle.residual(b, u))
+            assert rel_gpu == pytest.approx(rel_orc, rel=1e-6)
             u = ug
 
 
@@ -154,6 +196,30 @@ def test_full_size_3d_257_rbgs(torch_cuda):
     np.testing.assert_allclose(hist_g, hist_o, rtol=1e-6,
                                atol=_floor(d, uo, oracle.scale_rhs(f)))
     assert _rel(ud.cpu().numpy(), uo) <= 1e-10
+
+
+def test_full_size_3d_513_plain_solve(torch_cuda):
+    """The 3D 513^3 workload in plain FP64 (RB-GS V(2,2), 133.4M unknowns):
+    the oracle's cycle count and history, final iterate within 1e-10 of the
+    oracle's (globally and node by node)."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 512
+    f = inputs.rhs_sine_plus_gauss(d, n, 3)
+    uo = np.zeros_like(f)
+    it_o, hist_o = oracle.solve(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1), f, uo,
+                                rtol=1e-10, maxit=100)
+    fd = _dev(torch, f)
+    ud = torch.zeros_like(fd)
+    with Solver(d, n) as S:
+        it_g, rel_g, conv = S.solve(fd, ud, rtol=1e-10)
+        hist_g = np.array(S.history())
+    assert conv and it_g == it_o
+    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-6,
+                               atol=_floor(d, uo, oracle.scale_rhs(f)))
+    ug = ud.cpu().numpy()
+    assert _rel(ug, uo) <= 1e-10
+    assert _max_rel(ug, uo) <= 1e-10
 
 
 def test_solve_host_matches_device(torch_cuda):
