@@ -37,6 +37,10 @@ SM_MAX_MHZ = 2070.0
 # the 257^3 FP64 solve, from one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum: 269.5 MB + 85.8 MB)
 RB_HALF_L0_TRAFFIC = 356.4e6  # ncu dram read + write of one level-0 walker half sweep, 257^3
+# FP64 instructions of one updated node (adds, fmas) of the FP64 level
+# kernels that can dominate a solve: the diagonal-walker half sweep executes
+# 4 + 1/4 adds and one fma per node
+FP64_MIX = {"rb_half": (4.25, 1.0), "resnorm_red_sweep": (5.25, 2.0), "residual": (5.25, 1.0)}
 
 
 def peaks():
@@ -420,22 +424,28 @@ def run_paper_variant(torch, args):
     return out
 
 
-def run_sweeps(torch, args):
+def run_sweeps(torch, args, full=True):
     """Smoother x sweeps x inner-cycle sweeps of the refinement forms (3D
     513^3 workload input) and of the batched form (the 512-solve mix, default
-    tile and CTAs): time to 1e-10 for every combination."""
+    tile and CTAs): time to 1e-10 for every combination.  full = False: the
+    reduced default set -- red-black GS, nu = 1..3, FP32 with k = 2..4 and
+    BF16 with k = 1, no batch sweep."""
     from paper_1208_4247_gb300 import inputs
     from paper_1208_4247_gb300.autotune import sweep_batch, sweep_refinement
     out = {}
     d, n = 3, 512
     f = torch.from_numpy(inputs.rhs_sine_plus_gauss(d, n, 3)).cuda()
     u = torch.zeros_like(f)
-    sms = (("rbgs", 0.8), ("wjacobi", 6.0 / 7.0))
-    for prec, ks in (("fp32", (1, 2, 3, 4)), ("bf16", (1, 2))):
+    sms = (("rbgs", 0.8), ("wjacobi", 6.0 / 7.0)) if full else (("rbgs", 0.8),)
+    plan = (("fp32", (1, 2, 3, 4)), ("bf16", (1, 2))) if full else (("fp32", (2, 3, 4)),
+                                                                     ("bf16", (1,)))
+    for prec, ks in plan:
         rows, best = sweep_refinement(d, n, f, u, prec, sms, (1, 2, 3), ks=ks)
         out[f"{prec}_513"] = {"rows": rows, "best": best}
     del f, u
     torch.cuda.empty_cache()
+    if not full:
+        return out
     mix = inputs.batch_mix(512, 4)
     fd = [torch.from_numpy(x).cuda() for x in inputs.batch_rhs(mix, 4)]
     ud = [torch.zeros_like(x) for x in fd]
@@ -499,6 +509,70 @@ def run_learned(torch, args):
     out["speedup_learned_vs_rbgs_v22"] = runs["rbgs_v22"]["ms_per_step"] / runs["learned_v11"]["ms_per_step"]
     del f, u
     torch.cuda.empty_cache()
+    return out
+
+
+def config_of(cycles, ws):
+    """The workload's config (the same dict on both arms of the benchmark)."""
+    return {"workload": WORKLOAD, "cycles": cycles,
+            "l2": "inputs larger than L2 (u, q, r: 3 x 136 MB at level 0)",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
+def _r(x, digits=4):
+    """x rounded to `digits` significant digits (None passes through)."""
+    if x is None:
+        return None
+    if isinstance(x, bool) or not isinstance(x, (int, float)):
+        return x
+    return float(f"{x:.{digits}g}")
+
+
+def summarise(line):
+    """Compact per-form results: time per solve (ms), DOF/s, cycles or outer
+    steps, final relative residual and speed-up against the plain FP64 solve
+    of the same workload."""
+    out = {"plain_fp64_257": {"ms": _r(line["ms_per_step"]), "dofs": _r(line["value"]),
+                              "cyc": line["config"]["cycles"]}}
+    if line.get("e2e"):
+        out["e2e_257"] = {"ms": _r(line["e2e"]["ms_per_step"]), "dofs": _r(line["e2e"]["value"])}
+    rf = line.get("roofline") or {}
+    out["roofline"] = {"kernel": rf.get("kernel"), "frac": _r(rf.get("frac"), 3),
+                       "hbm_frac": _r(rf.get("hbm_frac"), 3), "bound": rf.get("bound")}
+    fft = line.get("cufft_dst_257")
+    if fft:
+        out["cufft_257"] = {"ms": _r(fft["ms_per_step"]), "rel": _r(fft["relres"], 2),
+                            "gmg_x": _r(fft["gmg_speedup_vs_fft"], 3)}
+    forms = (line.get("mixed_precision_513") or {}).get("forms") or {}
+    for name, v in forms.items():
+        out[name + "_513"] = {"ms": _r(v["ms_per_step"]), "dofs": _r(v["value"]),
+                              "it": v.get("outer_steps") or v.get("cycles"),
+                              "k": v.get("inner_cycles_per_step"), "rel": _r(v["relres"], 2),
+                              "x": _r(v.get("speedup_vs_fp64_plain"), 3)}
+    b = line.get("batched_512")
+    if b:
+        out["batch_512"] = {"ms": _r(b["ms_per_step"]), "dofs": _r(b["value"]),
+                            "maxrel": _r(b["max_relres"], 2),
+                            "x_1by1": _r(b["speedup_vs_one_by_one"], 3),
+                            "x_1by1_fp64": _r(b["speedup_vs_one_by_one_fp64"], 3),
+                            "tuned": b.get("autotuned")}
+    lr = line.get("learned_257")
+    if lr:
+        runs = lr["runs"]
+        out["learned_257"] = {"ms": _r(runs["learned_v11"]["ms_per_step"]),
+                              "cyc": runs["learned_v11"]["cycles"],
+                              "rho": _r(lr["contraction"]["learned_v11"], 3),
+                              "rho_rb_v11": _r(lr["contraction"]["rbgs_v11"], 3),
+                              "kept": lr["levels_kept"],
+                              "rb_v22_ms": _r(runs["rbgs_v22"]["ms_per_step"]),
+                              "x_rb_v22": _r(lr["speedup_learned_vs_rbgs_v22"], 3)}
+    fm = line.get("fmg_257") or {}
+    for k, v in fm.items():
+        out[k + "_257"] = {"ms": _r(v["ms_per_step"]), "cyc": v["cycles"],
+                           "x": _r(v["speedup_vs_plain_v22"], 3)}
+    cpu = line.get("cpu_baseline")
+    if cpu:
+        out["oracle_cpu_257"] = {"dofs": _r(cpu["value"]), "cores": cpu["cores"]}
     return out
 
 
@@ -618,7 +692,7 @@ def run_reference(args, rank, ws):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "cycles": its[-1]},
+            "data": "synthetic", "config": config_of(its[-1], ws),
             "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": c, "kind": "oracle",
                              "sample": "full 257^3 solve to 1e-10 per step (OpenMP, all cores)"},
             "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0,
@@ -707,21 +781,33 @@ def run_ours(args, rank, ws, local):
     rec = [r for r in by_kernel[dom] if r["level"] == 0][0]
     avg_s = rec["ms"] / rec["launches"] * 1e-3
     clocks = clk.summary()
-    peak_inst = FP64_INST_PER_CLK_SM * NUM_SMS * SM_MAX_MHZ * 1e6 / 1e12  # T inst/s
+    nominal_inst = FP64_INST_PER_CLK_SM * NUM_SMS * SM_MAX_MHZ * 1e6 / 1e12  # T inst/s
     achieved = rec["dp_ops"] / avg_s / 1e12
     pk, pk_kind = peaks()
     alg_bytes = sum(r["bytes"] * r["launches"] for r in stats) / args.steps
+    # the FP64 pipe's rate measured in this run (independent DFMA / DADD
+    # chains), weighted by the dominant kernel's add : fma mix
+    from paper_1208_4247_gb300.gmg import measure_fp64_rate
+    r_fma, r_add = measure_fp64_rate(0) / 1e12, measure_fp64_rate(1) / 1e12
+    n_add, n_fma = FP64_MIX.get(dom, (1.0, 0.0))
+    peak_meas = (n_add + n_fma) / (n_add / r_add + n_fma / r_fma)
+    kernel_gbs = rec["bytes"] / avg_s / 1e9
     roof = {"bound": "alu", "kernel": f"{dom} (level 0)", "achieved": achieved,
-            "peak": peak_inst, "unit": "T FP64-pipe inst/s", "frac": achieved / peak_inst,
+            "peak": peak_meas, "unit": "T FP64-pipe inst/s", "frac": achieved / peak_meas,
             "traffic": RB_HALF_L0_TRAFFIC if dom == "rb_half" else None,
             "traffic_unit": "bytes per launch (ncu)",
             "alg_bytes_per_launch": rec["bytes"],
-            "peak_note": "2 FP64 inst/clk/SM x 152 SMs x 2070 MHz (derived, nominal)",
+            "peak_note": (f"measured in this run: {r_fma:.4f} T DFMA/s, {r_add:.4f} T DADD/s "
+                          f"(gmg_measure_fp64_rate), weighted {n_add}:{n_fma} add:fma"),
+            "peak_measured": {"dfma": r_fma, "dadd": r_add, "mix": peak_meas},
+            "peak_nominal": nominal_inst,
+            "hbm_frac": kernel_gbs / pk["hbm_gbs"], "hbm_peak_gbs": pk["hbm_gbs"],
+            "hbm_peak_kind": pk_kind,
             "kernel_share": tot_ms[dom] / sum(tot_ms.values()),
             "timing": "per-kernel CUDA events (event nodes in the cycle graph on the "
                       "library's stream) over a repeat of the timed steps",
             "instrumented_ms_per_step": ms_instr,
-            "kernel_hbm_gbs": rec["bytes"] / avg_s / 1e9}
+            "kernel_hbm_gbs": kernel_gbs}
     hbm = {"solve_alg_bytes": alg_bytes, "achieved_gbs": alg_bytes / (ms_step * 1e-3) / 1e9,
            "peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind,
            "frac": alg_bytes / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"],
@@ -796,7 +882,7 @@ def run_ours(args, rank, ws, local):
         forms = run_forms(torch, args)
         batch = run_batch(torch, args)
         learned = run_learned(torch, args)
-    sweeps = run_sweeps(torch, args) if args.sweeps else None
+    sweeps = None if args.no_forms else run_sweeps(torch, args, full=args.sweeps)
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -815,9 +901,7 @@ def run_ours(args, rank, ws, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cycles": cycles,
-                       "l2": "inputs larger than L2 (u, q, r: 3 x 136 MB at level 0)",
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "config": config_of(cycles, ws),
             "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "cufft_dst_257": fft,
             "fmg_257": fmg_runs, "fmg_pass_vs_fft": fmg_fft, "paper_variant": paper_variant,
@@ -826,6 +910,9 @@ def run_ours(args, rank, ws, local):
             "learned_257": learned}
     if args.kernels:
         line["kernels"] = stats
+    # last key: the per-form results in a few hundred bytes, so that a reader
+    # of only the end of the line still sees every form's number
+    line["summary"] = summarise(line)
     print(json.dumps(line), flush=True)
 
 
@@ -840,7 +927,7 @@ def main():
     ap.add_argument("--kernels", action="store_true", help="add per-kernel records")
     ap.add_argument("--no-forms", action="store_true", help="skip the 513^3 precision forms")
     ap.add_argument("--sweeps", action="store_true",
-                    help="add smoother x sweeps x inner-cycle sweeps of the refinement and batched forms")
+                    help="the full smoother x sweeps x inner-cycle sweeps (default: a reduced set)")
     ap.add_argument("--form-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--train-steps65", type=int, default=1000)

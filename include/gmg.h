@@ -408,6 +408,15 @@ gmg_status gmg_destroy(gmg_handle h);
  * counterpart in the paper. */
 const char* gmg_last_error(void);
 
+/* Measured FP64 pipe rate of the current device (a library service; no
+ * counterpart in the paper): FP64 instructions per second of one kind (0:
+ * fused multiply-add, 1: add) issued by independent chains on every SM,
+ * timed with CUDA events on cuda_stream (NULL = legacy default stream) over
+ * five launches after a warm-up, into *inst_per_s.  The roofline peak of the
+ * FP64-bound kernels.  Synchronises cuda_stream; allocates nothing.
+ * Errors: GMG_ERR_ARG (kind not 0/1, NULL inst_per_s), GMG_ERR_CUDA. */
+gmg_status gmg_measure_fp64_rate(int kind, double* inst_per_s, void* cuda_stream);
+
 /* Version of this ABI (GMG_ABI_VERSION).  A library service. */
 int gmg_abi_version(void);
 #define GMG_ABI_VERSION 2

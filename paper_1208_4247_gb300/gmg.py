@@ -59,6 +59,7 @@ PD = ctypes.POINTER(ctypes.c_double)
 # name -> (argtypes, restype); every symbol include/gmg.h declares.
 SIGNATURES = {
     "gmg_abi_version": ([], I),
+    "gmg_measure_fp64_rate": ([I, PD, P], I),
     "gmg_last_error": ([], ctypes.c_char_p),
     "gmg_config_init": ([ctypes.POINTER(Config), I, I], I),
     "gmg_create": ([ctypes.POINTER(Config), P, ctypes.POINTER(P)], I),
@@ -473,6 +474,13 @@ def learned_train(d: int, n: int, steps: int, batch: int, w_init, lr: float = 1e
                                    ctypes.c_void_p(out.ctypes.data), hist.ctypes.data_as(PD),
                                    _stream_ptr(None)))
     return out, hist
+
+
+def measure_fp64_rate(kind: int = 0, stream=None) -> float:
+    """gmg_measure_fp64_rate: FP64 instructions/s (0: DFMA, 1: DADD)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().gmg_measure_fp64_rate(kind, ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 class FFTSolver:

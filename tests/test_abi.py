@@ -96,6 +96,8 @@ def test_learned_calls_reject_bad_sizes(L):
     assert L.gmg_learned_loss_grad(3, 2, w, None, 10, ctypes.byref(loss), None, None) == 1
     assert L.gmg_learned_train(3, 64, 0, 1, 1, 10, 1e-3, 1, w, w, None, None) == 1
     assert L.gmg_smoother_select(None, None, None, 0, 8, 2, None, None, None) == 1
+    assert L.gmg_measure_fp64_rate(2, ctypes.byref(loss), None) == 1
+    assert L.gmg_measure_fp64_rate(0, None, None) == 1
 
 
 def test_batch_and_fft_reject_bad_arguments(L):

@@ -125,3 +125,14 @@ def test_smoother_train_installs_weights(torch_cuda):
         assert flags == [1, 1, 0]
         it, rel, conv = S.solve(f, u, 1e-10)
     assert conv and rel <= 1e-10
+
+
+def test_measured_fp64_rate_is_plausible(torch_cuda):
+    """gmg_measure_fp64_rate: the FP64 pipe's measured DFMA and DADD rates
+    lie within a factor of two of the nominal 2 instructions per clock per SM
+    at the SM clock range of the part (152 SMs, up to 2.07 GHz)."""
+    from paper_1208_4247_gb300.gmg import measure_fp64_rate
+    nominal = 2 * 152 * 2.07e9
+    for kind in (0, 1):
+        r = measure_fp64_rate(kind)
+        assert 0.5 * nominal <= r <= 1.1 * nominal, (kind, r / nominal)

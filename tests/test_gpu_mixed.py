@@ -155,3 +155,31 @@ def test_small_grids_colour_split(torch_cuda, prec, d, n, sm):
     b = oracle.scale_rhs(f)
     assert oracle.norm2(oracle.residual(b, ug)) / oracle.norm2(b) <= 1e-10
     assert _rel(ug, uo) <= 1e-9
+
+
+def test_sweep_refinement_best_entry_matches_oracle(torch_cuda):
+    """The sweep over smoother x sweeps x inner cycles (autotune.sweep_refinement)
+    on a 65^3 grid returns converged entries, and its fastest setting solves to
+    the oracle's FP64 solution within 1e-9."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.autotune import sweep_refinement
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 64
+    fn = inputs.rhs_sine_plus_gauss(d, n, 3)
+    f = _dev(torch, fn)
+    u = torch.zeros_like(f)
+    rows, best = sweep_refinement(d, n, f, u, "fp32", (("rbgs", 0.8), ("wjacobi", 6 / 7)),
+                                  (1, 2), ks=(1, 2, 3))
+    assert len(rows) == 12 and best is not None
+    assert all(r["ms"] > 0 for r in rows if r["converged"])
+    assert sum(r["converged"] for r in rows) >= 6
+    with Solver(d, n, precision="fp32", inner_cycles=best["k"], smoother=best["smoother"],
+                omega=best["omega"], nu1=best["nu"], nu2=best["nu"], maxit=200) as S:
+        u.zero_()
+        it, rel, conv = S.solve(f, u, 1e-10)
+    assert conv and it == best["steps"]
+    ug = u.cpu().numpy()
+    uo = np.zeros_like(fn)
+    oracle.solve(oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, 2, 2, 1), fn, uo, rtol=1e-13,
+                 maxit=100)
+    assert _rel(ug, uo) <= 1e-9
