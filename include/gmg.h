@@ -59,7 +59,16 @@ typedef enum { GMG_WJACOBI = 0, GMG_RBGS = 1, GMG_LEARNED = 2, GMG_MCGS = 3 } gm
  * {0,1}^d nonzero) and the diagonal-linear prolongation of eq.
  * Prolongation2d (fine 2I + delta takes (e_I + e_{I+delta})/2). */
 typedef enum { GMG_TRANSFER_FW = 0, GMG_TRANSFER_PAPER = 1 } gmg_transfer;
-typedef enum { GMG_FP64 = 0, GMG_FP32_IR = 1, GMG_BF16_IR = 2 } gmg_precision;
+/* GMG_DF_IR: FP64 iterative refinement whose inner V-cycles run in
+ * double-float arithmetic (each value the unevaluated sum of two FP32
+ * numbers, about 48 significant bits, 8 bytes) on the FP32 pipe.  With
+ * inner_cycles = 1 a refinement step u <- u + V(b - A'u) equals one FP64
+ * V-cycle in exact arithmetic (the cycle is affine in u), and its rounding
+ * scales with the correction rather than with u: every step agrees with the
+ * plain FP64 cycle to far below 1e-12 (relative), so a solve takes the plain
+ * form's cycle count.  FP64 stays on the GPU for the outer residual, its
+ * norm and the update u += e. */
+typedef enum { GMG_FP64 = 0, GMG_FP32_IR = 1, GMG_BF16_IR = 2, GMG_DF_IR = 3 } gmg_precision;
 typedef enum { GMG_VCYCLE = 0, GMG_FMG = 1 } gmg_cycle;
 
 typedef struct {
@@ -76,10 +85,11 @@ typedef struct {
                           to every level, coarsest solved, then per level interpolation of
                           the coarse solution and one V-cycle; the initial u is ignored),
                           the following ones V-cycles (plain FP64, GS or Jacobi only) */
-    int precision;     /* gmg_precision: plain FP64, or FP32 / BF16 V-cycles inside
-                          FP64 iterative refinement */
+    int precision;     /* gmg_precision: plain FP64, or FP32 / BF16 / double-float
+                          V-cycles inside FP64 iterative refinement */
     int maxit;         /* cap on V-cycles (FP64) or on outer refinement steps */
-    int inner_cycles;  /* FP32 / BF16 forms: V-cycles per outer refinement step */
+    int inner_cycles;  /* refinement forms: V-cycles per outer refinement step (double-float:
+                          1 gives the plain FP64 cycle) */
     int coarse_sweeps; /* red-black sweeps from zero on a coarsest grid with more than
                           one unknown (truncated hierarchy); unused otherwise */
     int transfer;      /* gmg_transfer.  GMG_MCGS and GMG_TRANSFER_PAPER run in the plain

@@ -56,6 +56,7 @@ struct gmg_handle_s {
     std::vector<Level<double>> lv;
     std::vector<Level<float>> lvf;  // FP32 inner hierarchy (GMG_FP32_IR)
     std::vector<Level<bf16>> lvb;   // BF16 inner hierarchy (GMG_BF16_IR)
+    std::vector<Level<df32>> lvd;   // double-float inner hierarchy (GMG_DF_IR)
     double* partial = nullptr;
     double* d_res2 = nullptr;
     double* h_res2 = nullptr;  // pinned
@@ -155,7 +156,8 @@ gmg_status check_cfg(const gmg_config* c) {
         set_error("GMG_FMG runs in the plain FP64 form with GS or Jacobi smoothing");
         return GMG_ERR_UNSUPPORTED;
     }
-    if (c->precision != GMG_FP64 && c->precision != GMG_FP32_IR && c->precision != GMG_BF16_IR) {
+    if (c->precision != GMG_FP64 && c->precision != GMG_FP32_IR && c->precision != GMG_BF16_IR &&
+        c->precision != GMG_DF_IR) {
         set_error("unknown precision");
         return GMG_ERR_UNSUPPORTED;
     }
@@ -222,7 +224,7 @@ const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restri
                                   "update",      "memset",   "conv1",    "conv_tc_update", "tail",
                                   "rb_sweep_fused", "mc_sweep", "restrict_paper",
                                   "prolong_paper", "resnorm_red_sweep"};
-const char* kPrecSuffix[3] = {"", "_f32", "_bf16"};
+const char* kPrecSuffix[4] = {"", "_f32", "_bf16", "_df"};
 
 template <typename T>
 int prec_of();
@@ -232,6 +234,8 @@ template <>
 int prec_of<float>() { return 1; }
 template <>
 int prec_of<bf16>() { return 2; }
+template <>
+int prec_of<df32>() { return 3; }
 
 // Arithmetic model per launch: the operation's algorithmic instruction count
 // in the kernel's compute precision (FP64 for double storage and for the
@@ -283,7 +287,7 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
 template <class F>
 void timed(gmg_handle h, int kind, int level, int prec, int n, bool red_only, F&& launch,
            int kernels = 1) {
-    const double w = prec == 0 ? 8.0 : prec == 1 ? 4.0 : 2.0;
+    const double w = prec == 0 || prec == 3 ? 8.0 : prec == 1 ? 4.0 : 2.0;
     auto m = model(kind, h->cfg.d, n, red_only, w);
     h->timer.run(h->stream, std::string(kKindName[kind]) + kPrecSuffix[prec], level, m.first,
                  m.second, kernels, launch);
@@ -590,6 +594,8 @@ gmg_status enqueue_step_kernels(gmg_handle h) {
             2);
     } else if (c.precision == GMG_FP32_IR) {
         st = enqueue_refinement<float>(h, h->lvf);
+    } else if (c.precision == GMG_DF_IR) {
+        st = enqueue_refinement<df32>(h, h->lvd);
     } else {
         st = enqueue_refinement<bf16>(h, h->lvb);
     }
@@ -820,6 +826,9 @@ gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
         mixed::outer_residual<float>(c.d, h->lvf[0].lay, u, h->lv[0].q, h->lvf[0].q, h->partial,
                                      h->d_res2,
                                      h->stream);
+    else if (c.precision == GMG_DF_IR)
+        mixed::outer_residual<df32>(c.d, h->lvd[0].lay, u, h->lv[0].q, h->lvd[0].q, h->partial,
+                                    h->d_res2, h->stream);
     else
         mixed::outer_residual<bf16>(c.d, h->lvb[0].lay, u, h->lv[0].q, h->lvb[0].q, h->partial,
                                     h->d_res2,
@@ -948,8 +957,10 @@ gmg_status alloc_hierarchy(gmg_handle h, std::vector<Level<T>>& lv, int levels, 
         v.n = c.n >> l;
         // FP64 levels keep the caller's dense layout; the FP32/BF16 inner
         // hierarchies are colour-split (dense for the fused FP32 sweep)
-        v.lay = std::is_same<T, double>::value || use_fused_rb<T>(h) ? dense_lay(c.d, v.n)
-                                                                       : split_lay(c.d, v.n);
+        v.lay = std::is_same<T, double>::value || std::is_same<T, df32>::value ||
+                        use_fused_rb<T>(h)
+                    ? dense_lay(c.d, v.n)
+                    : split_lay(c.d, v.n);
         v.nodes = lay_elems(c.d, v.lay);
         if (l > 0 || alloc_u0)
             if ((st = dev_alloc(h, &v.u[0], v.nodes)) != GMG_OK) return st;
@@ -1049,6 +1060,7 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
         h->lv[0].nodes = nodes_of(d, cfg->n);
         if ((st = dev_alloc(h, &h->lv[0].q, h->lv[0].nodes)) != GMG_OK) return fail(st);
         st = cfg->precision == GMG_FP32_IR ? alloc_hierarchy<float>(h, h->lvf, L, true)
+             : cfg->precision == GMG_DF_IR ? alloc_hierarchy<df32>(h, h->lvd, L, true)
                                            : alloc_hierarchy<bf16>(h, h->lvb, L, true);
         if (st != GMG_OK) return fail(st);
     }

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "df.cuh"
 #include "gmg.h"
 
 namespace gmg {

@@ -1,6 +1,7 @@
 // Level kernels of the V-cycle (Algorithm 1), templated on the storage type
-// T (double, float, __nv_bfloat16) with arithmetic in C = double for double
-// storage and float otherwise.
+// T (double, float, __nv_bfloat16, df32) with arithmetic in C = double for
+// double storage, double-float for df32 storage (df.cuh) and float
+// otherwise.
 //
 // Scaled variables: with the unscaled 5/7-point operator A' (section 2.2)
 // and b = h^2 f, each level stores q = b / (2d); the Gauss-Seidel value of a
@@ -25,6 +26,7 @@
 
 #include <type_traits>
 
+#include "df.cuh"
 #include "gmg_internal.cuh"
 
 namespace gmg {
@@ -49,6 +51,12 @@ struct Num<__nv_bfloat16> {
     using C = float;
     __device__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
     __device__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+template <>
+struct Num<df32> {
+    using C = df32;
+    __device__ static df32 ld(df32 v) { return v; }
+    __device__ static df32 st(df32 v) { return v; }
 };
 
 __host__ __device__ inline int64_t sy_of(int n) { return (int64_t)n + 1; }
@@ -769,7 +777,7 @@ void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s) {
         k_rb_half3_walk<T><<<W.blocks, W.block, 0, s>>>(u, q, n, color, W.segs);
         return;
     }
-    if constexpr (!std::is_same<T, double>::value) {
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, __nv_bfloat16>::value) {
         if (L.he) {
             constexpr int V = vec_of<T>();
             const int G = (n / 2 + 1 + V - 1) / V;

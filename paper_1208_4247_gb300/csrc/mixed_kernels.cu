@@ -1,5 +1,6 @@
-// Mixed-precision form: V-cycles in FP32, or in BF16 storage with FP32
-// arithmetic, inside FP64 iterative refinement.  FP64 stays on the GPU for
+// Mixed-precision form: V-cycles in FP32, in BF16 storage with FP32
+// arithmetic, or in double-float arithmetic (df.cuh), inside FP64 iterative
+// refinement.  FP64 stays on the GPU for
 // the outer residual (and its norm, the stopping test) and the solution
 // update; the inner cycles solve A'e = b - A'u approximately from e = 0.
 //
@@ -21,6 +22,7 @@ namespace lk {
     template void prolong_add<T>(int, const Lay&, const Lay&, const T*, T*, cudaStream_t, bool);
 GMG_INSTANTIATE(float)
 GMG_INSTANTIATE(__nv_bfloat16)
+GMG_INSTANTIATE(df32)
 #undef GMG_INSTANTIATE
 }  // namespace lk
 
@@ -193,7 +195,10 @@ template void outer_residual<float>(int, const Lay&, const double*, const double
                                     double*, double*, cudaStream_t);
 template void outer_residual<__nv_bfloat16>(int, const Lay&, const double*, const double*,
                                             __nv_bfloat16*, double*, double*, cudaStream_t);
+template void outer_residual<df32>(int, const Lay&, const double*, const double*, df32*, double*,
+                                   double*, cudaStream_t);
 template void update<float>(int, const Lay&, double*, const float*, cudaStream_t);
+template void update<df32>(int, const Lay&, double*, const df32*, cudaStream_t);
 template void update<__nv_bfloat16>(int, const Lay&, double*, const __nv_bfloat16*, cudaStream_t);
 
 }  // namespace mixed

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(1024) k_tail(T* __restrict__ u_top, const T* _
     }
     // zero everything (boundaries stay zero), then load q of the top level
     for (int64_t p = threadIdx.x; p < base - reinterpret_cast<T*>(smem); p += blockDim.x)
-        reinterpret_cast<T*>(smem)[p] = Num<T>::st(0.f);
+        reinterpret_cast<T*>(smem)[p] = Num<T>::st(typename Num<T>::C(0));
     __syncthreads();
     // global addressing of dense node p of the top level (top's layout)
     auto gaddr = [&](int64_t p) {
@@ -353,6 +353,8 @@ template cudaError_t launch<float>(int, const Lay&, int, float*, const float*, i
 template cudaError_t launch<__nv_bfloat16>(int, const Lay&, int, __nv_bfloat16*,
                                            const __nv_bfloat16*, int, double, int, int, int,
                                            cudaStream_t);
+template cudaError_t launch<df32>(int, const Lay&, int, df32*, const df32*, int, double, int, int,
+                                  int, cudaStream_t);
 
 }  // namespace tail
 }  // namespace gmg

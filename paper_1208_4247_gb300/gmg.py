@@ -22,7 +22,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_LAYOUT", 3: "ERR_ALLOC", 4: "ERR_CUDA",
           8: "ERR_UNSUPPORTED"}
 SMOOTHERS = {"wjacobi": 0, "rbgs": 1, "learned": 2, "mcgs": 3}
 TRANSFERS = {"fw": 0, "paper": 1}
-PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "df": 3}
 CYCLES = {"v": 0, "fmg": 1}
 
 
