@@ -80,6 +80,8 @@ struct gmg_handle_s {
     std::vector<void*> allocs;
     KernelTimer timer;  // launch accounting and optional per-kernel event timing
     bool fused_rb = false;  // GMG_FUSED_RB=1 at create: fused FP32 3D red-black sweeps
+    bool df_dense = false;  // GMG_DF_SPLIT=0 at create: dense double-float inner layout
+    bool inner_ahead = true;  // GMG_INNER_AHEAD=0 at create: memset e + first red half sweep
     // plain red-black form: the stopping-test norm runs fused with the next
     // cycle's first level-0 red half sweep (norm_ahead_ok)
     bool ahead = false;
@@ -265,7 +267,8 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
             return red_only ? std::make_pair(N / 2 * (t ? 8 : 6), N * 12)
                             : std::make_pair(N * (t ? 8 : 6), N * 16);
         case K_COPY: return {0.0, N * 2 * w};
-        case K_OUTER_RES: return {N * (t ? 8 : 6), N * (16 + w)};
+        case K_OUTER_RES:  // red_only here: also writes the inner iterate (e_init)
+            return {N * (t ? 8 : 6), N * (16 + (red_only ? 2 : 1) * w)};
         case K_UPDATE: return {N, N * (16 + w)};
         case K_MEMSET: return {0.0, N * w};
         case K_CONV1: return {N * 8 * (t ? 27 : 9), N * (w + 32)};  // FP32 FMAs
@@ -337,9 +340,13 @@ bool sigma_carried(gmg_handle h) {
 // multi-colour smoother in decreasing order.
 // first_red_done: the first red half sweep already ran (fused with the
 // previous step's stopping-test norm).
+// exact_last: the last half sweep (a black one) uses the unbiased FP64 3D
+// Gauss-Seidel value (lk::gs_value), as the level-0 pre-smoothing before the
+// unbiased red-only residual must (the black residual then stays exactly 0).
 template <typename T>
 void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
-           bool sigma_ready = false, bool backward = false, bool first_red_done = false) {
+           bool sigma_ready = false, bool backward = false, bool first_red_done = false,
+           bool exact_last = false) {
     Level<T>& L = lv[l];
     const int d = h->cfg.d;
     const int p = prec_of<T>();
@@ -371,9 +378,11 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
             }
         }
         if (h->cfg.smoother == GMG_RBGS || h->cfg.smoother == GMG_LEARNED) {
-            for (int color = first_red_done && s == 0 ? 1 : 0; color < 2; ++color)
+            for (int color = first_red_done && s == 0 ? 1 : 0; color < 2; ++color) {
+                const bool ex = exact_last && s == sweeps - 1 && color == 1;
                 timed(h, K_RB_HALF, l, p, L.n, false,
-                      [&] { lk::rb_half<T>(d, L.lay, L.u[cur], L.q, color, h->stream); });
+                      [&] { lk::rb_half<T>(d, L.lay, L.u[cur], L.q, color, h->stream, ex); });
+            }
         } else {
             timed(h, K_WJ, l, p, L.n, false, [&] {
                 lk::wj_sweep<T>(d, L.lay, L.u[cur], L.u[cur ^ 1], L.q, h->cfg.omega, h->stream);
@@ -420,7 +429,7 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_re
         cudaError_t e = cudaSuccess;
         timed(h, K_TAIL, 0, p, lv[0].n, false, [&] {
             e = tail::launch<T>(d, lv[0].lay, L, lv[0].u[0], lv[0].q, c.smoother, c.omega, c.nu1,
-                                c.nu2, c.coarse_sweeps, h->stream);
+                                c.nu2, c.coarse_sweeps, h->stream, true);
         });
         GMG_CUDA_TRY(e);
     } else if (L == 1) {
@@ -428,9 +437,12 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_re
     } else {
         const int Ldown = lt < L ? lt : L - 1;  // levels smoothed by grid kernels going down
         for (int l = 0; l < Ldown; ++l) {
+            // level 0 of the plain FP64 form: the residual of the full
+            // iterate, unbiased in 3D (lk::gs_value)
+            const bool unbiased = l == 0 && std::is_same<T, double>::value && d == 3;
             relax(h, lv, l, c.nu1, cur[l],
                   l == 0 && std::is_same<T, double>::value && sigma_carried(h), false,
-                  l == 0 && first_red_done);
+                  l == 0 && first_red_done, unbiased);
             Level<T>& F = lv[l];
             Level<T>& C = lv[l + 1];
             // After a black half sweep the black residual vanishes identically.
@@ -439,7 +451,7 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_re
                             (c.smoother == GMG_LEARNED && !learned_level(h, l));
             const bool red_only = rb && c.nu1 > 0 && !paper;
             timed(h, K_RESIDUAL, l, p, F.n, red_only, [&] {
-                lk::residual<T>(d, F.lay, F.u[cur[l]], F.q, F.r, red_only, h->stream);
+                lk::residual<T>(d, F.lay, F.u[cur[l]], F.q, F.r, red_only, h->stream, unbiased);
             });
             const bool exact = C.n == 2;
             bool done = false;
@@ -509,27 +521,42 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_re
     return GMG_OK;
 }
 
+// Red-black inner cycles start from e = 0 with a red half sweep, which sets
+// e = sigma on the red nodes and reads only black zeros: the outer residual
+// writes that iterate directly (mixed::outer_residual's e_init), the first
+// inner cycle starts with its black half sweep, and no memset of e is
+// needed (boundary entries of e are never written and stay 0).  Same values
+// bit for bit: fma(c, 0, q) + nothing else = q in every inner precision.
+template <typename T>
+bool inner_red_ahead(gmg_handle h) {
+    const gmg_config& c = h->cfg;
+    return c.smoother == GMG_RBGS && c.nu1 > 0 && !use_fused_rb<T>(h) && h->inner_ahead;
+}
+
 // Refinement step: e = 0, k inner cycles on A'e = sigma, u += e, new sigma.
 template <typename T>
 gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
     const gmg_config& c = h->cfg;
     const int p = prec_of<T>();
-    cudaError_t e = cudaSuccess;
-    timed(h, K_MEMSET, 0, p, c.n, false, [&] {
-        e = cudaMemsetAsync(in[0].u[0], 0, sizeof(T) * in[0].nodes, h->stream);
-    });
-    GMG_CUDA_TRY(e);
+    const bool ahead = inner_red_ahead<T>(h);
+    if (!ahead) {
+        cudaError_t e = cudaSuccess;
+        timed(h, K_MEMSET, 0, p, c.n, false, [&] {
+            e = cudaMemsetAsync(in[0].u[0], 0, sizeof(T) * in[0].nodes, h->stream);
+        });
+        GMG_CUDA_TRY(e);
+    }
     for (int k = 0; k < c.inner_cycles; ++k) {
-        gmg_status st = enqueue_vcycle<T>(h, in);
+        gmg_status st = enqueue_vcycle<T>(h, in, ahead && k == 0);
         if (st != GMG_OK) return st;
     }
     timed(h, K_UPDATE, 0, p, c.n, false,
           [&] { mixed::update<T>(c.d, in[0].lay, h->lv[0].u[0], in[0].u[0], h->stream); });
     timed(
-        h, K_OUTER_RES, 0, p, c.n, false,
+        h, K_OUTER_RES, 0, p, c.n, ahead,
         [&] {
             mixed::outer_residual<T>(c.d, in[0].lay, h->lv[0].u[0], h->lv[0].q, in[0].q, h->partial,
-                                     h->d_res2, h->stream);
+                                     h->d_res2, h->stream, ahead ? in[0].u[0] : nullptr);
         },
         2);
     return GMG_OK;
@@ -824,15 +851,16 @@ gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
                       sigma_carried(h) ? h->lv[0].r : nullptr);
     } else if (c.precision == GMG_FP32_IR)
         mixed::outer_residual<float>(c.d, h->lvf[0].lay, u, h->lv[0].q, h->lvf[0].q, h->partial,
-                                     h->d_res2,
-                                     h->stream);
+                                     h->d_res2, h->stream,
+                                     inner_red_ahead<float>(h) ? h->lvf[0].u[0] : nullptr);
     else if (c.precision == GMG_DF_IR)
         mixed::outer_residual<df32>(c.d, h->lvd[0].lay, u, h->lv[0].q, h->lvd[0].q, h->partial,
-                                    h->d_res2, h->stream);
+                                    h->d_res2, h->stream,
+                                    inner_red_ahead<df32>(h) ? h->lvd[0].u[0] : nullptr);
     else
         mixed::outer_residual<bf16>(c.d, h->lvb[0].lay, u, h->lv[0].q, h->lvb[0].q, h->partial,
-                                    h->d_res2,
-                                    h->stream);
+                                    h->d_res2, h->stream,
+                                    inner_red_ahead<bf16>(h) ? h->lvb[0].u[0] : nullptr);
     h->timer.launches += 3;
     GMG_CUDA_TRY(cudaGetLastError());
     return GMG_OK;
@@ -957,8 +985,8 @@ gmg_status alloc_hierarchy(gmg_handle h, std::vector<Level<T>>& lv, int levels, 
         v.n = c.n >> l;
         // FP64 levels keep the caller's dense layout; the FP32/BF16 inner
         // hierarchies are colour-split (dense for the fused FP32 sweep)
-        v.lay = std::is_same<T, double>::value || std::is_same<T, df32>::value ||
-                        use_fused_rb<T>(h)
+        v.lay = std::is_same<T, double>::value || use_fused_rb<T>(h) ||
+                        (std::is_same<T, df32>::value && h->df_dense)
                     ? dense_lay(c.d, v.n)
                     : split_lay(c.d, v.n);
         v.nodes = lay_elems(c.d, v.lay);
@@ -1032,6 +1060,8 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     h->cfg = *cfg;
     h->user_stream = (cudaStream_t)cuda_stream;
     if (const char* v = std::getenv("GMG_FUSED_RB")) h->fused_rb = std::strcmp(v, "1") == 0;
+    if (const char* v = std::getenv("GMG_DF_SPLIT")) h->df_dense = std::strcmp(v, "0") == 0;
+    if (const char* v = std::getenv("GMG_INNER_AHEAD")) h->inner_ahead = std::strcmp(v, "0") != 0;
     if (const char* v = std::getenv("GMG_TAIL_N")) h->tail_max = std::max(0, std::atoi(v));
     if (const char* v = std::getenv("GMG_DEVICE_LOOP")) h->device_loop = std::strcmp(v, "0") != 0;
     auto fail = [&](gmg_status s) {

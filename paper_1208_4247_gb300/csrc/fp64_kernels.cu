@@ -17,11 +17,11 @@ bool rb_walk_enabled() {
     return on;
 }
 
-template void rb_half<double>(int, const Lay&, double*, const double*, int, cudaStream_t);
+template void rb_half<double>(int, const Lay&, double*, const double*, int, cudaStream_t, bool);
 template void wj_sweep<double>(int, const Lay&, const double*, double*, const double*, double,
                                cudaStream_t);
 template void residual<double>(int, const Lay&, const double*, const double*, double*, bool,
-                               cudaStream_t);
+                               cudaStream_t, bool);
 template void restrict_fw<double>(int, const Lay&, const Lay&, const double*, double*, double*,
                                   bool, bool, cudaStream_t);
 template void prolong_add<double>(int, const Lay&, const Lay&, const double*, double*,

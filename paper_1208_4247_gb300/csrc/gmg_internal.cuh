@@ -78,13 +78,16 @@ constexpr int kWalk = 4;
 bool rb_walk_enabled();
 // Launchers on a level with layout L (restriction: fine F -> coarse C;
 // prolongation: coarse C -> fine F).
+// exact (FP64 3D only): 1/(2d) = 1/6 carried as a double-double, an
+// unbiased Gauss-Seidel value and residual (level_kernels.cuh, gs_value)
 template <typename T>
-void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s);
+void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s, bool exact = false);
 template <typename T>
 void wj_sweep(int d, const Lay& L, const T* u_in, T* u_out, const T* q, double omega,
               cudaStream_t s);
 template <typename T>
-void residual(int d, const Lay& L, const T* u, const T* q, T* r, bool red_only, cudaStream_t s);
+void residual(int d, const Lay& L, const T* u, const T* q, T* r, bool red_only, cudaStream_t s,
+              bool exact = false);
 template <typename T>
 void restrict_fw(int d, const Lay& F, const Lay& C, const T* r, T* qc, T* uc, bool red_only,
                  bool exact_coarsest, cudaStream_t s);
@@ -106,12 +109,14 @@ void prolong_paper(int d, const Lay& C, const Lay& F, const T* uc, T* u, cudaStr
 
 // The same on dense levels given by n.
 template <typename T>
-inline void rb_half(int d, int n, T* u, const T* q, int color, cudaStream_t s) {
-    rb_half<T>(d, dense_lay(d, n), u, q, color, s);
+inline void rb_half(int d, int n, T* u, const T* q, int color, cudaStream_t s,
+                    bool exact = false) {
+    rb_half<T>(d, dense_lay(d, n), u, q, color, s, exact);
 }
 template <typename T>
-inline void residual(int d, int n, const T* u, const T* q, T* r, bool red_only, cudaStream_t s) {
-    residual<T>(d, dense_lay(d, n), u, q, r, red_only, s);
+inline void residual(int d, int n, const T* u, const T* q, T* r, bool red_only, cudaStream_t s,
+                     bool exact = false) {
+    residual<T>(d, dense_lay(d, n), u, q, r, red_only, s, exact);
 }
 template <typename T>
 inline void restrict_fw(int d, int n, const T* r, T* qc, T* uc, bool red_only,
@@ -158,10 +163,12 @@ void red_restore(int n, double* u, const double* save, cudaStream_t s);
 // Outer FP64 kernels of iterative refinement (mixed_kernels.cu).
 namespace mixed {
 int outer_partials(int d, int n);
-// q_in, e: the inner level-0 arrays, layout `in` (dense u, q: FP64, n = in.n)
+// q_in, e: the inner level-0 arrays, layout `in` (dense u, q: FP64, n = in.n).
+// e_init (may be NULL) receives the inner iterate after the first red half
+// sweep from e = 0: sigma on the red nodes, 0 on the black ones.
 template <typename T>
 void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q_in,
-                    double* partial, double* out, cudaStream_t s);
+                    double* partial, double* out, cudaStream_t s, T* e_init = nullptr);
 template <typename T>
 void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s);
 }  // namespace mixed
@@ -177,9 +184,13 @@ void rb_sweep3_f32(int n, const float* uin, float* uout, const float* q, cudaStr
 namespace tail {
 size_t smem_bytes(int d, int n_top, int levels, int smoother, size_t elem);
 // top: layout of u_top / q_top in global memory (n_top = top.n)
+// exact_top: the top level is level 0 of a plain FP64 3D hierarchy, whose
+// last pre-smoothing half sweep and residual use the unbiased value
+// (level_kernels.cuh, gs_value), as the grid kernels there do
 template <typename T>
 cudaError_t launch(int d, const Lay& top, int levels, T* u_top, const T* q_top, int smoother,
-                   double omega, int nu1, int nu2, int coarse_sweeps, cudaStream_t s);
+                   double omega, int nu1, int nu2, int coarse_sweeps, cudaStream_t s,
+                   bool exact_top = false);
 }  // namespace tail
 
 // Learned-smoother network kernels (learned.cu): z = conv1(x) (8 channel

