@@ -124,9 +124,11 @@ gmg_status gmg_config_init(gmg_config* cfg, int d, int n);
  * separate kernel instead of fusing it with the next cycle's first red half
  * sweep (3D levels 128 <= n <= 512; a solve that stops undoes that sweep);
  * u and the cycle count are the same bit for bit, the norms agree to
- * rounding.  GMG_DF_SPLIT=0 stores the GMG_DF_IR inner hierarchy densely (x
- * fastest, both colours interleaved) instead of colour-split; results are
- * the same bit for bit.  GMG_INNER_AHEAD=0 makes red-black refinement forms
+ * rounding.  GMG_OUTER_RED=0 makes GMG_DF_IR red-black handles update u and
+ * form the outer residual on every node (separate kernels) instead of on
+ * the red nodes only (the black residual after a black inner half sweep is
+ * zero up to the inner rounding); the results agree to that rounding.
+ * GMG_INNER_AHEAD=0 makes red-black refinement forms
  * zero the correction and run the first inner red half sweep as kernels of
  * their own instead of having the outer residual write that half sweep's
  * result (sigma on red nodes, 0 on black); results are the same bit for

@@ -80,8 +80,8 @@ struct gmg_handle_s {
     std::vector<void*> allocs;
     KernelTimer timer;  // launch accounting and optional per-kernel event timing
     bool fused_rb = false;  // GMG_FUSED_RB=1 at create: fused FP32 3D red-black sweeps
-    bool df_dense = false;  // GMG_DF_SPLIT=0 at create: dense double-float inner layout
     bool inner_ahead = true;  // GMG_INNER_AHEAD=0 at create: memset e + first red half sweep
+    bool outer_red = true;    // GMG_OUTER_RED=0 at create: full outer residual (double-float)
     // plain red-black form: the stopping-test norm runs fused with the next
     // cycle's first level-0 red half sweep (norm_ahead_ok)
     bool ahead = false;
@@ -219,13 +219,13 @@ int num_levels(const gmg_config& c) { return c.levels > 0 ? c.levels : ilog2(c.n
 enum Kind {
     K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_OUTER_RES,
     K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_TAIL, K_RB_FUSED, K_MC_SWEEP, K_RESTRICT_PAPER,
-    K_PROLONG_PAPER, K_NORM_AHEAD, K_COUNT
+    K_PROLONG_PAPER, K_NORM_AHEAD, K_OUTER_RED, K_COUNT
 };
 const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restrict",
                                   "prolong_add", "resnorm",  "copy",     "outer_residual",
                                   "update",      "memset",   "conv1",    "conv_tc_update", "tail",
                                   "rb_sweep_fused", "mc_sweep", "restrict_paper",
-                                  "prolong_paper", "resnorm_red_sweep"};
+                                  "prolong_paper", "resnorm_red_sweep", "outer_red_update"};
 const char* kPrecSuffix[4] = {"", "_f32", "_bf16", "_df"};
 
 template <typename T>
@@ -281,6 +281,9 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
         case K_PROLONG_PAPER: return {cells * (t ? 14 : 6), Nc * w + N * 2 * w};
         case K_NORM_AHEAD:  // red nodes: sigma^2 and the update; read u, q (red); write u, save
             return {N / 2 * (t ? 8 : 6), N * 2.5 * w};
+        case K_OUTER_RED:  // black: triple-float GS value into u (3 FP64 adds), e = q_in = 0;
+                           // red: u += e, sigma, q_in = e = sigma; u, e read on all nodes
+            return {N / 2 * (t ? 14.25 : 13), N * (16 + w) + N / 2 * (8 + 4 * w)};
     }
     return {0.0, 0.0};
 }
@@ -343,10 +346,12 @@ bool sigma_carried(gmg_handle h) {
 // exact_last: the last half sweep (a black one) uses the unbiased FP64 3D
 // Gauss-Seidel value (lk::gs_value), as the level-0 pre-smoothing before the
 // unbiased red-only residual must (the black residual then stays exactly 0).
+// skip_last_black: the last black half sweep is left to a later kernel
+// (mixed::outer_red_update forms it in triple-float).
 template <typename T>
 void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
            bool sigma_ready = false, bool backward = false, bool first_red_done = false,
-           bool exact_last = false) {
+           bool exact_last = false, bool skip_last_black = false) {
     Level<T>& L = lv[l];
     const int d = h->cfg.d;
     const int p = prec_of<T>();
@@ -379,6 +384,7 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
         }
         if (h->cfg.smoother == GMG_RBGS || h->cfg.smoother == GMG_LEARNED) {
             for (int color = first_red_done && s == 0 ? 1 : 0; color < 2; ++color) {
+                if (skip_last_black && s == sweeps - 1 && color == 1) break;
                 const bool ex = exact_last && s == sweeps - 1 && color == 1;
                 timed(h, K_RB_HALF, l, p, L.n, false,
                       [&] { lk::rb_half<T>(d, L.lay, L.u[cur], L.q, color, h->stream, ex); });
@@ -393,14 +399,19 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
 }
 
 // First level handled by the persistent tail kernel (L = none): the first
-// level with n <= 8 (3D) / 32 (2D) (GMG_TAIL_N overrides) whose tail arrays fit in 200 KB of shared
+// level with n <= 8 (3D; double-float 16) / 32 (2D) (GMG_TAIL_N overrides) whose tail arrays fit in 200 KB of shared
 // memory, below every learned level, leaving at least two tail levels.
 template <typename T>
 int tail_level(gmg_handle h, const std::vector<Level<T>>& lv) {
     const gmg_config& c = h->cfg;
     const int L = (int)lv.size();
     if (c.smoother == GMG_MCGS || c.transfer == GMG_TRANSFER_PAPER) return L;  // grid kernels
-    const int nmax = h->tail_max > 0 ? h->tail_max : c.d == 3 ? 8 : 32;
+    // 3D double-float levels run on the FP32 pipe, so one SM takes the 17^3
+    // level's sweeps in less time than the grid kernels' launches
+    const int nmax = h->tail_max > 0                         ? h->tail_max
+                     : c.d != 3                              ? 32
+                     : std::is_same<T, df32>::value ? 16
+                                                             : 8;
     int lo = 0;
     if (c.smoother == GMG_LEARNED)
         for (int l = 0; l < L && l < (int)h->lw.size(); ++l)
@@ -416,8 +427,11 @@ int tail_level(gmg_handle h, const std::vector<Level<T>>& lv) {
 // One cycle of Algorithm 1 on the hierarchy lv (level-0 iterate lv[0].u[0]
 // in and out), in stream order.  first_red_done: the cycle's first level-0
 // red half sweep already ran (fp64::red_ahead); it starts with the black one.
+// skip_last_black0: leave out the last level-0 black half sweep (red-black,
+// post-smoothing on grid kernels), which mixed::outer_red_update forms.
 template <typename T>
-gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_red_done = false) {
+gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_red_done = false,
+                          bool skip_last_black0 = false) {
     const gmg_config& c = h->cfg;
     const int d = c.d;
     const int L = (int)lv.size();
@@ -507,7 +521,7 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_re
                                        black);
                 });
             }
-            relax(h, lv, l, c.nu2, cur[l], false, true);
+            relax(h, lv, l, c.nu2, cur[l], false, true, false, false, skip_last_black0 && l == 0);
         }
     }
     if (cur[0] != 0) {
@@ -533,6 +547,19 @@ bool inner_red_ahead(gmg_handle h) {
     return c.smoother == GMG_RBGS && c.nu1 > 0 && !use_fused_rb<T>(h) && h->inner_ahead;
 }
 
+// Double-float red-black refinement with pre- and post-smoothing: after the
+// inner cycles (a black half sweep last) the black outer residual is zero up
+// to the inner rounding, so the update and the next outer residual run as
+// mixed::outer_red_update (red residual only; about 40% less FP64 work than
+// the update plus the full residual).  FP32 / BF16 inner cycles leave a
+// black residual of their own rounding (2^-24 / 2^-8 of e, and fl32(1/6)'s
+// bias), which the next step must see: they keep the full residual.
+template <typename T>
+bool outer_red_only(gmg_handle h) {
+    return std::is_same<T, df32>::value && inner_red_ahead<T>(h) && h->cfg.nu2 > 0 &&
+           h->outer_red;
+}
+
 // Refinement step: e = 0, k inner cycles on A'e = sigma, u += e, new sigma.
 template <typename T>
 gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
@@ -546,9 +573,21 @@ gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
         });
         GMG_CUDA_TRY(e);
     }
+    const bool red_only = outer_red_only<T>(h);
     for (int k = 0; k < c.inner_cycles; ++k) {
-        gmg_status st = enqueue_vcycle<T>(h, in, ahead && k == 0);
+        gmg_status st =
+            enqueue_vcycle<T>(h, in, ahead && k == 0, red_only && k == c.inner_cycles - 1);
         if (st != GMG_OK) return st;
+    }
+    if (red_only) {
+        timed(
+            h, K_OUTER_RED, 0, p, c.n, false,
+            [&] {
+                mixed::outer_red_update<T>(c.d, in[0].lay, h->lv[0].u[0], h->lv[0].q, in[0].q,
+                                           in[0].u[0], h->partial, h->d_res2, h->stream);
+            },
+            3);
+        return GMG_OK;
     }
     timed(h, K_UPDATE, 0, p, c.n, false,
           [&] { mixed::update<T>(c.d, in[0].lay, h->lv[0].u[0], in[0].u[0], h->stream); });
@@ -985,10 +1024,8 @@ gmg_status alloc_hierarchy(gmg_handle h, std::vector<Level<T>>& lv, int levels, 
         v.n = c.n >> l;
         // FP64 levels keep the caller's dense layout; the FP32/BF16 inner
         // hierarchies are colour-split (dense for the fused FP32 sweep)
-        v.lay = std::is_same<T, double>::value || use_fused_rb<T>(h) ||
-                        (std::is_same<T, df32>::value && h->df_dense)
-                    ? dense_lay(c.d, v.n)
-                    : split_lay(c.d, v.n);
+        v.lay = std::is_same<T, double>::value || use_fused_rb<T>(h) ? dense_lay(c.d, v.n)
+                                                                       : split_lay(c.d, v.n);
         v.nodes = lay_elems(c.d, v.lay);
         if (l > 0 || alloc_u0)
             if ((st = dev_alloc(h, &v.u[0], v.nodes)) != GMG_OK) return st;
@@ -1060,8 +1097,8 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     h->cfg = *cfg;
     h->user_stream = (cudaStream_t)cuda_stream;
     if (const char* v = std::getenv("GMG_FUSED_RB")) h->fused_rb = std::strcmp(v, "1") == 0;
-    if (const char* v = std::getenv("GMG_DF_SPLIT")) h->df_dense = std::strcmp(v, "0") == 0;
     if (const char* v = std::getenv("GMG_INNER_AHEAD")) h->inner_ahead = std::strcmp(v, "0") != 0;
+    if (const char* v = std::getenv("GMG_OUTER_RED")) h->outer_red = std::strcmp(v, "0") != 0;
     if (const char* v = std::getenv("GMG_TAIL_N")) h->tail_max = std::max(0, std::atoi(v));
     if (const char* v = std::getenv("GMG_DEVICE_LOOP")) h->device_loop = std::strcmp(v, "0") != 0;
     auto fail = [&](gmg_status s) {

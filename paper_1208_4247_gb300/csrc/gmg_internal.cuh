@@ -171,6 +171,15 @@ void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q
                     double* partial, double* out, cudaStream_t s, T* e_init = nullptr);
 template <typename T>
 void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s);
+// After red-black double-float inner cycles: the last black Gauss-Seidel
+// values formed in triple-float and added to u in FP64 (they replace the
+// inner cycle's last level-0 black half sweep), u += e on the red nodes, and
+// the next outer residual on the red nodes only (the black one is zero to
+// FP64 rounding): q_in = e = sigma on red nodes, 0 on black ones; sigma^2
+// sum into *out.  Two kernels and the sum.
+template <typename T>
+void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in, T* e,
+                      double* partial, double* out, cudaStream_t s);
 }  // namespace mixed
 
 // Fused red-black sweep (fused.cu, 3D FP32): u_out = one full sweep of u_in

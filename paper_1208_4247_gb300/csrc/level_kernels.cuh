@@ -59,7 +59,8 @@ struct Num<df32> {
     __device__ static df32 st(df32 v) { return v; }
 };
 
-// The Gauss-Seidel value q + c * s, c = 1/(2d).  In 3D c = 1/6 is not a
+// The Gauss-Seidel value q + c * s, c = 1/(2d), of a node whose
+// neighbours sum to s.  In 3D c = 1/6 is not a
 // binary number: fma with c = fl(1/6) = (1/6)(1 - 5.6e-17) biases every
 // product by the same relative amount.  In a residual of the full iterate u
 // (level 0) that bias is a smooth field of size 5.6e-17 |u|, which the coarse
@@ -70,9 +71,13 @@ struct Num<df32> {
 // uses the same expression, so the black residual stays exactly zero.
 constexpr double kSixthHi = 0x1.5555555555555p-3;   // fl(1/6)
 constexpr double kSixthLo = 0x1.5555555555555p-57;  // fl(1/6 - kSixthHi) = fl(2^-55 / 3)
-template <bool EXACT, typename C>
+// Double-float (C = df32): always unbiased -- s / 6 with a triple-float 1/6
+// (df.cuh, sixth), s / 4 exactly -- then q added (add_fast); c is not used.
+template <int DIM, bool EXACT, typename C>
 __device__ inline C gs_value(C c, C s, C q) {
-    if constexpr (EXACT && std::is_same<C, double>::value)
+    if constexpr (std::is_same<C, df32>::value)
+        return add_fast(DIM == 3 ? sixth(s) : quarter(s), q);
+    else if constexpr (EXACT && DIM == 3 && std::is_same<C, double>::value)
         return fma(c, s, fma(kSixthLo, s, q));
     else
         return fma(c, s, q);
@@ -110,6 +115,11 @@ template <int DIM, typename T>
 __device__ inline typename Num<T>::C nbr_sum_x(const T* u, int64_t p, int64_t xm, int64_t xp,
                                                int64_t sy, int64_t sz) {
     using N = Num<T>;
+    if constexpr (std::is_same<T, df32>::value) {  // same tree, compensated (df.cuh)
+        if (DIM == 3)
+            return sum6(u[p + xm], u[p + xp], u[p - sy], u[p - sz], u[p + sy], u[p + sz]);
+        return sum4(u[p + xm], u[p + xp], u[p - sy], u[p + sy]);
+    }
     const auto sx = N::ld(u[p + xm]) + N::ld(u[p + xp]);
     if (DIM == 3) {
         const auto lo = N::ld(u[p - sy]) + N::ld(u[p - sz]);
@@ -160,7 +170,8 @@ __global__ void __launch_bounds__(256) k_rb_half(T* __restrict__ u, const T* __r
     xnb<SPLIT>(L, i0, xm, xp);  // every node of the loop has i0's parity
     for (int i = i0 + 2 * threadIdx.x; i < n; i += 2 * blockDim.x) {
         const int64_t p = row + xo<SPLIT>(L, i);
-        u[p] = N::st(gs_value<EXACT>(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])));
+        u[p] = N::st(
+            gs_value<DIM, EXACT>(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])));
     }
 }
 
@@ -283,7 +294,7 @@ __device__ inline void stv2(df32* p, df32 a, df32 b) {
 // thread (32 bytes, two 16-byte vectors per operand row), the x neighbours
 // the V+1 consecutive entries of the row's other half.  Same operands in the
 // same order as nbr_sum_x, so the results equal k_rb_half's on the dense
-// layout bit for bit.
+// layout bit for bit (nbr_sum_x's compensated sum, gs_value).
 template <int DIM>
 __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
                                                         const df32* __restrict__ q, Lay L,
@@ -333,14 +344,9 @@ __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
     }
 #pragma unroll
     for (int t = 0; t < V; ++t) {
-        const df32 sx = xo[t] + xo[t + 1];
-        if (DIM == 3) {
-            const df32 lo = ym[t] + zm[t];
-            const df32 hi = yp[t] + zp[t];
-            out[t] = fma(c, (sx + lo) + hi, qv[t]);
-        } else {
-            out[t] = fma(c, sx + (ym[t] + yp[t]), qv[t]);
-        }
+        const df32 sum = DIM == 3 ? sum6(xo[t], xo[t + 1], ym[t], zm[t], yp[t], zp[t])
+                                  : sum4(xo[t], xo[t + 1], ym[t], yp[t]);
+        out[t] = gs_value<DIM, true>(c, sum, qv[t]);
     }
     if (x0 >= 1 && x0 + 2 * (V - 1) <= n - 1) {
         stv2(u + base, out[0], out[1]);
@@ -406,7 +412,8 @@ __global__ void __launch_bounds__(256, 4) k_rb_half3_walk(T* __restrict__ u, con
             for (int r = 0; r < kWalk; ++r) {
                 if (r < run) {
                     const C hi = yp[r] + zp[r];
-                    u[p0 + r * dp] = N::st(gs_value<EXACT>(c, ((xm[r] + xp[r]) + lo) + hi, qv[r]));
+                    u[p0 + r * dp] =
+                        N::st(gs_value<3, EXACT>(c, ((xm[r] + xp[r]) + lo) + hi, qv[r]));
                     lo = hi;
                 }
             }
@@ -463,7 +470,7 @@ __global__ void __launch_bounds__(256, 4) k_residual3_walk(const T* __restrict__
     const int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
     if (w >= (int64_t)(n - 1) * segs) return;
     walk_nodes(u, n, 0, w, segs, [&](int64_t p, C sum, int, int, int) {
-        r[p] = N::st(gs_value<EXACT>(c, sum, N::ld(q[p])) - N::ld(u[p]));
+        r[p] = N::st(gs_value<3, EXACT>(c, sum, N::ld(q[p])) - N::ld(u[p]));
     });
 }
 
@@ -509,7 +516,8 @@ __global__ void __launch_bounds__(256) k_wj(const T* __restrict__ u, T* __restri
         int64_t xm, xp;
         xnb<SPLIT>(L, i, xm, xp);
         const C up = N::ld(u[p]);
-        const C sig = fma(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])) - up;
+        const C sig =
+            gs_value<DIM, false>(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])) - up;
         uo[p] = N::st(fma(omega, sig, up));
     }
 }
@@ -533,8 +541,9 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
         const int64_t p = row + xo<SPLIT>(L, i);
         int64_t xm, xp;
         xnb<SPLIT>(L, i, xm, xp);
-        r[p] = N::st(gs_value<EXACT>(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])) -
-                     N::ld(u[p]));
+        r[p] = N::st(
+            gs_value<DIM, EXACT>(c, nbr_sum_x<DIM>(u, p, xm, xp, L.sy, L.sz), N::ld(q[p])) -
+            N::ld(u[p]));
     }
 }
 

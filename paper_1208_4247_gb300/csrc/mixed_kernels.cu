@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
         const int64_t row_in = k * in.sz + j * in.sy;
         for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
             const int64_t p = row + i;
-            const double sig = lk::gs_value<DIM == 3>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
+            const double sig = lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
             store_inner(q_in, e_init, row_in + lk::xo<SPLIT>(in, i), sig, ((i + j + k) & 1) == 0);
             acc = fma(sig, sig, acc);
         }
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256, 4) k_outer_residual3_walk(const double* _
          w += (int64_t)gridDim.x * blockDim.y)
         for (int color = 0; color < 2; ++color)
             lk::walk_nodes(u, n, color, w, segs, [&](int64_t p, double sum, int i, int j, int k) {
-                const double sig = lk::gs_value<true>(c, sum, q[p]) - u[p];
+                const double sig = lk::gs_value<3, true>(c, sum, q[p]) - u[p];
                 store_inner(q_in, e_init, k * in.sz + j * in.sy + lk::xo<SPLIT>(in, i), sig,
                             color == 0);
                 acc = fma(sig, sig, acc);
@@ -143,7 +143,183 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ u, const T*
     }
 }
 
+// Double-float refinement after the inner cycles (red-black): the black
+// nodes' last Gauss-Seidel values are formed here, from the red corrections,
+// in triple-float (df.cuh, sum_tf / fma_tf) and added to u in FP64, so that
+// the black residual of the new u is zero up to FP64 rounding, and the next
+// outer residual runs on the red nodes only (k_outer_red).  (Stored as
+// double-float, the black correction's own rounding, 2^-47 of it, would stay
+// in the black residual for good: the red-only residual never sees it.)
+// e = q_in = 0 on the black nodes: the next step's inner iterate after its
+// first red half sweep, and its black right-hand side.  Replaces the inner
+// cycle's last level-0 black half sweep (it is a function of the red values
+// only, so recomputing it after a tail that ran it changes nothing).
+template <int DIM, bool SPLIT>
+__global__ void __launch_bounds__(256) k_black_exact_update(double* __restrict__ u,
+                                                            df32* __restrict__ e,
+                                                            df32* __restrict__ q_in, Lay in) {
+    const int n = in.n;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
+         r += (int64_t)gridDim.x * blockDim.y) {
+        const int j = (int)(r % (n - 1)) + 1;
+        const int k = DIM == 3 ? (int)(r / (n - 1)) + 1 : 0;
+        const int64_t row = k * sz + j * sy;
+        const int64_t row_in = k * in.sz + j * in.sy;
+        for (int i = 1 + ((j + k) & 1) + 2 * threadIdx.x; i < n; i += 2 * blockDim.x) {
+            const int64_t idx = row_in + lk::xo<SPLIT>(in, i);
+            int64_t xm, xp;
+            lk::xnb<SPLIT>(in, i, xm, xp);
+            tf32 v;
+            if constexpr (DIM == 3) {
+                const df32 x[6] = {e[idx + xm],    e[idx + xp],    e[idx - in.sy],
+                                   e[idx - in.sz], e[idx + in.sy], e[idx + in.sz]};
+                v = fma_tf(sum_tf(x), kSixth0, kSixth1, kSixth2, q_in[idx]);
+            } else {
+                const df32 x[4] = {e[idx + xm], e[idx + xp], e[idx - in.sy], e[idx + in.sy]};
+                v = fma_tf(sum_tf(x), 0.25f, 0.f, 0.f, q_in[idx]);
+            }
+            u[row + i] += tf_to_double(v);
+            e[idx] = df32(0.f, 0.f);
+            q_in[idx] = df32(0.f, 0.f);
+        }
+    }
+}
+
+// The red nodes: u += e, sigma (unbiased 1/(2d)) from the updated neighbours,
+// q_in = e = sigma (the next step's first inner red half sweep), partial sums
+// of sigma^2 (the stopping-test norm: the black terms are zero to rounding).
+template <int DIM, bool SPLIT, typename T>
+__global__ void __launch_bounds__(kThreads) k_outer_red(double* __restrict__ u,
+                                                        const double* __restrict__ q,
+                                                        T* __restrict__ q_in, T* __restrict__ e,
+                                                        double* __restrict__ partial, Lay in) {
+    using N = lk::Num<T>;
+    __shared__ double warp_sums[kThreads / 32];
+    const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
+    const int n = in.n;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
+    double acc = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
+         r += (int64_t)gridDim.x * blockDim.y) {
+        const int j = (int)(r % (n - 1)) + 1;
+        const int k = DIM == 3 ? (int)(r / (n - 1)) + 1 : 0;
+        const int64_t row = k * sz + j * sy;
+        const int64_t row_in = k * in.sz + j * in.sy;
+        for (int i = 1 + ((1 + j + k) & 1) + 2 * threadIdx.x; i < n; i += 2 * blockDim.x) {
+            const int64_t p = row + i;
+            const int64_t idx = row_in + lk::xo<SPLIT>(in, i);
+            const double un = u[p] + (double)N::ld(e[idx]);
+            u[p] = un;
+            const double sig = lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - un;
+            const T st = N::st(typename N::C(sig));
+            q_in[idx] = st;
+            e[idx] = st;
+            acc = fma(sig, sig, acc);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((t & 31) == 0) warp_sums[t >> 5] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += warp_sums[w];
+        partial[blockIdx.x] = sum;
+    }
+}
+
+// The same by the diagonal walkers (red nodes; the black neighbours are read
+// through uc, never written here; each red node is read and written through
+// u by its own thread only).
+template <bool SPLIT, typename T>
+__global__ void __launch_bounds__(256, 4) k_outer_red3_walk(double* __restrict__ u,
+                                                            const double* __restrict__ uc,
+                                                            const double* __restrict__ q,
+                                                            T* __restrict__ q_in,
+                                                            T* __restrict__ e,
+                                                            double* __restrict__ partial, Lay in,
+                                                            int segs) {
+    using N = lk::Num<T>;
+    __shared__ double warp_sums[kThreads / 32];
+    const double c = 1.0 / 6.0;
+    const int n = in.n;
+    const int64_t walkers = (int64_t)(n - 1) * segs;
+    double acc = 0.0;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; w < walkers;
+         w += (int64_t)gridDim.x * blockDim.y)
+        lk::walk_nodes(uc, n, 0, w, segs, [&](int64_t p, double sum, int i, int j, int k) {
+            const int64_t idx = k * in.sz + j * in.sy + lk::xo<SPLIT>(in, i);
+            const double un = u[p] + (double)N::ld(e[idx]);
+            u[p] = un;
+            const double sig = lk::gs_value<3, true>(c, sum, q[p]) - un;
+            const T st = N::st(typename N::C(sig));
+            q_in[idx] = st;
+            e[idx] = st;
+            acc = fma(sig, sig, acc);
+        });
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((t & 31) == 0) warp_sums[t >> 5] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double sum = 0.0;
+        for (int ww = 0; ww < kThreads / 32; ++ww) sum += warp_sums[ww];
+        partial[blockIdx.x] = sum;
+    }
+}
+
 }  // namespace
+
+template <typename T>
+void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in, T* e,
+                      double* partial, double* out, cudaStream_t s) {
+    static_assert(std::is_same<T, df32>::value, "the red-only outer residual is double-float");
+    const int n = in.n;
+    int bx = 32;
+    while (bx < n / 2 && bx < 128) bx *= 2;
+    const dim3 block(bx, kThreads / bx, 1);
+    const int64_t rows = d == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
+    const int ublocks = (int)std::min<int64_t>((rows + block.y - 1) / block.y, 152 * 16);
+    if (d == 3) {
+        if (in.he)
+            k_black_exact_update<3, true><<<ublocks, block, 0, s>>>(u, e, q_in, in);
+        else
+            k_black_exact_update<3, false><<<ublocks, block, 0, s>>>(u, e, q_in, in);
+    } else {
+        if (in.he)
+            k_black_exact_update<2, true><<<ublocks, block, 0, s>>>(u, e, q_in, in);
+        else
+            k_black_exact_update<2, false><<<ublocks, block, 0, s>>>(u, e, q_in, in);
+    }
+    if (lk::walk_applies(d, n, sizeof(double))) {
+        const lk::WalkLaunch W = lk::walk_launch(n);
+        const int blocks = (int)std::min<int64_t>(W.blocks, outer_partials(d, n));
+        if (in.he)
+            k_outer_red3_walk<true, T><<<blocks, W.block, 0, s>>>(u, u, q, q_in, e, partial, in,
+                                                                  W.segs);
+        else
+            k_outer_red3_walk<false, T><<<blocks, W.block, 0, s>>>(u, u, q, q_in, e, partial, in,
+                                                                   W.segs);
+        fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
+        return;
+    }
+    const int blocks = outer_partials(d, n);
+    if (d == 3) {
+        if (in.he)
+            k_outer_red<3, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+        else
+            k_outer_red<3, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+    } else {
+        if (in.he)
+            k_outer_red<2, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+        else
+            k_outer_red<2, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+    }
+    fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
+}
 
 int outer_partials(int d, int n) {
     int bx = 32;
@@ -215,6 +391,8 @@ template void outer_residual<__nv_bfloat16>(int, const Lay&, const double*, cons
                                             __nv_bfloat16*);
 template void outer_residual<df32>(int, const Lay&, const double*, const double*, df32*, double*,
                                    double*, cudaStream_t, df32*);
+template void outer_red_update<df32>(int, const Lay&, double*, const double*, df32*, df32*,
+                                     double*, double*, cudaStream_t);
 template void update<float>(int, const Lay&, double*, const float*, cudaStream_t);
 template void update<df32>(int, const Lay&, double*, const df32*, cudaStream_t);
 template void update<__nv_bfloat16>(int, const Lay&, double*, const __nv_bfloat16*, cudaStream_t);

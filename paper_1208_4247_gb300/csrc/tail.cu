@@ -75,8 +75,8 @@ __device__ void rb_half(SLevel<T>& L, int color, bool ex = false) {
             const int64_t p = inode<DIM, NN>(idx, i, j, k);
             if (((i + j + k) & 1) != color) continue;
             const C s = lk::nbr_sum<DIM>(L.u, p, sy, sz);
-            L.u[p] = N::st(ex ? lk::gs_value<true>(c, s, N::ld(L.q[p]))
-                              : lk::gs_value<false>(c, s, N::ld(L.q[p])));
+            L.u[p] = N::st(ex ? lk::gs_value<DIM, true>(c, s, N::ld(L.q[p]))
+                              : lk::gs_value<DIM, false>(c, s, N::ld(L.q[p])));
         }
     });
     __syncthreads();
@@ -94,7 +94,8 @@ __device__ void wj_sweep(SLevel<T>& L, double omega_d) {
             int i, j, k;
             const int64_t p = inode<DIM, NN>(idx, i, j, k);
             const C up = N::ld(L.u[p]);
-            const C sig = fma(c, lk::nbr_sum<DIM>(L.u, p, sy, sz), N::ld(L.q[p])) - up;
+            const C sig =
+                lk::gs_value<DIM, false>(c, lk::nbr_sum<DIM>(L.u, p, sy, sz), N::ld(L.q[p])) - up;
             L.u2[p] = N::st(fma(omega, sig, up));
         }
     });
@@ -129,8 +130,8 @@ __device__ void residual(SLevel<T>& L, bool red_only, bool ex = false) {
             const int64_t p = inode<DIM, NN>(idx, i, j, k);
             if (red_only && ((i + j + k) & 1)) continue;
             const C s = lk::nbr_sum<DIM>(L.u, p, sy, sz);
-            const C v = ex ? lk::gs_value<true>(c, s, N::ld(L.q[p]))
-                           : lk::gs_value<false>(c, s, N::ld(L.q[p]));
+            const C v = ex ? lk::gs_value<DIM, true>(c, s, N::ld(L.q[p]))
+                           : lk::gs_value<DIM, false>(c, s, N::ld(L.q[p]));
             L.r[p] = N::st(v - N::ld(L.u[p]));
         }
     });

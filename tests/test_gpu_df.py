@@ -138,23 +138,45 @@ def test_df_solve_takes_the_oracle_cycles(torch_cuda, case):
 
 
 @pytest.mark.parametrize("d,n", [(3, 128), (3, 32), (2, 256)])
-@pytest.mark.parametrize("env", [("GMG_DF_SPLIT", "0"), ("GMG_INNER_AHEAD", "0")])
-def test_df_variants_bit_identical(torch_cuda, monkeypatch, d, n, env):
-    """The colour-split double-float layout (vector half sweeps) against the
-    dense one (row kernels / diagonal walkers), and the first inner red half
-    sweep written by the outer residual against a memset plus a separate
-    half sweep: the same iterate bit for bit after two steps."""
+def test_df_inner_ahead_bit_identical(torch_cuda, monkeypatch, d, n):
+    """The first inner red half sweep written by the outer residual against a
+    memset plus a separate half sweep: the same iterate bit for bit after two
+    steps (both with the full outer residual)."""
     torch = torch_cuda
     from paper_1208_4247_gb300.gmg import Solver
     f = torch.from_numpy(inputs.rhs_uniform(d, n, 6)).cuda()
+    monkeypatch.setenv("GMG_OUTER_RED", "0")
     out = []
-    for flag in ("1", env[1]):
-        monkeypatch.setenv(env[0], flag)
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GMG_INNER_AHEAD", flag)
         u = torch.zeros_like(f)
         with Solver(d, n, precision="df", inner_cycles=1) as S:
             S.cycles(f, u, 2)
         out.append(u.cpu().numpy())
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("d,n", [(3, 256), (3, 32), (2, 256)])
+def test_df_red_only_outer_residual(torch_cuda, monkeypatch, d, n):
+    """Red-only outer residual with the update fused (default) against the
+    update plus the full residual: the black residual it leaves out is the
+    inner cycle's rounding, so three steps agree to far below the per-cycle
+    bar and whole solves take the same number of cycles."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    fn = inputs.rhs_uniform(d, n, 6)
+    f = torch.from_numpy(fn).cuda()
+    out, its = [], []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GMG_OUTER_RED", flag)
+        u = torch.zeros_like(f)
+        with Solver(d, n, precision="df", inner_cycles=1) as S:
+            S.cycles(f, u, 3)
+            out.append(u.cpu().numpy())
+            u.zero_()
+            its.append(S.solve(f, u, 1e-10)[0])
+    assert _max_rel(out[0], out[1]) <= TOL_CYCLE
+    assert its[0] == its[1]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
