@@ -43,17 +43,29 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the level-0 red-black half sweep of
 # the 257^3 FP64 solve, from one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum: 269.5 MB + 85.8 MB)
-RB_HALF_L0_TRAFFIC = 356.4e6  # ncu dram read + write of one level-0 walker half sweep, 257^3
 # FP64 instructions of one updated node (adds, fmas) of the FP64 level
 # kernels that can dominate a solve: the diagonal-walker half sweep executes
 # 4 + 1/4 adds and one fma per node
 FP64_MIX = {"rb_half": (4.25, 1.0), "resnorm_red_sweep": (5.25, 2.0), "residual": (5.25, 1.0),
             # double-float step: black 3 adds; red 4.25 + 3 adds, 3 fmas (per node, both halves)
             "outer_red_update_df": (10.25, 3.0)}
-# DRAM bytes (read + write) per launch of the double-float step's FP64 outer
-# kernels at 257^3 (k_black_exact_update + k_outer_red3_walk, one ncu capture
-# each: 290.4 + 210.3 MB and 345.4 + 212.9 MB)
-OUTER_RED_TRAFFIC = 1059.0e6
+# DRAM bytes (read + write) per launch at 257^3 from one ncu capture each
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (kernel record,
+# level); a kernel changed since its capture has no entry.
+TRAFFIC = {
+    ("rb_half", 0): 356.4e6,  # FP64 walker half sweep: 269.5 + 85.8 MB
+    # double-float step's outer kernels: k_black_exact_update 290.4 + 210.3 MB,
+    # k_outer_red3_walk 345.4 + 212.9 MB
+    ("outer_red_update_df", 0): 1059.0e6,
+}
+
+
+def fp64_bound(name: str) -> bool:
+    """Kernels whose arithmetic runs on the FP64 pipe: the plain FP64 level
+    kernels and every refinement form's outer residual / update."""
+    if name.startswith(("outer_", "update")):
+        return True
+    return not name.endswith(("_df", "_f32", "_bf16"))
 
 
 def peaks():
@@ -126,14 +138,10 @@ class ClockSampler:
 
 
 def dominant(stats):
-    """Kernel with the largest summed device time; its level-0 record."""
-    by_kernel = {}
-    for s in stats:
-        by_kernel.setdefault(s["kernel"], []).append(s)
-    tot_ms = {k: sum(r["ms"] for r in v) for k, v in by_kernel.items()}
-    dom = max(tot_ms, key=tot_ms.get)
-    recs = sorted(by_kernel[dom], key=lambda r: r["level"])
-    return dom, recs[0], tot_ms[dom] / sum(tot_ms.values())
+    """The (kernel, level) record with the largest summed device time: its
+    kernel name, the record and its share of all kernel time."""
+    rec = max(stats, key=lambda r: r["ms"])
+    return rec["kernel"], rec, rec["ms"] / sum(r["ms"] for r in stats)
 
 
 def time_solves(torch, S, f, u, steps, warmup, timing=True):
@@ -791,42 +799,50 @@ def run_ours(args, rank, ws, local):
 
     # dominant kernel: largest summed device time; achieved = its per-launch
     # FP64 instruction count / its average launch time (level 0 record)
-    by_kernel = {}
-    for s in stats:
-        by_kernel.setdefault(s["kernel"], []).append(s)
-    tot_ms = {k: sum(r["ms"] for r in v) for k, v in by_kernel.items()}
-    dom = max(tot_ms, key=tot_ms.get)
-    rec = [r for r in by_kernel[dom] if r["level"] == 0][0]
-    avg_s = rec["ms"] / rec["launches"] * 1e-3
     clocks = clk.summary()
-    nominal_inst = FP64_INST_PER_CLK_SM * NUM_SMS * SM_MAX_MHZ * 1e6 / 1e12  # T inst/s
-    achieved = rec["dp_ops"] / avg_s / 1e12
     pk, pk_kind = peaks()
     alg_bytes = sum(r["bytes"] * r["launches"] for r in stats) / args.steps
     # the FP64 pipe's rate measured in this run (independent DFMA / DADD
-    # chains), weighted by the dominant kernel's add : fma mix
+    # chains), weighted by a kernel's add : fma mix
     from paper_1208_4247_gb300.gmg import measure_fp64_rate
     r_fma, r_add = measure_fp64_rate(0) / 1e12, measure_fp64_rate(1) / 1e12
-    n_add, n_fma = FP64_MIX.get(dom, (1.0, 0.0))
-    peak_meas = (n_add + n_fma) / (n_add / r_add + n_fma / r_fma)
-    kernel_gbs = rec["bytes"] / avg_s / 1e9
-    roof = {"bound": "alu", "kernel": f"{dom} (level 0)", "achieved": achieved,
-            "peak": peak_meas, "unit": "T FP64-pipe inst/s", "frac": achieved / peak_meas,
-            "traffic": {"rb_half": RB_HALF_L0_TRAFFIC,
-                        "outer_red_update_df": OUTER_RED_TRAFFIC}.get(dom),
-            "traffic_unit": "bytes per launch (ncu)",
-            "alg_bytes_per_launch": rec["bytes"],
-            "peak_note": (f"measured in this run: {r_fma:.4f} T DFMA/s, {r_add:.4f} T DADD/s "
-                          f"(gmg_measure_fp64_rate), weighted {n_add}:{n_fma} add:fma"),
-            "peak_measured": {"dfma": r_fma, "dadd": r_add, "mix": peak_meas},
-            "peak_nominal": nominal_inst,
-            "hbm_frac": kernel_gbs / pk["hbm_gbs"], "hbm_peak_gbs": pk["hbm_gbs"],
-            "hbm_peak_kind": pk_kind,
-            "kernel_share": tot_ms[dom] / sum(tot_ms.values()),
-            "timing": "per-kernel CUDA events (event nodes in the cycle graph on the "
-                      "library's stream) over a repeat of the timed steps",
-            "instrumented_ms_per_step": ms_instr,
-            "kernel_hbm_gbs": kernel_gbs}
+    nominal_inst = FP64_INST_PER_CLK_SM * NUM_SMS * SM_MAX_MHZ * 1e6 / 1e12  # T inst/s
+    total_ms = sum(r["ms"] for r in stats)
+
+    def roofline_of(rec):
+        """The roofline record of one (kernel, level): FP64-pipe bound for the
+        FP64 kernels, HBM bound for the double-float / FP32 / BF16 ones."""
+        name = rec["kernel"]
+        avg_s = rec["ms"] / rec["launches"] * 1e-3
+        gbs = rec["bytes"] / avg_s / 1e9
+        common = {"kernel": f"{name} (level {rec['level']})", "alg_bytes_per_launch": rec["bytes"],
+                  "traffic": TRAFFIC.get((name, rec["level"])),
+                  "traffic_unit": "bytes per launch (ncu dram read + write)",
+                  "kernel_share": rec["ms"] / total_ms, "avg_launch_us": avg_s * 1e6,
+                  "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"]}
+        if fp64_bound(name):
+            n_add, n_fma = FP64_MIX.get(name, (1.0, 0.0))
+            peak = (n_add + n_fma) / (n_add / r_add + n_fma / r_fma)
+            ach = rec["dp_ops"] / avg_s / 1e12
+            return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP64-pipe inst/s",
+                    "frac": ach / peak,
+                    "peak_note": (f"measured in this run: {r_fma:.4f} T DFMA/s, {r_add:.4f} T "
+                                  f"DADD/s (gmg_measure_fp64_rate), weighted {n_add}:{n_fma} "
+                                  "add:fma"), **common}
+        return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / pk["hbm_gbs"], "peak_note": f"{pk_kind} copy bandwidth", **common}
+
+    dom_rec = max(stats, key=lambda r: r["ms"])  # the largest (kernel, level) record
+    roof = roofline_of(dom_rec)
+    roof.update({"peak_measured_fp64": {"dfma": r_fma, "dadd": r_add},
+                 "peak_nominal_fp64": nominal_inst, "hbm_peak_gbs": pk["hbm_gbs"],
+                 "hbm_peak_kind": pk_kind,
+                 "timing": "per-kernel CUDA events (event nodes in the cycle graph on the "
+                           "library's stream) over a repeat of the timed steps",
+                 "instrumented_ms_per_step": ms_instr})
+    hbm_recs = [r for r in stats if not fp64_bound(r["kernel"])]
+    if hbm_recs:
+        roof["hbm_kernel"] = roofline_of(max(hbm_recs, key=lambda r: r["ms"]))
     hbm = {"solve_alg_bytes": alg_bytes, "achieved_gbs": alg_bytes / (ms_step * 1e-3) / 1e9,
            "peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind,
            "frac": alg_bytes / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"],

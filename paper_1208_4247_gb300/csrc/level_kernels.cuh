@@ -280,6 +280,12 @@ __global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T*
     }
 }
 
+// Double-float nodes per thread of the colour-split half sweep.
+#ifndef GMG_DF_VEC
+#define GMG_DF_VEC 2
+#endif
+constexpr int kDfVec = GMG_DF_VEC;
+
 // Two double-float nodes = one 16-byte vector of a colour-split half row.
 __device__ inline void ldv2(const df32* p, df32& a, df32& b) {
     const float4 v = *reinterpret_cast<const float4*>(p);
@@ -290,16 +296,20 @@ __device__ inline void stv2(df32* p, df32 a, df32 b) {
     *reinterpret_cast<float4*>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
 }
 
-// k_rb_half_vec for double-float storage: V = 4 nodes of the colour per
-// thread (32 bytes, two 16-byte vectors per operand row), the x neighbours
-// the V+1 consecutive entries of the row's other half.  Same operands in the
-// same order as nbr_sum_x, so the results equal k_rb_half's on the dense
-// layout bit for bit (nbr_sum_x's compensated sum, gs_value).
-template <int DIM>
+// k_rb_half_vec for double-float storage: V (2 or 4) nodes of the colour per
+// thread (V/2 16-byte vectors per operand row), the x neighbours the V+1
+// consecutive entries of the row's other half.  Same operands in the same
+// order as nbr_sum_x on the dense layout (its compensated sum, gs_value).
+template <int V>
+__device__ __forceinline__ void ldvn(const df32* p, df32 (&v)[V]) {
+#pragma unroll
+    for (int h = 0; h < V / 2; ++h) ldv2(p + 2 * h, v[2 * h], v[2 * h + 1]);
+}
+template <int DIM, int V>
 __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
                                                         const df32* __restrict__ q, Lay L,
                                                         int color, int G) {
-    constexpr int V = 4;
+    static_assert(V == 2 || V == 4, "V nodes of 8 bytes per thread: one or two 16-byte vectors");
     const df32 c = DIM == 3 ? df32(1.0 / 6.0) : df32(0.25);
     const int n = L.n, m = n - 1;
     const int64_t rows = DIM == 3 ? (int64_t)m * m : m;
@@ -319,8 +329,7 @@ __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
         // entries V g - 1 + par .. V g + V - 1 + par of the other half, with
         // compile-time indices only (a runtime index would put xo on the stack)
         df32 v[V];
-        ldv2(u + ob, v[0], v[1]);
-        ldv2(u + ob + 2, v[2], v[3]);
+        ldvn(u + ob, v);
         const df32 edge = par ? u[ob + V] : g > 0 ? u[ob - 1] : df32(0.f, 0.f);  // g == 0: x = 0
 #pragma unroll
         for (int t = 0; t <= V; ++t) {
@@ -330,17 +339,12 @@ __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
         }
     }
     df32 qv[V], ym[V], yp[V], zm[V], zp[V], out[V];
-    ldv2(q + base, qv[0], qv[1]);
-    ldv2(q + base + 2, qv[2], qv[3]);
-    ldv2(u + base - L.sy, ym[0], ym[1]);
-    ldv2(u + base - L.sy + 2, ym[2], ym[3]);
-    ldv2(u + base + L.sy, yp[0], yp[1]);
-    ldv2(u + base + L.sy + 2, yp[2], yp[3]);
+    ldvn(q + base, qv);
+    ldvn(u + base - L.sy, ym);
+    ldvn(u + base + L.sy, yp);
     if (DIM == 3) {
-        ldv2(u + base - L.sz, zm[0], zm[1]);
-        ldv2(u + base - L.sz + 2, zm[2], zm[3]);
-        ldv2(u + base + L.sz, zp[0], zp[1]);
-        ldv2(u + base + L.sz + 2, zp[2], zp[3]);
+        ldvn(u + base - L.sz, zm);
+        ldvn(u + base + L.sz, zp);
     }
 #pragma unroll
     for (int t = 0; t < V; ++t) {
@@ -349,8 +353,8 @@ __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
         out[t] = gs_value<DIM, true>(c, sum, qv[t]);
     }
     if (x0 >= 1 && x0 + 2 * (V - 1) <= n - 1) {
-        stv2(u + base, out[0], out[1]);
-        stv2(u + base + 2, out[2], out[3]);
+#pragma unroll
+        for (int h = 0; h < V / 2; ++h) stv2(u + base + 2 * h, out[2 * h], out[2 * h + 1]);
     } else {
 #pragma unroll
         for (int t = 0; t < V; ++t) {
@@ -917,14 +921,14 @@ void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s, b
     }
     if constexpr (std::is_same<T, df32>::value) {
         if (L.he) {
-            constexpr int V = 4;
+            constexpr int V = kDfVec;
             const int G = (n / 2 + 1 + V - 1) / V;
             const int64_t items = (int64_t)G * (d == 3 ? (int64_t)(n - 1) * (n - 1) : n - 1);
             const unsigned blocks = (unsigned)((items + 255) / 256);
             if (d == 3)
-                k_rb_half_vec_df<3><<<blocks, 256, 0, s>>>(u, q, L, color, G);
+                k_rb_half_vec_df<3, V><<<blocks, 256, 0, s>>>(u, q, L, color, G);
             else
-                k_rb_half_vec_df<2><<<blocks, 256, 0, s>>>(u, q, L, color, G);
+                k_rb_half_vec_df<2, V><<<blocks, 256, 0, s>>>(u, q, L, color, G);
             return;
         }
     }
