@@ -310,7 +310,10 @@ typedef struct gmg_batch_s* gmg_batch;
 
 /* count solves; d[i], n[i] per solve (as in gmg_config); *common gives the
  * smoother, omega, nu1, nu2, precision, inner_cycles and maxit (its d, n,
- * levels are ignored: every solve uses all its levels).  chunk: nodes per
+ * levels are ignored: every solve uses all its levels).  omega = 0 gives the
+ * 2D solves weighted Jacobi with 4/5 and the 3D ones 6/7 (the weight with the
+ * smaller two-grid contraction in 3D); any other omega in (0, 2) applies to
+ * every solve.  chunk: nodes per
  * work item (0 = 1024); ctas: CTAs per launch (0 = 4 x SM count). */
 gmg_status gmg_batch_create(int count, const int* d, const int* n, const gmg_config* common,
                             int chunk, int ctas, void* cuda_stream, gmg_batch* out);

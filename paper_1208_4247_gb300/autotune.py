@@ -29,15 +29,21 @@ def _time(torch, fn, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
-def tune_batch(dims, ns, fd, ud, rtol=1e-10, ks=(1, 2, 3), chunks=(512, 1024, 2048, 4096),
-               ctas=(152, 304, 608, 1216), **kw):
-    """Returns (best parameter dict, list of (params, ms) tried)."""
+def tune_batch(dims, ns, fd, ud, rtol=1e-10, ks=(1, 2, 3), chunks=(512, 1024, 2048, 4096, 8192),
+               ctas=(152, 304, 608, 1216, 2432, 4864), **kw):
+    """Returns (best parameter dict, list of (params, ms) tried).  Coordinate
+    search (inner cycles, then tile, then CTAs), then inner cycles and tile
+    once more at the chosen CTA count; settings already timed are reused."""
     import torch
     from .gmg import Batch
 
     tried = []
+    seen = {}
 
     def measure(p):
+        key = (p["inner_cycles"], p["chunk"], p["ctas"])
+        if key in seen:
+            return seen[key]
         with Batch(dims, ns, inner_cycles=p["inner_cycles"], chunk=p["chunk"], ctas=p["ctas"],
                    **kw) as B:
             def run():
@@ -47,10 +53,12 @@ def tune_batch(dims, ns, fd, ud, rtol=1e-10, ks=(1, 2, 3), chunks=(512, 1024, 20
                 assert conv
             ms = _time(torch, run)
         tried.append((dict(p), ms))
+        seen[key] = ms
         return ms
 
     best = {"inner_cycles": ks[0], "chunk": 1024, "ctas": 608}
-    for key, values in (("inner_cycles", ks), ("chunk", chunks), ("ctas", ctas)):
+    for key, values in (("inner_cycles", ks), ("chunk", chunks), ("ctas", ctas),
+                        ("inner_cycles", ks), ("chunk", chunks)):
         scores = {}
         for v in values:
             p = dict(best)

@@ -114,13 +114,14 @@ __global__ void __launch_bounds__(256) k_smooth(const Item* __restrict__ items, 
                                                 const T* __restrict__ pool_in,
                                                 T* __restrict__ pool_out,
                                                 const int* __restrict__ active, int src, int dst,
-                                                int color, float omega) {
+                                                int color, float omega2, float omega3) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const Item w = items[it];
         if (!active[w.solve]) continue;
         const BLevel L = lv[sv[w.solve].lev0 + w.level];
         const bool three = L.d == 3;
         const float c = three ? 1.f / 6.f : 0.25f;
+        const float omega = three ? omega3 : omega2;
         const int64_t sy = L.n + 1, sz = three ? sy * sy : 0;
         const T* u = pool_in + off_u(L, src);
         T* uo = pool_out + off_u(L, dst);
@@ -507,7 +508,10 @@ gmg_status enqueue_step(gmg_batch b, double rtol2) {
     T* pool = static_cast<T*>(b->pool);
     const double w = sizeof(T);
     const bool rbgs = c.smoother == GMG_RBGS;
-    const float omega = (float)c.omega;
+    // weighted-Jacobi weight per dimension: the configured one, or with
+    // omega = 0 the defaults 4/5 (2D) and 6/7 (3D)
+    const float omega2 = c.omega > 0.0 ? (float)c.omega : 0.8f;
+    const float omega3 = c.omega > 0.0 ? (float)c.omega : (float)(6.0 / 7.0);
     b->timer.begin_capture();
     const int64_t n0 = range_nodes(b, b->level0);
     launch_op<T>(b, "b_zero", 0, b->level0, w, 0, n0, [&](int grid, const Item* it, int ni) {
@@ -524,14 +528,14 @@ gmg_status enqueue_step(gmg_batch b, double rtol2) {
                                  [&](int grid, const Item* it, int ni) {
                                      k_smooth<T><<<grid, 256, 0, b->stream>>>(
                                          it, ni, b->ds, b->dl, pool, pool, b->active, cur[g],
-                                         cur[g], color, omega);
+                                         cur[g], color, omega2, omega3);
                                  });
             } else {
                 launch_op<T>(b, "b_wj_sweep", g, r, 3 * w, 8.0, nn,
                              [&](int grid, const Item* it, int ni) {
                                  k_smooth<T><<<grid, 256, 0, b->stream>>>(
                                      it, ni, b->ds, b->dl, pool, pool, b->active, cur[g],
-                                     cur[g] ^ 1, -1, omega);
+                                     cur[g] ^ 1, -1, omega2, omega3);
                              });
                 cur[g] ^= 1;
             }
@@ -669,7 +673,7 @@ gmg_status gmg_batch_create(int count, const int* d, const int* n, const gmg_con
     }
     if (common->nu1 < 0 || common->nu2 < 0 || common->nu1 > 16 || common->nu2 > 16 ||
         common->inner_cycles < 1 || common->inner_cycles > 64 || common->maxit < 0 ||
-        !(common->omega > 0.0 && common->omega < 2.0)) {
+        !(common->omega >= 0.0 && common->omega < 2.0)) {
         set_error("gmg_batch_create: nu1, nu2, inner_cycles, maxit or omega out of range");
         return GMG_ERR_ARG;
     }
