@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "gmg_internal.cuh"
+#include "legs_api.h"
 #include "timing.cuh"
 
 namespace gmg {
@@ -86,6 +87,14 @@ struct gmg_handle_s {
     // cycle's first level-0 red half sweep (norm_ahead_ok)
     bool ahead = false;
     int tail_max = 0;       // GMG_TAIL_N at create: largest tail level n (0 = default)
+    // fused leg kernels (legs.cu) on large 3D levels of the red-black inner
+    // hierarchies.  legs_mode 1 (default): FP32 levels with n >= 512, where
+    // they beat the unfused kernels; 2 (GMG_FUSED_LEGS=1 at create): FP32
+    // and double-float levels with n >= 128; 0 (GMG_FUSED_LEGS=0): off.
+    // GMG_LEG_NMIN overrides the smallest level n.
+    int legs_mode = 1;
+    int leg_nmin = 0;
+    bool legs_used = false;
     // learned smoother (GMG_LEARNED): per level BF16-rounded weights on the
     // device (NULL: red-black GS on that level) and the hidden-layer buffer
     std::vector<float*> lw, lz;
@@ -219,13 +228,14 @@ int num_levels(const gmg_config& c) { return c.levels > 0 ? c.levels : ilog2(c.n
 enum Kind {
     K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_OUTER_RES,
     K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_TAIL, K_RB_FUSED, K_MC_SWEEP, K_RESTRICT_PAPER,
-    K_PROLONG_PAPER, K_NORM_AHEAD, K_OUTER_RED, K_COUNT
+    K_PROLONG_PAPER, K_NORM_AHEAD, K_OUTER_RED, K_LEG_DOWN, K_LEG_UP, K_COUNT
 };
 const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restrict",
                                   "prolong_add", "resnorm",  "copy",     "outer_residual",
                                   "update",      "memset",   "conv1",    "conv_tc_update", "tail",
                                   "rb_sweep_fused", "mc_sweep", "restrict_paper",
-                                  "prolong_paper", "resnorm_red_sweep", "outer_red_update"};
+                                  "prolong_paper", "resnorm_red_sweep", "outer_red_update",
+                                  "leg_down", "leg_up"};
 const char* kPrecSuffix[4] = {"", "_f32", "_bf16", "_df"};
 
 template <typename T>
@@ -245,7 +255,7 @@ int prec_of<df32>() { return 3; }
 // 2d-1 adds + 1 fma even where the diagonal walkers share one add between
 // two nodes) and algorithmic DRAM bytes (each value the operation needs read
 // once, each value it produces written once) with w bytes per stored value.
-std::pair<double, double> model(int kind, int d, int n, bool red_only, double w) {
+std::pair<double, double> model(int kind, int d, int n, bool red_only, double w, int sweeps) {
     const double N = std::pow((double)(n - 1), d);
     const int nc = n / 2;
     const double Nc = std::pow((double)std::max(nc - 1, 0), d);
@@ -284,6 +294,10 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
         case K_OUTER_RED:  // black: triple-float GS value into u (3 FP64 adds), e = q_in = 0;
                            // red: u += e, sigma, q_in = e = sigma; u, e read on all nodes
             return {N / 2 * (t ? 14.25 : 13), N * (16 + w) + N / 2 * (8 + 4 * w)};
+        case K_LEG_DOWN:  // `sweeps` half sweeps, red residual, restriction: read u, q; write u, q_c, u_c
+            return {N / 2 * 6 * sweeps + N / 2 * 7 + Nc * 13, (N * 3 + Nc * 2) * w};
+        case K_LEG_UP:  // black prolongation + `sweeps` half sweeps: read u_c, u, q; write u
+            return {cells * 13 + N / 2 * 6 * sweeps, (N * 3 + Nc) * w};
     }
     return {0.0, 0.0};
 }
@@ -292,9 +306,9 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w)
 // is on; `kernels` = kernel launches launch() makes.
 template <class F>
 void timed(gmg_handle h, int kind, int level, int prec, int n, bool red_only, F&& launch,
-           int kernels = 1) {
+           int kernels = 1, int sweeps = 0) {
     const double w = prec == 0 || prec == 3 ? 8.0 : prec == 1 ? 4.0 : 2.0;
-    auto m = model(kind, h->cfg.d, n, red_only, w);
+    auto m = model(kind, h->cfg.d, n, red_only, w, sweeps);
     h->timer.run(h->stream, std::string(kKindName[kind]) + kPrecSuffix[prec], level, m.first,
                  m.second, kernels, launch);
 }
@@ -398,6 +412,26 @@ void relax(gmg_handle h, std::vector<Level<T>>& lv, int l, int sweeps, int& cur,
     }
 }
 
+// The fused leg kernels (legs.cu) run level l of an FP32 / double-float 3D
+// red-black hierarchy: ping-pong iterate arrays, a level that legs::applies
+// takes, at least GMG_LEG_NMIN intervals.
+template <typename T>
+bool leg_possible(gmg_handle h, int n) {
+    const gmg_config& c = h->cfg;
+    const int nmin = h->leg_nmin > 0 ? h->leg_nmin : h->legs_mode == 1 ? 512 : 128;
+    const bool type_ok = std::is_same<T, float>::value ||
+                         (std::is_same<T, df32>::value && h->legs_mode == 2);
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, df32>::value)
+        return h->legs_mode > 0 && type_ok && c.d == 3 && c.smoother == GMG_RBGS &&
+               c.transfer != GMG_TRANSFER_PAPER && !use_fused_rb<T>(h) && n >= nmin &&
+               legs::applies<T>(c.d, n);
+    return false;
+}
+template <typename T>
+bool leg_level(gmg_handle h, const std::vector<Level<T>>& lv, int l) {
+    return l + 1 < (int)lv.size() && leg_possible<T>(h, lv[l].n) && lv[l].u[1] != nullptr;
+}
+
 // First level handled by the persistent tail kernel (L = none): the first
 // level with n <= 8 (3D; double-float 16) / 32 (2D) (GMG_TAIL_N overrides) whose tail arrays fit in 200 KB of shared
 // memory, below every learned level, leaving at least two tail levels.
@@ -451,6 +485,26 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_re
     } else {
         const int Ldown = lt < L ? lt : L - 1;  // levels smoothed by grid kernels going down
         for (int l = 0; l < Ldown; ++l) {
+            // fused down leg: the pre-smoothing half sweeps, the red residual
+            // and the restriction in one pass (u ping-pongs)
+            const int s_down = 2 * c.nu1 - (l == 0 && first_red_done ? 1 : 0);
+            if (leg_level<T>(h, lv, l) && s_down >= 2 && s_down <= 4) {
+                Level<T>& F = lv[l];
+                Level<T>& C = lv[l + 1];
+                cudaError_t e = cudaSuccess;
+                timed(
+                    h, K_LEG_DOWN, l, p, F.n, true,
+                    [&] {
+                        e = legs::down<T>(F.lay, C.lay, F.u[cur[l]], F.u[cur[l] ^ 1], F.q, C.q,
+                                          C.u[0], s_down, h->stream);
+                    },
+                    1, s_down);
+                GMG_CUDA_TRY(e);
+                h->legs_used = true;
+                cur[l] ^= 1;
+                cur[l + 1] = 0;
+                continue;
+            }
             // level 0 of the plain FP64 form: the residual of the full
             // iterate, unbiased in 3D (lk::gs_value)
             const bool unbiased = l == 0 && std::is_same<T, double>::value && d == 3;
@@ -504,6 +558,23 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_re
         for (int l = Ldown - 1; l >= 0; --l) {
             Level<T>& F = lv[l];
             Level<T>& C = lv[l + 1];
+            // fused up leg: black prolongation + correction and the
+            // post-smoothing half sweeps in one pass (u ping-pongs)
+            const int s_up = 2 * c.nu2 - (skip_last_black0 && l == 0 ? 1 : 0);
+            if (leg_level<T>(h, lv, l) && s_up >= 2 && s_up <= 4) {
+                cudaError_t e = cudaSuccess;
+                timed(
+                    h, K_LEG_UP, l, p, F.n, true,
+                    [&] {
+                        e = legs::up<T>(C.lay, F.lay, C.u[cur[l + 1]], F.u[cur[l]],
+                                        F.u[cur[l] ^ 1], F.q, s_up, h->stream);
+                    },
+                    1, s_up);
+                GMG_CUDA_TRY(e);
+                h->legs_used = true;
+                cur[l] ^= 1;
+                continue;
+            }
             bool done = false;
             if constexpr (std::is_same<T, double>::value) {
                 if (c.transfer == GMG_TRANSFER_PAPER) {
@@ -1005,6 +1076,10 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
         }
     }
     if ((st = finish()) != GMG_OK) return st;
+    if (h->legs_used && legs::fault() != 0) {
+        set_error("a fused leg kernel gave up waiting for its plane loads; results are invalid");
+        return GMG_ERR_CUDA;
+    }
     if (iters_out) *iters_out = it;
     if (stop && relres_out) *relres_out = res0 > 0.0 ? res / res0 : 0.0;
     if (stop && res > rtol * res0) {
@@ -1029,7 +1104,8 @@ gmg_status alloc_hierarchy(gmg_handle h, std::vector<Level<T>>& lv, int levels, 
         v.nodes = lay_elems(c.d, v.lay);
         if (l > 0 || alloc_u0)
             if ((st = dev_alloc(h, &v.u[0], v.nodes)) != GMG_OK) return st;
-        const bool pingpong = c.smoother == GMG_WJACOBI || use_fused_rb<T>(h);
+        const bool pingpong =
+            c.smoother == GMG_WJACOBI || use_fused_rb<T>(h) || (l + 1 < levels && leg_possible<T>(h, v.n));
         if (pingpong && (st = dev_alloc(h, &v.u[1], v.nodes)) != GMG_OK) return st;
         if ((st = dev_alloc(h, &v.q, v.nodes)) != GMG_OK) return st;
         const bool need_r = l + 1 < levels || c.smoother == GMG_LEARNED;
@@ -1101,6 +1177,8 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     if (const char* v = std::getenv("GMG_OUTER_RED")) h->outer_red = std::strcmp(v, "0") != 0;
     if (const char* v = std::getenv("GMG_TAIL_N")) h->tail_max = std::max(0, std::atoi(v));
     if (const char* v = std::getenv("GMG_DEVICE_LOOP")) h->device_loop = std::strcmp(v, "0") != 0;
+    if (const char* v = std::getenv("GMG_FUSED_LEGS")) h->legs_mode = std::strcmp(v, "0") ? 2 : 0;
+    if (const char* v = std::getenv("GMG_LEG_NMIN")) h->leg_nmin = std::max(2, std::atoi(v));
     auto fail = [&](gmg_status s) {
         gmg_destroy(h);
         return s;
