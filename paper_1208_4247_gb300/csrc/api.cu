@@ -83,6 +83,11 @@ struct gmg_handle_s {
     bool fused_rb = false;  // GMG_FUSED_RB=1 at create: fused FP32 3D red-black sweeps
     bool inner_ahead = true;  // GMG_INNER_AHEAD=0 at create: memset e + first red half sweep
     bool outer_red = true;    // GMG_OUTER_RED=0 at create: full outer residual (double-float)
+    // refinement forms: the outer residual by the integer-pipe fixed-point
+    // evaluation (fx.cuh) with GMG_OUTER_FX=1 at create; FP64 by default
+    // (measured faster: the 128-bit integer sums cost more issue slots than
+    // the FP64 pipe they spare)
+    bool outer_fx = false;
     // plain red-black form: the stopping-test norm runs fused with the next
     // cycle's first level-0 red half sweep (norm_ahead_ok)
     bool ahead = false;
@@ -655,7 +660,8 @@ gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
             h, K_OUTER_RED, 0, p, c.n, false,
             [&] {
                 mixed::outer_red_update<T>(c.d, in[0].lay, h->lv[0].u[0], h->lv[0].q, in[0].q,
-                                           in[0].u[0], h->partial, h->d_res2, h->stream);
+                                           in[0].u[0], h->partial, h->d_res2, h->stream,
+                                           h->outer_fx);
             },
             3);
         return GMG_OK;
@@ -666,7 +672,8 @@ gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
         h, K_OUTER_RES, 0, p, c.n, ahead,
         [&] {
             mixed::outer_residual<T>(c.d, in[0].lay, h->lv[0].u[0], h->lv[0].q, in[0].q, h->partial,
-                                     h->d_res2, h->stream, ahead ? in[0].u[0] : nullptr);
+                                     h->d_res2, h->stream, ahead ? in[0].u[0] : nullptr,
+                                     h->outer_fx);
         },
         2);
     return GMG_OK;
@@ -962,15 +969,18 @@ gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
     } else if (c.precision == GMG_FP32_IR)
         mixed::outer_residual<float>(c.d, h->lvf[0].lay, u, h->lv[0].q, h->lvf[0].q, h->partial,
                                      h->d_res2, h->stream,
-                                     inner_red_ahead<float>(h) ? h->lvf[0].u[0] : nullptr);
+                                     inner_red_ahead<float>(h) ? h->lvf[0].u[0] : nullptr,
+                                     h->outer_fx);
     else if (c.precision == GMG_DF_IR)
         mixed::outer_residual<df32>(c.d, h->lvd[0].lay, u, h->lv[0].q, h->lvd[0].q, h->partial,
                                     h->d_res2, h->stream,
-                                    inner_red_ahead<df32>(h) ? h->lvd[0].u[0] : nullptr);
+                                    inner_red_ahead<df32>(h) ? h->lvd[0].u[0] : nullptr,
+                                    h->outer_fx);
     else
         mixed::outer_residual<bf16>(c.d, h->lvb[0].lay, u, h->lv[0].q, h->lvb[0].q, h->partial,
                                     h->d_res2, h->stream,
-                                    inner_red_ahead<bf16>(h) ? h->lvb[0].u[0] : nullptr);
+                                    inner_red_ahead<bf16>(h) ? h->lvb[0].u[0] : nullptr,
+                                    h->outer_fx);
     h->timer.launches += 3;
     GMG_CUDA_TRY(cudaGetLastError());
     return GMG_OK;
@@ -1175,6 +1185,7 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     if (const char* v = std::getenv("GMG_FUSED_RB")) h->fused_rb = std::strcmp(v, "1") == 0;
     if (const char* v = std::getenv("GMG_INNER_AHEAD")) h->inner_ahead = std::strcmp(v, "0") != 0;
     if (const char* v = std::getenv("GMG_OUTER_RED")) h->outer_red = std::strcmp(v, "0") != 0;
+    if (const char* v = std::getenv("GMG_OUTER_FX")) h->outer_fx = std::strcmp(v, "1") == 0;
     if (const char* v = std::getenv("GMG_TAIL_N")) h->tail_max = std::max(0, std::atoi(v));
     if (const char* v = std::getenv("GMG_DEVICE_LOOP")) h->device_loop = std::strcmp(v, "0") != 0;
     if (const char* v = std::getenv("GMG_FUSED_LEGS")) h->legs_mode = std::strcmp(v, "0") ? 2 : 0;

@@ -166,9 +166,11 @@ int outer_partials(int d, int n);
 // q_in, e: the inner level-0 arrays, layout `in` (dense u, q: FP64, n = in.n).
 // e_init (may be NULL) receives the inner iterate after the first red half
 // sweep from e = 0: sigma on the red nodes, 0 on the black ones.
+// fx: sigma by the integer-pipe fixed-point evaluation (fx.cuh) instead of FP64
 template <typename T>
 void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q_in,
-                    double* partial, double* out, cudaStream_t s, T* e_init = nullptr);
+                    double* partial, double* out, cudaStream_t s, T* e_init = nullptr,
+                    bool fx = false);
 template <typename T>
 void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s);
 // After red-black double-float inner cycles: the last black Gauss-Seidel
@@ -179,7 +181,7 @@ void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s);
 // sum into *out.  Two kernels and the sum.
 template <typename T>
 void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in, T* e,
-                      double* partial, double* out, cudaStream_t s);
+                      double* partial, double* out, cudaStream_t s, bool fx = false);
 }  // namespace mixed
 
 // Fused red-black sweep (fused.cu, 3D FP32): u_out = one full sweep of u_in

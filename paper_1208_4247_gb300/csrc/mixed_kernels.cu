@@ -8,6 +8,7 @@
 // residual itself: A'e = b - A'u  <=>  e = sigma + c * (sum of e's
 // neighbours) at the fixed point, so q_inner = sigma rounded to the storage
 // type.
+#include "fx.cuh"
 #include "level_kernels.cuh"
 
 namespace gmg {
@@ -35,6 +36,38 @@ using lk::sz_of;
 
 constexpr int kThreads = 256;
 
+// The scaled residual of an FP64 node from its 2d neighbours, q and u: by
+// the integer-pipe fixed-point evaluation (fx.cuh) when FX, as a
+// double-float; in FP64 otherwise (and where fx reports an operand or a
+// result it does not take), with 1/6 as a double-double (lk::gs_value).
+template <int DIM, bool FX>
+__device__ __forceinline__ df32 sigma_at(const double* __restrict__ u, int64_t p, int64_t sy,
+                                         int64_t sz, double q, double un) {
+    if constexpr (FX) {
+        bool ok;
+        if constexpr (DIM == 3) {
+            const double a[6] = {u[p - 1], u[p + 1], u[p - sy], u[p - sz], u[p + sy], u[p + sz]};
+            const df32 r = fx::sigma<6>(a, q, un, ok);
+            if (ok) return r;
+        } else {
+            const double a[4] = {u[p - 1], u[p + 1], u[p - sy], u[p + sy]};
+            const df32 r = fx::sigma<4>(a, q, un, ok);
+            if (ok) return r;
+        }
+    }
+    const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
+    return df32(lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q) - un);
+}
+// a double-float sigma stored in T (float, BF16: the double-float value
+// rounded once to float first)
+template <typename T>
+__device__ __forceinline__ T store_of(df32 v) {
+    if constexpr (std::is_same<T, df32>::value)
+        return v;
+    else
+        return lk::Num<T>::st(rn::add(v.hi, v.lo));
+}
+
 // sigma = q + c * sum - u in FP64 on every interior node (in 3D with 1/6
 // as a double-double: the outer residual of the full iterate must not carry
 // the bias of fl(1/6), lk::gs_value), stored to the inner right-hand side in
@@ -52,7 +85,7 @@ __device__ inline void store_inner(T* __restrict__ q_in, T* __restrict__ e_init,
     if (e_init) e_init[idx] = red ? s : N::st(C(0));
 }
 
-template <int DIM, bool SPLIT, typename T>
+template <int DIM, bool SPLIT, typename T, bool FX = false>
 __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __restrict__ u,
                                                              const double* __restrict__ q,
                                                              T* __restrict__ q_in,
@@ -65,6 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
     const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
     const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
     double acc = 0.0;
+    df32 acc2(0.f, 0.f);  // FX: sigma^2 summed in double-float
     for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
          r += (int64_t)gridDim.x * blockDim.y) {
         const int j = (int)(r % (n - 1)) + 1;
@@ -73,11 +107,23 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
         const int64_t row_in = k * in.sz + j * in.sy;
         for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
             const int64_t p = row + i;
-            const double sig = lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
-            store_inner(q_in, e_init, row_in + lk::xo<SPLIT>(in, i), sig, ((i + j + k) & 1) == 0);
-            acc = fma(sig, sig, acc);
+            if constexpr (FX) {
+                const df32 sg = sigma_at<DIM, true>(u, p, sy, sz, q[p], u[p]);
+                const T st = store_of<T>(sg);
+                const int64_t idx = row_in + lk::xo<SPLIT>(in, i);
+                q_in[idx] = st;
+                if (e_init) e_init[idx] = ((i + j + k) & 1) == 0 ? st : store_of<T>(df32(0.f, 0.f));
+                acc2 = acc2 + sg * sg;
+            } else {
+                const double sig =
+                    lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
+                store_inner(q_in, e_init, row_in + lk::xo<SPLIT>(in, i), sig,
+                            ((i + j + k) & 1) == 0);
+                acc = fma(sig, sig, acc);
+            }
         }
     }
+    if constexpr (FX) acc = (double)acc2;
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
     if ((t & 31) == 0) warp_sums[t >> 5] = acc;
@@ -190,7 +236,7 @@ __global__ void __launch_bounds__(256) k_black_exact_update(double* __restrict__
 // The red nodes: u += e, sigma (unbiased 1/(2d)) from the updated neighbours,
 // q_in = e = sigma (the next step's first inner red half sweep), partial sums
 // of sigma^2 (the stopping-test norm: the black terms are zero to rounding).
-template <int DIM, bool SPLIT, typename T>
+template <int DIM, bool SPLIT, typename T, bool FX = false>
 __global__ void __launch_bounds__(kThreads) k_outer_red(double* __restrict__ u,
                                                         const double* __restrict__ q,
                                                         T* __restrict__ q_in, T* __restrict__ e,
@@ -202,6 +248,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_red(double* __restrict__ u,
     const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
     const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
     double acc = 0.0;
+    df32 acc2(0.f, 0.f);  // FX: sigma^2 summed in double-float
     for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
          r += (int64_t)gridDim.x * blockDim.y) {
         const int j = (int)(r % (n - 1)) + 1;
@@ -213,13 +260,23 @@ __global__ void __launch_bounds__(kThreads) k_outer_red(double* __restrict__ u,
             const int64_t idx = row_in + lk::xo<SPLIT>(in, i);
             const double un = u[p] + (double)N::ld(e[idx]);
             u[p] = un;
-            const double sig = lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - un;
-            const T st = N::st(typename N::C(sig));
-            q_in[idx] = st;
-            e[idx] = st;
-            acc = fma(sig, sig, acc);
+            if constexpr (FX) {
+                const df32 sg = sigma_at<DIM, true>(u, p, sy, sz, q[p], un);
+                const T st = store_of<T>(sg);
+                q_in[idx] = st;
+                e[idx] = st;
+                acc2 = acc2 + sg * sg;
+            } else {
+                const double sig =
+                    lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - un;
+                const T st = N::st(typename N::C(sig));
+                q_in[idx] = st;
+                e[idx] = st;
+                acc = fma(sig, sig, acc);
+            }
         }
     }
+    if constexpr (FX) acc = (double)acc2;
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
     if ((t & 31) == 0) warp_sums[t >> 5] = acc;
@@ -275,7 +332,7 @@ __global__ void __launch_bounds__(256, 4) k_outer_red3_walk(double* __restrict__
 
 template <typename T>
 void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in, T* e,
-                      double* partial, double* out, cudaStream_t s) {
+                      double* partial, double* out, cudaStream_t s, bool fx) {
     static_assert(std::is_same<T, df32>::value, "the red-only outer residual is double-float");
     const int n = in.n;
     int bx = 32;
@@ -293,6 +350,22 @@ void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in,
             k_black_exact_update<2, true><<<ublocks, block, 0, s>>>(u, e, q_in, in);
         else
             k_black_exact_update<2, false><<<ublocks, block, 0, s>>>(u, e, q_in, in);
+    }
+    if (fx) {
+        const int blocks = outer_partials(d, n);
+        if (d == 3) {
+            if (in.he)
+                k_outer_red<3, true, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+            else
+                k_outer_red<3, false, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+        } else {
+            if (in.he)
+                k_outer_red<2, true, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+            else
+                k_outer_red<2, false, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+        }
+        fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
+        return;
     }
     if (lk::walk_applies(d, n, sizeof(double))) {
         const lk::WalkLaunch W = lk::walk_launch(n);
@@ -331,8 +404,31 @@ int outer_partials(int d, int n) {
 
 template <typename T>
 void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q_in,
-                    double* partial, double* out, cudaStream_t s, T* e_init) {
+                    double* partial, double* out, cudaStream_t s, T* e_init, bool fx) {
     const int n = in.n;
+    if (fx) {
+        int bx = 32;
+        while (bx < n && bx < 128) bx *= 2;
+        dim3 block(bx, kThreads / bx, 1);
+        const int blocks = outer_partials(d, n);
+        if (d == 3) {
+            if (in.he)
+                k_outer_residual<3, true, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e_init,
+                                                                           partial, in);
+            else
+                k_outer_residual<3, false, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e_init,
+                                                                            partial, in);
+        } else {
+            if (in.he)
+                k_outer_residual<2, true, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e_init,
+                                                                           partial, in);
+            else
+                k_outer_residual<2, false, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e_init,
+                                                                            partial, in);
+        }
+        fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
+        return;
+    }
     if (lk::walk_applies(d, n, sizeof(double))) {
         const lk::WalkLaunch W = lk::walk_launch(n);
         const int blocks = (int)std::min<int64_t>(W.blocks, outer_partials(d, n));
@@ -385,14 +481,14 @@ void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s) {
 }
 
 template void outer_residual<float>(int, const Lay&, const double*, const double*, float*,
-                                    double*, double*, cudaStream_t, float*);
+                                    double*, double*, cudaStream_t, float*, bool);
 template void outer_residual<__nv_bfloat16>(int, const Lay&, const double*, const double*,
                                             __nv_bfloat16*, double*, double*, cudaStream_t,
-                                            __nv_bfloat16*);
+                                            __nv_bfloat16*, bool);
 template void outer_residual<df32>(int, const Lay&, const double*, const double*, df32*, double*,
-                                   double*, cudaStream_t, df32*);
+                                   double*, cudaStream_t, df32*, bool);
 template void outer_red_update<df32>(int, const Lay&, double*, const double*, df32*, df32*,
-                                     double*, double*, cudaStream_t);
+                                     double*, double*, cudaStream_t, bool);
 template void update<float>(int, const Lay&, double*, const float*, cudaStream_t);
 template void update<df32>(int, const Lay&, double*, const df32*, cudaStream_t);
 template void update<__nv_bfloat16>(int, const Lay&, double*, const __nv_bfloat16*, cudaStream_t);

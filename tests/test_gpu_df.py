@@ -194,3 +194,33 @@ def test_inner_ahead_bit_identical_fp32_bf16(torch_cuda, monkeypatch, prec):
             S.cycles(f, u, 2)
         out.append(u.cpu().numpy())
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("prec,n,k", [("df", 256, 1), ("fp32", 128, 3), ("bf16", 128, 1)])
+def test_fixed_point_outer_residual(torch_cuda, monkeypatch, prec, n, k):
+    """The outer residual by the integer-pipe fixed-point evaluation
+    (GMG_OUTER_FX=1, csrc/fx.cuh) against the FP64 one: three steps from a
+    random iterate agree within the per-cycle bar (double-float) or the
+    inner precision's step accuracy, and whole solves reach 1e-10 in the same
+    number of steps."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d = 3
+    f = torch.from_numpy(inputs.rhs_uniform(d, n, 6)).cuda()
+    rng = np.random.default_rng(41)
+    u0 = np.zeros((n + 1,) * d)
+    u0[(slice(1, -1),) * d] = rng.standard_normal((n - 1,) * d)
+    out, its = [], []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GMG_OUTER_FX", flag)
+        u = torch.from_numpy(u0.copy()).cuda()
+        with Solver(d, n, precision=prec, inner_cycles=k) as S:
+            S.cycles(f, u, 3)
+            out.append(u.cpu().numpy())
+            u.zero_()
+            it, rel, conv = S.solve(f, u, 1e-10)
+            assert conv and rel <= 1e-10
+            its.append(it)
+    tol = TOL_CYCLE if prec == "df" else 1e-6
+    assert _max_rel(out[0], out[1]) <= tol, _max_rel(out[0], out[1])
+    assert its[0] == its[1], its
