@@ -59,6 +59,15 @@ struct gmg_handle_s {
     std::vector<Level<bf16>> lvb;   // BF16 inner hierarchy (GMG_BF16_IR)
     std::vector<Level<df32>> lvd;   // double-float inner hierarchy (GMG_DF_IR)
     double* partial = nullptr;
+    // double-float red-only refinement: the black remainder of the starting
+    // outer residual and its flag (mixed::outer_residual / outer_red_update)
+    float* resid_b = nullptr;
+    int* resid_flag = nullptr;
+    // the steps of this solve use the full outer residual (step_full): a
+    // double-float solve whose starting residual exceeds twice that of u = 0
+    // (section 4.11); the captured graphs' mode (graph_step_full)
+    bool step_full = false;
+    bool graph_step_full = false;
     double* d_res2 = nullptr;
     double* h_res2 = nullptr;  // pinned
     cudaGraphExec_t graph = nullptr;
@@ -83,11 +92,6 @@ struct gmg_handle_s {
     bool fused_rb = false;  // GMG_FUSED_RB=1 at create: fused FP32 3D red-black sweeps
     bool inner_ahead = true;  // GMG_INNER_AHEAD=0 at create: memset e + first red half sweep
     bool outer_red = true;    // GMG_OUTER_RED=0 at create: full outer residual (double-float)
-    // refinement forms: the outer residual by the integer-pipe fixed-point
-    // evaluation (fx.cuh) with GMG_OUTER_FX=1 at create; FP64 by default
-    // (measured faster: the 128-bit integer sums cost more issue slots than
-    // the FP64 pipe they spare)
-    bool outer_fx = false;
     // plain red-black form: the stopping-test norm runs fused with the next
     // cycle's first level-0 red half sweep (norm_ahead_ok)
     bool ahead = false;
@@ -630,10 +634,21 @@ bool inner_red_ahead(gmg_handle h) {
 // the update plus the full residual).  FP32 / BF16 inner cycles leave a
 // black residual of their own rounding (2^-24 / 2^-8 of e, and fl32(1/6)'s
 // bias), which the next step must see: they keep the full residual.
+//
+// The red-only scheme never corrects the black residual that the FP64
+// updates' roundings leave (about eps |u| per step): harmless while |u| stays
+// near the solution's size, but from a starting iterate much larger than
+// the solution the iterate shrinks and those errors grow relative to it.  So
+// a solve uses it only when its starting residual is at most twice the
+// residual of u = 0 (step_full decides per solve).
 template <typename T>
-bool outer_red_only(gmg_handle h) {
+bool outer_red_possible(gmg_handle h) {
     return std::is_same<T, df32>::value && inner_red_ahead<T>(h) && h->cfg.nu2 > 0 &&
            h->outer_red;
+}
+template <typename T>
+bool outer_red_only(gmg_handle h) {
+    return outer_red_possible<T>(h) && !h->step_full;
 }
 
 // Refinement step: e = 0, k inner cycles on A'e = sigma, u += e, new sigma.
@@ -661,7 +676,7 @@ gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
             [&] {
                 mixed::outer_red_update<T>(c.d, in[0].lay, h->lv[0].u[0], h->lv[0].q, in[0].q,
                                            in[0].u[0], h->partial, h->d_res2, h->stream,
-                                           h->outer_fx);
+                                           h->resid_b, h->resid_flag);
             },
             3);
         return GMG_OK;
@@ -672,8 +687,7 @@ gmg_status enqueue_refinement(gmg_handle h, std::vector<Level<T>>& in) {
         h, K_OUTER_RES, 0, p, c.n, ahead,
         [&] {
             mixed::outer_residual<T>(c.d, in[0].lay, h->lv[0].u[0], h->lv[0].q, in[0].q, h->partial,
-                                     h->d_res2, h->stream, ahead ? in[0].u[0] : nullptr,
-                                     h->outer_fx);
+                                     h->d_res2, h->stream, ahead ? in[0].u[0] : nullptr);
         },
         2);
     return GMG_OK;
@@ -911,7 +925,7 @@ gmg_status capture(gmg_handle h, cudaGraphExec_t* out, gmg_status (*enqueue)(gmg
 }
 
 gmg_status ensure_graph(gmg_handle h, double* u) {
-    if (h->graph && h->graph_u == u) return GMG_OK;
+    if (h->graph && h->graph_u == u && h->graph_step_full == h->step_full) return GMG_OK;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -934,6 +948,7 @@ gmg_status ensure_graph(gmg_handle h, double* u) {
     if ((st = capture(h, &h->graph, enqueue_step)) != GMG_OK) return st;
     if (h->device_loop && h->d_loop && !h->timer.enabled) build_loop_graph(h);
     h->graph_u = u;
+    h->graph_step_full = h->step_full;
     return GMG_OK;
 }
 
@@ -969,18 +984,18 @@ gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
     } else if (c.precision == GMG_FP32_IR)
         mixed::outer_residual<float>(c.d, h->lvf[0].lay, u, h->lv[0].q, h->lvf[0].q, h->partial,
                                      h->d_res2, h->stream,
-                                     inner_red_ahead<float>(h) ? h->lvf[0].u[0] : nullptr,
-                                     h->outer_fx);
+                                     inner_red_ahead<float>(h) ? h->lvf[0].u[0] : nullptr);
     else if (c.precision == GMG_DF_IR)
         mixed::outer_residual<df32>(c.d, h->lvd[0].lay, u, h->lv[0].q, h->lvd[0].q, h->partial,
                                     h->d_res2, h->stream,
                                     inner_red_ahead<df32>(h) ? h->lvd[0].u[0] : nullptr,
-                                    h->outer_fx);
+                                    outer_red_possible<df32>(h) ? h->resid_b : nullptr,
+                                    outer_red_possible<df32>(h) ? h->resid_flag : nullptr,
+                                    outer_red_possible<df32>(h) ? h->d_res2 + 2 : nullptr);
     else
         mixed::outer_residual<bf16>(c.d, h->lvb[0].lay, u, h->lv[0].q, h->lvb[0].q, h->partial,
                                     h->d_res2, h->stream,
-                                    inner_red_ahead<bf16>(h) ? h->lvb[0].u[0] : nullptr,
-                                    h->outer_fx);
+                                    inner_red_ahead<bf16>(h) ? h->lvb[0].u[0] : nullptr);
     h->timer.launches += 3;
     GMG_CUDA_TRY(cudaGetLastError());
     return GMG_OK;
@@ -991,14 +1006,16 @@ gmg_status start(gmg_handle h, const double* f, double* u, double* res0) {
     GMG_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev, 0));
     gmg_status st = enqueue_start(h, f, u);
     if (st != GMG_OK) return st;
-    GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
-                                 h->stream));
+    const bool choose = outer_red_possible<df32>(h);
+    GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double) * (choose ? 3 : 1),
+                                 cudaMemcpyDeviceToHost, h->stream));
     GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
     *res0 = std::sqrt(*h->h_res2);
     if (!std::isfinite(*res0)) {
         set_error("initial residual norm is not finite (NaN/Inf in f or u)");
         return GMG_ERR_NONFINITE;
     }
+    if (choose) h->step_full = !(h->h_res2[0] <= 4.0 * h->h_res2[2]);
     return ensure_graph(h, u);
 }
 
@@ -1185,7 +1202,6 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     if (const char* v = std::getenv("GMG_FUSED_RB")) h->fused_rb = std::strcmp(v, "1") == 0;
     if (const char* v = std::getenv("GMG_INNER_AHEAD")) h->inner_ahead = std::strcmp(v, "0") != 0;
     if (const char* v = std::getenv("GMG_OUTER_RED")) h->outer_red = std::strcmp(v, "0") != 0;
-    if (const char* v = std::getenv("GMG_OUTER_FX")) h->outer_fx = std::strcmp(v, "1") == 0;
     if (const char* v = std::getenv("GMG_TAIL_N")) h->tail_max = std::max(0, std::atoi(v));
     if (const char* v = std::getenv("GMG_DEVICE_LOOP")) h->device_loop = std::strcmp(v, "0") != 0;
     if (const char* v = std::getenv("GMG_FUSED_LEGS")) h->legs_mode = std::strcmp(v, "0") ? 2 : 0;
@@ -1219,16 +1235,21 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
              : cfg->precision == GMG_DF_IR ? alloc_hierarchy<df32>(h, h->lvd, L, true)
                                            : alloc_hierarchy<bf16>(h, h->lvb, L, true);
         if (st != GMG_OK) return fail(st);
+        if (cfg->precision == GMG_DF_IR &&
+            ((st = dev_alloc(h, &h->resid_b, h->lvd[0].nodes)) != GMG_OK ||
+             (st = dev_alloc(h, &h->resid_flag, 1)) != GMG_OK))
+            return fail(st);
     }
     if (cfg->smoother == GMG_LEARNED) {
         h->lw.assign(L, nullptr);
         h->lz.assign(L, nullptr);
         if ((st = dev_alloc(h, &h->lw_scratch, 2 * 8 * 27)) != GMG_OK) return fail(st);
     }
-    const int np = std::max(fp64::resnorm_partials(d, cfg->n), mixed::outer_partials(d, cfg->n));
+    // partials: the residual's, and (refinement start) those of q^2 after them
+    const int np = std::max(fp64::resnorm_partials(d, cfg->n), 2 * mixed::outer_partials(d, cfg->n));
     if ((st = dev_alloc(h, &h->partial, np)) != GMG_OK) return fail(st);
-    if ((st = dev_alloc(h, &h->d_res2, 2)) != GMG_OK) return fail(st);
-    if (cudaMallocHost((void**)&h->h_res2, sizeof(double)) != cudaSuccess) {
+    if ((st = dev_alloc(h, &h->d_res2, 3)) != GMG_OK) return fail(st);
+    if (cudaMallocHost((void**)&h->h_res2, 3 * sizeof(double)) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         return fail(GMG_ERR_ALLOC);
     }

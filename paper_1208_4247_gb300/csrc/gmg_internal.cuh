@@ -166,11 +166,16 @@ int outer_partials(int d, int n);
 // q_in, e: the inner level-0 arrays, layout `in` (dense u, q: FP64, n = in.n).
 // e_init (may be NULL) receives the inner iterate after the first red half
 // sweep from e = 0: sigma on the red nodes, 0 on the black ones.
-// fx: sigma by the integer-pipe fixed-point evaluation (fx.cuh) instead of FP64
+// resid (double-float only; may be NULL): the black nodes' sigma minus its
+// double-float value, for the first outer_red_update after this residual
+// (*resid_flag set here, cleared there).  qnorm_out (may be NULL): the sum
+// of q^2, the squared norm of the residual of u = 0 (partial must then hold
+// 2 outer_partials entries).
 template <typename T>
 void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q_in,
                     double* partial, double* out, cudaStream_t s, T* e_init = nullptr,
-                    bool fx = false);
+                    float* resid = nullptr, int* resid_flag = nullptr,
+                    double* qnorm_out = nullptr);
 template <typename T>
 void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s);
 // After red-black double-float inner cycles: the last black Gauss-Seidel
@@ -181,7 +186,8 @@ void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s);
 // sum into *out.  Two kernels and the sum.
 template <typename T>
 void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in, T* e,
-                      double* partial, double* out, cudaStream_t s, bool fx = false);
+                      double* partial, double* out, cudaStream_t s, const float* resid = nullptr,
+                      int* resid_flag = nullptr);
 }  // namespace mixed
 
 // Fused red-black sweep (fused.cu, 3D FP32): u_out = one full sweep of u_in

@@ -8,7 +8,6 @@
 // residual itself: A'e = b - A'u  <=>  e = sigma + c * (sum of e's
 // neighbours) at the fixed point, so q_inner = sigma rounded to the storage
 // type.
-#include "fx.cuh"
 #include "level_kernels.cuh"
 
 namespace gmg {
@@ -36,38 +35,6 @@ using lk::sz_of;
 
 constexpr int kThreads = 256;
 
-// The scaled residual of an FP64 node from its 2d neighbours, q and u: by
-// the integer-pipe fixed-point evaluation (fx.cuh) when FX, as a
-// double-float; in FP64 otherwise (and where fx reports an operand or a
-// result it does not take), with 1/6 as a double-double (lk::gs_value).
-template <int DIM, bool FX>
-__device__ __forceinline__ df32 sigma_at(const double* __restrict__ u, int64_t p, int64_t sy,
-                                         int64_t sz, double q, double un) {
-    if constexpr (FX) {
-        bool ok;
-        if constexpr (DIM == 3) {
-            const double a[6] = {u[p - 1], u[p + 1], u[p - sy], u[p - sz], u[p + sy], u[p + sz]};
-            const df32 r = fx::sigma<6>(a, q, un, ok);
-            if (ok) return r;
-        } else {
-            const double a[4] = {u[p - 1], u[p + 1], u[p - sy], u[p + sy]};
-            const df32 r = fx::sigma<4>(a, q, un, ok);
-            if (ok) return r;
-        }
-    }
-    const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
-    return df32(lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q) - un);
-}
-// a double-float sigma stored in T (float, BF16: the double-float value
-// rounded once to float first)
-template <typename T>
-__device__ __forceinline__ T store_of(df32 v) {
-    if constexpr (std::is_same<T, df32>::value)
-        return v;
-    else
-        return lk::Num<T>::st(rn::add(v.hi, v.lo));
-}
-
 // sigma = q + c * sum - u in FP64 on every interior node (in 3D with 1/6
 // as a double-double: the outer residual of the full iterate must not carry
 // the bias of fl(1/6), lk::gs_value), stored to the inner right-hand side in
@@ -75,30 +42,53 @@ __device__ __forceinline__ T store_of(df32 v) {
 // e_init (may be NULL): also the inner iterate after the first red half
 // sweep from e = 0 -- sigma on the red nodes (q_in + c * 0), 0 on the black
 // ones -- so that the first inner cycle starts with its black half sweep.
+// resid (double-float inner storage only; may be NULL): on the black nodes
+// the part of sigma the double-float value of q_in leaves out (about 2^-49
+// of sigma; see k_black_exact_update).
 template <typename T>
 __device__ inline void store_inner(T* __restrict__ q_in, T* __restrict__ e_init, int64_t idx,
-                                   double sig, bool red) {
+                                   double sig, bool red, float* __restrict__ resid) {
     using N = lk::Num<T>;
     using C = typename N::C;
     const T s = N::st(C(sig));
     q_in[idx] = s;
     if (e_init) e_init[idx] = red ? s : N::st(C(0));
+    if constexpr (std::is_same<T, df32>::value) {
+        if (resid && !red) resid[idx] = (float)((sig - cvt::widen(s.hi)) - cvt::widen(s.lo));
+    }
 }
 
-template <int DIM, bool SPLIT, typename T, bool FX = false>
+// The block's sum of acc (a fixed order: warp shuffles, then the warps in
+// turn) into *slot; every thread of the block calls it.
+__device__ inline void block_partial(double acc, double* warp_sums, double* slot) {
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((t & 31) == 0) warp_sums[t >> 5] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += warp_sums[w];
+        *slot = s;
+    }
+    __syncthreads();
+}
+
+template <int DIM, bool SPLIT, typename T>
 __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __restrict__ u,
                                                              const double* __restrict__ q,
                                                              T* __restrict__ q_in,
                                                              T* __restrict__ e_init,
                                                              double* __restrict__ partial,
-                                                             Lay in) {
+                                                             Lay in, float* __restrict__ resid,
+                                                             int* __restrict__ resid_flag,
+                                                             double* __restrict__ qpart) {
     __shared__ double warp_sums[kThreads / 32];
     const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
+    if (resid_flag && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *resid_flag = 1;
     const int n = in.n;
     const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
     const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
-    double acc = 0.0;
-    df32 acc2(0.f, 0.f);  // FX: sigma^2 summed in double-float
+    double acc = 0.0, accq = 0.0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
          r += (int64_t)gridDim.x * blockDim.y) {
         const int j = (int)(r % (n - 1)) + 1;
@@ -107,32 +97,15 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
         const int64_t row_in = k * in.sz + j * in.sy;
         for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
             const int64_t p = row + i;
-            if constexpr (FX) {
-                const df32 sg = sigma_at<DIM, true>(u, p, sy, sz, q[p], u[p]);
-                const T st = store_of<T>(sg);
-                const int64_t idx = row_in + lk::xo<SPLIT>(in, i);
-                q_in[idx] = st;
-                if (e_init) e_init[idx] = ((i + j + k) & 1) == 0 ? st : store_of<T>(df32(0.f, 0.f));
-                acc2 = acc2 + sg * sg;
-            } else {
-                const double sig =
-                    lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
-                store_inner(q_in, e_init, row_in + lk::xo<SPLIT>(in, i), sig,
-                            ((i + j + k) & 1) == 0);
-                acc = fma(sig, sig, acc);
-            }
+            const double sig = lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - u[p];
+            store_inner(q_in, e_init, row_in + lk::xo<SPLIT>(in, i), sig, ((i + j + k) & 1) == 0,
+                        resid);
+            acc = fma(sig, sig, acc);
+            if (qpart) accq = fma(q[p], q[p], accq);
         }
     }
-    if constexpr (FX) acc = (double)acc2;
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    const int t = threadIdx.y * blockDim.x + threadIdx.x;
-    if ((t & 31) == 0) warp_sums[t >> 5] = acc;
-    __syncthreads();
-    if (t == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += warp_sums[w];
-        partial[blockIdx.x] = s;
-    }
+    block_partial(acc, warp_sums, partial + blockIdx.x);
+    if (qpart) block_partial(accq, warp_sums, qpart + blockIdx.x);
 }
 
 // The same by the diagonal walkers of the FP64 3D sweeps (both colours per
@@ -144,30 +117,28 @@ __global__ void __launch_bounds__(256, 4) k_outer_residual3_walk(const double* _
                                                                  T* __restrict__ q_in,
                                                                  T* __restrict__ e_init,
                                                                  double* __restrict__ partial,
-                                                                 Lay in, int segs) {
+                                                                 Lay in, int segs,
+                                                                 float* __restrict__ resid,
+                                                                 int* __restrict__ resid_flag,
+                                                                 double* __restrict__ qpart) {
     __shared__ double warp_sums[kThreads / 32];
     const double c = 1.0 / 6.0;
     const int n = in.n;
     const int64_t walkers = (int64_t)(n - 1) * segs;
-    double acc = 0.0;
+    if (resid_flag && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *resid_flag = 1;
+    double acc = 0.0, accq = 0.0;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; w < walkers;
          w += (int64_t)gridDim.x * blockDim.y)
         for (int color = 0; color < 2; ++color)
             lk::walk_nodes(u, n, color, w, segs, [&](int64_t p, double sum, int i, int j, int k) {
                 const double sig = lk::gs_value<3, true>(c, sum, q[p]) - u[p];
                 store_inner(q_in, e_init, k * in.sz + j * in.sy + lk::xo<SPLIT>(in, i), sig,
-                            color == 0);
+                            color == 0, resid);
                 acc = fma(sig, sig, acc);
+                if (qpart) accq = fma(q[p], q[p], accq);
             });
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    const int t = threadIdx.y * blockDim.x + threadIdx.x;
-    if ((t & 31) == 0) warp_sums[t >> 5] = acc;
-    __syncthreads();
-    if (t == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += warp_sums[w];
-        partial[blockIdx.x] = s;
-    }
+    block_partial(acc, warp_sums, partial + blockIdx.x);
+    if (qpart) block_partial(accq, warp_sums, qpart + blockIdx.x);
 }
 
 // u += e on the interior nodes (e, layout `in`, is zero on the boundary;
@@ -200,10 +171,19 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ u, const T*
 // first red half sweep, and its black right-hand side.  Replaces the inner
 // cycle's last level-0 black half sweep (it is a function of the red values
 // only, so recomputing it after a tail that ran it changes nothing).
+// After a full outer residual (the start of a solve) the black right-hand
+// side is sigma rounded to a double-float; its remainder (resid, valid while
+// *resid_flag is set) is added here, once: left out, it would stay in the
+// black residual for the rest of the solve, about 2^-49 of the starting
+// residual, which is far larger than the solution when the solve starts from
+// a rough iterate.
 template <int DIM, bool SPLIT>
 __global__ void __launch_bounds__(256) k_black_exact_update(double* __restrict__ u,
                                                             df32* __restrict__ e,
-                                                            df32* __restrict__ q_in, Lay in) {
+                                                            df32* __restrict__ q_in, Lay in,
+                                                            const float* __restrict__ resid,
+                                                            const int* __restrict__ resid_flag) {
+    const bool add_resid = resid && *resid_flag;
     const int n = in.n;
     const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
     const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
@@ -226,6 +206,7 @@ __global__ void __launch_bounds__(256) k_black_exact_update(double* __restrict__
                 const df32 x[4] = {e[idx + xm], e[idx + xp], e[idx - in.sy], e[idx + in.sy]};
                 v = fma_tf(sum_tf(x), 0.25f, 0.f, 0.f, q_in[idx]);
             }
+            if (add_resid) v.t2 = rn::add(v.t2, resid[idx]);
             u[row + i] += tf_to_double(v);
             e[idx] = df32(0.f, 0.f);
             q_in[idx] = df32(0.f, 0.f);
@@ -236,19 +217,20 @@ __global__ void __launch_bounds__(256) k_black_exact_update(double* __restrict__
 // The red nodes: u += e, sigma (unbiased 1/(2d)) from the updated neighbours,
 // q_in = e = sigma (the next step's first inner red half sweep), partial sums
 // of sigma^2 (the stopping-test norm: the black terms are zero to rounding).
-template <int DIM, bool SPLIT, typename T, bool FX = false>
+template <int DIM, bool SPLIT, typename T>
 __global__ void __launch_bounds__(kThreads) k_outer_red(double* __restrict__ u,
                                                         const double* __restrict__ q,
                                                         T* __restrict__ q_in, T* __restrict__ e,
-                                                        double* __restrict__ partial, Lay in) {
+                                                        double* __restrict__ partial, Lay in,
+                                                        int* __restrict__ resid_flag) {
     using N = lk::Num<T>;
     __shared__ double warp_sums[kThreads / 32];
+    if (resid_flag && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *resid_flag = 0;
     const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
     const int n = in.n;
     const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
     const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
     double acc = 0.0;
-    df32 acc2(0.f, 0.f);  // FX: sigma^2 summed in double-float
     for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
          r += (int64_t)gridDim.x * blockDim.y) {
         const int j = (int)(r % (n - 1)) + 1;
@@ -260,23 +242,13 @@ __global__ void __launch_bounds__(kThreads) k_outer_red(double* __restrict__ u,
             const int64_t idx = row_in + lk::xo<SPLIT>(in, i);
             const double un = u[p] + (double)N::ld(e[idx]);
             u[p] = un;
-            if constexpr (FX) {
-                const df32 sg = sigma_at<DIM, true>(u, p, sy, sz, q[p], un);
-                const T st = store_of<T>(sg);
-                q_in[idx] = st;
-                e[idx] = st;
-                acc2 = acc2 + sg * sg;
-            } else {
-                const double sig =
-                    lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - un;
-                const T st = N::st(typename N::C(sig));
-                q_in[idx] = st;
-                e[idx] = st;
-                acc = fma(sig, sig, acc);
-            }
+            const double sig = lk::gs_value<DIM, true>(c, lk::nbr_sum<DIM>(u, p, sy, sz), q[p]) - un;
+            const T st = N::st(typename N::C(sig));
+            q_in[idx] = st;
+            e[idx] = st;
+            acc = fma(sig, sig, acc);
         }
     }
-    if constexpr (FX) acc = (double)acc2;
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
     if ((t & 31) == 0) warp_sums[t >> 5] = acc;
@@ -298,9 +270,10 @@ __global__ void __launch_bounds__(256, 4) k_outer_red3_walk(double* __restrict__
                                                             T* __restrict__ q_in,
                                                             T* __restrict__ e,
                                                             double* __restrict__ partial, Lay in,
-                                                            int segs) {
+                                                            int segs, int* __restrict__ resid_flag) {
     using N = lk::Num<T>;
     __shared__ double warp_sums[kThreads / 32];
+    if (resid_flag && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *resid_flag = 0;
     const double c = 1.0 / 6.0;
     const int n = in.n;
     const int64_t walkers = (int64_t)(n - 1) * segs;
@@ -332,7 +305,8 @@ __global__ void __launch_bounds__(256, 4) k_outer_red3_walk(double* __restrict__
 
 template <typename T>
 void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in, T* e,
-                      double* partial, double* out, cudaStream_t s, bool fx) {
+                      double* partial, double* out, cudaStream_t s, const float* resid,
+                      int* resid_flag) {
     static_assert(std::is_same<T, df32>::value, "the red-only outer residual is double-float");
     const int n = in.n;
     int bx = 32;
@@ -342,54 +316,46 @@ void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in,
     const int ublocks = (int)std::min<int64_t>((rows + block.y - 1) / block.y, 152 * 16);
     if (d == 3) {
         if (in.he)
-            k_black_exact_update<3, true><<<ublocks, block, 0, s>>>(u, e, q_in, in);
+            k_black_exact_update<3, true><<<ublocks, block, 0, s>>>(u, e, q_in, in, resid,
+                                                                   resid_flag);
         else
-            k_black_exact_update<3, false><<<ublocks, block, 0, s>>>(u, e, q_in, in);
+            k_black_exact_update<3, false><<<ublocks, block, 0, s>>>(u, e, q_in, in, resid,
+                                                                   resid_flag);
     } else {
         if (in.he)
-            k_black_exact_update<2, true><<<ublocks, block, 0, s>>>(u, e, q_in, in);
+            k_black_exact_update<2, true><<<ublocks, block, 0, s>>>(u, e, q_in, in, resid,
+                                                                   resid_flag);
         else
-            k_black_exact_update<2, false><<<ublocks, block, 0, s>>>(u, e, q_in, in);
-    }
-    if (fx) {
-        const int blocks = outer_partials(d, n);
-        if (d == 3) {
-            if (in.he)
-                k_outer_red<3, true, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
-            else
-                k_outer_red<3, false, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
-        } else {
-            if (in.he)
-                k_outer_red<2, true, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
-            else
-                k_outer_red<2, false, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
-        }
-        fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
-        return;
+            k_black_exact_update<2, false><<<ublocks, block, 0, s>>>(u, e, q_in, in, resid,
+                                                                   resid_flag);
     }
     if (lk::walk_applies(d, n, sizeof(double))) {
         const lk::WalkLaunch W = lk::walk_launch(n);
         const int blocks = (int)std::min<int64_t>(W.blocks, outer_partials(d, n));
         if (in.he)
             k_outer_red3_walk<true, T><<<blocks, W.block, 0, s>>>(u, u, q, q_in, e, partial, in,
-                                                                  W.segs);
+                                                                  W.segs, resid_flag);
         else
             k_outer_red3_walk<false, T><<<blocks, W.block, 0, s>>>(u, u, q, q_in, e, partial, in,
-                                                                   W.segs);
+                                                                   W.segs, resid_flag);
         fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
         return;
     }
     const int blocks = outer_partials(d, n);
     if (d == 3) {
         if (in.he)
-            k_outer_red<3, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+            k_outer_red<3, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in,
+                                                          resid_flag);
         else
-            k_outer_red<3, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+            k_outer_red<3, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in,
+                                                          resid_flag);
     } else {
         if (in.he)
-            k_outer_red<2, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+            k_outer_red<2, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in,
+                                                          resid_flag);
         else
-            k_outer_red<2, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in);
+            k_outer_red<2, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in,
+                                                          resid_flag);
     }
     fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
 }
@@ -404,41 +370,22 @@ int outer_partials(int d, int n) {
 
 template <typename T>
 void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q_in,
-                    double* partial, double* out, cudaStream_t s, T* e_init, bool fx) {
+                    double* partial, double* out, cudaStream_t s, T* e_init, float* resid,
+                    int* resid_flag, double* qnorm_out) {
     const int n = in.n;
-    if (fx) {
-        int bx = 32;
-        while (bx < n && bx < 128) bx *= 2;
-        dim3 block(bx, kThreads / bx, 1);
-        const int blocks = outer_partials(d, n);
-        if (d == 3) {
-            if (in.he)
-                k_outer_residual<3, true, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e_init,
-                                                                           partial, in);
-            else
-                k_outer_residual<3, false, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e_init,
-                                                                            partial, in);
-        } else {
-            if (in.he)
-                k_outer_residual<2, true, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e_init,
-                                                                           partial, in);
-            else
-                k_outer_residual<2, false, T, true><<<blocks, block, 0, s>>>(u, q, q_in, e_init,
-                                                                            partial, in);
-        }
-        fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
-        return;
-    }
+    const int np = outer_partials(d, n);  // the q partials follow the sigma partials
+    double* qpart = qnorm_out ? partial + np : nullptr;
     if (lk::walk_applies(d, n, sizeof(double))) {
         const lk::WalkLaunch W = lk::walk_launch(n);
         const int blocks = (int)std::min<int64_t>(W.blocks, outer_partials(d, n));
         if (in.he)
             k_outer_residual3_walk<true, T><<<blocks, W.block, 0, s>>>(u, q, q_in, e_init, partial, in,
-                                                                     W.segs);
+                                                                     W.segs, resid, resid_flag, qpart);
         else
             k_outer_residual3_walk<false, T><<<blocks, W.block, 0, s>>>(u, q, q_in, e_init, partial, in,
-                                                                      W.segs);
+                                                                      W.segs, resid, resid_flag, qpart);
         fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
+        if (qpart) fp64::k_sum_partials<<<1, 1024, 0, s>>>(qpart, blocks, qnorm_out);
         return;
     }
     int bx = 32;
@@ -447,16 +394,21 @@ void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q
     const int blocks = outer_partials(d, n);
     if (d == 3) {
         if (in.he)
-            k_outer_residual<3, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in);
+            k_outer_residual<3, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in,
+                                                                   resid, resid_flag, qpart);
         else
-            k_outer_residual<3, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in);
+            k_outer_residual<3, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in,
+                                                                   resid, resid_flag, qpart);
     } else {
         if (in.he)
-            k_outer_residual<2, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in);
+            k_outer_residual<2, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in,
+                                                                   resid, resid_flag, qpart);
         else
-            k_outer_residual<2, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in);
+            k_outer_residual<2, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in,
+                                                                   resid, resid_flag, qpart);
     }
     fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
+    if (qpart) fp64::k_sum_partials<<<1, 1024, 0, s>>>(qpart, blocks, qnorm_out);
 }
 
 template <typename T>
@@ -481,14 +433,15 @@ void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s) {
 }
 
 template void outer_residual<float>(int, const Lay&, const double*, const double*, float*,
-                                    double*, double*, cudaStream_t, float*, bool);
+                                    double*, double*, cudaStream_t, float*, float*, int*,
+                                    double*);
 template void outer_residual<__nv_bfloat16>(int, const Lay&, const double*, const double*,
                                             __nv_bfloat16*, double*, double*, cudaStream_t,
-                                            __nv_bfloat16*, bool);
+                                            __nv_bfloat16*, float*, int*, double*);
 template void outer_residual<df32>(int, const Lay&, const double*, const double*, df32*, double*,
-                                   double*, cudaStream_t, df32*, bool);
+                                   double*, cudaStream_t, df32*, float*, int*, double*);
 template void outer_red_update<df32>(int, const Lay&, double*, const double*, df32*, df32*,
-                                     double*, double*, cudaStream_t, bool);
+                                     double*, double*, cudaStream_t, const float*, int*);
 template void update<float>(int, const Lay&, double*, const float*, cudaStream_t);
 template void update<df32>(int, const Lay&, double*, const df32*, cudaStream_t);
 template void update<__nv_bfloat16>(int, const Lay&, double*, const __nv_bfloat16*, cudaStream_t);

@@ -131,6 +131,25 @@ def test_cycle_parity_full_size(torch_cuda, n):
             u = ug
 
 
+@pytest.mark.parametrize("n", [256, 512])
+def test_cycle_parity_full_size_chained(torch_cuda, n):
+    """The same workloads with the three cycles back to back in one call (the
+    fused norm carries the next cycle's first red half sweep from cycle to
+    cycle): the iterate after c cycles against one oracle cycle applied to the
+    GPU iterate after c - 1 cycles, node by node within 1e-12."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    from test_gpu_df import chained_cycle_errors
+    d = 3
+    f = inputs.rhs_uniform(d, n, 2) if n == 256 else inputs.rhs_sine_plus_gauss(d, n, 3)
+    rng = np.random.default_rng(29)
+    u0 = np.zeros_like(f)
+    u0[(slice(1, -1),) * d] = rng.standard_normal((n - 1,) * d)
+    errs = chained_cycle_errors(torch, lambda: Solver(d, n), d, n, f, u0)
+    for c, (mx, l2) in enumerate(errs):
+        assert mx <= 1e-12 and l2 <= 1e-12, (c + 1, mx, l2)
+
+
 SOLVE_CASES = [
     # the 2D 257^2 workload: WJ(4/5) V(2,2), sine + 1e-3 uniform noise
     (2, 256, "wjacobi", 0.8, 2, 2, "sine_uniform"),
