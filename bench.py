@@ -54,9 +54,9 @@ FP64_MIX = {"rb_half": (4.25, 1.0), "resnorm_red_sweep": (5.25, 2.0), "residual"
 # level); a kernel changed since its capture has no entry.
 TRAFFIC = {
     ("rb_half", 0): 356.4e6,  # FP64 walker half sweep: 269.5 + 85.8 MB
-    # double-float step's outer kernels: k_black_exact_update 290.4 + 210.3 MB,
-    # k_outer_red3_walk 345.4 + 212.9 MB
-    ("outer_red_update_df", 0): 1059.0e6,
+    # double-float step's outer kernels: k_black_exact_update 331.4 + 213.1 MB,
+    # k_outer_red3_walk 345.2 + 213.0 MB
+    ("outer_red_update_df", 0): 1102.7e6,
 }
 
 

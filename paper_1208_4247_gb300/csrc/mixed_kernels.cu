@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
     const int n = in.n;
     const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
     const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
-    double acc = 0.0, accq = 0.0;
+    double acc = 0.0;
+    float accq = 0.f;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
          r += (int64_t)gridDim.x * blockDim.y) {
         const int j = (int)(r % (n - 1)) + 1;
@@ -101,11 +102,14 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
             store_inner(q_in, e_init, row_in + lk::xo<SPLIT>(in, i), sig, ((i + j + k) & 1) == 0,
                         resid);
             acc = fma(sig, sig, acc);
-            if (qpart) accq = fma(q[p], q[p], accq);
+            if (qpart) {  // FP32: a threshold test, kept off the FP64 pipe
+                const float qf = (float)q[p];
+                accq = fmaf(qf, qf, accq);
+            }
         }
     }
     block_partial(acc, warp_sums, partial + blockIdx.x);
-    if (qpart) block_partial(accq, warp_sums, qpart + blockIdx.x);
+    if (qpart) block_partial((double)accq, warp_sums, qpart + blockIdx.x);
 }
 
 // The same by the diagonal walkers of the FP64 3D sweeps (both colours per
@@ -126,7 +130,8 @@ __global__ void __launch_bounds__(256, 4) k_outer_residual3_walk(const double* _
     const int n = in.n;
     const int64_t walkers = (int64_t)(n - 1) * segs;
     if (resid_flag && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *resid_flag = 1;
-    double acc = 0.0, accq = 0.0;
+    double acc = 0.0;
+    float accq = 0.f;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; w < walkers;
          w += (int64_t)gridDim.x * blockDim.y)
         for (int color = 0; color < 2; ++color)
@@ -135,10 +140,13 @@ __global__ void __launch_bounds__(256, 4) k_outer_residual3_walk(const double* _
                 store_inner(q_in, e_init, k * in.sz + j * in.sy + lk::xo<SPLIT>(in, i), sig,
                             color == 0, resid);
                 acc = fma(sig, sig, acc);
-                if (qpart) accq = fma(q[p], q[p], accq);
+                if (qpart) {  // FP32: a threshold test, kept off the FP64 pipe
+                const float qf = (float)q[p];
+                accq = fmaf(qf, qf, accq);
+            }
             });
     block_partial(acc, warp_sums, partial + blockIdx.x);
-    if (qpart) block_partial(accq, warp_sums, qpart + blockIdx.x);
+    if (qpart) block_partial((double)accq, warp_sums, qpart + blockIdx.x);
 }
 
 // u += e on the interior nodes (e, layout `in`, is zero on the boundary;
