@@ -44,9 +44,15 @@ __device__ inline uint32_t fastdiv(uint32_t x, const FastDiv& f) {
     return (t + ((x - t) >> 1)) >> (f.l - 1);
 }
 
+// A level of one solve.  The inner (FP32 / BF16) pool stores its arrays with
+// rows padded to sy elements (a multiple of 8: every row starts on a 16-byte
+// boundary) and planes of sz = sy (n+1); the FP64 arrays of a solve (f, u,
+// q64) keep the caller's dense layout, pitch n+1.
 struct BLevel {
     int d, n;
     int64_t u0, u1, q, r;  // element offsets into the inner pool (-1: none)
+    int64_t sy, sz;        // inner pool row / plane pitch
+    int lgG;               // log2 of the 16-byte groups per row the vector kernels take
     FastDiv rows;          // division by n - 1 (interior nodes per row)
 };
 struct BSolve {
@@ -65,8 +71,8 @@ struct Item {
 using lk::Num;
 
 // Node (i, j, k) of interior index idx (x fastest over the (n-1)^d interior
-// nodes of level L) and its offset in the level's (n+1)^d array; no integer
-// division (interior counts stay below 2^32).
+// nodes of level L) and its offset in the level's inner-pool array; no
+// integer division (interior counts stay below 2^32).
 __device__ inline int64_t node_of(const BLevel& L, uint32_t idx, int& i, int& j, int& k) {
     const uint32_t m = L.rows.d;
     const uint32_t t = fastdiv(idx, L.rows);
@@ -79,6 +85,10 @@ __device__ inline int64_t node_of(const BLevel& L, uint32_t idx, int& i, int& j,
         j = (int)t + 1;
         k = 0;
     }
+    return (int64_t)k * L.sz + (int64_t)j * L.sy + i;
+}
+// offset of node (i, j, k) in the solve's dense FP64 arrays
+__device__ inline int64_t dense_of(const BLevel& L, int i, int j, int k) {
     return ((int64_t)k * (L.n + 1) + j) * (L.n + 1) + i;
 }
 __device__ inline int64_t node_of(const BLevel& L, uint32_t idx) {
@@ -86,27 +96,73 @@ __device__ inline int64_t node_of(const BLevel& L, uint32_t idx) {
     return node_of(L, idx, i, j, k);
 }
 
-template <typename T>
-__device__ inline float nsum(const T* u, int64_t p, int64_t sy, int64_t sz, bool three) {
-    float s = Num<T>::ld(u[p - 1]) + Num<T>::ld(u[p + 1]);
-    s += Num<T>::ld(u[p - sy]);
-    s += Num<T>::ld(u[p + sy]);
-    if (three) {
-        s += Num<T>::ld(u[p - sz]);
-        s += Num<T>::ld(u[p + sz]);
-    }
-    return s;
-}
-
 __device__ inline int64_t off_u(const BLevel& L, int which) { return which ? L.u1 : L.u0; }
 
-// smoothing sweep on the items' interior nodes: weighted Jacobi (src -> dst)
-// or one colour of red-black Gauss-Seidel (in place, src == dst).  pool_in
-// and pool_out are the same pool: what a launch reads through pool_in (the
-// src iterate, or the other colour, and q) is never written during the
-// launch, so the two may be declared not to alias, which lets the compiler
-// issue a node's loads ahead of the previous node's store.  (Loading four
-// nodes' operands ahead by hand measured slower: 93 vs 82 ms of sweeps.)
+// V = 16 bytes of inner-pool values (4 FP32, 8 BF16) as floats, and back
+template <typename T>
+__device__ inline void ldv(const T* p, float* v);
+template <>
+__device__ inline void ldv<float>(const float* p, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+}
+template <>
+__device__ inline void ldv<__nv_bfloat16>(const __nv_bfloat16* p, float* v) {
+    const uint4 a = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&w[h]);
+        v[2 * h] = __low2float(b);
+        v[2 * h + 1] = __high2float(b);
+    }
+}
+template <typename T>
+__device__ inline void stv(T* p, const float* v);
+template <>
+__device__ inline void stv<float>(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ inline void stv<__nv_bfloat16>(__nv_bfloat16* p, const float* v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+        *reinterpret_cast<__nv_bfloat162*>(&w[h]) = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+    *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Vector items: index gid over (interior row) x (16-byte group of the row),
+// 2^lgG groups per row (x = V g .. V g + V - 1 covers 0 .. n - 1); the group's
+// offset in the level's inner-pool array and its first x.
+template <int V>
+__device__ inline int64_t group_of(const BLevel& L, uint32_t gid, int& x0, int& j, int& k) {
+    const uint32_t row = gid >> L.lgG;
+    x0 = V * (int)(gid & ((1u << L.lgG) - 1u));
+    if (L.d == 3) {
+        const uint32_t m = L.rows.d;
+        const uint32_t kk = fastdiv(row, L.rows);
+        j = (int)(row - kk * m) + 1;
+        k = (int)kk + 1;
+    } else {
+        j = (int)row + 1;
+        k = 0;
+    }
+    return (int64_t)k * L.sz + (int64_t)j * L.sy + x0;
+}
+
+// Smoothing sweep over the items' groups: weighted Jacobi (src -> dst) or one
+// colour of red-black Gauss-Seidel (in place, src == dst; the group's other
+// nodes are written back unchanged, and no other thread writes them).  Per
+// group: one 16-byte load each of the row, its y and z neighbour rows and q,
+// the two x neighbours beyond the group as single loads, one 16-byte store;
+// nodes outside 1..n-1 are written as 0 (Jacobi) or left unchanged.  The
+// neighbour sum is ((x- + x+) + y- + y+) + z- + z+ in this order.  pool_in and pool_out are the
+// same pool: what a launch reads through pool_in is never written during the
+// launch (the Jacobi source, q; in red-black the other colour).
 template <typename T>
 __global__ void __launch_bounds__(256) k_smooth(const Item* __restrict__ items, int nitems,
                                                 const BSolve* __restrict__ sv,
@@ -115,6 +171,7 @@ __global__ void __launch_bounds__(256) k_smooth(const Item* __restrict__ items, 
                                                 T* __restrict__ pool_out,
                                                 const int* __restrict__ active, int src, int dst,
                                                 int color, float omega2, float omega3) {
+    constexpr int V = 16 / (int)sizeof(T);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const Item w = items[it];
         if (!active[w.solve]) continue;
@@ -122,27 +179,46 @@ __global__ void __launch_bounds__(256) k_smooth(const Item* __restrict__ items, 
         const bool three = L.d == 3;
         const float c = three ? 1.f / 6.f : 0.25f;
         const float omega = three ? omega3 : omega2;
-        const int64_t sy = L.n + 1, sz = three ? sy * sy : 0;
         const T* u = pool_in + off_u(L, src);
         T* uo = pool_out + off_u(L, dst);
         const T* q = pool_in + L.q;
         for (int t = threadIdx.x; t < w.count; t += blockDim.x) {
-            int i, j, k;
-            const int64_t p = node_of(L, (uint32_t)(w.start + t), i, j, k);
-            if (color >= 0) {
-                if (((i + j + k) & 1) != color) continue;
-                uo[p] = Num<T>::st(fmaf(c, nsum(u, p, sy, sz, three), Num<T>::ld(q[p])));
-            } else {
-                const float up = Num<T>::ld(u[p]);
-                const float sig = fmaf(c, nsum(u, p, sy, sz, three), Num<T>::ld(q[p])) - up;
-                uo[p] = Num<T>::st(fmaf(omega, sig, up));
+            int x0, j, k;
+            const int64_t p = group_of<V>(L, (uint32_t)(w.start + t), x0, j, k);
+            float x[V], ym[V], yp[V], zm[V], zp[V], qv[V], out[V];
+            ldv(u + p, x);
+            const float xl = Num<T>::ld(u[p - 1]), xr = Num<T>::ld(u[p + V]);
+            ldv(u + p - L.sy, ym);
+            ldv(u + p + L.sy, yp);
+            if (three) {
+                ldv(u + p - L.sz, zm);
+                ldv(u + p + L.sz, zp);
             }
+            ldv(q + p, qv);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                float s = (v > 0 ? x[v - 1] : xl) + (v < V - 1 ? x[v + 1] : xr);
+                s += ym[v];
+                s += yp[v];
+                if (three) {
+                    s += zm[v];
+                    s += zp[v];
+                }
+                const float g = fmaf(c, s, qv[v]);
+                const int xi = x0 + v;
+                const bool in = xi >= 1 && xi <= L.n - 1;
+                if (color >= 0)
+                    out[v] = in && ((xi + j + k) & 1) == color ? g : x[v];
+                else
+                    out[v] = in ? fmaf(omega, g - x[v], x[v]) : 0.f;
+            }
+            stv(uo + p, out);
         }
     }
 }
 
-// r = sigma on the items' interior nodes (pool_in / pool_out: the same pool,
-// as in k_smooth; u and q are not written during the launch)
+// r = sigma over the items' groups (0 outside the interior); pool_in /
+// pool_out: the same pool, as in k_smooth (u and q are not written here)
 template <typename T>
 __global__ void __launch_bounds__(256) k_residual(const Item* __restrict__ items, int nitems,
                                                   const BSolve* __restrict__ sv,
@@ -150,20 +226,42 @@ __global__ void __launch_bounds__(256) k_residual(const Item* __restrict__ items
                                                   const T* __restrict__ pool_in,
                                                   T* __restrict__ pool_out,
                                                   const int* __restrict__ active, int src) {
+    constexpr int V = 16 / (int)sizeof(T);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const Item w = items[it];
         if (!active[w.solve]) continue;
         const BLevel L = lv[sv[w.solve].lev0 + w.level];
         const bool three = L.d == 3;
         const float c = three ? 1.f / 6.f : 0.25f;
-        const int64_t sy = L.n + 1, sz = three ? sy * sy : 0;
         const T* u = pool_in + off_u(L, src);
         const T* q = pool_in + L.q;
         T* r = pool_out + L.r;
         for (int t = threadIdx.x; t < w.count; t += blockDim.x) {
-            const int64_t p = node_of(L, (uint32_t)(w.start + t));
-            r[p] = Num<T>::st(fmaf(c, nsum(u, p, sy, sz, three), Num<T>::ld(q[p])) -
-                              Num<T>::ld(u[p]));
+            int x0, j, k;
+            const int64_t p = group_of<V>(L, (uint32_t)(w.start + t), x0, j, k);
+            float x[V], ym[V], yp[V], zm[V], zp[V], qv[V], out[V];
+            ldv(u + p, x);
+            const float xl = Num<T>::ld(u[p - 1]), xr = Num<T>::ld(u[p + V]);
+            ldv(u + p - L.sy, ym);
+            ldv(u + p + L.sy, yp);
+            if (three) {
+                ldv(u + p - L.sz, zm);
+                ldv(u + p + L.sz, zp);
+            }
+            ldv(q + p, qv);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                float s = (v > 0 ? x[v - 1] : xl) + (v < V - 1 ? x[v + 1] : xr);
+                s += ym[v];
+                s += yp[v];
+                if (three) {
+                    s += zm[v];
+                    s += zp[v];
+                }
+                const int xi = x0 + v;
+                out[v] = xi >= 1 && xi <= L.n - 1 ? fmaf(c, s, qv[v]) - x[v] : 0.f;
+            }
+            stv(r + p, out);
         }
     }
 }
@@ -184,8 +282,7 @@ __global__ void __launch_bounds__(256) k_restrict(const Item* __restrict__ items
         const BLevel F = lv[sv[w.solve].lev0 + w.level];
         const BLevel C = lv[sv[w.solve].lev0 + w.level + 1];
         const bool three = F.d == 3;
-        const int64_t sy = F.n + 1, sz = three ? sy * sy : 0;
-        const int64_t cy = C.n + 1, cz = three ? cy * cy : 0;
+        const int64_t sy = F.sy, sz = three ? F.sz : 0;
         const T* r = pool_in + F.r;
         for (int t = threadIdx.x; t < w.count; t += blockDim.x) {
             int I, J, K;
@@ -227,8 +324,8 @@ __global__ void __launch_bounds__(256) k_prolong(const Item* __restrict__ items,
         const BLevel C = lv[sv[w.solve].lev0 + w.level + 1];
         const bool three = F.d == 3;
         const int nc = C.n;
-        const int64_t sy = F.n + 1, sz = three ? sy * sy : 0;
-        const int64_t cy = nc + 1, cz = three ? cy * cy : 0;
+        const int64_t sy = F.sy, sz = three ? F.sz : 0;
+        const int64_t cy = C.sy, cz = three ? C.sz : 0;
         const T* uc = pool + off_u(C, ccur);
         T* u = pool + off_u(F, fcur);
         const int lg = __ffs(nc) - 1;  // nc is a power of two
@@ -301,8 +398,9 @@ __global__ void __launch_bounds__(256) k_update(const Item* __restrict__ items, 
         const BLevel L = lv[S.lev0];
         const T* e = pool + L.u0;
         for (int t = threadIdx.x; t < w.count; t += blockDim.x) {
-            const int64_t p = node_of(L, (uint32_t)(w.start + t));
-            S.u[p] += (double)Num<T>::ld(e[p]);
+            int i, j, k;
+            const int64_t p = node_of(L, (uint32_t)(w.start + t), i, j, k);
+            S.u[dense_of(L, i, j, k)] += (double)Num<T>::ld(e[p]);
         }
     }
 }
@@ -321,7 +419,9 @@ __global__ void __launch_bounds__(256) k_prepare(const Item* __restrict__ items,
         const double scale = h * h / (2.0 * S.d);
         double* q = pool64 + S.q64;
         for (int t = threadIdx.x; t < w.count; t += blockDim.x) {
-            const int64_t p = node_of(L, (uint32_t)(w.start + t));
+            int i, j, k;
+            node_of(L, (uint32_t)(w.start + t), i, j, k);
+            const int64_t p = dense_of(L, i, j, k);
             q[p] = scale * S.f[p];
         }
     }
@@ -368,7 +468,9 @@ __global__ void __launch_bounds__(256) k_outer(const Item* __restrict__ items, i
         T* qin = pool + L.q;
         double acc = 0.0;
         for (int t = threadIdx.x; t < w.count; t += blockDim.x) {
-            const int64_t p = node_of(L, (uint32_t)(w.start + t));
+            int i, j, k;
+            const int64_t pin = node_of(L, (uint32_t)(w.start + t), i, j, k);
+            const int64_t p = dense_of(L, i, j, k);
             double s = u[p - 1] + u[p + 1];
             s += u[p - sy];
             s += u[p + sy];
@@ -377,7 +479,7 @@ __global__ void __launch_bounds__(256) k_outer(const Item* __restrict__ items, i
                 s += u[p + sz];
             }
             const double sig = fma(c, s, q[p]) - u[p];
-            qin[p] = Num<T>::st((float)sig);
+            qin[pin] = Num<T>::st((float)sig);
             acc = fma(sig, sig, acc);
         }
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
@@ -520,7 +622,7 @@ gmg_status enqueue_step(gmg_batch b, double rtol2) {
     std::vector<int> cur(b->G + 1, 0);  // which u buffer holds each level step's iterate
     auto relax = [&](int g, int sweeps) {
         const Range& r = b->fine[g];
-        const int64_t nn = range_nodes(b, r);
+        const int64_t nn = range_nodes(b, r) * (16 / b->elem);  // groups x V nodes
         for (int s = 0; s < sweeps; ++s) {
             if (rbgs) {
                 for (int color = 0; color < 2; ++color)
@@ -546,7 +648,7 @@ gmg_status enqueue_step(gmg_batch b, double rtol2) {
         // down: level steps g = G..1 (fine levels of the deepest solves first)
         for (int g = b->G; g >= 1; --g) {
             relax(g, c.nu1);
-            const int64_t nn = range_nodes(b, b->fine[g]);
+            const int64_t nn = range_nodes(b, b->fine[g]) * (16 / b->elem);
             launch_op<T>(b, "b_residual", g, b->fine[g], 3 * w, 7.0, nn,
                          [&](int grid, const Item* it, int ni) {
                              k_residual<T><<<grid, 256, 0, b->stream>>>(
@@ -728,7 +830,15 @@ gmg_status gmg_batch_create(int count, const int* d, const int* n, const gmg_con
             lv.d = d[s];
             lv.n = n[s] >> l;
             lv.rows = fastdiv_make((uint32_t)(lv.n - 1));
-            const int64_t m = lv.n + 1, nodes = d[s] == 3 ? m * m * m : m * m;
+            // rows padded to a multiple of 8 elements (16 bytes in BF16, 32 in FP32)
+            const int64_t m = lv.n + 1;
+            lv.sy = up(m, 8);
+            lv.sz = d[s] == 3 ? lv.sy * m : 0;
+            const int V = 16 / b->elem;
+            int lg = 0;
+            while ((V << (lg + 1)) <= lv.n) ++lg;  // 2^lg groups of V cover x = 0 .. n-1
+            lv.lgG = lg;
+            const int64_t nodes = d[s] == 3 ? lv.sz * m : lv.sy * m;
             lv.u0 = poff;
             poff = up(poff + nodes, align);
             lv.u1 = -1;
@@ -776,9 +886,18 @@ gmg_status gmg_batch_create(int count, const int* d, const int* n, const gmg_con
                 const int l = S.levels - 1 - g;
                 if (l < 0) continue;
                 const int nl = S.n >> l, nc = nl / 2;
-                const int64_t total = kind == OP_FINE     ? pw(nl - 1, S.d)
-                                      : kind == OP_COARSE ? pw(nc - 1, S.d)
-                                                          : pw(nc, S.d);
+                if (kind == OP_FINE) {
+                    // the vector kernels' items: (interior row, 16-byte group)
+                    // pairs, chunk / V groups per item
+                    const int V = 16 / b->elem;
+                    const int64_t groups = (int64_t)(S.d == 3 ? (nl - 1) * (nl - 1) : nl - 1)
+                                           << b->hl[S.lev0 + l].lgG;
+                    const int64_t gchunk = std::max<int64_t>(1, b->chunk / V);
+                    for (int64_t st = 0; st < groups; st += gchunk)
+                        b->items.push_back({s, l, st, (int)std::min<int64_t>(gchunk, groups - st)});
+                    continue;
+                }
+                const int64_t total = kind == OP_COARSE ? pw(nc - 1, S.d) : pw(nc, S.d);
                 add_items(s, l, total, b->items);
             }
             r.count = (int)b->items.size() - r.off;
