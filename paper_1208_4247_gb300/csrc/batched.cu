@@ -24,30 +24,10 @@
 namespace gmg {
 namespace batch {
 
-// x / d for 32-bit unsigned x and a fixed divisor d >= 1 by one multiply-high
-// and shifts: the round-up method of Granlund & Montgomery, "Division by
-// invariant integers using multiplication" (PLDI 1994, Fig. 4.1), with
-// l = ceil(log2 d) and mag = floor(2^32 (2^l - d) / d) + 1 (< 2^32).
-struct FastDiv {
-    uint32_t d, mag;
-    int l;
-};
-inline FastDiv fastdiv_make(uint32_t d) {
-    FastDiv f{d, 0u, 0};
-    while ((1ull << f.l) < d) ++f.l;
-    f.mag = (uint32_t)((((1ull << f.l) - d) << 32) / d + 1);
-    return f;
-}
-__device__ inline uint32_t fastdiv(uint32_t x, const FastDiv& f) {
-    if (f.l == 0) return x;  // d = 1
-    const uint32_t t = __umulhi(x, f.mag);
-    return (t + ((x - t) >> 1)) >> (f.l - 1);
-}
+using lk::fastdiv;
+using lk::FastDiv;
+using lk::fastdiv_make;
 
-// A level of one solve.  The inner (FP32 / BF16) pool stores its arrays with
-// rows padded to sy elements (a multiple of 8: every row starts on a 16-byte
-// boundary) and planes of sz = sy (n+1); the FP64 arrays of a solve (f, u,
-// q64) keep the caller's dense layout, pitch n+1.
 struct BLevel {
     int d, n;
     int64_t u0, u1, q, r;  // element offsets into the inner pool (-1: none)

@@ -32,6 +32,26 @@
 namespace gmg {
 namespace lk {
 
+// x / d for 32-bit unsigned x and a fixed divisor d >= 1 by one multiply-high
+// and shifts: the round-up method of Granlund & Montgomery, "Division by
+// invariant integers using multiplication" (PLDI 1994, Fig. 4.1), with
+// l = ceil(log2 d) and mag = floor(2^32 (2^l - d) / d) + 1 (< 2^32).
+struct FastDiv {
+    uint32_t d, mag;
+    int l;
+};
+inline FastDiv fastdiv_make(uint32_t d) {
+    FastDiv f{d, 0u, 0};
+    while ((1ull << f.l) < d) ++f.l;
+    f.mag = (uint32_t)((((1ull << f.l) - d) << 32) / d + 1);
+    return f;
+}
+__device__ inline uint32_t fastdiv(uint32_t x, const FastDiv& f) {
+    if (f.l == 0) return x;  // d = 1
+    const uint32_t t = __umulhi(x, f.mag);
+    return (t + ((x - t) >> 1)) >> (f.l - 1);
+}
+
 template <typename T>
 struct Num;
 template <>
@@ -219,17 +239,20 @@ __host__ __device__ constexpr int vec_of() {
 // per half row.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T* __restrict__ q,
-                                                     Lay L, int color, int G) {
+                                                     Lay L, int color, FastDiv fG, FastDiv fm,
+                                                     uint32_t items) {
     using N = Num<T>;
     constexpr int V = vec_of<T>();
     const float c = DIM == 3 ? 1.f / 6.f : 0.25f;
-    const int n = L.n, m = n - 1;
-    const int64_t rows = DIM == 3 ? (int64_t)m * m : m;
-    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= rows * G) return;
-    const int64_t r = w / G;
-    const int g = (int)(w - r * G);
-    const int j = (int)(r % m) + 1, k = DIM == 3 ? (int)(r / m) + 1 : 0;
+    const int n = L.n;
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= items) return;
+    // work item w = (row r, group g), row r = (j-1) + (k-1)(n-1): divisions
+    // by multiply-high (the counts stay below 2^32)
+    const uint32_t r = fastdiv(w, fG);
+    const int g = (int)(w - r * fG.d);
+    const uint32_t kk = DIM == 3 ? fastdiv(r, fm) : 0;
+    const int j = (int)(r - kk * fm.d) + 1, k = DIM == 3 ? (int)kk + 1 : 0;
     const int par = (color + j + k) & 1;  // x parity of the colour in this row
     const int x0 = 2 * V * g + par;       // x of the group's first node
     if (x0 > n - 1) return;
@@ -308,16 +331,17 @@ __device__ __forceinline__ void ldvn(const df32* p, df32 (&v)[V]) {
 template <int DIM, int V>
 __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
                                                         const df32* __restrict__ q, Lay L,
-                                                        int color, int G) {
+                                                        int color, FastDiv fG, FastDiv fm,
+                                                        uint32_t items) {
     static_assert(V == 2 || V == 4, "V nodes of 8 bytes per thread: one or two 16-byte vectors");
     const df32 c = DIM == 3 ? df32(1.0 / 6.0) : df32(0.25);
-    const int n = L.n, m = n - 1;
-    const int64_t rows = DIM == 3 ? (int64_t)m * m : m;
-    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= rows * G) return;
-    const int64_t r = w / G;
-    const int g = (int)(w - r * G);
-    const int j = (int)(r % m) + 1, k = DIM == 3 ? (int)(r / m) + 1 : 0;
+    const int n = L.n;
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= items) return;
+    const uint32_t r = fastdiv(w, fG);
+    const int g = (int)(w - r * fG.d);
+    const uint32_t kk = DIM == 3 ? fastdiv(r, fm) : 0;
+    const int j = (int)(r - kk * fm.d) + 1, k = DIM == 3 ? (int)kk + 1 : 0;
     const int par = (color + j + k) & 1;
     const int x0 = 2 * V * g + par;
     if (x0 > n - 1) return;
@@ -912,10 +936,11 @@ void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s, b
             const int G = (n / 2 + 1 + V - 1) / V;
             const int64_t items = (int64_t)G * (d == 3 ? (int64_t)(n - 1) * (n - 1) : n - 1);
             const unsigned blocks = (unsigned)((items + 255) / 256);
+            const FastDiv fG = fastdiv_make((uint32_t)G), fm = fastdiv_make((uint32_t)(n - 1));
             if (d == 3)
-                k_rb_half_vec<3, T><<<blocks, 256, 0, s>>>(u, q, L, color, G);
+                k_rb_half_vec<3, T><<<blocks, 256, 0, s>>>(u, q, L, color, fG, fm, (uint32_t)items);
             else
-                k_rb_half_vec<2, T><<<blocks, 256, 0, s>>>(u, q, L, color, G);
+                k_rb_half_vec<2, T><<<blocks, 256, 0, s>>>(u, q, L, color, fG, fm, (uint32_t)items);
             return;
         }
     }
@@ -925,10 +950,13 @@ void rb_half(int d, const Lay& L, T* u, const T* q, int color, cudaStream_t s, b
             const int G = (n / 2 + 1 + V - 1) / V;
             const int64_t items = (int64_t)G * (d == 3 ? (int64_t)(n - 1) * (n - 1) : n - 1);
             const unsigned blocks = (unsigned)((items + 255) / 256);
+            const FastDiv fG = fastdiv_make((uint32_t)G), fm = fastdiv_make((uint32_t)(n - 1));
             if (d == 3)
-                k_rb_half_vec_df<3, V><<<blocks, 256, 0, s>>>(u, q, L, color, G);
+                k_rb_half_vec_df<3, V><<<blocks, 256, 0, s>>>(u, q, L, color, fG, fm,
+                                                              (uint32_t)items);
             else
-                k_rb_half_vec_df<2, V><<<blocks, 256, 0, s>>>(u, q, L, color, G);
+                k_rb_half_vec_df<2, V><<<blocks, 256, 0, s>>>(u, q, L, color, fG, fm,
+                                                              (uint32_t)items);
             return;
         }
     }
