@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_red(double* __restrict__ u,
     const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
     const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
     double acc = 0.0;
+    df32 acc2(0.f, 0.f);  // sigma^2 summed in double-float (2^-47 relative)
     for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
          r += (int64_t)gridDim.x * blockDim.y) {
         const int j = (int)(r % (n - 1)) + 1;
@@ -254,9 +255,10 @@ __global__ void __launch_bounds__(kThreads) k_outer_red(double* __restrict__ u,
             const T st = N::st(typename N::C(sig));
             q_in[idx] = st;
             e[idx] = st;
-            acc = fma(sig, sig, acc);
+            acc2 = acc2 + st * st;  // on the FP32 pipe: the FP64 pipe bounds this kernel
         }
     }
+    acc = (double)acc2;
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
     if ((t & 31) == 0) warp_sums[t >> 5] = acc;
@@ -286,6 +288,7 @@ __global__ void __launch_bounds__(256, 4) k_outer_red3_walk(double* __restrict__
     const int n = in.n;
     const int64_t walkers = (int64_t)(n - 1) * segs;
     double acc = 0.0;
+    df32 acc2(0.f, 0.f);  // sigma^2 summed in double-float (2^-47 relative)
     for (int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; w < walkers;
          w += (int64_t)gridDim.x * blockDim.y)
         lk::walk_nodes(uc, n, 0, w, segs, [&](int64_t p, double sum, int i, int j, int k) {
@@ -296,8 +299,9 @@ __global__ void __launch_bounds__(256, 4) k_outer_red3_walk(double* __restrict__
             const T st = N::st(typename N::C(sig));
             q_in[idx] = st;
             e[idx] = st;
-            acc = fma(sig, sig, acc);
+            acc2 = acc2 + st * st;  // on the FP32 pipe: the FP64 pipe bounds this kernel
         });
+    acc = (double)acc2;
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
     if ((t & 31) == 0) warp_sums[t >> 5] = acc;
