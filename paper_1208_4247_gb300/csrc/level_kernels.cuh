@@ -237,10 +237,13 @@ __host__ __device__ constexpr int vec_of() {
 // consecutive entries of the row's other half.  Same operands in the same
 // order as nbr_sum_x: the results equal k_rb_half's bit for bit.  G = groups
 // per half row.
-template <int DIM, typename T>
+// RES: the scaled residual of the colour's nodes (sigma = value - u) into
+// res instead of the new values into u (the red-only residual after a black half
+// sweep; the same expression as k_residual).
+template <int DIM, typename T, bool RES = false>
 __global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T* __restrict__ q,
                                                      Lay L, int color, FastDiv fG, FastDiv fm,
-                                                     uint32_t items) {
+                                                     uint32_t items, T* __restrict__ res = nullptr) {
     using N = Num<T>;
     constexpr int V = vec_of<T>();
     const float c = DIM == 3 ? 1.f / 6.f : 0.25f;
@@ -292,13 +295,21 @@ __global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T*
             out[t] = fmaf(c, sx + (ym[t] + yp[t]), qv[t]);
         }
     }
+    T* dst = u;
+    if constexpr (RES) {
+        float own[V];
+        ldv(u + base, own);
+#pragma unroll
+        for (int t = 0; t < V; ++t) out[t] = out[t] - own[t];
+        dst = res;
+    }
     if (x0 >= 1 && x0 + 2 * (V - 1) <= n - 1) {
-        stv(u + base, out);
+        stv(dst + base, out);
     } else {
 #pragma unroll
         for (int t = 0; t < V; ++t) {
             const int x = x0 + 2 * t;
-            if (x >= 1 && x <= n - 1) u[base + t] = N::st(out[t]);
+            if (x >= 1 && x <= n - 1) dst[base + t] = N::st(out[t]);
         }
     }
 }
@@ -328,11 +339,12 @@ __device__ __forceinline__ void ldvn(const df32* p, df32 (&v)[V]) {
 #pragma unroll
     for (int h = 0; h < V / 2; ++h) ldv2(p + 2 * h, v[2 * h], v[2 * h + 1]);
 }
-template <int DIM, int V>
+template <int DIM, int V, bool RES = false>
 __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
                                                         const df32* __restrict__ q, Lay L,
                                                         int color, FastDiv fG, FastDiv fm,
-                                                        uint32_t items) {
+                                                        uint32_t items,
+                                                        df32* __restrict__ res = nullptr) {
     static_assert(V == 2 || V == 4, "V nodes of 8 bytes per thread: one or two 16-byte vectors");
     const df32 c = DIM == 3 ? df32(1.0 / 6.0) : df32(0.25);
     const int n = L.n;
@@ -376,14 +388,22 @@ __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
                                   : sum4(xo[t], xo[t + 1], ym[t], yp[t]);
         out[t] = gs_value<DIM, true>(c, sum, qv[t]);
     }
+    df32* dst = u;
+    if constexpr (RES) {  // sigma = value - u, as k_residual
+        df32 own[V];
+        ldvn(u + base, own);
+#pragma unroll
+        for (int t = 0; t < V; ++t) out[t] = out[t] - own[t];
+        dst = res;
+    }
     if (x0 >= 1 && x0 + 2 * (V - 1) <= n - 1) {
 #pragma unroll
-        for (int h = 0; h < V / 2; ++h) stv2(u + base + 2 * h, out[2 * h], out[2 * h + 1]);
+        for (int h = 0; h < V / 2; ++h) stv2(dst + base + 2 * h, out[2 * h], out[2 * h + 1]);
     } else {
 #pragma unroll
         for (int t = 0; t < V; ++t) {
             const int x = x0 + 2 * t;
-            if (x >= 1 && x <= n - 1) u[base + t] = out[t];
+            if (x >= 1 && x <= n - 1) dst[base + t] = out[t];
         }
     }
 }
@@ -1017,6 +1037,34 @@ void residual(int d, const Lay& L, const T* u, const T* q, T* r, bool red_only, 
     if (exact && L.he == 0) {
         residual_rows<3, false, T, kFp64>(L, u, q, r, red_only, s);
         return;
+    }
+    if constexpr (!kFp64) {
+        // red-only on the colour-split layout: the vector half-sweep kernel's
+        // residual mode (16 bytes of red nodes per operand row and thread)
+        if (red_only && L.he) {
+            constexpr int V = std::is_same<T, df32>::value ? kDfVec : vec_of<T>();
+            const int G = (n / 2 + 1 + V - 1) / V;
+            const int64_t items = (int64_t)G * (d == 3 ? (int64_t)(n - 1) * (n - 1) : n - 1);
+            const unsigned blocks = (unsigned)((items + 255) / 256);
+            const FastDiv fG = fastdiv_make((uint32_t)G), fm = fastdiv_make((uint32_t)(n - 1));
+            T* uu = const_cast<T*>(u);  // read only in this mode
+            if constexpr (std::is_same<T, df32>::value) {
+                if (d == 3)
+                    k_rb_half_vec_df<3, V, true><<<blocks, 256, 0, s>>>(uu, q, L, 0, fG, fm,
+                                                                        (uint32_t)items, r);
+                else
+                    k_rb_half_vec_df<2, V, true><<<blocks, 256, 0, s>>>(uu, q, L, 0, fG, fm,
+                                                                        (uint32_t)items, r);
+            } else {
+                if (d == 3)
+                    k_rb_half_vec<3, T, true><<<blocks, 256, 0, s>>>(uu, q, L, 0, fG, fm,
+                                                                     (uint32_t)items, r);
+                else
+                    k_rb_half_vec<2, T, true><<<blocks, 256, 0, s>>>(uu, q, L, 0, fG, fm,
+                                                                     (uint32_t)items, r);
+            }
+            return;
+        }
     }
     if (d == 3) {
         if (L.he)
