@@ -132,7 +132,22 @@ gmg_status gmg_config_init(gmg_config* cfg, int d, int n);
  * zero the correction and run the first inner red half sweep as kernels of
  * their own instead of having the outer residual write that half sweep's
  * result (sigma on red nodes, 0 on black); results are the same bit for
- * bit. */
+ * bit.  GMG_DF_STEP_CYCLES=k (default 8) sets, for GMG_DF_IR red-black
+ * handles with one inner cycle, the V-cycles per FP64 refinement step after
+ * a solve's first step (which has one): the FP64 update, residual and norm
+ * follow every k-th cycle, while the stopping test still runs after every
+ * cycle (on the inner residual, folded into the next red half sweep, which
+ * is undone when the test stops); k = 1 runs the FP64 step after every
+ * cycle.  Cycle counts are the same; iterates agree to the double-float
+ * rounding of the correction (far below 1e-12 of u per cycle).
+ * GMG_FUSED_LEGS=0/1 turns the fused leg kernels off / on for every FP32
+ * and double-float level that takes them (default: FP32 levels n >= 512);
+ * GMG_LEG_NMIN / GMG_LEG_NMAX bound the level sizes; results are the same bit
+ * for bit.  GMG_GRID_TAIL_N=m runs the levels with n <= m (red-black) and
+ * all smaller ones as one cooperative launch with grid barriers between the
+ * steps, the levels with n <= GMG_GRID_TAIL_CTA_N (default 8) in one CTA of
+ * it (default off: slower than the per-level kernels on GB300); results are
+ * the same bit for bit (3D FP64: levels n <= 64). */
 gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out);
 
 /* GMGSolve (Algorithm 3, all levels on the device): starting from the initial

@@ -44,6 +44,17 @@ struct LoopState {
     double hist[1];          // [cap]: relative residual after each cycle
 };
 constexpr size_t kLoopHeader = offsetof(LoopState, hist);
+
+// Double-float refinement in steps of several cycles (chain_on): the device's
+// plan for the cycle that runs now, and the step it belongs to.
+struct ChainState {
+    int step_it;   // cycles of the current step before this one
+    int kmax;      // cycles per step after a solve's first step (which has one)
+    int skip_mid;  // the cycle continues the step: black half sweep, red half sweep + norm
+    int skip_end;  // the cycle ends the step: the FP64 red update, residual and norm
+    int restore;   // the step ends after the norm said stop: undo that red half sweep
+    int counted;   // the norm inside the step counted this cycle
+};
 }  // namespace gmg
 
 struct gmg_handle_s {
@@ -82,6 +93,12 @@ struct gmg_handle_s {
     LoopState* d_loop = nullptr;
     LoopState* h_loop = nullptr;  // pinned
     bool device_loop = true;      // GMG_DEVICE_LOOP=0 at create: host loop
+    // double-float refinement: cycles per step after the first (chain_on;
+    // GMG_DF_STEP_CYCLES at create, 1 = one cycle per step), device plan
+    int chain_k = 8;
+    ChainState* d_chain = nullptr;
+    ChainState* h_chain = nullptr;  // pinned
+    bool graph_chain = false;       // the captured graphs are chain bodies
     int fmg_kernels = 0;
     std::vector<KernelTimer::Pending> fmg_pending;
     std::vector<double> hist;
@@ -103,6 +120,17 @@ struct gmg_handle_s {
     // GMG_LEG_NMIN overrides the smallest level n.
     int legs_mode = 1;
     int leg_nmin = 0;
+    int leg_nmax = 0;  // GMG_LEG_NMAX: the largest level n (0 = no bound)
+    // grid tail (tail::launch_grid): the levels with n <= gtail_nmax (and the
+    // small ones, n <= gtail_cta_n in one CTA) in one cooperative launch of
+    // gtail_blocks CTAs; GMG_GRID_TAIL_N at create (default 0 = off: slower
+    // than the per-level kernels and the single-CTA tail on GB300),
+    // GMG_GRID_TAIL_CTA_N
+    int gtail_nmax = 0;
+    int gtail_cta_n = 8;
+    int gtail_blocks = 0;
+    void* gtail_bar = nullptr;
+    bool gtail_used = false;
     bool legs_used = false;
     // learned smoother (GMG_LEARNED): per level BF16-rounded weights on the
     // device (NULL: red-black GS on that level) and the hidden-layer buffer
@@ -237,14 +265,14 @@ int num_levels(const gmg_config& c) { return c.levels > 0 ? c.levels : ilog2(c.n
 enum Kind {
     K_RB_HALF, K_WJ, K_RESIDUAL, K_RESTRICT, K_PROLONG, K_RESNORM, K_COPY, K_OUTER_RES,
     K_UPDATE, K_MEMSET, K_CONV1, K_CONV2, K_TAIL, K_RB_FUSED, K_MC_SWEEP, K_RESTRICT_PAPER,
-    K_PROLONG_PAPER, K_NORM_AHEAD, K_OUTER_RED, K_LEG_DOWN, K_LEG_UP, K_COUNT
+    K_PROLONG_PAPER, K_NORM_AHEAD, K_OUTER_RED, K_LEG_DOWN, K_LEG_UP, K_RESTORE, K_COUNT
 };
 const char* kKindName[K_COUNT] = {"rb_half",     "wj_sweep", "residual", "restrict",
                                   "prolong_add", "resnorm",  "copy",     "outer_residual",
                                   "update",      "memset",   "conv1",    "conv_tc_update", "tail",
                                   "rb_sweep_fused", "mc_sweep", "restrict_paper",
                                   "prolong_paper", "resnorm_red_sweep", "outer_red_update",
-                                  "leg_down", "leg_up"};
+                                  "leg_down", "leg_up", "red_restore"};
 const char* kPrecSuffix[4] = {"", "_f32", "_bf16", "_df"};
 
 template <typename T>
@@ -307,6 +335,8 @@ std::pair<double, double> model(int kind, int d, int n, bool red_only, double w,
             return {N / 2 * 6 * sweeps + N / 2 * 7 + Nc * 13, (N * 3 + Nc * 2) * w};
         case K_LEG_UP:  // black prolongation + `sweeps` half sweeps: read u_c, u, q; write u
             return {cells * 13 + N / 2 * 6 * sweeps, (N * 3 + Nc) * w};
+        case K_RESTORE:  // red nodes: u -= saved change; read u, r; write u
+            return {N / 2, N / 2 * 3 * w};
     }
     return {0.0, 0.0};
 }
@@ -433,7 +463,7 @@ bool leg_possible(gmg_handle h, int n) {
     if constexpr (std::is_same<T, float>::value || std::is_same<T, df32>::value)
         return h->legs_mode > 0 && type_ok && c.d == 3 && c.smoother == GMG_RBGS &&
                c.transfer != GMG_TRANSFER_PAPER && !use_fused_rb<T>(h) && n >= nmin &&
-               legs::applies<T>(c.d, n);
+               (h->leg_nmax == 0 || n <= h->leg_nmax) && legs::applies<T>(c.d, n);
     return false;
 }
 template <typename T>
@@ -467,6 +497,67 @@ int tail_level(gmg_handle h, const std::vector<Level<T>>& lv) {
     return L;
 }
 
+// The grid tail (tail::launch_grid) takes the levels from the first level
+// l >= 1 with n <= gtail_nmax down to the coarsest (at least two of them):
+// red-black smoothing with full weighting, a device that launches it
+// cooperatively, at most 12 levels, dense arrays there, and no fused leg on
+// the level above (a leg writes its coarse level in the colour-split layout).
+bool grid_tail_ok(gmg_handle h) {
+    const gmg_config& c = h->cfg;
+    return h->gtail_blocks > 0 && h->gtail_nmax > 0 && h->gtail_bar && c.smoother == GMG_RBGS &&
+           c.transfer != GMG_TRANSFER_PAPER;
+}
+// The largest level n it takes.  FP64 3D restrictions from fine n >= 128
+// run as z-walkers, which sum the same terms in another order than the
+// one-cell kernel (whose order the grid tail follows): FP64 levels up to 64.
+template <typename T>
+int grid_tail_nmax(gmg_handle h) {
+    return std::is_same<T, double>::value && h->cfg.d == 3 ? std::min(h->gtail_nmax, 64)
+                                                           : h->gtail_nmax;
+}
+// At allocation, from the level sizes: the first level stored dense for it.
+template <typename T>
+int grid_tail_alloc(gmg_handle h, int L) {
+    if (!grid_tail_ok(h)) return L;
+    const int n0 = h->cfg.n;
+    for (int l = 1; l + 1 < L; ++l)
+        if ((n0 >> l) <= grid_tail_nmax<T>(h))
+            return !leg_possible<T>(h, n0 >> (l - 1)) && L - l <= 12 ? l : L;
+    return L;
+}
+template <typename T>
+int grid_tail_level(gmg_handle h, const std::vector<Level<T>>& lv) {
+    const int L = (int)lv.size();
+    if (!grid_tail_ok(h)) return L;
+    for (int l = 1; l + 1 < L; ++l)
+        if (lv[l].n <= grid_tail_nmax<T>(h)) {
+            bool ok = !leg_level<T>(h, lv, l - 1) && L - l <= 12;
+            for (int k = l; k < L && ok; ++k) ok = lv[k].lay.he == 0;
+            return ok ? l : L;
+        }
+    return L;
+}
+
+template <typename T>
+cudaError_t launch_grid_tail(gmg_handle h, std::vector<Level<T>>& lv, int lg) {
+    const gmg_config& c = h->cfg;
+    const int L = (int)lv.size();
+    int n[12];
+    T* u[12];
+    T* q[12];
+    T* r[12];
+    for (int l = lg; l < L; ++l) {
+        n[l - lg] = lv[l].n;
+        u[l - lg] = lv[l].u[0];
+        q[l - lg] = lv[l].q;
+        r[l - lg] = lv[l].r;
+    }
+    h->gtail_used = true;
+    return tail::launch_grid<T>(c.d, L - lg, n, u, q, r, c.smoother, c.omega, c.nu1, c.nu2,
+                                c.coarse_sweeps, h->gtail_cta_n, h->gtail_bar, h->gtail_blocks,
+                                h->stream);
+}
+
 // One cycle of Algorithm 1 on the hierarchy lv (level-0 iterate lv[0].u[0]
 // in and out), in stream order.  first_red_done: the cycle's first level-0
 // red half sweep already ran (fp64::red_ahead); it starts with the black one.
@@ -481,6 +572,7 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_re
     const int p = prec_of<T>();
     std::vector<int> cur(L, 0);
     const int lt = tail_level<T>(h, lv);
+    const int lg = lt == 0 ? L : grid_tail_level<T>(h, lv);
     if (lt == 0) {
         // the whole hierarchy is small: one persistent launch
         cudaError_t e = cudaSuccess;
@@ -492,7 +584,8 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_re
     } else if (L == 1) {
         relax(h, lv, 0, c.nu1, cur[0], false, false, first_red_done);
     } else {
-        const int Ldown = lt < L ? lt : L - 1;  // levels smoothed by grid kernels going down
+        // levels smoothed by grid kernels going down
+        const int Ldown = lg < L ? lg : lt < L ? lt : L - 1;
         for (int l = 0; l < Ldown; ++l) {
             // fused down leg: the pre-smoothing half sweeps, the red residual
             // and the restriction in one pass (u ping-pongs)
@@ -548,7 +641,12 @@ gmg_status enqueue_vcycle(gmg_handle h, std::vector<Level<T>>& lv, bool first_re
                 });
             cur[l + 1] = 0;
         }
-        if (lt < L) {
+        if (lg < L) {
+            cudaError_t e = cudaSuccess;
+            timed(h, K_TAIL, lg, p, lv[lg].n, false,
+                  [&] { e = launch_grid_tail<T>(h, lv, lg); });
+            GMG_CUDA_TRY(e);
+        } else if (lt < L) {
             cudaError_t e = cudaSuccess;
             timed(h, K_TAIL, lt, p, lv[lt].n, false, [&] {
                 e = tail::launch<T>(d, lv[lt].lay, L - lt, lv[lt].u[0], lv[lt].q, c.smoother,
@@ -728,14 +826,151 @@ void enqueue_norm_ahead(gmg_handle h) {
         2);
 }
 
+// Double-float refinement in steps of several cycles.  Each cycle of the
+// FP64 V-cycle iteration is still one double-float inner V-cycle, but an
+// FP64 step (the triple-float black values, u += e, the red FP64 residual and
+// its norm: mixed::outer_red_update) follows only every kmax cycles: the
+// inner correction e, and with it the double-float rounding, is then a small
+// fraction of u (after a solve's first step, which has one cycle: its
+// correction is nearly all of u).  The stopping test still runs after every
+// cycle, exactly: after a black half sweep the residual vanishes on the
+// black nodes, and on a red node it is the change the next red half sweep
+// makes, so that sweep runs right away with the norm folded in
+// (mixed::df_red_ahead); if the test stops, the sweep is undone and the step
+// ends.  The norm inside a step is that of the inner equation, which is the
+// outer one's up to the double-float rounding of sigma (2^-48 relative);
+// the step's FP64 norm decides where it ends.  Cycle counts and histories
+// are the one-cycle-per-step form's.
+bool chain_on(gmg_handle h) {
+    const gmg_config& c = h->cfg;
+    return h->chain_k > 1 && c.precision == GMG_DF_IR && c.inner_cycles == 1 &&
+           c.cycle == GMG_VCYCLE && outer_red_only<df32>(h) && h->lvd.size() > 1 &&
+           h->lvd[0].lay.he != 0;
+}
+
+// hist holds st->pad entries (the loop state's history capacity).
+}  // namespace
+namespace gmg {
+// The plan of the cycle that runs now: it continues the step (mid) unless the
+// step has its cycles or the cap is one cycle away.
+__global__ void k_chain_plan(const LoopState* __restrict__ st, ChainState* __restrict__ c) {
+    const int k_eff = st->it == c->step_it ? 1 : c->kmax;  // a solve's first step: one cycle
+    const bool mid = c->step_it + 1 < k_eff && st->it + 1 < st->cap;
+    c->skip_mid = mid ? 0 : 1;
+    c->skip_end = mid ? 1 : 0;
+    c->restore = 0;
+    c->counted = 0;
+}
+
+// Inside a step: the norm after the cycle (partials of df_red_ahead, summed
+// in k_sum_partials' order), counted as a cycle; if the test stops, the step
+// ends here (the red half sweep run ahead is undone first).
+__global__ void __launch_bounds__(1024) k_chain_test(const double* __restrict__ partial, int count,
+                                                     LoopState* __restrict__ st,
+                                                     ChainState* __restrict__ c,
+                                                     cudaGraphConditionalHandle cond, int has_cond) {
+    __shared__ double warp_sums[32];
+    if (c->skip_mid) return;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) acc += partial[i];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double res2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) res2 += warp_sums[w];
+    const int it = st->it + 1;
+    st->it = it;
+    const double res = sqrt(res2);
+    st->res = res;
+    if (it - 1 < st->pad) st->hist[it - 1] = st->res0 > 0.0 ? res / st->res0 : 0.0;
+    c->step_it += 1;
+    const bool more = isfinite(res) && (!st->stop || res > st->rtol * st->res0);
+    if (!more) {
+        c->skip_end = 0;
+        c->restore = 1;
+        c->counted = 1;
+    } else if (has_cond) {
+        cudaGraphSetConditional(cond, 1u);
+    }
+}
+
+// After the step's FP64 update and residual: k_loop_test's test (the cycle
+// counted unless the norm inside the step already did), then a new step.
+__global__ void k_chain_end_test(const double* __restrict__ res2, LoopState* __restrict__ st,
+                                 ChainState* __restrict__ c, cudaGraphConditionalHandle cond,
+                                 int has_cond) {
+    if (c->skip_end) return;
+    int it = st->it;
+    if (!c->counted) st->it = ++it;
+    const double res = sqrt(res2[0]);
+    st->res = res;
+    if (it - 1 < st->pad) st->hist[it - 1] = st->res0 > 0.0 ? res / st->res0 : 0.0;
+    c->step_it = 0;
+    c->counted = 0;
+    const bool more = it < st->cap && isfinite(res) && (!st->stop || res > st->rtol * st->res0);
+    if (has_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+}  // namespace gmg
+namespace {
+
+// One cycle of the chained form: the inner V-cycle (its first red half sweep
+// already done, its last level-0 black one left to the step's end), then the
+// device-side plan's mid part (timer group 1) or end part (group 2; the
+// restore, group 3, only after a stop inside the step).  in_loop: inside the
+// while node (the test kernels set its condition).
+gmg_status enqueue_chain_kernels(gmg_handle h, bool in_loop) {
+    const gmg_config& c = h->cfg;
+    Level<df32>& I0 = h->lvd[0];
+    ChainState* C = h->d_chain;
+    const int p = prec_of<df32>();
+    k_chain_plan<<<1, 1, 0, h->stream>>>(h->d_loop, C);
+    h->timer.graph_kernels += 1;
+    gmg_status st = enqueue_vcycle<df32>(h, h->lvd, true, true);
+    if (st != GMG_OK) return st;
+    h->timer.cur_group = 1;
+    timed(h, K_RB_HALF, 0, p, c.n, false, [&] {
+        mixed::df_black_half(c.d, I0.lay, I0.u[0], I0.q, &C->skip_mid, h->stream);
+    });
+    int np = 0;
+    timed(h, K_NORM_AHEAD, 0, p, c.n, true, [&] {
+        np = mixed::df_red_ahead(c.d, I0.lay, I0.u[0], I0.q, I0.r, h->partial, &C->skip_mid,
+                                 h->stream);
+    });
+    k_chain_test<<<1, 1024, 0, h->stream>>>(h->partial, np, h->d_loop, C, h->loop_cond,
+                                            in_loop ? 1 : 0);
+    h->timer.graph_kernels += 1;
+    h->timer.cur_group = 3;
+    timed(h, K_RESTORE, 0, p, c.n, true, [&] {
+        mixed::df_red_restore(c.d, I0.lay, I0.u[0], I0.r, &C->restore, h->stream);
+    });
+    h->timer.cur_group = 2;
+    timed(
+        h, K_OUTER_RED, 0, p, c.n, false,
+        [&] {
+            mixed::outer_red_update<df32>(c.d, I0.lay, h->lv[0].u[0], h->lv[0].q, I0.q, I0.u[0],
+                                          h->partial, h->d_res2, h->stream, h->resid_b,
+                                          h->resid_flag, &C->skip_end);
+        },
+        3);
+    k_chain_end_test<<<1, 1, 0, h->stream>>>(h->d_res2, h->d_loop, C, h->loop_cond,
+                                             in_loop ? 1 : 0);
+    h->timer.graph_kernels += 1;
+    h->timer.cur_group = 0;
+    GMG_CUDA_TRY(cudaGetLastError());
+    return GMG_OK;
+}
+
 // One step of the stopping loop: a plain cycle plus the FP64 norm, or one
 // refinement step; the squared scaled norm lands in h->d_res2 (enqueue_step:
 // and is copied to h->h_res2).
-gmg_status enqueue_step_kernels(gmg_handle h) {
+gmg_status enqueue_step_kernels(gmg_handle h, bool in_loop = false) {
     const gmg_config& c = h->cfg;
     h->timer.begin_capture();
     gmg_status st = GMG_OK;
-    if (c.precision == GMG_FP64 && h->ahead) {
+    if (chain_on(h)) {
+        st = enqueue_chain_kernels(h, in_loop);
+    } else if (c.precision == GMG_FP64 && h->ahead) {
         st = enqueue_vcycle<double>(h, h->lv, true);
         if (st != GMG_OK) return st;
         enqueue_norm_ahead(h);
@@ -765,6 +1000,14 @@ gmg_status enqueue_step_kernels(gmg_handle h) {
 gmg_status enqueue_step(gmg_handle h) {
     gmg_status st = enqueue_step_kernels(h);
     if (st != GMG_OK) return st;
+    if (chain_on(h)) {  // the loop state the step's test kernels keep, and their plan
+        GMG_CUDA_TRY(cudaMemcpyAsync(h->h_loop, h->d_loop, kLoopHeader, cudaMemcpyDeviceToHost,
+                                     h->stream));
+        GMG_CUDA_TRY(cudaMemcpyAsync(h->h_chain, h->d_chain, sizeof(ChainState),
+                                     cudaMemcpyDeviceToHost, h->stream));
+        GMG_CUDA_TRY(cudaGetLastError());
+        return GMG_OK;
+    }
     GMG_CUDA_TRY(cudaMemcpyAsync(h->h_res2, h->d_res2, sizeof(double), cudaMemcpyDeviceToHost,
                                  h->stream));
     GMG_CUDA_TRY(cudaGetLastError());
@@ -823,9 +1066,13 @@ void build_loop_graph(gmg_handle h) {
     capturing = true;
     const int step_kernels = h->timer.graph_kernels;
     h->timer.begin_capture();
-    if (enqueue_step_kernels(h) != GMG_OK) return give_up();
-    k_loop_test<<<1, 1, 0, h->stream>>>(h->d_res2, h->d_loop, h->loop_cond);
-    h->loop_kernels = h->timer.graph_kernels + 1;
+    if (enqueue_step_kernels(h, true) != GMG_OK) return give_up();
+    if (chain_on(h)) {  // the chain's test kernels set the condition
+        h->loop_kernels = h->timer.graph_kernels;
+    } else {
+        k_loop_test<<<1, 1, 0, h->stream>>>(h->d_res2, h->d_loop, h->loop_cond);
+        h->loop_kernels = h->timer.graph_kernels + 1;
+    }
     h->timer.graph_kernels = step_kernels;
     capturing = false;
     if (cudaStreamEndCapture(h->stream, &body) != cudaSuccess) return give_up();
@@ -925,7 +1172,9 @@ gmg_status capture(gmg_handle h, cudaGraphExec_t* out, gmg_status (*enqueue)(gmg
 }
 
 gmg_status ensure_graph(gmg_handle h, double* u) {
-    if (h->graph && h->graph_u == u && h->graph_step_full == h->step_full) return GMG_OK;
+    if (h->graph && h->graph_u == u && h->graph_step_full == h->step_full &&
+        h->graph_chain == chain_on(h))
+        return GMG_OK;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -949,6 +1198,7 @@ gmg_status ensure_graph(gmg_handle h, double* u) {
     if (h->device_loop && h->d_loop && !h->timer.enabled) build_loop_graph(h);
     h->graph_u = u;
     h->graph_step_full = h->step_full;
+    h->graph_chain = chain_on(h);
     return GMG_OK;
 }
 
@@ -1045,6 +1295,25 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
         }
         return GMG_OK;
     };
+    // chained double-float steps: the plan and the test run on the device in
+    // either loop, on the loop state set here
+    const bool chain = chain_on(h);
+    if (chain) {
+        LoopState* L = h->h_loop;
+        L->res0 = res0;
+        L->rtol = rtol;
+        L->res = res;
+        L->cap = cap;
+        L->stop = stop ? 1 : 0;
+        L->it = 0;
+        L->pad = h->loop_cap;
+        ChainState* C = h->h_chain;
+        *C = ChainState{0, h->chain_k, 0, 0, 0, 0};
+        GMG_CUDA_TRY(
+            cudaMemcpyAsync(h->d_loop, L, kLoopHeader, cudaMemcpyHostToDevice, h->stream));
+        GMG_CUDA_TRY(cudaMemcpyAsync(h->d_chain, C, sizeof(ChainState), cudaMemcpyHostToDevice,
+                                     h->stream));
+    }
     while (it < cap && (!stop || res > rtol * res0)) {
         const bool fmg = it == 0 && h->fmg_graph;
         if (!fmg && h->loop_graph && !h->timer.enabled && cap <= h->loop_cap) {
@@ -1056,6 +1325,7 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
             L->cap = cap;
             L->stop = stop ? 1 : 0;
             L->it = it;
+            L->pad = h->loop_cap;
             GMG_CUDA_TRY(
                 cudaMemcpyAsync(h->d_loop, L, kLoopHeader, cudaMemcpyHostToDevice, h->stream));
             GMG_CUDA_TRY(cudaGraphLaunch(h->loop_graph, h->stream));
@@ -1080,6 +1350,23 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
         }
         GMG_CUDA_TRY(cudaGraphLaunch(fmg ? h->fmg_graph : h->graph, h->stream));
         GMG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        if (chain) {
+            // one cycle; the timer leaves out the groups the plan skipped
+            const ChainState* C = h->h_chain;
+            h->timer.after_graph_run((C->skip_mid ? 2u : 0u) | (C->skip_end ? 4u : 0u) |
+                                     (C->restore ? 0u : 8u));
+            it = h->h_loop->it;
+            res = h->h_loop->res;
+            const double rel = res0 > 0.0 ? res / res0 : 0.0;
+            h->hist.push_back(rel);
+            if (!stop && relres_out) relres_out[it - 1] = rel;
+            if (!std::isfinite(res)) {
+                if (iters_out) *iters_out = it;
+                set_error("residual norm became non-finite");
+                return GMG_ERR_NONFINITE;
+            }
+            continue;
+        }
         if (fmg) {
             // the FMG graph's own launch count and (when timing) event pairs
             std::swap(h->timer.pending, h->fmg_pending);
@@ -1103,6 +1390,10 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
         }
     }
     if ((st = finish()) != GMG_OK) return st;
+    if (h->gtail_used && tail::grid_fault(h->gtail_bar) != 0) {
+        set_error("the grid tail gave up waiting at a grid barrier; results are invalid");
+        return GMG_ERR_CUDA;
+    }
     if (h->legs_used && legs::fault() != 0) {
         set_error("a fused leg kernel gave up waiting for its plane loads; results are invalid");
         return GMG_ERR_CUDA;
@@ -1125,9 +1416,11 @@ gmg_status alloc_hierarchy(gmg_handle h, std::vector<Level<T>>& lv, int levels, 
         Level<T>& v = lv[l];
         v.n = c.n >> l;
         // FP64 levels keep the caller's dense layout; the FP32/BF16 inner
-        // hierarchies are colour-split (dense for the fused FP32 sweep)
-        v.lay = std::is_same<T, double>::value || use_fused_rb<T>(h) ? dense_lay(c.d, v.n)
-                                                                       : split_lay(c.d, v.n);
+        // hierarchies are colour-split (dense for the fused FP32 sweep and on
+        // the levels of the grid tail)
+        const bool dense = std::is_same<T, double>::value || use_fused_rb<T>(h) ||
+                           l >= grid_tail_alloc<T>(h, levels);
+        v.lay = dense ? dense_lay(c.d, v.n) : split_lay(c.d, v.n);
         v.nodes = lay_elems(c.d, v.lay);
         if (l > 0 || alloc_u0)
             if ((st = dev_alloc(h, &v.u[0], v.nodes)) != GMG_OK) return st;
@@ -1179,6 +1472,7 @@ gmg_status gmg_destroy(gmg_handle h) {
     if (h->fmg_graph) cudaGraphExecDestroy(h->fmg_graph);
     if (h->loop_graph) cudaGraphExecDestroy(h->loop_graph);
     if (h->h_loop) cudaFreeHost(h->h_loop);
+    if (h->h_chain) cudaFreeHost(h->h_chain);
     h->timer.destroy();
     for (void* p : h->allocs) cudaFree(p);
     if (h->h_res2) cudaFreeHost(h->h_res2);
@@ -1206,6 +1500,12 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     if (const char* v = std::getenv("GMG_DEVICE_LOOP")) h->device_loop = std::strcmp(v, "0") != 0;
     if (const char* v = std::getenv("GMG_FUSED_LEGS")) h->legs_mode = std::strcmp(v, "0") ? 2 : 0;
     if (const char* v = std::getenv("GMG_LEG_NMIN")) h->leg_nmin = std::max(2, std::atoi(v));
+    if (const char* v = std::getenv("GMG_LEG_NMAX")) h->leg_nmax = std::max(0, std::atoi(v));
+    if (const char* v = std::getenv("GMG_GRID_TAIL_N")) h->gtail_nmax = std::max(0, std::atoi(v));
+    if (const char* v = std::getenv("GMG_GRID_TAIL_CTA_N"))
+        h->gtail_cta_n = std::max(2, std::atoi(v));
+    if (const char* v = std::getenv("GMG_DF_STEP_CYCLES"))
+        h->chain_k = std::max(1, std::min(64, std::atoi(v)));
     auto fail = [&](gmg_status s) {
         gmg_destroy(h);
         return s;
@@ -1222,6 +1522,15 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     }
     const int d = cfg->d;
     const int L = num_levels(*cfg);
+    if (h->gtail_nmax > 0 && cfg->smoother == GMG_RBGS) {
+        h->gtail_blocks = cfg->precision == GMG_FP64      ? tail::grid_blocks<double>(d)
+                          : cfg->precision == GMG_FP32_IR ? tail::grid_blocks<float>(d)
+                          : cfg->precision == GMG_DF_IR   ? tail::grid_blocks<df32>(d)
+                                                          : tail::grid_blocks<bf16>(d);
+        if (h->gtail_blocks > 0 &&
+            (st = dev_alloc(h, (char**)&h->gtail_bar, (int64_t)tail::grid_bar_bytes())) != GMG_OK)
+            return fail(st);
+    }
     if (cfg->precision == GMG_FP64) {
         if ((st = alloc_hierarchy<double>(h, h->lv, L, false)) != GMG_OK) return fail(st);
     } else {
@@ -1257,6 +1566,12 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     const size_t loop_bytes = kLoopHeader + sizeof(double) * h->loop_cap;
     if ((st = dev_alloc(h, (char**)&h->d_loop, (int64_t)loop_bytes)) != GMG_OK) return fail(st);
     if (cudaMallocHost((void**)&h->h_loop, loop_bytes) != cudaSuccess) {
+        set_error("cudaMallocHost failed");
+        return fail(GMG_ERR_ALLOC);
+    }
+    if ((st = dev_alloc(h, (char**)&h->d_chain, (int64_t)sizeof(ChainState))) != GMG_OK)
+        return fail(st);
+    if (cudaMallocHost((void**)&h->h_chain, sizeof(ChainState)) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         return fail(GMG_ERR_ALLOC);
     }

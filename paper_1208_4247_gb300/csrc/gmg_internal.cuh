@@ -184,10 +184,28 @@ void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s);
 // the next outer residual on the red nodes only (the black one is zero to
 // FP64 rounding): q_in = e = sigma on red nodes, 0 on black ones; sigma^2
 // sum into *out.  Two kernels and the sum.
+// skip (may be NULL): the kernels do nothing while *skip is nonzero.
 template <typename T>
 void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in, T* e,
                       double* partial, double* out, cudaStream_t s, const float* resid = nullptr,
-                      int* resid_flag = nullptr);
+                      int* resid_flag = nullptr, const int* skip = nullptr);
+
+// Steps of several double-float cycles (mixed_kernels.cu), on the inner
+// level 0 (colour-split layout `in`, red = i+j+k even).  skip / flag: device
+// flags read by every thread; a launch does nothing while *skip is nonzero
+// (while *flag is zero for the restore).
+// The level's black half sweep.
+void df_black_half(int d, const Lay& in, df32* e, const df32* q_in, const int* skip,
+                   cudaStream_t s);
+// The next cycle's first red half sweep with the stopping-test norm folded
+// in: e = the red Gauss-Seidel values, r = their change (the red residual),
+// per block the sum of its squares into partial; returns the partial count
+// (at most outer_partials(d, n)).
+int df_red_ahead(int d, const Lay& in, df32* e, const df32* q_in, df32* r, double* partial,
+                 const int* skip, cudaStream_t s);
+// e -= r on the red nodes: undoes df_red_ahead.
+void df_red_restore(int d, const Lay& in, df32* e, const df32* r, const int* flag,
+                    cudaStream_t s);
 }  // namespace mixed
 
 // Fused red-black sweep (fused.cu, 3D FP32): u_out = one full sweep of u_in
@@ -208,6 +226,21 @@ template <typename T>
 cudaError_t launch(int d, const Lay& top, int levels, T* u_top, const T* q_top, int smoother,
                    double omega, int nu1, int nu2, int coarse_sweeps, cudaStream_t s,
                    bool exact_top = false);
+// The same on the levels' own dense arrays (n[l], u[l], q[l], r[l] for the
+// `levels` levels from the first one down), one cooperative launch of
+// `blocks` CTAs (grid_blocks: one wave; 0 when the device cannot) with grid
+// barriers between the steps on levels with n > cta_n and one CTA below.
+// bar: grid_bar_bytes() of device memory, zeroed once; its fault flag
+// (grid_fault) is set if a barrier wait ran past its limit (the results of
+// that launch are then invalid).  Red-black smoothing only.
+template <typename T>
+int grid_blocks(int d);
+template <typename T>
+cudaError_t launch_grid(int d, int levels, const int* n, T* const* u, T* const* q, T* const* r,
+                        int smoother, double omega, int nu1, int nu2, int coarse_sweeps,
+                        int cta_n, void* bar, int blocks, cudaStream_t s);
+size_t grid_bar_bytes();
+int grid_fault(const void* bar);
 }  // namespace tail
 
 // Learned-smoother network kernels (learned.cu): z = conv1(x) (8 channel

@@ -159,6 +159,11 @@ template <bool SPLIT>
 __host__ __device__ inline int64_t xo(const Lay& L, int i) {
     return SPLIT ? ((i & 1) ? L.he + (i >> 1) : (i >> 1)) : i;
 }
+// The same for a layout known only at run time (he = 0: dense): the coarse
+// level of a transfer may be dense under a colour-split fine level.
+__host__ __device__ inline int64_t xo_any(const Lay& L, int i) {
+    return L.he ? xo<true>(L, i) : i;
+}
 template <bool SPLIT>
 __device__ inline void xnb(const Lay& L, int i, int64_t& xm, int64_t& xp) {
     if (!SPLIT) {
@@ -339,26 +344,25 @@ __device__ __forceinline__ void ldvn(const df32* p, df32 (&v)[V]) {
 #pragma unroll
     for (int h = 0; h < V / 2; ++h) ldv2(p + 2 * h, v[2 * h], v[2 * h + 1]);
 }
-template <int DIM, int V, bool RES = false>
-__global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
-                                                        const df32* __restrict__ q, Lay L,
-                                                        int color, FastDiv fG, FastDiv fm,
-                                                        uint32_t items,
-                                                        df32* __restrict__ res = nullptr) {
-    static_assert(V == 2 || V == 4, "V nodes of 8 bytes per thread: one or two 16-byte vectors");
+// One work item w of the colour-split double-float half sweep: the colour's
+// Gauss-Seidel values out[] at its V nodes, from row offset base on (x of
+// the first node x0).  False when the item lies past the row's end.
+template <int DIM, int V>
+__device__ __forceinline__ bool vec_df_item(const df32* __restrict__ u,
+                                            const df32* __restrict__ q, const Lay& L, int color,
+                                            FastDiv fG, FastDiv fm, uint32_t w, int64_t& base,
+                                            int& x0, df32 (&out)[V]) {
     const df32 c = DIM == 3 ? df32(1.0 / 6.0) : df32(0.25);
     const int n = L.n;
-    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= items) return;
     const uint32_t r = fastdiv(w, fG);
     const int g = (int)(w - r * fG.d);
     const uint32_t kk = DIM == 3 ? fastdiv(r, fm) : 0;
     const int j = (int)(r - kk * fm.d) + 1, k = DIM == 3 ? (int)kk + 1 : 0;
     const int par = (color + j + k) & 1;
-    const int x0 = 2 * V * g + par;
-    if (x0 > n - 1) return;
+    x0 = 2 * V * g + par;
+    if (x0 > n - 1) return false;
     const int64_t row = k * L.sz + j * L.sy;
-    const int64_t base = row + (par ? L.he : 0) + V * g;
+    base = row + (par ? L.he : 0) + V * g;
     const int64_t ob = row + (par ? 0 : L.he) + V * g;
     df32 xo[V + 1];
     {
@@ -374,7 +378,7 @@ __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
             xo[t] = par ? a : b;
         }
     }
-    df32 qv[V], ym[V], yp[V], zm[V], zp[V], out[V];
+    df32 qv[V], ym[V], yp[V], zm[V], zp[V];
     ldvn(q + base, qv);
     ldvn(u + base - L.sy, ym);
     ldvn(u + base + L.sy, yp);
@@ -388,14 +392,14 @@ __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
                                   : sum4(xo[t], xo[t + 1], ym[t], yp[t]);
         out[t] = gs_value<DIM, true>(c, sum, qv[t]);
     }
-    df32* dst = u;
-    if constexpr (RES) {  // sigma = value - u, as k_residual
-        df32 own[V];
-        ldvn(u + base, own);
-#pragma unroll
-        for (int t = 0; t < V; ++t) out[t] = out[t] - own[t];
-        dst = res;
-    }
+    return true;
+}
+
+// Store V double-float values of one work item (one 16-byte vector per two
+// nodes where the whole group is interior, node by node at the row's ends).
+template <int V>
+__device__ __forceinline__ void vec_df_store(df32* __restrict__ dst, int64_t base, int x0, int n,
+                                             const df32 (&out)[V]) {
     if (x0 >= 1 && x0 + 2 * (V - 1) <= n - 1) {
 #pragma unroll
         for (int h = 0; h < V / 2; ++h) stv2(dst + base + 2 * h, out[2 * h], out[2 * h + 1]);
@@ -406,6 +410,108 @@ __global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
             if (x >= 1 && x <= n - 1) dst[base + t] = out[t];
         }
     }
+}
+
+// skip (may be NULL): the launch does nothing while *skip is nonzero (a
+// kernel of a captured step that the step's device-side plan leaves out).
+template <int DIM, int V, bool RES = false>
+__global__ void __launch_bounds__(256) k_rb_half_vec_df(df32* __restrict__ u,
+                                                        const df32* __restrict__ q, Lay L,
+                                                        int color, FastDiv fG, FastDiv fm,
+                                                        uint32_t items,
+                                                        df32* __restrict__ res = nullptr,
+                                                        const int* __restrict__ skip = nullptr) {
+    static_assert(V == 2 || V == 4, "V nodes of 8 bytes per thread: one or two 16-byte vectors");
+    if (skip && *skip) return;
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= items) return;
+    int64_t base;
+    int x0;
+    df32 out[V];
+    if (!vec_df_item<DIM, V>(u, q, L, color, fG, fm, w, base, x0, out)) return;
+    df32* dst = u;
+    if constexpr (RES) {  // sigma = value - u, as k_residual
+        df32 own[V];
+        ldvn(u + base, own);
+#pragma unroll
+        for (int t = 0; t < V; ++t) out[t] = out[t] - own[t];
+        dst = res;
+    }
+    vec_df_store<V>(dst, base, x0, L.n, out);
+}
+
+// The red half sweep that opens the next cycle, with the stopping-test norm
+// of the current iterate folded in: after a black half sweep the residual
+// vanishes on the black nodes, and on a red node it is the change the red
+// update makes (sigma = value - u).  Writes u = value and r = sigma on the
+// red nodes, and per block the sum of sigma^2 (double-float, then FP64
+// across the block in a fixed order) to partial[blockIdx.x].  Grid-stride
+// over the work items with a fixed grid (one wave: kAheadCtasPerSm CTAs of
+// 256 threads per SM), so the partials' count and order do not depend on
+// timing.
+// k_red_restore_df undoes the update from r.
+constexpr int kAheadCtasPerSm = 6;
+template <int DIM, int V>
+__global__ void __launch_bounds__(256, kAheadCtasPerSm) k_red_ahead_df(df32* __restrict__ u,
+                                                      const df32* __restrict__ q,
+                                                      df32* __restrict__ r, Lay L, FastDiv fG,
+                                                      FastDiv fm, uint32_t items,
+                                                      double* __restrict__ partial,
+                                                      const int* __restrict__ skip) {
+    __shared__ double warp_sums[8];
+    if (skip && *skip) return;
+    df32 acc2(0.f, 0.f);
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < items;
+         w += gridDim.x * blockDim.x) {
+        int64_t base;
+        int x0;
+        df32 out[V];
+        if (!vec_df_item<DIM, V>(u, q, L, 0, fG, fm, w, base, x0, out)) continue;
+        df32 own[V], sig[V];
+        ldvn(u + base, own);
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+            sig[t] = out[t] - own[t];
+            const int x = x0 + 2 * t;
+            if (x >= 1 && x <= L.n - 1) acc2 = acc2 + sig[t] * sig[t];
+        }
+        vec_df_store<V>(u, base, x0, L.n, out);
+        vec_df_store<V>(r, base, x0, L.n, sig);
+    }
+    double acc = (double)acc2;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 8; ++k) s += warp_sums[k];
+        partial[blockIdx.x] = s;
+    }
+}
+
+// Undo k_red_ahead_df: u -= r on the red nodes, while *flag is nonzero.
+template <int DIM, int V>
+__global__ void __launch_bounds__(256) k_red_restore_df(df32* __restrict__ u,
+                                                        const df32* __restrict__ r, Lay L,
+                                                        FastDiv fG, FastDiv fm, uint32_t items,
+                                                        const int* __restrict__ flag) {
+    if (!*flag) return;
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= items) return;
+    const uint32_t rr = fastdiv(w, fG);
+    const int g = (int)(w - rr * fG.d);
+    const uint32_t kk = DIM == 3 ? fastdiv(rr, fm) : 0;
+    const int j = (int)(rr - kk * fm.d) + 1, k = DIM == 3 ? (int)kk + 1 : 0;
+    const int par = (j + k) & 1;
+    const int x0 = 2 * V * g + par;
+    if (x0 > L.n - 1) return;
+    const int64_t base = k * L.sz + j * L.sy + (par ? L.he : 0) + V * g;
+    df32 v[V], d[V];
+    ldvn(u + base, v);
+    ldvn(r + base, d);
+#pragma unroll
+    for (int t = 0; t < V; ++t) v[t] = v[t] - d[t];
+    vec_df_store<V>(u, base, x0, L.n, v);
 }
 
 // 3D red-black half sweep by diagonal walkers.  The (n-1)^2 interior rows
@@ -657,7 +763,7 @@ __global__ void __launch_bounds__(256) k_restrict(const T* __restrict__ r, T* __
             v = fma(C(0.25), co, fma(C(0.5), fc, R(0)));
         }
     }
-    const int64_t P = (int64_t)K * Cl.sz + (int64_t)J * Cl.sy + xo<SPLIT>(Cl, I);
+    const int64_t P = (int64_t)K * Cl.sz + (int64_t)J * Cl.sy + xo_any(Cl, I);
     qc[P] = N::st(v);
     uc[P] = exact ? N::st(v) : N::st(C(0));
 }
@@ -681,7 +787,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, T
     if (I >= nc || J >= nc) return;
     const int64_t sy = F.sy, sz = F.sz, cy = Cl.sy, cz = Cl.sz;
     const int64_t Pr = K * cz + J * cy;
-    const int64_t P = Pr + xo<SPLIT>(Cl, I), P1 = Pr + xo<SPLIT>(Cl, I + 1);  // x = I, I+1
+    const int64_t P = Pr + xo_any(Cl, I), P1 = Pr + xo_any(Cl, I + 1);  // x = I, I+1
     const int64_t pr = (2 * K) * sz + (2 * J) * sy;
     const int64_t p = pr + xo<SPLIT>(F, 2 * I), p1 = pr + xo<SPLIT>(F, 2 * I + 1);  // x = 2I, 2I+1
     const C c000 = N::ld(uc[P]), c100 = N::ld(uc[P1]), c010 = N::ld(uc[P + cy]),

@@ -190,7 +190,9 @@ __global__ void __launch_bounds__(256) k_black_exact_update(double* __restrict__
                                                             df32* __restrict__ e,
                                                             df32* __restrict__ q_in, Lay in,
                                                             const float* __restrict__ resid,
-                                                            const int* __restrict__ resid_flag) {
+                                                            const int* __restrict__ resid_flag,
+                                                            const int* __restrict__ skip) {
+    if (skip && *skip) return;
     const bool add_resid = resid && *resid_flag;
     const int n = in.n;
     const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
@@ -230,9 +232,11 @@ __global__ void __launch_bounds__(kThreads) k_outer_red(double* __restrict__ u,
                                                         const double* __restrict__ q,
                                                         T* __restrict__ q_in, T* __restrict__ e,
                                                         double* __restrict__ partial, Lay in,
-                                                        int* __restrict__ resid_flag) {
+                                                        int* __restrict__ resid_flag,
+                                                        const int* __restrict__ skip) {
     using N = lk::Num<T>;
     __shared__ double warp_sums[kThreads / 32];
+    if (skip && *skip) return;  // uniform over the grid: before any barrier
     if (resid_flag && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *resid_flag = 0;
     const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
     const int n = in.n;
@@ -280,9 +284,11 @@ __global__ void __launch_bounds__(256, 4) k_outer_red3_walk(double* __restrict__
                                                             T* __restrict__ q_in,
                                                             T* __restrict__ e,
                                                             double* __restrict__ partial, Lay in,
-                                                            int segs, int* __restrict__ resid_flag) {
+                                                            int segs, int* __restrict__ resid_flag,
+                                                            const int* __restrict__ skip) {
     using N = lk::Num<T>;
     __shared__ double warp_sums[kThreads / 32];
+    if (skip && *skip) return;  // uniform over the grid: before any barrier
     if (resid_flag && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *resid_flag = 0;
     const double c = 1.0 / 6.0;
     const int n = in.n;
@@ -313,12 +319,30 @@ __global__ void __launch_bounds__(256, 4) k_outer_red3_walk(double* __restrict__
     }
 }
 
+// fp64::k_sum_partials (the same order) while *skip is zero.
+__global__ void __launch_bounds__(1024) k_sum_partials_skip(const double* __restrict__ partial,
+                                                            int count, double* __restrict__ out,
+                                                            const int* __restrict__ skip) {
+    __shared__ double warp_sums[32];
+    if (skip && *skip) return;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) acc += partial[i];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += warp_sums[w];
+        out[0] = t;
+    }
+}
+
 }  // namespace
 
 template <typename T>
 void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in, T* e,
                       double* partial, double* out, cudaStream_t s, const float* resid,
-                      int* resid_flag) {
+                      int* resid_flag, const int* skip) {
     static_assert(std::is_same<T, df32>::value, "the red-only outer residual is double-float");
     const int n = in.n;
     int bx = 32;
@@ -329,47 +353,47 @@ void outer_red_update(int d, const Lay& in, double* u, const double* q, T* q_in,
     if (d == 3) {
         if (in.he)
             k_black_exact_update<3, true><<<ublocks, block, 0, s>>>(u, e, q_in, in, resid,
-                                                                   resid_flag);
+                                                                   resid_flag, skip);
         else
             k_black_exact_update<3, false><<<ublocks, block, 0, s>>>(u, e, q_in, in, resid,
-                                                                   resid_flag);
+                                                                   resid_flag, skip);
     } else {
         if (in.he)
             k_black_exact_update<2, true><<<ublocks, block, 0, s>>>(u, e, q_in, in, resid,
-                                                                   resid_flag);
+                                                                   resid_flag, skip);
         else
             k_black_exact_update<2, false><<<ublocks, block, 0, s>>>(u, e, q_in, in, resid,
-                                                                   resid_flag);
+                                                                   resid_flag, skip);
     }
     if (lk::walk_applies(d, n, sizeof(double))) {
         const lk::WalkLaunch W = lk::walk_launch(n);
         const int blocks = (int)std::min<int64_t>(W.blocks, outer_partials(d, n));
         if (in.he)
             k_outer_red3_walk<true, T><<<blocks, W.block, 0, s>>>(u, u, q, q_in, e, partial, in,
-                                                                  W.segs, resid_flag);
+                                                                  W.segs, resid_flag, skip);
         else
             k_outer_red3_walk<false, T><<<blocks, W.block, 0, s>>>(u, u, q, q_in, e, partial, in,
-                                                                   W.segs, resid_flag);
-        fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
+                                                                   W.segs, resid_flag, skip);
+        k_sum_partials_skip<<<1, 1024, 0, s>>>(partial, blocks, out, skip);
         return;
     }
     const int blocks = outer_partials(d, n);
     if (d == 3) {
         if (in.he)
             k_outer_red<3, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in,
-                                                          resid_flag);
+                                                          resid_flag, skip);
         else
             k_outer_red<3, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in,
-                                                          resid_flag);
+                                                          resid_flag, skip);
     } else {
         if (in.he)
             k_outer_red<2, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in,
-                                                          resid_flag);
+                                                          resid_flag, skip);
         else
             k_outer_red<2, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e, partial, in,
-                                                          resid_flag);
+                                                          resid_flag, skip);
     }
-    fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
+    k_sum_partials_skip<<<1, 1024, 0, s>>>(partial, blocks, out, skip);
 }
 
 int outer_partials(int d, int n) {
@@ -453,7 +477,62 @@ template void outer_residual<__nv_bfloat16>(int, const Lay&, const double*, cons
 template void outer_residual<df32>(int, const Lay&, const double*, const double*, df32*, double*,
                                    double*, cudaStream_t, df32*, float*, int*, double*);
 template void outer_red_update<df32>(int, const Lay&, double*, const double*, df32*, df32*,
-                                     double*, double*, cudaStream_t, const float*, int*);
+                                     double*, double*, cudaStream_t, const float*, int*,
+                                     const int*);
+
+// Work items of the colour-split double-float kernels on level `in`: groups
+// of lk::kDfVec nodes of one colour in a row, rows (j, k).
+struct DfItems {
+    lk::FastDiv fG, fm;
+    uint32_t items;
+};
+DfItems df_items(int d, const Lay& in) {
+    const int n = in.n;
+    constexpr int V = lk::kDfVec;
+    const int G = (n / 2 + 1 + V - 1) / V;
+    const int64_t items = (int64_t)G * (d == 3 ? (int64_t)(n - 1) * (n - 1) : n - 1);
+    return {lk::fastdiv_make((uint32_t)G), lk::fastdiv_make((uint32_t)(n - 1)), (uint32_t)items};
+}
+
+void df_black_half(int d, const Lay& in, df32* e, const df32* q_in, const int* skip,
+                   cudaStream_t s) {
+    constexpr int V = lk::kDfVec;
+    const DfItems I = df_items(d, in);
+    const unsigned blocks = (I.items + 255) / 256;
+    if (d == 3)
+        lk::k_rb_half_vec_df<3, V><<<blocks, 256, 0, s>>>(e, q_in, in, 1, I.fG, I.fm, I.items,
+                                                          nullptr, skip);
+    else
+        lk::k_rb_half_vec_df<2, V><<<blocks, 256, 0, s>>>(e, q_in, in, 1, I.fG, I.fm, I.items,
+                                                          nullptr, skip);
+}
+
+int df_red_ahead(int d, const Lay& in, df32* e, const df32* q_in, df32* r, double* partial,
+                 const int* skip, cudaStream_t s) {
+    constexpr int V = lk::kDfVec;
+    const DfItems I = df_items(d, in);
+    const int blocks = (int)std::min<int64_t>(((int64_t)I.items + 255) / 256,
+                                              std::min(152 * lk::kAheadCtasPerSm,
+                                                       outer_partials(d, in.n)));
+    if (d == 3)
+        lk::k_red_ahead_df<3, V><<<blocks, 256, 0, s>>>(e, q_in, r, in, I.fG, I.fm, I.items,
+                                                        partial, skip);
+    else
+        lk::k_red_ahead_df<2, V><<<blocks, 256, 0, s>>>(e, q_in, r, in, I.fG, I.fm, I.items,
+                                                        partial, skip);
+    return blocks;
+}
+
+void df_red_restore(int d, const Lay& in, df32* e, const df32* r, const int* flag,
+                    cudaStream_t s) {
+    constexpr int V = lk::kDfVec;
+    const DfItems I = df_items(d, in);
+    const unsigned blocks = (I.items + 255) / 256;
+    if (d == 3)
+        lk::k_red_restore_df<3, V><<<blocks, 256, 0, s>>>(e, r, in, I.fG, I.fm, I.items, flag);
+    else
+        lk::k_red_restore_df<2, V><<<blocks, 256, 0, s>>>(e, r, in, I.fG, I.fm, I.items, flag);
+}
 template void update<float>(int, const Lay&, double*, const float*, cudaStream_t);
 template void update<df32>(int, const Lay&, double*, const df32*, cudaStream_t);
 template void update<__nv_bfloat16>(int, const Lay&, double*, const __nv_bfloat16*, cudaStream_t);

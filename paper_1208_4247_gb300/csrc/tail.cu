@@ -26,6 +26,9 @@ struct SLevel {
     T* r;
 };
 
+constexpr int kMaxGridLevels = 12;
+constexpr int kGridThreads = 512;
+
 template <int DIM>
 __device__ inline int64_t nodes_of(int n) {
     const int64_t m = n + 1;
@@ -48,7 +51,7 @@ __device__ constexpr int interior_count() {
     return DIM == 3 ? (NN - 1) * (NN - 1) * (NN - 1) : (NN - 1) * (NN - 1);
 }
 
-// f.template operator()<NN>() for the level size n (a power of two, 2..64)
+// f.template operator()<NN>() for the level size n (a power of two, 2..128)
 template <class F>
 __device__ inline void dispatch_n(int n, F&& f) {
     switch (n) {
@@ -57,40 +60,106 @@ __device__ inline void dispatch_n(int n, F&& f) {
         case 8: f.template operator()<8>(); break;
         case 16: f.template operator()<16>(); break;
         case 32: f.template operator()<32>(); break;
-        default: f.template operator()<64>(); break;
+        case 64: f.template operator()<64>(); break;
+        default: f.template operator()<128>(); break;
     }
 }
 
+// Interior nodes of one colour ((i + j + k) & 1 == color), NN/2 slots per
+// interior row: slot idx -> (node index, i, j, k); false for the one slot per
+// row that lies past the row's end.
+template <int DIM, int NN>
+__device__ constexpr int color_slots() {
+    return DIM == 3 ? (NN - 1) * (NN - 1) * (NN / 2) : (NN - 1) * (NN / 2);
+}
+template <int DIM, int NN>
+__device__ inline bool cnode(int idx, int color, int64_t& p, int& i, int& j, int& k) {
+    constexpr int h = NN / 2, m = NN - 1;
+    const int t = idx % h;
+    const int row = idx / h;
+    j = row % m + 1;
+    k = DIM == 3 ? row / m + 1 : 0;
+    i = 2 * t + (((color + j + k) & 1) ? 1 : 2);
+    p = ((int64_t)k * (NN + 1) + j) * (NN + 1) + i;
+    return i <= m;
+}
+
+// Who runs a step and how the steps are separated: one CTA (__syncthreads),
+// or every CTA of a cooperative launch (a grid barrier).
+struct CtaX {
+    __device__ int tid() const { return threadIdx.x; }
+    __device__ int nt() const { return blockDim.x; }
+    __device__ void sync() { __syncthreads(); }
+};
+
+// Grid barrier: a monotonic arrival count (zeroed before the launch); the
+// b-th barrier waits until b * gridDim.x CTAs have arrived.  Thread 0 of each
+// CTA publishes the CTA's writes (fence after the CTA barrier), arrives and
+// spins with a limit of kSpinCycles SM clocks; past it the barrier sets
+// bar->fault and every later one returns at once, so the kernel always ends
+// (the host then reports the fault).  The fence after the spin orders the
+// CTA's later loads after the other CTAs' published writes.
+struct GridBar {
+    unsigned count;
+    int fault;
+};
+constexpr long long kSpinCycles = 200000000LL;  // about 0.1 s
+struct GridX {
+    GridBar* bar;
+    unsigned target = 0;
+    __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ int nt() const { return gridDim.x * blockDim.x; }
+    __device__ void sync() {
+        __syncthreads();
+        target += gridDim.x;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&bar->count, 1u);
+            volatile unsigned* c = &bar->count;
+            volatile int* f = &bar->fault;
+            const long long t0 = clock64();
+            while (*c < target && *f == 0) {
+                if (clock64() - t0 > kSpinCycles) {
+                    *f = 1;
+                    break;
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+    }
+};
+
 // ex: the unbiased FP64 3D value (lk::gs_value), as the grid kernels take
 // it on level 0 of a plain FP64 hierarchy
-template <int DIM, typename T>
-__device__ void rb_half(SLevel<T>& L, int color, bool ex = false) {
+template <int DIM, typename T, class X>
+__device__ void rb_half(X& x, SLevel<T>& L, int color, bool ex = false) {
     using N = Num<T>;
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
     dispatch_n(L.n, [&]<int NN>() {
         constexpr int64_t sy = NN + 1, sz = DIM == 3 ? sy * sy : 0;
-        for (int idx = threadIdx.x; idx < interior_count<DIM, NN>(); idx += blockDim.x) {
+        for (int idx = x.tid(); idx < color_slots<DIM, NN>(); idx += x.nt()) {
             int i, j, k;
-            const int64_t p = inode<DIM, NN>(idx, i, j, k);
-            if (((i + j + k) & 1) != color) continue;
+            int64_t p;
+            if (!cnode<DIM, NN>(idx, color, p, i, j, k)) continue;
             const C s = lk::nbr_sum<DIM>(L.u, p, sy, sz);
             L.u[p] = N::st(ex ? lk::gs_value<DIM, true>(c, s, N::ld(L.q[p]))
                               : lk::gs_value<DIM, false>(c, s, N::ld(L.q[p])));
         }
     });
-    __syncthreads();
+    x.sync();
 }
 
-template <int DIM, typename T>
-__device__ void wj_sweep(SLevel<T>& L, double omega_d) {
+template <int DIM, typename T, class X>
+__device__ void wj_sweep(X& x, SLevel<T>& L, double omega_d) {
     using N = Num<T>;
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
     const C omega = C(omega_d);
     dispatch_n(L.n, [&]<int NN>() {
         constexpr int64_t sy = NN + 1, sz = DIM == 3 ? sy * sy : 0;
-        for (int idx = threadIdx.x; idx < interior_count<DIM, NN>(); idx += blockDim.x) {
+        for (int idx = x.tid(); idx < interior_count<DIM, NN>(); idx += x.nt()) {
             int i, j, k;
             const int64_t p = inode<DIM, NN>(idx, i, j, k);
             const C up = N::ld(L.u[p]);
@@ -99,54 +168,63 @@ __device__ void wj_sweep(SLevel<T>& L, double omega_d) {
             L.u2[p] = N::st(fma(omega, sig, up));
         }
     });
-    __syncthreads();
+    x.sync();
     T* t = L.u;
     L.u = L.u2;
     L.u2 = t;
 }
 
-template <int DIM, typename T>
-__device__ void relax(SLevel<T>& L, int smoother, double omega, int sweeps,
+template <int DIM, typename T, class X>
+__device__ void relax(X& x, SLevel<T>& L, int smoother, double omega, int sweeps,
                       bool exact_last = false) {
     for (int s = 0; s < sweeps; ++s) {
         if (smoother == GMG_WJACOBI) {
-            wj_sweep<DIM>(L, omega);
+            wj_sweep<DIM>(x, L, omega);
         } else {
-            rb_half<DIM>(L, 0);
-            rb_half<DIM>(L, 1, exact_last && s == sweeps - 1);
+            rb_half<DIM>(x, L, 0);
+            rb_half<DIM>(x, L, 1, exact_last && s == sweeps - 1);
         }
     }
 }
 
-template <int DIM, typename T>
-__device__ void residual(SLevel<T>& L, bool red_only, bool ex = false) {
+template <int DIM, typename T, class X>
+__device__ void residual(X& x, SLevel<T>& L, bool red_only, bool ex = false) {
     using N = Num<T>;
     using C = typename N::C;
     const C c = DIM == 3 ? C(1.0 / 6.0) : C(0.25);
     dispatch_n(L.n, [&]<int NN>() {
         constexpr int64_t sy = NN + 1, sz = DIM == 3 ? sy * sy : 0;
-        for (int idx = threadIdx.x; idx < interior_count<DIM, NN>(); idx += blockDim.x) {
-            int i, j, k;
-            const int64_t p = inode<DIM, NN>(idx, i, j, k);
-            if (red_only && ((i + j + k) & 1)) continue;
+        auto node = [&](int64_t p) {
             const C s = lk::nbr_sum<DIM>(L.u, p, sy, sz);
             const C v = ex ? lk::gs_value<DIM, true>(c, s, N::ld(L.q[p]))
                            : lk::gs_value<DIM, false>(c, s, N::ld(L.q[p]));
             L.r[p] = N::st(v - N::ld(L.u[p]));
+        };
+        if (red_only) {
+            for (int idx = x.tid(); idx < color_slots<DIM, NN>(); idx += x.nt()) {
+                int i, j, k;
+                int64_t p;
+                if (cnode<DIM, NN>(idx, 0, p, i, j, k)) node(p);
+            }
+        } else {
+            for (int idx = x.tid(); idx < interior_count<DIM, NN>(); idx += x.nt()) {
+                int i, j, k;
+                node(inode<DIM, NN>(idx, i, j, k));
+            }
         }
     });
-    __syncthreads();
+    x.sync();
 }
 
-template <int DIM, typename T>
-__device__ void restrict_fw(SLevel<T>& F, SLevel<T>& Cl, bool red_only) {
+template <int DIM, typename T, class X>
+__device__ void restrict_fw(X& x, SLevel<T>& F, SLevel<T>& Cl, bool red_only) {
     using N = Num<T>;
     using C = typename N::C;
     const int nc = Cl.n;
     const int64_t sy = F.n + 1, sz = DIM == 3 ? sy * sy : 0;
     const bool exact = nc == 2;
     dispatch_n(nc, [&]<int NC>() {
-    for (int idx = threadIdx.x; idx < interior_count<DIM, NC>(); idx += blockDim.x) {
+    for (int idx = x.tid(); idx < interior_count<DIM, NC>(); idx += x.nt()) {
         int I, J, K;
         const int64_t P = inode<DIM, NC>(idx, I, J, K);
         const int64_t p = (2 * K) * sz + (2 * J) * sy + 2 * I;
@@ -198,11 +276,11 @@ __device__ void restrict_fw(SLevel<T>& F, SLevel<T>& Cl, bool red_only) {
         Cl.u[P] = exact ? N::st(v) : N::st(C(0));
     }
     });
-    __syncthreads();
+    x.sync();
 }
 
-template <int DIM, typename T>
-__device__ void prolong_add(SLevel<T>& Cl, SLevel<T>& F) {
+template <int DIM, typename T, class X>
+__device__ void prolong_add(X& x, SLevel<T>& Cl, SLevel<T>& F) {
     using N = Num<T>;
     using C = typename N::C;
     const int nc = Cl.n;
@@ -212,7 +290,7 @@ __device__ void prolong_add(SLevel<T>& Cl, SLevel<T>& F) {
     const T* uc = Cl.u;
     dispatch_n(nc, [&]<int NC>() {
     constexpr int cells = DIM == 3 ? NC * NC * NC : NC * NC;
-    for (int cell = threadIdx.x; cell < cells; cell += blockDim.x) {
+    for (int cell = x.tid(); cell < cells; cell += x.nt()) {
         const int I = cell % NC, J = (cell / NC) % NC, K = DIM == 3 ? cell / (NC * NC) : 0;
         const int64_t P = K * cz + J * cy + I;
         const int64_t p = (2 * K) * sz + (2 * J) * sy + 2 * I;
@@ -252,7 +330,35 @@ __device__ void prolong_add(SLevel<T>& Cl, SLevel<T>& F) {
         }
     }
     });
-    __syncthreads();
+    x.sync();
+}
+
+// The V-cycle on levels lv[from..levels-1] (lv[from] given: q set, u = 0 or
+// a start), run by x: down (pre-smoothing, residual, restriction), the
+// coarsest grid, up (prolongation with correction, post-smoothing).
+// exact0: lv[from] is level 0 of a plain FP64 3D hierarchy (unbiased value).
+template <int DIM, typename T, class X>
+__device__ void vcycle(X& x, SLevel<T>* lv, int from, int levels, int smoother, double omega,
+                       int nu1, int nu2, int coarse_sweeps, bool exact0) {
+    const bool red_only = smoother != GMG_WJACOBI && nu1 > 0;
+    for (int l = from; l + 1 < levels; ++l) {
+        relax<DIM>(x, lv[l], smoother, omega, nu1, exact0 && l == from);
+        residual<DIM>(x, lv[l], red_only, exact0 && l == from);
+        restrict_fw<DIM>(x, lv[l], lv[l + 1], red_only);
+    }
+    SLevel<T>& B = lv[levels - 1];
+    if (levels - from == 1) {
+        relax<DIM>(x, B, smoother, omega, nu1);
+    } else if (B.n > 2) {
+        for (int s = 0; s < coarse_sweeps; ++s) {
+            rb_half<DIM>(x, B, 0);
+            rb_half<DIM>(x, B, 1);
+        }
+    }
+    for (int l = levels - 2; l >= from; --l) {
+        prolong_add<DIM>(x, lv[l + 1], lv[l]);
+        relax<DIM>(x, lv[l], smoother, omega, nu2);
+    }
 }
 
 // The V-cycle on levels with n = n_top, n_top/2, ..., n_top >> (levels-1).
@@ -298,27 +404,48 @@ __global__ void __launch_bounds__(1024) k_tail(T* __restrict__ u_top, const T* _
         lv[0].u[p] = u_top[g];
     }
     __syncthreads();
-    const bool red_only = smoother != GMG_WJACOBI && nu1 > 0;
-    for (int l = 0; l + 1 < levels; ++l) {
-        relax<DIM>(lv[l], smoother, omega, nu1, exact0 && l == 0);
-        residual<DIM>(lv[l], red_only, exact0 && l == 0);
-        restrict_fw<DIM>(lv[l], lv[l + 1], red_only);
-    }
-    SLevel<T>& B = lv[levels - 1];
-    if (levels == 1) {
-        relax<DIM>(B, smoother, omega, nu1);
-    } else if (B.n > 2) {
-        for (int s = 0; s < coarse_sweeps; ++s) {
-            rb_half<DIM>(B, 0);
-            rb_half<DIM>(B, 1);
-        }
-    }
-    for (int l = levels - 2; l >= 0; --l) {
-        prolong_add<DIM>(lv[l + 1], lv[l]);
-        relax<DIM>(lv[l], smoother, omega, nu2);
-    }
+    CtaX x;
+    vcycle<DIM>(x, lv, 0, levels, smoother, omega, nu1, nu2, coarse_sweeps, exact0 != 0);
     for (int64_t p = threadIdx.x; p < nodes_of<DIM>(n_top); p += blockDim.x)
         u_top[gaddr(p)] = lv[0].u[p];
+}
+
+// The same V-cycle on the levels' own arrays in global memory (dense
+// layout), run by every CTA of a cooperative launch with grid barriers
+// between the steps, on the levels with n > cta_n; block 0 alone runs the
+// levels with n <= cta_n (__syncthreads) while the others wait at the next
+// grid barrier.  One launch replaces the grid kernels of the middle levels
+// (launch latency bound there) and the single-CTA tail.
+template <typename T>
+struct GridArgs {
+    SLevel<T> lv[kMaxGridLevels];
+    int levels, smoother, nu1, nu2, coarse_sweeps, cta_n;
+    double omega;
+    GridBar* bar;
+};
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(kGridThreads) k_gtail(GridArgs<T> a) {
+    GridX gx{a.bar};
+    SLevel<T>* lv = a.lv;
+    const bool red_only = a.smoother != GMG_WJACOBI && a.nu1 > 0;
+    int lc = 0;  // first level that block 0 takes alone
+    while (lc + 1 < a.levels && lv[lc].n > a.cta_n) ++lc;
+    for (int l = 0; l < lc; ++l) {
+        relax<DIM>(gx, lv[l], a.smoother, a.omega, a.nu1);
+        residual<DIM>(gx, lv[l], red_only);
+        restrict_fw<DIM>(gx, lv[l], lv[l + 1], red_only);
+    }
+    if (blockIdx.x == 0) {
+        CtaX cx;
+        vcycle<DIM>(cx, lv, lc, a.levels, a.smoother, a.omega, a.nu1, a.nu2, a.coarse_sweeps,
+                    false);
+    }
+    gx.sync();
+    for (int l = lc - 1; l >= 0; --l) {
+        prolong_add<DIM>(gx, lv[l + 1], lv[l]);
+        relax<DIM>(gx, lv[l], a.smoother, a.omega, a.nu2);
+    }
 }
 
 }  // namespace
@@ -355,6 +482,73 @@ cudaError_t launch(int d, const Lay& top, int levels, T* u_top, const T* q_top, 
     }
     return cudaGetLastError();
 }
+
+template <typename T>
+int grid_blocks(int d) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+        return 0;
+    const cudaError_t e =
+        d == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gtail<3, T>,
+                                                               kGridThreads, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gtail<2, T>,
+                                                               kGridThreads, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms * per_sm;
+}
+
+template <typename T>
+cudaError_t launch_grid(int d, int levels, const int* n, T* const* u, T* const* q, T* const* r,
+                        int smoother, double omega, int nu1, int nu2, int coarse_sweeps,
+                        int cta_n, void* bar, int blocks, cudaStream_t s) {
+    if (levels < 1 || levels > kMaxGridLevels || blocks < 1 || smoother != GMG_RBGS)
+        return cudaErrorInvalidValue;
+    GridArgs<T> a{};
+    for (int l = 0; l < levels; ++l) a.lv[l] = SLevel<T>{n[l], u[l], nullptr, q[l], r[l]};
+    a.levels = levels;
+    a.smoother = smoother;
+    a.nu1 = nu1;
+    a.nu2 = nu2;
+    a.coarse_sweeps = coarse_sweeps;
+    a.cta_n = cta_n;
+    a.omega = omega;
+    a.bar = static_cast<GridBar*>(bar);
+    cudaError_t e = cudaMemsetAsync(&a.bar->count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&a};
+    e = d == 3 ? cudaLaunchCooperativeKernel((const void*)k_gtail<3, T>, dim3(blocks),
+                                             dim3(kGridThreads), args, 0, s)
+               : cudaLaunchCooperativeKernel((const void*)k_gtail<2, T>, dim3(blocks),
+                                             dim3(kGridThreads), args, 0, s);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+size_t grid_bar_bytes() { return sizeof(GridBar); }
+
+int grid_fault(const void* bar) {
+    int v = 0;
+    if (cudaMemcpy(&v, &static_cast<const GridBar*>(bar)->fault, sizeof(int),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    return v;
+}
+
+#define GMG_GRID_INST(T)                                                                        \
+    template int grid_blocks<T>(int);                                                           \
+    template cudaError_t launch_grid<T>(int, int, const int*, T* const*, T* const*, T* const*,  \
+                                        int, double, int, int, int, int, void*, int,            \
+                                        cudaStream_t);
+GMG_GRID_INST(double)
+GMG_GRID_INST(float)
+GMG_GRID_INST(__nv_bfloat16)
+GMG_GRID_INST(df32)
+#undef GMG_GRID_INST
 
 template cudaError_t launch<double>(int, const Lay&, int, double*, const double*, int, double,
                                     int, int, int, cudaStream_t, bool);

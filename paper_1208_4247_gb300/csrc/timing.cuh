@@ -26,7 +26,12 @@ struct KernelTimer {
         std::string name;
         int level;
         double ops, bytes;
+        int group;  // cur_group at enqueue time
     };
+    // Launches enqueued while cur_group = g > 0 belong to group g; a graph run
+    // whose device-side plan skipped group g passes bit g to after_graph_run,
+    // which then leaves their (empty) brackets out of the records.
+    int cur_group = 0;
     std::vector<Pending> pending;  // timed launches of one graph, in order
     std::vector<cudaEvent_t> ev;   // two per timed launch
     struct Stat {
@@ -54,7 +59,7 @@ struct KernelTimer {
             cudaEventRecordWithFlags(ev[2 * i], s, cudaEventRecordExternal);
             launch();
             cudaEventRecordWithFlags(ev[2 * i + 1], s, cudaEventRecordExternal);
-            pending.push_back({name, level, ops, bytes});
+            pending.push_back({name, level, ops, bytes, cur_group});
         } else {
             launch();
         }
@@ -62,10 +67,11 @@ struct KernelTimer {
     }
 
     // After a run of the captured graph.
-    void after_graph_run() {
+    void after_graph_run(unsigned skipped_groups = 0) {
         launches += graph_kernels;
         if (!enabled) return;
         for (size_t i = 0; i < pending.size(); ++i) {
+            if (pending[i].group > 0 && (skipped_groups >> pending[i].group & 1u)) continue;
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) != cudaSuccess) {
                 cudaGetLastError();

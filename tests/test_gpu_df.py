@@ -240,3 +240,93 @@ def test_df_chained_cycles_per_cycle(torch_cuda, n, start):
                                 n, f, u0)
     for c, (mx, l2) in enumerate(errs):
         assert mx <= TOL_CYCLE and l2 <= TOL_CYCLE, (c + 1, mx, l2)
+
+
+# Steps of several double-float cycles: the FP64 step (triple-float black
+# values, u += e, red FP64 residual and norm) after every k cycles, the
+# stopping test after every cycle by the norm folded into the next red half
+# sweep (undone when the test stops inside a step).
+
+def _solve_df(torch, monkeypatch, d, n, f, k, device_loop="1", timing=False):
+    from paper_1208_4247_gb300.gmg import Solver
+    monkeypatch.setenv("GMG_DF_STEP_CYCLES", str(k))
+    monkeypatch.setenv("GMG_DEVICE_LOOP", device_loop)
+    fd = _dev(torch, f)
+    u = torch.zeros_like(fd)
+    with Solver(d, n, precision="df", inner_cycles=1) as S:
+        if timing:
+            S.set_timing(True)
+        it, rel, conv = S.solve(fd, u, rtol=1e-10)
+        hist = np.array(S.history())
+    return it, rel, conv, hist, u.cpu().numpy()
+
+
+@pytest.mark.parametrize("k", [2, 3, 5, 8])
+def test_df_steps_of_k_cycles_match_one_cycle_steps(torch_cuda, monkeypatch, k):
+    """257^3: with 9 cycles to 1e-10, k = 2 and 8 end the solve at a step's
+    end, k = 3 and 5 inside a step (the red half sweep run ahead is undone).
+    Same cycle count and history as one cycle per step (the oracle's, checked
+    elsewhere), solutions within the per-cycle bar of each other and of the
+    oracle's solve."""
+    torch = torch_cuda
+    d, n = 3, 256
+    f = inputs.rhs_uniform(d, n, 2)
+    it1, rel1, c1, h1, u1 = _solve_df(torch, monkeypatch, d, n, f, 1)
+    itk, relk, ck, hk, uk = _solve_df(torch, monkeypatch, d, n, f, k)
+    assert c1 and ck and it1 == itk == 9, (it1, itk)
+    b = oracle.scale_rhs(f)
+    np.testing.assert_allclose(hk, h1, rtol=1e-6, atol=_floor(d, u1, b))
+    assert _max_rel(uk, u1) <= TOL_CYCLE
+    assert oracle.norm2(oracle.residual(b, uk)) / oracle.norm2(b) <= 1e-10
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_df_steps_of_k_cycles_per_cycle(torch_cuda, monkeypatch, n):
+    """Five cycles from u = 0 in steps of three (1 + 3 + 1): every cycle, those
+    inside a step included, within 1e-12 of the FP64 oracle's cycle from the
+    GPU's previous iterate."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    monkeypatch.setenv("GMG_DF_STEP_CYCLES", "3")
+    d = 3
+    f = _rhs(d, n)
+    u0 = np.zeros_like(f)
+    errs = chained_cycle_errors(torch, lambda: Solver(d, n, precision="df", inner_cycles=1), d,
+                                n, f, u0, cycles=5)
+    for c, (mx, l2) in enumerate(errs):
+        assert mx <= TOL_CYCLE and l2 <= TOL_CYCLE, (c + 1, mx, l2)
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_df_steps_host_loop_equals_device_loop(torch_cuda, monkeypatch, k):
+    """The plan and the tests run on the device in either loop: the host loop
+    (one graph launch and sync per cycle; also the timed one) gives the same
+    solution bit for bit, the same cycle count and history."""
+    torch = torch_cuda
+    d, n = 3, 128
+    f = inputs.rhs_uniform(d, n, 4)
+    a = _solve_df(torch, monkeypatch, d, n, f, k, device_loop="1")
+    b = _solve_df(torch, monkeypatch, d, n, f, k, device_loop="0")
+    t = _solve_df(torch, monkeypatch, d, n, f, k, device_loop="1", timing=True)
+    for other in (b, t):
+        assert other[0] == a[0] and other[2] and a[2]
+        assert np.array_equal(other[3], a[3])
+        assert np.array_equal(other[4], a[4])
+
+
+def test_df_steps_exact_cycle_count_small(torch_cuda, monkeypatch):
+    """Capped runs (gmg_cycles, no stopping test) of c = 1..7 cycles in steps
+    of four end exactly after c cycles: each run's first c - 1 relative
+    residuals are those of the 7-cycle run."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    monkeypatch.setenv("GMG_DF_STEP_CYCLES", "4")
+    d, n = 3, 64
+    fd = _dev(torch, inputs.rhs_uniform(d, n, 3))
+    with Solver(d, n, precision="df", inner_cycles=1) as S:
+        ref = S.cycles(fd, torch.zeros_like(fd), 7)
+        for c in range(1, 8):
+            got = S.cycles(fd, torch.zeros_like(fd), c)
+            assert len(got) == c
+            np.testing.assert_allclose(got[:-1], ref[:c - 1], rtol=1e-6)
+            assert got[-1] == pytest.approx(ref[c - 1], rel=1e-6)
