@@ -60,6 +60,8 @@ TRAFFIC = {
     # double-float step's outer kernels: k_black_exact_update 331.4 + 213.1 MB,
     # k_outer_red3_walk 345.2 + 213.0 MB
     ("outer_red_update_df", 0): 1102.7e6,
+    # level-0 double-float half sweep (k_rb_half_vec_df): 143.2 + 42.3 MB
+    ("rb_half_df", 0): 185.5e6,
 }
 
 
@@ -975,7 +977,7 @@ def run_ours(args, rank, ws, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")

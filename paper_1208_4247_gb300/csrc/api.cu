@@ -472,19 +472,15 @@ bool leg_level(gmg_handle h, const std::vector<Level<T>>& lv, int l) {
 }
 
 // First level handled by the persistent tail kernel (L = none): the first
-// level with n <= 8 (3D; double-float 16) / 32 (2D) (GMG_TAIL_N overrides) whose tail arrays fit in 200 KB of shared
-// memory, below every learned level, leaving at least two tail levels.
+// level with n <= 8 (3D) / 32 (2D) (GMG_TAIL_N overrides) whose tail arrays
+// fit in 200 KB of shared memory, below every learned level, leaving at
+// least two tail levels.
 template <typename T>
 int tail_level(gmg_handle h, const std::vector<Level<T>>& lv) {
     const gmg_config& c = h->cfg;
     const int L = (int)lv.size();
     if (c.smoother == GMG_MCGS || c.transfer == GMG_TRANSFER_PAPER) return L;  // grid kernels
-    // 3D double-float levels run on the FP32 pipe, so one SM takes the 17^3
-    // level's sweeps in less time than the grid kernels' launches
-    const int nmax = h->tail_max > 0                         ? h->tail_max
-                     : c.d != 3                              ? 32
-                     : std::is_same<T, df32>::value ? 16
-                                                             : 8;
+    const int nmax = h->tail_max > 0 ? h->tail_max : c.d != 3 ? 32 : 8;
     int lo = 0;
     if (c.smoother == GMG_LEARNED)
         for (int l = 0; l < L && l < (int)h->lw.size(); ++l)

@@ -490,28 +490,31 @@ __global__ void __launch_bounds__(256, kAheadCtasPerSm) k_red_ahead_df(df32* __r
 }
 
 // Undo k_red_ahead_df: u -= r on the red nodes, while *flag is nonzero.
+// Grid-stride over the work items with a small grid: the launch runs once
+// per solve and returns at once in every other cycle.
 template <int DIM, int V>
 __global__ void __launch_bounds__(256) k_red_restore_df(df32* __restrict__ u,
                                                         const df32* __restrict__ r, Lay L,
                                                         FastDiv fG, FastDiv fm, uint32_t items,
                                                         const int* __restrict__ flag) {
     if (!*flag) return;
-    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= items) return;
-    const uint32_t rr = fastdiv(w, fG);
-    const int g = (int)(w - rr * fG.d);
-    const uint32_t kk = DIM == 3 ? fastdiv(rr, fm) : 0;
-    const int j = (int)(rr - kk * fm.d) + 1, k = DIM == 3 ? (int)kk + 1 : 0;
-    const int par = (j + k) & 1;
-    const int x0 = 2 * V * g + par;
-    if (x0 > L.n - 1) return;
-    const int64_t base = k * L.sz + j * L.sy + (par ? L.he : 0) + V * g;
-    df32 v[V], d[V];
-    ldvn(u + base, v);
-    ldvn(r + base, d);
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < items;
+         w += gridDim.x * blockDim.x) {
+        const uint32_t rr = fastdiv(w, fG);
+        const int g = (int)(w - rr * fG.d);
+        const uint32_t kk = DIM == 3 ? fastdiv(rr, fm) : 0;
+        const int j = (int)(rr - kk * fm.d) + 1, k = DIM == 3 ? (int)kk + 1 : 0;
+        const int par = (j + k) & 1;
+        const int x0 = 2 * V * g + par;
+        if (x0 > L.n - 1) continue;
+        const int64_t base = k * L.sz + j * L.sy + (par ? L.he : 0) + V * g;
+        df32 v[V], d[V];
+        ldvn(u + base, v);
+        ldvn(r + base, d);
 #pragma unroll
-    for (int t = 0; t < V; ++t) v[t] = v[t] - d[t];
-    vec_df_store<V>(u, base, x0, L.n, v);
+        for (int t = 0; t < V; ++t) v[t] = v[t] - d[t];
+        vec_df_store<V>(u, base, x0, L.n, v);
+    }
 }
 
 // 3D red-black half sweep by diagonal walkers.  The (n-1)^2 interior rows

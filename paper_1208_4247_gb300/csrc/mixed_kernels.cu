@@ -527,7 +527,7 @@ void df_red_restore(int d, const Lay& in, df32* e, const df32* r, const int* fla
                     cudaStream_t s) {
     constexpr int V = lk::kDfVec;
     const DfItems I = df_items(d, in);
-    const unsigned blocks = (I.items + 255) / 256;
+    const unsigned blocks = std::min<unsigned>((I.items + 255) / 256, 152 * 8);
     if (d == 3)
         lk::k_red_restore_df<3, V><<<blocks, 256, 0, s>>>(e, r, in, I.fG, I.fm, I.items, flag);
     else
