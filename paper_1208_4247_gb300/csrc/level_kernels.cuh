@@ -69,7 +69,9 @@ struct Num<float> {
 template <>
 struct Num<__nv_bfloat16> {
     using C = float;
-    __device__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static float ld(__nv_bfloat16 v) {  // exact: BF16 = FP32's upper half
+        return __uint_as_float((uint32_t)__bfloat16_as_ushort(v) << 16);
+    }
     __device__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
 };
 template <>
@@ -209,14 +211,15 @@ __device__ inline void ldv(const float* p, float* v) {
     v[2] = a.z;
     v[3] = a.w;
 }
+// BF16 is the upper half of an FP32 bit pattern: each value is widened
+// exactly by one shift or mask on the integer pipe.
 __device__ inline void ldv(const __nv_bfloat16* p, float* v) {
     const uint4 a = *reinterpret_cast<const uint4*>(p);
     const uint32_t w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-        const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&w[h]);
-        v[2 * h] = __low2float(b);
-        v[2 * h + 1] = __high2float(b);
+        v[2 * h] = __uint_as_float(w[h] << 16);
+        v[2 * h + 1] = __uint_as_float(w[h] & 0xffff0000u);
     }
 }
 __device__ inline void stv(float* p, const float* v) {
