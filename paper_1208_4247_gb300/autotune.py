@@ -29,7 +29,8 @@ def _time(torch, fn, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
-def tune_batch(dims, ns, fd, ud, rtol=1e-10, ks=(1, 2, 3), chunks=(512, 1024, 2048, 4096, 8192),
+def tune_batch(dims, ns, fd, ud, rtol=1e-10, ks=(2, 4, 6, 8, 10, 12),
+               chunks=(512, 1024, 2048, 4096, 8192),
                ctas=(152, 304, 608, 1216, 2432, 4864), **kw):
     """Returns (best parameter dict, list of (params, ms) tried).  Coordinate
     search (inner cycles, then tile, then CTAs), then inner cycles and tile

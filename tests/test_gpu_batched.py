@@ -89,7 +89,7 @@ def test_batch_rerun_and_second_rtol(torch_cuda):
 BATCH_KW = dict(smoother="wjacobi", omega=0.0, nu1=1, nu2=1, precision="fp32")
 
 
-@pytest.mark.parametrize("k,chunk,ctas", [(3, 4096, 1216), (2, 0, 0)])
+@pytest.mark.parametrize("k,chunk,ctas", [(8, 4096, 2432), (10, 4096, 2432), (2, 0, 0)])
 def test_full_batch_512(torch_cuda, k, chunk, ctas):
     """The 512-solve mix (seed 4): every solve's FP64 residual <= 1e-10
     (numpy), and two solves of each of the nine size classes within 1e-9 of
