@@ -98,6 +98,9 @@ struct gmg_handle_s {
     int chain_k = 8;
     ChainState* d_chain = nullptr;
     ChainState* h_chain = nullptr;  // pinned
+    // refinement forms: set by the start's prepare when the starting iterate
+    // has a nonzero interior entry (else the first outer residual is q)
+    int* d_unz = nullptr;
     bool graph_chain = false;       // the captured graphs are chain bodies
     int fmg_kernels = 0;
     std::vector<KernelTimer::Pending> fmg_pending;
@@ -1215,7 +1218,9 @@ struct DeviceGuard {
 // residual norm (and, for refinement, the first inner right-hand side).
 gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
     const gmg_config& c = h->cfg;
-    fp64::prepare(c.d, c.n, f, h->lv[0].q, u, h->stream);
+    int* unz = c.precision != GMG_FP64 ? h->d_unz : nullptr;
+    if (unz) GMG_CUDA_TRY(cudaMemsetAsync(unz, 0, sizeof(int), h->stream));
+    fp64::prepare(c.d, c.n, f, h->lv[0].q, u, h->stream, unz);
     if (c.precision == GMG_FP64 && h->ahead && c.cycle != GMG_FMG) {
         // the first norm in two colour halves: the black one from u_0, then
         // the red one fused with the first cycle's first red half sweep
@@ -1230,18 +1235,20 @@ gmg_status enqueue_start(gmg_handle h, const double* f, double* u) {
     } else if (c.precision == GMG_FP32_IR)
         mixed::outer_residual<float>(c.d, h->lvf[0].lay, u, h->lv[0].q, h->lvf[0].q, h->partial,
                                      h->d_res2, h->stream,
-                                     inner_red_ahead<float>(h) ? h->lvf[0].u[0] : nullptr);
+                                     inner_red_ahead<float>(h) ? h->lvf[0].u[0] : nullptr,
+                                     nullptr, nullptr, nullptr, unz);
     else if (c.precision == GMG_DF_IR)
         mixed::outer_residual<df32>(c.d, h->lvd[0].lay, u, h->lv[0].q, h->lvd[0].q, h->partial,
                                     h->d_res2, h->stream,
                                     inner_red_ahead<df32>(h) ? h->lvd[0].u[0] : nullptr,
                                     outer_red_possible<df32>(h) ? h->resid_b : nullptr,
                                     outer_red_possible<df32>(h) ? h->resid_flag : nullptr,
-                                    outer_red_possible<df32>(h) ? h->d_res2 + 2 : nullptr);
+                                    outer_red_possible<df32>(h) ? h->d_res2 + 2 : nullptr, unz);
     else
         mixed::outer_residual<bf16>(c.d, h->lvb[0].lay, u, h->lv[0].q, h->lvb[0].q, h->partial,
                                     h->d_res2, h->stream,
-                                    inner_red_ahead<bf16>(h) ? h->lvb[0].u[0] : nullptr);
+                                    inner_red_ahead<bf16>(h) ? h->lvb[0].u[0] : nullptr,
+                                    nullptr, nullptr, nullptr, unz);
     h->timer.launches += 3;
     GMG_CUDA_TRY(cudaGetLastError());
     return GMG_OK;
@@ -1540,6 +1547,7 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
              : cfg->precision == GMG_DF_IR ? alloc_hierarchy<df32>(h, h->lvd, L, true)
                                            : alloc_hierarchy<bf16>(h, h->lvb, L, true);
         if (st != GMG_OK) return fail(st);
+        if ((st = dev_alloc(h, &h->d_unz, 1)) != GMG_OK) return fail(st);
         if (cfg->precision == GMG_DF_IR &&
             ((st = dev_alloc(h, &h->resid_b, h->lvd[0].nodes)) != GMG_OK ||
              (st = dev_alloc(h, &h->resid_flag, 1)) != GMG_OK))

@@ -43,7 +43,9 @@ using lk::sz_of;
 // boundary.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_prepare(const double* __restrict__ f, double* __restrict__ q,
-                                                 double* __restrict__ u, int n, double scale) {
+                                                 double* __restrict__ u, int n, double scale,
+                                                 int* __restrict__ u_nonzero) {
+    bool nz = false;
     // rows (j, k) of (n+1) nodes, x contiguous (no per-node index division)
     const int64_t m = sy_of(n);
     const int64_t rows = DIM == 3 ? m * m : m;
@@ -57,12 +59,14 @@ __global__ void __launch_bounds__(256) k_prepare(const double* __restrict__ f, d
             const int64_t p = base + i;
             if (row_inner && i > 0 && i < n) {
                 q[p] = scale * f[p];
+                if (u_nonzero) nz = nz || __double_as_longlong(u[p]) != 0;
             } else {
                 q[p] = 0.0;
                 u[p] = 0.0;
             }
         }
     }
+    if (nz) *u_nonzero = 1;  // every writer stores the same value
 }
 
 constexpr int kNormThreads = 256;
@@ -296,7 +300,8 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict_
     }
 }
 
-void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s) {
+void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s,
+             int* u_nonzero) {
     const double h = 1.0 / n;
     const double scale = h * h / (2.0 * d);
     int bx = 32;
@@ -305,9 +310,9 @@ void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s
     const int64_t rows = d == 3 ? (int64_t)(n + 1) * (n + 1) : (int64_t)(n + 1);
     const int blocks = (int)std::min<int64_t>((rows + block.y - 1) / block.y, 152 * 16);
     if (d == 3)
-        k_prepare<3><<<blocks, block, 0, s>>>(f, q, u, n, scale);
+        k_prepare<3><<<blocks, block, 0, s>>>(f, q, u, n, scale, u_nonzero);
     else
-        k_prepare<2><<<blocks, block, 0, s>>>(f, q, u, n, scale);
+        k_prepare<2><<<blocks, block, 0, s>>>(f, q, u, n, scale, u_nonzero);
 }
 
 namespace {

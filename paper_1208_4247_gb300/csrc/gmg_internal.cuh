@@ -133,7 +133,10 @@ inline void prolong_add(int d, int nc, const T* uc, T* u, cudaStream_t s,
 
 // FP64 preparation and stopping-test norm (fp64_kernels.cu).
 namespace fp64 {
-void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s);
+// u_nonzero (may be NULL; zeroed by the caller): set to 1 when an interior
+// entry of u has a bit pattern other than +0.0.
+void prepare(int d, int n, const double* f, double* q, double* u, cudaStream_t s,
+             int* u_nonzero = nullptr);
 int resnorm_partials(int d, int n);
 // dst = src on every node of a (n+1)^d grid; src / dst row and plane pitches
 // in elements (x contiguous)
@@ -171,11 +174,14 @@ int outer_partials(int d, int n);
 // (*resid_flag set here, cleared there).  qnorm_out (may be NULL): the sum
 // of q^2, the squared norm of the residual of u = 0 (partial must then hold
 // 2 outer_partials entries).
+// u_nonzero (may be NULL): fp64::prepare's flag; where it is 0 (u = +0.0
+// everywhere) sigma = q + 0.0 exactly (the stencil's value for a zero
+// iterate, bit for bit), formed without the FP64 stencil.
 template <typename T>
 void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q_in,
                     double* partial, double* out, cudaStream_t s, T* e_init = nullptr,
                     float* resid = nullptr, int* resid_flag = nullptr,
-                    double* qnorm_out = nullptr);
+                    double* qnorm_out = nullptr, const int* u_nonzero = nullptr);
 template <typename T>
 void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s);
 // After red-black double-float inner cycles: the last black Gauss-Seidel

@@ -73,6 +73,38 @@ __device__ inline void block_partial(double acc, double* warp_sums, double* slot
     __syncthreads();
 }
 
+// sigma of the iterate u = +0.0 everywhere: q + 0.0, the stencil's value bit
+// for bit (every product with a +0 sum is +0, and q + (+0) turns a -0 q into
+// +0 as the stencil's adds do).  Rows of the interior over the CTAs' thread
+// rows; the stores and sums are those of the stencil path.
+template <int DIM, bool SPLIT, typename T>
+__device__ inline void zero_iterate_sigma(const double* __restrict__ q, T* __restrict__ q_in,
+                                          T* __restrict__ e_init, const Lay& in,
+                                          float* __restrict__ resid, bool qsum, double& acc,
+                                          float& accq) {
+    const int n = in.n;
+    const int64_t sy = sy_of(n), sz = sz_of<DIM>(n);
+    const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.y + ty; r < rows;
+         r += (int64_t)gridDim.x * blockDim.y) {
+        const int j = (int)(r % (n - 1)) + 1;
+        const int k = DIM == 3 ? (int)(r / (n - 1)) + 1 : 0;
+        const int64_t row = k * sz + j * sy;
+        const int64_t row_in = k * in.sz + j * in.sy;
+        for (int i = 1 + tx; i < n; i += blockDim.x) {
+            const double sig = q[row + i] + 0.0;
+            store_inner(q_in, e_init, row_in + lk::xo<SPLIT>(in, i), sig, ((i + j + k) & 1) == 0,
+                        resid);
+            acc = fma(sig, sig, acc);
+            if (qsum) {
+                const float qf = (float)q[row + i];
+                accq = fmaf(qf, qf, accq);
+            }
+        }
+    }
+}
+
 template <int DIM, bool SPLIT, typename T>
 __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __restrict__ u,
                                                              const double* __restrict__ q,
@@ -81,7 +113,8 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
                                                              double* __restrict__ partial,
                                                              Lay in, float* __restrict__ resid,
                                                              int* __restrict__ resid_flag,
-                                                             double* __restrict__ qpart) {
+                                                             double* __restrict__ qpart,
+                                                             const int* __restrict__ unz) {
     __shared__ double warp_sums[kThreads / 32];
     const double c = DIM == 3 ? 1.0 / 6.0 : 0.25;
     if (resid_flag && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *resid_flag = 1;
@@ -90,6 +123,9 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual(const double* __res
     const int64_t rows = DIM == 3 ? (int64_t)(n - 1) * (n - 1) : (n - 1);
     double acc = 0.0;
     float accq = 0.f;
+    if (unz && *unz == 0)
+        zero_iterate_sigma<DIM, SPLIT>(q, q_in, e_init, in, resid, qpart != nullptr, acc, accq);
+    else
     for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
          r += (int64_t)gridDim.x * blockDim.y) {
         const int j = (int)(r % (n - 1)) + 1;
@@ -124,7 +160,8 @@ __global__ void __launch_bounds__(256, 4) k_outer_residual3_walk(const double* _
                                                                  Lay in, int segs,
                                                                  float* __restrict__ resid,
                                                                  int* __restrict__ resid_flag,
-                                                                 double* __restrict__ qpart) {
+                                                                 double* __restrict__ qpart,
+                                                                 const int* __restrict__ unz) {
     __shared__ double warp_sums[kThreads / 32];
     const double c = 1.0 / 6.0;
     const int n = in.n;
@@ -132,6 +169,9 @@ __global__ void __launch_bounds__(256, 4) k_outer_residual3_walk(const double* _
     if (resid_flag && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) *resid_flag = 1;
     double acc = 0.0;
     float accq = 0.f;
+    if (unz && *unz == 0)
+        zero_iterate_sigma<3, SPLIT>(q, q_in, e_init, in, resid, qpart != nullptr, acc, accq);
+    else
     for (int64_t w = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; w < walkers;
          w += (int64_t)gridDim.x * blockDim.y)
         for (int color = 0; color < 2; ++color)
@@ -407,7 +447,7 @@ int outer_partials(int d, int n) {
 template <typename T>
 void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q_in,
                     double* partial, double* out, cudaStream_t s, T* e_init, float* resid,
-                    int* resid_flag, double* qnorm_out) {
+                    int* resid_flag, double* qnorm_out, const int* unz) {
     const int n = in.n;
     const int np = outer_partials(d, n);  // the q partials follow the sigma partials
     double* qpart = qnorm_out ? partial + np : nullptr;
@@ -416,10 +456,10 @@ void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q
         const int blocks = (int)std::min<int64_t>(W.blocks, outer_partials(d, n));
         if (in.he)
             k_outer_residual3_walk<true, T><<<blocks, W.block, 0, s>>>(u, q, q_in, e_init, partial, in,
-                                                                     W.segs, resid, resid_flag, qpart);
+                                                                     W.segs, resid, resid_flag, qpart, unz);
         else
             k_outer_residual3_walk<false, T><<<blocks, W.block, 0, s>>>(u, q, q_in, e_init, partial, in,
-                                                                      W.segs, resid, resid_flag, qpart);
+                                                                      W.segs, resid, resid_flag, qpart, unz);
         fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
         if (qpart) fp64::k_sum_partials<<<1, 1024, 0, s>>>(qpart, blocks, qnorm_out);
         return;
@@ -431,17 +471,17 @@ void outer_residual(int d, const Lay& in, const double* u, const double* q, T* q
     if (d == 3) {
         if (in.he)
             k_outer_residual<3, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in,
-                                                                   resid, resid_flag, qpart);
+                                                                   resid, resid_flag, qpart, unz);
         else
             k_outer_residual<3, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in,
-                                                                   resid, resid_flag, qpart);
+                                                                   resid, resid_flag, qpart, unz);
     } else {
         if (in.he)
             k_outer_residual<2, true, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in,
-                                                                   resid, resid_flag, qpart);
+                                                                   resid, resid_flag, qpart, unz);
         else
             k_outer_residual<2, false, T><<<blocks, block, 0, s>>>(u, q, q_in, e_init, partial, in,
-                                                                   resid, resid_flag, qpart);
+                                                                   resid, resid_flag, qpart, unz);
     }
     fp64::k_sum_partials<<<1, 1024, 0, s>>>(partial, blocks, out);
     if (qpart) fp64::k_sum_partials<<<1, 1024, 0, s>>>(qpart, blocks, qnorm_out);
@@ -470,12 +510,13 @@ void update(int d, const Lay& in, double* u, const T* e, cudaStream_t s) {
 
 template void outer_residual<float>(int, const Lay&, const double*, const double*, float*,
                                     double*, double*, cudaStream_t, float*, float*, int*,
-                                    double*);
+                                    double*, const int*);
 template void outer_residual<__nv_bfloat16>(int, const Lay&, const double*, const double*,
                                             __nv_bfloat16*, double*, double*, cudaStream_t,
-                                            __nv_bfloat16*, float*, int*, double*);
+                                            __nv_bfloat16*, float*, int*, double*, const int*);
 template void outer_residual<df32>(int, const Lay&, const double*, const double*, df32*, double*,
-                                   double*, cudaStream_t, df32*, float*, int*, double*);
+                                   double*, cudaStream_t, df32*, float*, int*, double*,
+                                   const int*);
 template void outer_red_update<df32>(int, const Lay&, double*, const double*, df32*, df32*,
                                      double*, double*, cudaStream_t, const float*, int*,
                                      const int*);

@@ -330,3 +330,23 @@ def test_df_steps_exact_cycle_count_small(torch_cuda, monkeypatch):
             assert len(got) == c
             np.testing.assert_allclose(got[:-1], ref[:c - 1], rtol=1e-6)
             assert got[-1] == pytest.approx(ref[c - 1], rel=1e-6)
+
+
+@pytest.mark.parametrize("prec,n", [("df", 256), ("df", 64), ("fp32", 128), ("bf16", 64)])
+def test_zero_start_residual_bit_identical(torch_cuda, prec, n):
+    """From u = +0.0 everywhere the start's outer residual is q + 0.0, formed
+    without the FP64 stencil; u = -0.0 is the same iterate with other bits
+    and takes the stencil.  Two steps from each: the same iterate bit for
+    bit, relative residuals equal up to the order of the norm's sums."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    d = 3
+    f = _dev(torch, inputs.rhs_uniform(d, n, 5))
+    out, rels = [], []
+    for neg in (False, True):
+        u = torch.full_like(f, -0.0) if neg else torch.zeros_like(f)
+        with Solver(d, n, precision=prec, inner_cycles=1 if prec == "df" else 2) as S:
+            rels.append(S.cycles(f, u, 2))
+        out.append(u.cpu().numpy())
+    assert np.array_equal(out[0].view(np.int64), out[1].view(np.int64))
+    np.testing.assert_allclose(rels[0], rels[1], rtol=1e-13)
