@@ -350,3 +350,29 @@ def test_zero_start_residual_bit_identical(torch_cuda, prec, n):
         out.append(u.cpu().numpy())
     assert np.array_equal(out[0].view(np.int64), out[1].view(np.int64))
     np.testing.assert_allclose(rels[0], rels[1], rtol=1e-13)
+
+
+@pytest.mark.parametrize("d,n,nu", [(2, 1024, 2), (3, 128, 1), (2, 256, 1)])
+def test_df_steps_other_shapes(torch_cuda, monkeypatch, d, n, nu):
+    """Steps of eight cycles in 2D and with V(1,1): the cycle count and
+    history of one-cycle steps (and so the oracle's), solutions within the
+    per-cycle bar of each other (2D: its first-cycle bar, R23)."""
+    torch = torch_cuda
+    from paper_1208_4247_gb300.gmg import Solver
+    f = inputs.rhs_uniform(d, n, 12)
+    fd = _dev(torch, f)
+    res = []
+    for k in ("1", "8"):
+        monkeypatch.setenv("GMG_DF_STEP_CYCLES", k)
+        u = torch.zeros_like(fd)
+        with Solver(d, n, precision="df", inner_cycles=1, nu1=nu, nu2=nu) as S:
+            it, rel, conv = S.solve(fd, u, rtol=1e-10)
+            res.append((it, conv, np.array(S.history()), u.cpu().numpy()))
+    (it1, c1, h1, u1), (it8, c8, h8, u8) = res
+    assert c1 and c8 and it1 == it8 and it1 > 2
+    b = oracle.scale_rhs(f)
+    np.testing.assert_allclose(h8, h1, rtol=1e-6, atol=_floor(d, u1, b))
+    assert _max_rel(u8, u1) <= (TOL_CYCLE if d == 3 else TOL_CYCLE_2D)
+    cfg = oracle.make_cfg(d, n, 0, oracle.RBGS, 0.8, nu, nu, 1)
+    it_o, _ = oracle.solve(cfg, f, np.zeros_like(f), rtol=1e-10, maxit=100)
+    assert it8 == it_o
