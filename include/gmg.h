@@ -146,8 +146,10 @@ gmg_status gmg_config_init(gmg_config* cfg, int d, int n);
  * for bit.  GMG_GRID_TAIL_N=m runs the levels with n <= m (red-black) and
  * all smaller ones as one cooperative launch with grid barriers between the
  * steps, the levels with n <= GMG_GRID_TAIL_CTA_N (default 8) in one CTA of
- * it (default off: slower than the per-level kernels on GB300); results are
- * the same bit for bit (3D FP64: levels n <= 64). */
+ * it (default off: slower than the per-level kernels on GB300);
+ * GMG_GRID_TAIL_CLUSTER=c (2..16) runs it as one thread-block cluster of c
+ * CTAs with the hardware cluster barrier instead; results are the same bit
+ * for bit (3D FP64: levels n <= 64). */
 gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out);
 
 /* GMGSolve (Algorithm 3, all levels on the device): starting from the initial

@@ -132,6 +132,7 @@ struct gmg_handle_s {
     int gtail_nmax = 0;
     int gtail_cta_n = 8;
     int gtail_blocks = 0;
+    int gtail_cluster = 0;  // GMG_GRID_TAIL_CLUSTER=c: one cluster of c CTAs instead
     void* gtail_bar = nullptr;
     bool gtail_used = false;
     bool legs_used = false;
@@ -503,8 +504,8 @@ int tail_level(gmg_handle h, const std::vector<Level<T>>& lv) {
 // the level above (a leg writes its coarse level in the colour-split layout).
 bool grid_tail_ok(gmg_handle h) {
     const gmg_config& c = h->cfg;
-    return h->gtail_blocks > 0 && h->gtail_nmax > 0 && h->gtail_bar && c.smoother == GMG_RBGS &&
-           c.transfer != GMG_TRANSFER_PAPER;
+    return ((h->gtail_blocks > 0 && h->gtail_bar) || h->gtail_cluster > 0) && h->gtail_nmax > 0 &&
+           c.smoother == GMG_RBGS && c.transfer != GMG_TRANSFER_PAPER;
 }
 // The largest level n it takes.  FP64 3D restrictions from fine n >= 128
 // run as z-walkers, which sum the same terms in another order than the
@@ -554,7 +555,7 @@ cudaError_t launch_grid_tail(gmg_handle h, std::vector<Level<T>>& lv, int lg) {
     h->gtail_used = true;
     return tail::launch_grid<T>(c.d, L - lg, n, u, q, r, c.smoother, c.omega, c.nu1, c.nu2,
                                 c.coarse_sweeps, h->gtail_cta_n, h->gtail_bar, h->gtail_blocks,
-                                h->stream);
+                                h->stream, h->gtail_cluster);
 }
 
 // One cycle of Algorithm 1 on the hierarchy lv (level-0 iterate lv[0].u[0]
@@ -1393,7 +1394,8 @@ gmg_status run(gmg_handle h, const double* f, double* u, double rtol, int ncycle
         }
     }
     if ((st = finish()) != GMG_OK) return st;
-    if (h->gtail_used && tail::grid_fault(h->gtail_bar) != 0) {
+    if (h->gtail_used && h->gtail_bar && h->gtail_cluster == 0 &&
+        tail::grid_fault(h->gtail_bar) != 0) {
         set_error("the grid tail gave up waiting at a grid barrier; results are invalid");
         return GMG_ERR_CUDA;
     }
@@ -1507,6 +1509,8 @@ gmg_status gmg_create(const gmg_config* cfg, void* cuda_stream, gmg_handle* out)
     if (const char* v = std::getenv("GMG_GRID_TAIL_N")) h->gtail_nmax = std::max(0, std::atoi(v));
     if (const char* v = std::getenv("GMG_GRID_TAIL_CTA_N"))
         h->gtail_cta_n = std::max(2, std::atoi(v));
+    if (const char* v = std::getenv("GMG_GRID_TAIL_CLUSTER"))
+        h->gtail_cluster = std::max(0, std::min(16, std::atoi(v)));
     if (const char* v = std::getenv("GMG_DF_STEP_CYCLES"))
         h->chain_k = std::max(1, std::min(64, std::atoi(v)));
     auto fail = [&](gmg_status s) {

@@ -235,7 +235,9 @@ cudaError_t launch(int d, const Lay& top, int levels, T* u_top, const T* q_top, 
 // The same on the levels' own dense arrays (n[l], u[l], q[l], r[l] for the
 // `levels` levels from the first one down), one cooperative launch of
 // `blocks` CTAs (grid_blocks: one wave; 0 when the device cannot) with grid
-// barriers between the steps on levels with n > cta_n and one CTA below.
+// barriers between the steps on levels with n > cta_n and one CTA below;
+// cluster > 0 (at most 16): instead one thread-block cluster of that many
+// CTAs with the hardware cluster barrier (bar unused).
 // bar: grid_bar_bytes() of device memory, zeroed once; its fault flag
 // (grid_fault) is set if a barrier wait ran past its limit (the results of
 // that launch are then invalid).  Red-black smoothing only.
@@ -244,7 +246,7 @@ int grid_blocks(int d);
 template <typename T>
 cudaError_t launch_grid(int d, int levels, const int* n, T* const* u, T* const* q, T* const* r,
                         int smoother, double omega, int nu1, int nu2, int coarse_sweeps,
-                        int cta_n, void* bar, int blocks, cudaStream_t s);
+                        int cta_n, void* bar, int blocks, cudaStream_t s, int cluster = 0);
 size_t grid_bar_bytes();
 int grid_fault(const void* bar);
 }  // namespace tail

@@ -130,6 +130,20 @@ struct GridX {
     }
 };
 
+// The whole grid is one thread-block cluster: the hardware cluster barrier
+// (release / acquire at cluster scope, which orders the CTAs' global
+// memory accesses too) between the steps.  Every thread of every CTA
+// reaches each barrier (the steps call sync() outside divergent code).
+struct ClusterX {
+    __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ int nt() const { return gridDim.x * blockDim.x; }
+    __device__ void sync() {
+        asm volatile(
+            "barrier.cluster.arrive.release.aligned;\n\t"
+            "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+};
+
 // ex: the unbiased FP64 3D value (lk::gs_value), as the grid kernels take
 // it on level 0 of a plain FP64 hierarchy
 template <int DIM, typename T, class X>
@@ -424,9 +438,8 @@ struct GridArgs {
     GridBar* bar;
 };
 
-template <int DIM, typename T>
-__global__ void __launch_bounds__(kGridThreads) k_gtail(GridArgs<T> a) {
-    GridX gx{a.bar};
+template <int DIM, typename T, class X>
+__device__ void gtail_body(X& gx, GridArgs<T>& a) {
     SLevel<T>* lv = a.lv;
     const bool red_only = a.smoother != GMG_WJACOBI && a.nu1 > 0;
     int lc = 0;  // first level that block 0 takes alone
@@ -446,6 +459,19 @@ __global__ void __launch_bounds__(kGridThreads) k_gtail(GridArgs<T> a) {
         prolong_add<DIM>(gx, lv[l + 1], lv[l]);
         relax<DIM>(gx, lv[l], a.smoother, a.omega, a.nu2);
     }
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(kGridThreads) k_gtail(GridArgs<T> a) {
+    GridX gx{a.bar};
+    gtail_body<DIM>(gx, a);
+}
+
+// The same as one thread-block cluster (the grid is the cluster).
+template <int DIM, typename T>
+__global__ void __launch_bounds__(kGridThreads) k_ctail(GridArgs<T> a) {
+    ClusterX cx;
+    gtail_body<DIM>(cx, a);
 }
 
 }  // namespace
@@ -506,8 +532,9 @@ int grid_blocks(int d) {
 template <typename T>
 cudaError_t launch_grid(int d, int levels, const int* n, T* const* u, T* const* q, T* const* r,
                         int smoother, double omega, int nu1, int nu2, int coarse_sweeps,
-                        int cta_n, void* bar, int blocks, cudaStream_t s) {
-    if (levels < 1 || levels > kMaxGridLevels || blocks < 1 || smoother != GMG_RBGS)
+                        int cta_n, void* bar, int blocks, cudaStream_t s, int cluster) {
+    if (levels < 1 || levels > kMaxGridLevels || smoother != GMG_RBGS ||
+        (cluster <= 0 && blocks < 1) || cluster > 16)
         return cudaErrorInvalidValue;
     GridArgs<T> a{};
     for (int l = 0; l < levels; ++l) a.lv[l] = SLevel<T>{n[l], u[l], nullptr, q[l], r[l]};
@@ -519,6 +546,26 @@ cudaError_t launch_grid(int d, int levels, const int* n, T* const* u, T* const* 
     a.cta_n = cta_n;
     a.omega = omega;
     a.bar = static_cast<GridBar*>(bar);
+    if (cluster > 0) {
+        auto kern = d == 3 ? k_ctail<3, T> : k_ctail<2, T>;
+        cudaError_t e = cudaSuccess;
+        if (cluster > 8)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(cluster);
+        cfg.blockDim = dim3(kGridThreads);
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, kern, a);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     cudaError_t e = cudaMemsetAsync(&a.bar->count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     void* args[] = {&a};
@@ -543,7 +590,7 @@ int grid_fault(const void* bar) {
     template int grid_blocks<T>(int);                                                           \
     template cudaError_t launch_grid<T>(int, int, const int*, T* const*, T* const*, T* const*,  \
                                         int, double, int, int, int, int, void*, int,            \
-                                        cudaStream_t);
+                                        cudaStream_t, int);
 GMG_GRID_INST(double)
 GMG_GRID_INST(float)
 GMG_GRID_INST(__nv_bfloat16)

@@ -24,7 +24,7 @@ def torch_cuda():
 
 def _cycles(torch, monkeypatch, d, n, prec, env, cycles=2, nu=2):
     from paper_1208_4247_gb300.gmg import Solver
-    for k in ("GMG_GRID_TAIL_N", "GMG_GRID_TAIL_CTA_N"):
+    for k in ("GMG_GRID_TAIL_N", "GMG_GRID_TAIL_CTA_N", "GMG_GRID_TAIL_CLUSTER"):
         monkeypatch.delenv(k, raising=False)
     for k, v in env.items():
         monkeypatch.setenv(k, v)
@@ -62,3 +62,16 @@ def test_grid_tail_thresholds(torch_cuda, monkeypatch, cta_n, top):
         got, _ = _cycles(torch_cuda, monkeypatch, 3, 256, "df",
                          {"GMG_GRID_TAIL_N": str(top), "GMG_GRID_TAIL_CTA_N": str(cta_n)}, nu=nu)
         assert np.array_equal(got, ref), (cta_n, top, nu)
+
+
+@pytest.mark.parametrize("cluster,top,prec", [(8, 32, "df"), (16, 64, "df"), (16, 32, "fp32"),
+                                              (8, 64, "fp64")])
+def test_cluster_tail_bit_identical(torch_cuda, monkeypatch, cluster, top, prec):
+    """The same steps run by one thread-block cluster (hardware cluster
+    barrier between the steps, GMG_GRID_TAIL_CLUSTER): bit for bit the
+    per-level kernels' iterates (3D 257^3, two cycles)."""
+    ref, rel_ref = _cycles(torch_cuda, monkeypatch, 3, 256, prec, {"GMG_GRID_TAIL_N": "0"})
+    got, rel = _cycles(torch_cuda, monkeypatch, 3, 256, prec,
+                       {"GMG_GRID_TAIL_N": str(top), "GMG_GRID_TAIL_CLUSTER": str(cluster)})
+    assert np.array_equal(got, ref)
+    assert rel == rel_ref
