@@ -103,6 +103,10 @@ def test_df_step_is_the_fp64_cycle(torch_cuda, case):
 
 SOLVE_CASES = [
     (2, 256, "wjacobi", 0.8, 2, 2, "sine_uniform"),
+    # n = 16: the whole hierarchy in the single-CTA tail (it also forms the
+    # last black half sweep that the steps' FP64 update replaces)
+    (3, 16, "rbgs", 0.8, 2, 2, "uniform"),
+    (3, 32, "rbgs", 0.8, 2, 2, "sine_gauss"),
     (3, 64, "rbgs", 0.8, 2, 2, "uniform"),
     (3, 128, "rbgs", 0.8, 1, 1, "uniform"),
     (3, 256, "rbgs", 0.8, 2, 2, "uniform"),
