@@ -249,7 +249,7 @@ __host__ __device__ constexpr int vec_of() {
 // res instead of the new values into u (the red-only residual after a black half
 // sweep; the same expression as k_residual).
 template <int DIM, typename T, bool RES = false>
-__global__ void __launch_bounds__(256) k_rb_half_vec(T* __restrict__ u, const T* __restrict__ q,
+__global__ void __launch_bounds__(256, sizeof(T) == 2 ? 8 : 1) k_rb_half_vec(T* __restrict__ u, const T* __restrict__ q,
                                                      Lay L, int color, FastDiv fG, FastDiv fm,
                                                      uint32_t items, T* __restrict__ res = nullptr) {
     using N = Num<T>;
